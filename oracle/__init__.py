@@ -1,0 +1,191 @@
+"""FP64 CPU oracle for the track-finding hot path -- TEST INFRASTRUCTURE.
+
+Only the test suite, the package smoke check and the benchmark's CPU-baseline
+leg may import this package. The product path (the CUDA library and its Python
+binding) never imports it.
+
+The arithmetic lives in `oracle.cpp` (plain C++, double precision), compiled to
+`liboracle.so` by `build()`; this module only marshals numpy arrays. `metrics`
+holds the track-finding metrics of the thesis (efficiency, ghost rate, clone
+rate, hit purity, hit efficiency).
+
+Parity status: every step is pinned by tests against closed forms, hand-worked
+examples and brute force (see tests/test_oracle_pins.py). The composition of
+the steps into the whole pipeline has no external pin of its own (parity
+unpinned beyond the per-step pins).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+DEFAULT_FEAT_SCALE = (45.0, math.pi, 750.0, 45.0, 45.0, 750.0)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into liboracle.so (plain g++, no GPU code)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.orc_model_load.restype = vp
+        L.orc_model_load.argtypes = [vp, ctypes.c_size_t, i32, vp, i32, i32, ctypes.c_char_p, i32]
+        L.orc_model_free.argtypes = [vp]
+        L.orc_embed.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.orc_radius_graph.restype = i64
+        L.orc_radius_graph.argtypes = [i64, vp, vp, i32, i32, dbl, i32, vp, vp, vp, i64]
+        L.orc_in_logits.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.orc_components.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.orc_find_tracks_event.restype = i64
+        L.orc_find_tracks_event.argtypes = [vp, i32, i32, dbl, dbl, vp, i64, vp, vp, vp, vp,
+                                            vp, vp, vp, vp, vp, vp, i64]
+        L.orc_find_tracks_batch.restype = i64
+        L.orc_find_tracks_batch.argtypes = [vp, i32, i32, dbl, dbl, vp, i32, vp, vp, vp, vp,
+                                            vp, vp, i32]
+        L.orc_candidate_d2.restype = i64
+        L.orc_candidate_d2.argtypes = [i64, vp, vp, i32, i32, vp, i64]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def cut_logit(score_cut: float) -> float:
+    """Score cut s on sigmoid(logit) as a cut on the logit: log(s / (1 - s))."""
+    return math.log(score_cut / (1.0 - score_cut))
+
+
+class Model:
+    """FP64 copy of a weight blob, checked against the architecture."""
+
+    def __init__(self, blob: bytes, embed_dims, hidden: int, iters: int):
+        self._blob = np.frombuffer(blob, dtype=np.uint8).copy()
+        dims = np.asarray(embed_dims, dtype=np.int32)
+        err = ctypes.create_string_buffer(256)
+        self.D = int(dims[-1])
+        self.hidden, self.iters = hidden, iters
+        self.ptr = lib().orc_model_load(_p(self._blob), self._blob.size, len(dims) - 1,
+                                        _p(dims), hidden, iters, err, 256)
+        self._dims = dims
+        if not self.ptr:
+            raise ValueError("oracle: " + err.value.decode())
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc_model_free(self.ptr)
+            self.ptr = None
+
+
+def embed(model: Model, x, y, z, feat_scale=DEFAULT_FEAT_SCALE) -> np.ndarray:
+    x, y, z = _c(x, np.float32), _c(y, np.float32), _c(z, np.float32)
+    out = np.zeros((x.size, model.D), dtype=np.float64)
+    fs = _c(feat_scale, np.float64)
+    lib().orc_embed(model.ptr, x.size, _p(x), _p(y), _p(z), _p(fs), _p(out))
+    return out
+
+
+def radius_graph(plane, emb, r2: float, k_max: int, n_planes: int = 26):
+    """(src, dst, d2) of the rough graph of one event."""
+    plane = _c(plane, np.uint8)
+    emb = _c(emb, np.float64)
+    n, D = emb.shape
+    ne = lib().orc_radius_graph(n, _p(plane), _p(emb), D, n_planes, r2, k_max,
+                                None, None, None, 0)
+    src, dst = np.zeros(ne, np.int32), np.zeros(ne, np.int32)
+    d2 = np.zeros(ne, np.float64)
+    lib().orc_radius_graph(n, _p(plane), _p(emb), D, n_planes, r2, k_max,
+                           _p(src), _p(dst), _p(d2), ne)
+    return src, dst, d2
+
+
+def in_logits(model: Model, x, y, z, src, dst, feat_scale=DEFAULT_FEAT_SCALE) -> np.ndarray:
+    x, y, z = _c(x, np.float32), _c(y, np.float32), _c(z, np.float32)
+    src, dst = _c(src, np.int32), _c(dst, np.int32)
+    out = np.zeros(src.size, np.float64)
+    fs = _c(feat_scale, np.float64)
+    lib().orc_in_logits(model.ptr, x.size, _p(x), _p(y), _p(z), _p(fs), src.size,
+                        _p(src), _p(dst), _p(out))
+    return out
+
+
+def components(n: int, src, dst, keep=None) -> np.ndarray:
+    src, dst = _c(src, np.int32), _c(dst, np.int32)
+    k = None if keep is None else _c(keep, np.uint8)
+    out = np.zeros(n, np.int32)
+    lib().orc_components(n, src.size, _p(src), _p(dst), _p(k), _p(out))
+    return out
+
+
+class EventResult:
+    def __init__(self, labels, src, dst, d2, logit, keep):
+        self.labels, self.src, self.dst = labels, src, dst
+        self.d2, self.logit, self.keep = d2, logit, keep
+
+
+def find_tracks_event(model: Model, x, y, z, plane, r2: float, k_max: int, cut: float = 0.5,
+                      n_planes: int = 26, feat_scale=DEFAULT_FEAT_SCALE) -> EventResult:
+    x, y, z = _c(x, np.float32), _c(y, np.float32), _c(z, np.float32)
+    plane = _c(plane, np.uint8)
+    fs = _c(feat_scale, np.float64)
+    n = x.size
+    labels = np.zeros(n, np.int32)
+    cap = max(64, 40 * n)
+    while True:
+        src, dst = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+        d2, lg = np.zeros(cap, np.float64), np.zeros(cap, np.float64)
+        keep = np.zeros(cap, np.uint8)
+        ne = lib().orc_find_tracks_event(model.ptr, n_planes, k_max, r2, cut_logit(cut), _p(fs),
+                                         n, _p(x), _p(y), _p(z), _p(plane), _p(labels),
+                                         _p(src), _p(dst), _p(d2), _p(lg), _p(keep), cap)
+        if ne <= cap:
+            return EventResult(labels, src[:ne], dst[:ne], d2[:ne], lg[:ne], keep[:ne])
+        cap = ne
+
+
+def find_tracks_batch(model: Model, x, y, z, plane, offsets, r2: float, k_max: int,
+                      cut: float = 0.5, threads: int = 1, n_planes: int = 26,
+                      feat_scale=DEFAULT_FEAT_SCALE):
+    """Event-local labels for every hit of a batch; returns (labels, n_edges)."""
+    x, y, z = _c(x, np.float32), _c(y, np.float32), _c(z, np.float32)
+    plane, offsets = _c(plane, np.uint8), _c(offsets, np.int64)
+    fs = _c(feat_scale, np.float64)
+    labels = np.zeros(x.size, np.int32)
+    ne = lib().orc_find_tracks_batch(model.ptr, n_planes, k_max, r2, cut_logit(cut), _p(fs),
+                                     offsets.size - 1, _p(offsets), _p(x), _p(y), _p(z),
+                                     _p(plane), _p(labels), threads)
+    return labels, ne
+
+
+def candidate_d2(plane, emb, n_planes: int = 26) -> np.ndarray:
+    plane = _c(plane, np.uint8)
+    emb = _c(emb, np.float64)
+    n, D = emb.shape
+    c = lib().orc_candidate_d2(n, _p(plane), _p(emb), D, n_planes, None, 0)
+    out = np.zeros(c, np.float64)
+    lib().orc_candidate_d2(n, _p(plane), _p(emb), D, n_planes, _p(out), c)
+    return out
