@@ -1,0 +1,220 @@
+/*
+ * gnntrk -- GPU track finding with a graph neural network, for one GB300
+ * (sm_103a). C ABI.
+ *
+ * The library runs, per event of a silicon-pixel vertex detector, the
+ * data-parallel hot path of the ETX4VELO method (thesis "Real-Time Analysis of
+ * Unstructured Data with Machine Learning on Heterogeneous Architectures",
+ * chapter "ETX4VELO"):
+ *
+ *   1. hit embedding MLP on the normalised cylindrical (r, phi, z) of each hit
+ *      (Sec. "Hit Embedding and Rough Graph Construction");
+ *   2. rough graph: a hit on plane p joins hits on planes p+1 and p+2 whose
+ *      squared embedding distance d^2 (Eq. of d^2) is below d^2_max, at most
+ *      k_max per hit (same section, Algorithm 1);
+ *   3. interaction-network GNN: node encoder on normalised (x, y, z), edge
+ *      encoder on [h_i, h_j], K message-passing steps with message
+ *      m_l = [sum of outgoing e, sum of incoming e] (Eq. of m^k_l) and residual
+ *      node and edge networks, then the edge classifier
+ *      (Sec. "Graph Neural Network and Classifiers");
+ *   4. edge-score cut: edges scoring below s_edge,min are dropped, giving the
+ *      purified hit graph (Sec. "The ETX4VELO Pipeline");
+ *   5. weakly connected components of the purified graph as track candidates
+ *      (Sec. "WCC Implementation", Algorithms 2-3).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named "device" are CUDA device pointers the caller owns; the
+ *     library never frees or keeps them past the call (except as documented).
+ *   - Pointers named "host" are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *     Device work is enqueued on it and the call returns without waiting,
+ *     unless stated otherwise.
+ *   - Argument errors are reported synchronously by the return value.
+ *     Errors detected on the device (capacity overflow, an input out of range,
+ *     a bounded wait that ran out) are latched in a status word in device
+ *     memory and surface from gnntrk_sync_status(). No kernel traps.
+ *   - gnntrk_last_error() returns a human-readable description of the last
+ *     error of a handle (valid until the next call on that handle).
+ *   - A handle is not thread safe: one host thread at a time, and calls on one
+ *     handle are stream-ordered on the stream they are given.
+ */
+#ifndef GNNTRK_H
+#define GNNTRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gnntrk_status {
+  GNNTRK_OK = 0,
+  GNNTRK_ERR_INVALID_ARG = 1, /* bad argument or input value */
+  GNNTRK_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GNNTRK_ERR_OOM = 3,         /* device memory allocation failed */
+  GNNTRK_ERR_CAPACITY = 4,    /* more edges than the edge workspace holds */
+  GNNTRK_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  GNNTRK_ERR_WEIGHTS = 6,     /* weight blob malformed or of the wrong shape */
+  GNNTRK_ERR_UNSUPPORTED = 7  /* configuration outside what is built */
+} gnntrk_status;
+
+/* Arithmetic of the MLP contractions. All of them accumulate in FP32; bias,
+ * layer normalisation, residual adds, distances and the cut are FP32. */
+typedef enum gnntrk_precision {
+  GNNTRK_FP32 = 0,     /* FP32 operands, FP32 states (SIMT) */
+  GNNTRK_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores */
+  GNNTRK_FP8_E4M3 = 2  /* E4M3 operands with per-output-channel weight
+                          scales and per-row activation scales */
+} gnntrk_precision;
+
+/*
+ * Model and run configuration.
+ *
+ * Model (must match the weight blob):
+ *   n_embed_layers, embed_dims[0..n_embed_layers]: embedding MLP widths,
+ *       embed_dims[0] = 3 (r, phi, z), embed_dims[n] = D (1..8 or 16).
+ *       ReLU between layers, no activation after the last.
+ *   hidden: GNN width n_h = n_e (32, 64 or 128).
+ *   iters:  message-passing steps K (0..16), distinct weights per step.
+ *   Every GNN sub-network is Linear -> LayerNorm (no affine, eps 1e-5) ->
+ *   ReLU -> Linear.
+ * Graph and cut:
+ *   n_planes: detector planes (hits carry a plane id in [0, n_planes)).
+ *   k_max:   maximum out-edges per hit; the k_max smallest by (d^2, plane of
+ *            the target, input index of the target) are kept.
+ *   radius2: d^2_max; an edge needs d^2 < radius2 (strict).
+ *   score_cut: s_edge,min; an edge is kept iff sigmoid(logit) >= score_cut,
+ *            evaluated as logit >= log(score_cut / (1 - score_cut)).
+ *   feat_scale: divisors of the features: embedding input
+ *            (r/fs[0], phi/fs[1], z/fs[2]) with phi = atan2(y, x); node
+ *            encoder input (x/fs[3], y/fs[4], z/fs[5]).
+ * Precision:
+ *   precision: a gnntrk_precision value.
+ *   rescore_band: for BF16/FP8, edges with |sigmoid(logit) - score_cut| <
+ *            rescore_band are re-decided in FP32: every event holding such an
+ *            edge has its GNN re-run in FP32 and only those edges take the
+ *            FP32 decision. 0 disables re-scoring.
+ * Capacity:
+ *   max_hits, max_events: largest call this handle accepts.
+ *   edges_per_hit: edge workspace, in edges per hit of max_hits. A call whose
+ *            graph needs more latches GNNTRK_ERR_CAPACITY (labels then invalid).
+ *   use_graph: 1 = capture each call shape into a CUDA graph on first use and
+ *            replay it afterwards; 0 = plain launches.
+ */
+typedef struct gnntrk_cfg {
+  int32_t n_embed_layers;
+  int32_t embed_dims[9];
+  int32_t hidden;
+  int32_t iters;
+  int32_t n_planes;
+  int32_t k_max;
+  float radius2;
+  float score_cut;
+  float feat_scale[6];
+  int32_t precision;
+  float rescore_band;
+  int64_t max_hits;
+  int32_t max_events;
+  int32_t edges_per_hit;
+  int32_t use_graph;
+  int32_t reserved[7];
+} gnntrk_cfg;
+
+typedef struct gnntrk_handle gnntrk_handle;
+
+/* Fill `cfg` with the defaults: embedding 3-64-64-4, hidden 32, 4 steps,
+ * 26 planes, k_max 64, radius2 1, score cut 0.5, feature scales
+ * (45, pi, 750, 45, 45, 750), FP32, no re-scoring, 1 << 20 hits, 4096 events,
+ * 24 edges per hit, no CUDA graphs. */
+void gnntrk_default_cfg(gnntrk_cfg* cfg);
+
+/*
+ * Create a handle on the current CUDA device.
+ *   weights, weights_bytes: host; the weight blob (little endian):
+ *     uint32 magic 0x57544E47, uint32 version 1, uint32 n_layers, uint32 0,
+ *     n_layers x (uint32 fan_in, uint32 fan_out), then per layer float32
+ *     W[fan_out][fan_in] followed by float32 b[fan_out]. Layer order:
+ *     embedding layers; node encoder (3->h, h->h); edge encoder (2h->h, h->h);
+ *     per step k: node network (3h->h, h->h), edge network (3h->h, h->h);
+ *     classifier (h->h, h->1). The blob is copied; the caller keeps ownership.
+ *   cfg: host; copied.
+ *   out: host; receives the handle.
+ * The library allocates its device weights and workspace here and keeps them
+ * until gnntrk_destroy. Errors: INVALID_ARG, WEIGHTS, UNSUPPORTED, OOM, CUDA.
+ * On error *out is NULL.
+ */
+gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnntrk_cfg* cfg,
+                            gnntrk_handle** out);
+
+/*
+ * Find track candidates in a batch of events.
+ *   n_events: 1..cfg.max_events.
+ *   n_hits:   total hits = offsets[n_events], 0..cfg.max_hits.
+ *   hits_xyz: device float32 [3][n_hits]: x (mm) at hits_xyz[0..n_hits),
+ *             y at hits_xyz[n_hits..), z at hits_xyz[2 n_hits..).
+ *   plane:    device uint8 [n_hits], plane id of each hit, < cfg.n_planes.
+ *   offsets:  device int64 [n_events + 1]; event e owns hits
+ *             [offsets[e], offsets[e+1]); offsets[0] = 0, non-decreasing.
+ *   out_labels: device int32 [n_hits]; receives, for every hit, the smallest
+ *             event-local input index (hit index minus offsets[e]) of its
+ *             connected component in the purified graph. A track candidate
+ *             is a component of at least 3 hits.
+ * Hits need not be ordered by plane. Asynchronous on `stream`; the handle's
+ * workspace holds the last call's graph until the next call (see
+ * gnntrk_get_graph). Device-detected errors (a plane id out of range,
+ * offsets inconsistent with n_hits, capacity) are latched: check them with
+ * gnntrk_sync_status. Synchronous errors: INVALID_ARG, CUDA.
+ */
+gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                                 const float* hits_xyz, const uint8_t* plane,
+                                 const int64_t* offsets, int32_t* out_labels, void* stream);
+
+/*
+ * Wait for `stream`, then return and clear the status latched by device-side
+ * checks of the previous calls on this handle: OK, INVALID_ARG (input value
+ * out of range), CAPACITY (edge workspace too small; labels invalid),
+ * TIMEOUT (a bounded wait ran out), or CUDA (an asynchronous CUDA error).
+ */
+gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream);
+
+/*
+ * Copy the rough graph of one event of the LAST gnntrk_find_tracks call to
+ * host memory (for checks and debugging; synchronises the device).
+ *   event: 0..n_events-1 of that call.
+ *   capacity: size of the host arrays below, in edges.
+ *   src, dst: host int32 [capacity]; event-local input indices of each edge
+ *             (src on the lower plane).
+ *   d2:    host float32 [capacity]; squared embedding distance.
+ *   logit: host float32 [capacity]; final edge logit (after any FP32
+ *          re-score); score = sigmoid(logit).
+ *   kept:  host uint8 [capacity]; 1 iff the edge survives the cut.
+ *   n_edges: host; receives the event's edge count.
+ * Any of src..kept may be NULL to skip it. If capacity < *n_edges nothing is
+ * written and CAPACITY is returned (query with capacity 0).
+ */
+gnntrk_status gnntrk_get_graph(gnntrk_handle* h, int32_t event, int64_t capacity, int32_t* src,
+                               int32_t* dst, float* d2, float* logit, uint8_t* kept,
+                               int64_t* n_edges);
+
+/*
+ * Statistics of the last gnntrk_find_tracks call (synchronises the device).
+ *   out: host int64 [8]: [0] total edges, [1] kept edges, [2] edges in the
+ *        re-score band, [3] events re-run in FP32, [4] events, [5] hits,
+ *        [6] edge capacity, [7] reserved (0).
+ */
+gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out);
+
+/* Description of the last error on this handle ("" if none). The string is
+ * owned by the handle. NULL handle: description of the last create failure. */
+const char* gnntrk_last_error(const gnntrk_handle* h);
+
+/* Release the handle's device memory, CUDA graphs and streams. NULL is a no-op.
+ * The caller must make sure no work of this handle is still running. */
+void gnntrk_destroy(gnntrk_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNNTRK_H */

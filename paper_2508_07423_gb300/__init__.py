@@ -1,0 +1,229 @@
+"""gnntrk: GNN track finding for one GB300 -- Python binding of libgnntrk.
+
+This module only marshals arguments to the C ABI of include/gnntrk.h (ctypes,
+plain pointers); every step of the hot path runs in the library's CUDA
+kernels. Importing works without a GPU; using a Tracker needs the built
+library (`paper_2508_07423_gb300.build.build()`) and a CUDA device, and fails
+loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgnntrk.so")
+
+FP32, BF16, FP8_E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8_E4M3}
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIMEOUT",
+          6: "WEIGHTS", 7: "UNSUPPORTED"}
+
+EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
+           "gnntrk_get_graph", "gnntrk_stats", "gnntrk_last_error", "gnntrk_destroy"]
+
+
+class GnntrkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gnntrk {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Cfg(ctypes.Structure):
+    """Mirror of gnntrk_cfg (include/gnntrk.h)."""
+    _fields_ = [
+        ("n_embed_layers", ctypes.c_int32),
+        ("embed_dims", ctypes.c_int32 * 9),
+        ("hidden", ctypes.c_int32),
+        ("iters", ctypes.c_int32),
+        ("n_planes", ctypes.c_int32),
+        ("k_max", ctypes.c_int32),
+        ("radius2", ctypes.c_float),
+        ("score_cut", ctypes.c_float),
+        ("feat_scale", ctypes.c_float * 6),
+        ("precision", ctypes.c_int32),
+        ("rescore_band", ctypes.c_float),
+        ("max_hits", ctypes.c_int64),
+        ("max_events", ctypes.c_int32),
+        ("edges_per_hit", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgnntrk.so and declare its exports (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgnntrk.so not built ({path}); run paper_2508_07423_gb300.build")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    L.gnntrk_default_cfg.argtypes = [ctypes.POINTER(Cfg)]
+    L.gnntrk_default_cfg.restype = None
+    L.gnntrk_create.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(Cfg), ctypes.POINTER(vp)]
+    L.gnntrk_create.restype = st
+    L.gnntrk_find_tracks.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp]
+    L.gnntrk_find_tracks.restype = st
+    L.gnntrk_sync_status.argtypes = [vp, vp]
+    L.gnntrk_sync_status.restype = st
+    L.gnntrk_get_graph.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+    L.gnntrk_get_graph.restype = st
+    L.gnntrk_stats.argtypes = [vp, vp]
+    L.gnntrk_stats.restype = st
+    L.gnntrk_last_error.argtypes = [vp]
+    L.gnntrk_last_error.restype = ctypes.c_char_p
+    L.gnntrk_destroy.argtypes = [vp]
+    L.gnntrk_destroy.restype = None
+    _lib = L
+    return L
+
+
+def default_cfg() -> Cfg:
+    c = Cfg()
+    load_library().gnntrk_default_cfg(ctypes.byref(c))
+    return c
+
+
+def make_cfg(model: dict, radius2: float, k_max: int = 64, score_cut: float = 0.5,
+             precision="fp32", rescore_band: float = 0.0, max_hits: int = 1 << 20,
+             max_events: int = 4096, edges_per_hit: int = 24, use_graph: bool = False,
+             n_planes: int = 26, feat_scale=None) -> Cfg:
+    """Build a cfg from a model description {"embed": [...], "hidden", "iters"}."""
+    c = default_cfg()
+    emb = list(model["embed"])
+    c.n_embed_layers = len(emb) - 1
+    for i in range(9):
+        c.embed_dims[i] = emb[i] if i < len(emb) else 0
+    c.hidden = int(model["hidden"])
+    c.iters = int(model["iters"])
+    c.n_planes = n_planes
+    c.k_max = k_max
+    c.radius2 = radius2
+    c.score_cut = score_cut
+    if feat_scale is not None:
+        for i in range(6):
+            c.feat_scale[i] = feat_scale[i]
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.rescore_band = rescore_band
+    c.max_hits = max_hits
+    c.max_events = max_events
+    c.edges_per_hit = edges_per_hit
+    c.use_graph = int(bool(use_graph))
+    return c
+
+
+def feat_scale_of(cfg: Cfg):
+    """The float32 feature scales the library uses (for an identical oracle input)."""
+    return tuple(float(np.float32(cfg.feat_scale[i])) for i in range(6))
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Tracker:
+    """One library handle: resident weights and workspace on the current GPU."""
+
+    def __init__(self, weights: bytes, cfg: Cfg):
+        L = load_library()
+        self._L = L
+        self.cfg = cfg
+        self._blob = ctypes.create_string_buffer(weights, len(weights))
+        h = ctypes.c_void_p()
+        st = L.gnntrk_create(self._blob, len(weights), ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise GnntrkError(st, self._L.gnntrk_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.gnntrk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def find_tracks(self, n_events: int, n_hits: int, hits_xyz, plane, offsets, out_labels,
+                    stream=None):
+        """Enqueue the hot path on `stream` (torch.cuda.Stream or raw handle).
+
+        hits_xyz: float32 CUDA tensor [3, n_hits]; plane: uint8 [n_hits];
+        offsets: int64 [n_events + 1]; out_labels: int32 [n_hits].
+        """
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._check(self._L.gnntrk_find_tracks(self._h, n_events, n_hits, _ptr(hits_xyz),
+                                               _ptr(plane), _ptr(offsets), _ptr(out_labels),
+                                               ctypes.c_void_p(s)))
+
+    def sync_status(self, stream=None):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._check(self._L.gnntrk_sync_status(self._h, ctypes.c_void_p(s)))
+
+    def stats(self) -> dict:
+        out = np.zeros(8, np.int64)
+        self._check(self._L.gnntrk_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return {"edges": int(out[0]), "kept": int(out[1]), "band": int(out[2]),
+                "rerun_events": int(out[3]), "events": int(out[4]), "hits": int(out[5]),
+                "edge_capacity": int(out[6])}
+
+    def get_graph(self, event: int) -> dict:
+        """Rough graph of one event of the last call (host numpy arrays)."""
+        n = ctypes.c_int64(0)
+        st = self._L.gnntrk_get_graph(self._h, event, 0, None, None, None, None, None,
+                                      ctypes.byref(n))
+        if st not in (0, 4):
+            self._check(st)
+        ne = n.value
+        src, dst = np.zeros(ne, np.int32), np.zeros(ne, np.int32)
+        d2, lg = np.zeros(ne, np.float32), np.zeros(ne, np.float32)
+        kept = np.zeros(ne, np.uint8)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._L.gnntrk_get_graph(self._h, event, ne, p(src), p(dst), p(d2), p(lg),
+                                             p(kept), ctypes.byref(n)))
+        return {"src": src, "dst": dst, "d2": d2, "logit": lg, "kept": kept}
+
+
+def run_batch(tracker: Tracker, batch, device="cuda", stream=None, check=True):
+    """Copy a host `synth.Batch` to the device, find tracks, return labels (numpy)."""
+    import torch
+    xyz = torch.from_numpy(batch.xyz_soa()).to(device)
+    plane = torch.from_numpy(batch.plane).to(device)
+    offs = torch.from_numpy(batch.offsets).to(device)
+    labels = torch.full((batch.n_hits,), -7, dtype=torch.int32, device=device)
+    tracker.find_tracks(batch.n_events, batch.n_hits, xyz, plane, offs, labels, stream)
+    if check:
+        tracker.sync_status(stream)
+    return labels.cpu().numpy()
+
+
+def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
+    """A Tracker for a workload of workloads.json (weights from its seed)."""
+    from . import synth
+    band = 0.0
+    prec = precision if precision is not None else wl.get("precision", "fp32")
+    if prec != "fp32":
+        band = float(wl.get("rescore_band_score", 0.0))
+    args = dict(k_max=wl["k_max"], score_cut=wl["cut"], precision=prec, rescore_band=band)
+    args.update(kw)
+    cfg = make_cfg(wl["model"], wl["radius2"], **args)
+    return Tracker(synth.workload_weights(wl), cfg)
+
+
+def cut_logit(score_cut: float) -> float:
+    return math.log(score_cut / (1.0 - score_cut))

@@ -1,0 +1,483 @@
+// C ABI of libgnntrk: handle life cycle, weight upload, workspace and the
+// launch sequence of the hot path. See include/gnntrk.h for the contract.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gnntrk.h"
+#include "internal.cuh"
+#include "tc.cuh"
+
+using namespace gnntrk;
+
+namespace gnntrk {
+int device_sms();
+}
+
+struct gnntrk_handle {
+  gnntrk_cfg cfg{};
+  int device = 0;
+  int D = 0, h = 0, K = 0, n_embed = 0;
+  // FP32 weights (SIMT layout)
+  float* d_wf32 = nullptr;
+  LayerF32 embed[kMaxEmbedLayers]{};
+  Mlp2F32 node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
+  // tensor-core weights (BF16 / FP8 packed operands)
+  TcModel tc{};
+  void* d_wtc = nullptr;
+  // workspace
+  Ws ws{};
+  std::vector<void*> allocs;
+  // last call
+  int last_events = 0, last_hits = 0;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+gnntrk_status fail(gnntrk_handle* h, gnntrk_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+gnntrk_status cuda_fail(gnntrk_handle* h, cudaError_t e, const char* what) {
+  return fail(h, GNNTRK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+uint32_t rd_u32(const unsigned char* p) {
+  return uint32_t(p[0]) | (uint32_t(p[1]) << 8) | (uint32_t(p[2]) << 16) | (uint32_t(p[3]) << 24);
+}
+
+// Parse and shape-check the weight blob.
+bool parse_weights(const void* blob, size_t n, const gnntrk_cfg& c, std::vector<HostLayer>& L,
+                   std::string& why) {
+  const unsigned char* p = static_cast<const unsigned char*>(blob);
+  if (!blob || n < 16) return why = "weight blob too short", false;
+  if (rd_u32(p) != 0x57544E47u) return why = "weight blob: bad magic", false;
+  if (rd_u32(p + 4) != 1u) return why = "weight blob: unsupported version", false;
+  const uint32_t nl = rd_u32(p + 8);
+  std::vector<std::pair<int, int>> want;
+  for (int l = 0; l < c.n_embed_layers; ++l) want.push_back({c.embed_dims[l], c.embed_dims[l + 1]});
+  const int h = c.hidden;
+  want.push_back({3, h});
+  want.push_back({h, h});
+  want.push_back({2 * h, h});
+  want.push_back({h, h});
+  for (int k = 0; k < c.iters; ++k) {
+    want.push_back({3 * h, h});
+    want.push_back({h, h});
+    want.push_back({3 * h, h});
+    want.push_back({h, h});
+  }
+  want.push_back({h, h});
+  want.push_back({h, 1});
+  if (nl != want.size()) return why = "weight blob: layer count does not match cfg", false;
+  if (n < 16 + 8 * size_t(nl)) return why = "weight blob: truncated header", false;
+  size_t need = 16 + 8 * size_t(nl);
+  L.resize(nl);
+  for (uint32_t l = 0; l < nl; ++l) {
+    L[l].in = int(rd_u32(p + 16 + 8 * l));
+    L[l].out = int(rd_u32(p + 20 + 8 * l));
+    if (L[l].in != want[l].first || L[l].out != want[l].second)
+      return why = "weight blob: layer " + std::to_string(l) + " shape does not match cfg", false;
+    need += 4 * (size_t(L[l].in) * L[l].out + L[l].out);
+  }
+  if (n != need) return why = "weight blob: size does not match its header", false;
+  size_t off = 16 + 8 * size_t(nl);
+  for (uint32_t l = 0; l < nl; ++l) {
+    L[l].W.resize(size_t(L[l].in) * L[l].out);
+    L[l].b.resize(L[l].out);
+    std::memcpy(L[l].W.data(), p + off, 4 * L[l].W.size());
+    off += 4 * L[l].W.size();
+    std::memcpy(L[l].b.data(), p + off, 4 * L[l].b.size());
+    off += 4 * L[l].b.size();
+  }
+  return true;
+}
+
+gnntrk_status alloc(gnntrk_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GNNTRK_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->allocs.push_back(*p);
+  return GNNTRK_OK;
+}
+
+template <class T>
+gnntrk_status alloc_n(gnntrk_handle* h, T** p, size_t n) {
+  return alloc(h, reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+gnntrk_status upload_f32(gnntrk_handle* h, const std::vector<HostLayer>& L) {
+  std::vector<float> img;
+  std::vector<size_t> wofs(L.size()), bofs(L.size());
+  std::vector<int> ldo(L.size());
+  for (size_t l = 0; l < L.size(); ++l) {
+    ldo[l] = (L[l].out + 3) & ~3;
+    wofs[l] = img.size();
+    img.resize(img.size() + size_t(L[l].in) * ldo[l], 0.f);
+    for (int o = 0; o < L[l].out; ++o)
+      for (int i = 0; i < L[l].in; ++i)
+        img[wofs[l] + size_t(i) * ldo[l] + o] = L[l].W[size_t(o) * L[l].in + i];
+    bofs[l] = img.size();
+    img.resize(img.size() + ldo[l], 0.f);
+    for (int o = 0; o < L[l].out; ++o) img[bofs[l] + o] = L[l].b[o];
+  }
+  gnntrk_status st = alloc_n(h, &h->d_wf32, img.size());
+  if (st) return st;
+  cudaError_t e = cudaMemcpy(h->d_wf32, img.data(), img.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "weight upload");
+  auto lay = [&](size_t l) {
+    return LayerF32{h->d_wf32 + wofs[l], h->d_wf32 + bofs[l], L[l].in, L[l].out, ldo[l]};
+  };
+  size_t c = 0;
+  for (int l = 0; l < h->n_embed; ++l) h->embed[l] = lay(c++);
+  h->node_enc = {lay(c), lay(c + 1)};
+  c += 2;
+  h->edge_enc = {lay(c), lay(c + 1)};
+  c += 2;
+  for (int k = 0; k < h->K; ++k) {
+    h->node[k] = {lay(c), lay(c + 1)};
+    h->edge[k] = {lay(c + 2), lay(c + 3)};
+    c += 4;
+  }
+  h->cls = {lay(c), lay(c + 1)};
+  return GNNTRK_OK;
+}
+
+gnntrk_status alloc_workspace(gnntrk_handle* h) {
+  const gnntrk_cfg& c = h->cfg;
+  const int64_t H = c.max_hits, E = int64_t(c.max_hits) * c.edges_per_hit;
+  Ws& w = h->ws;
+  w.h_cap = H;
+  w.e_cap = E;
+  gnntrk_status st;
+#define A(ptr, n)                                   \
+  if ((st = alloc_n(h, &w.ptr, size_t(n))) != 0) return st;
+  A(perm, H);
+  A(node_event, H);
+  A(pos, H);
+  A(plane_off, int64_t(c.max_events) * (c.n_planes + 1));
+  A(emb, H * h->D);
+  A(deg, H);
+  A(row_ptr, H + 1);
+  A(col, E);
+  A(src, E);
+  A(d2, E);
+  A(in_cnt, H);
+  A(in_ptr, H + 1);
+  A(in_edge, E);
+  A(hstate, H * h->h);
+  A(estate, E * h->h);
+  if (c.precision != GNNTRK_FP32) {
+    A(hstate16, H * h->h);
+    A(estate16, E * h->h);
+  }
+  A(logit, E);
+  A(keep, E);
+  A(parent, H);
+  A(counters, C_COUNT);
+  A(scan_blocks, (H + 4095) / 4096 + 1);
+  A(ev_flag, c.max_events);
+  A(rerun_list, c.max_events);
+  A(ev_off, int64_t(c.max_events) + 1);
+#undef A
+  cudaMemset(w.counters, 0, C_COUNT * sizeof(int32_t));
+  return GNNTRK_OK;
+}
+
+GraphParams graph_params(const gnntrk_handle* h) {
+  GraphParams g{};
+  g.n_planes = h->cfg.n_planes;
+  g.k_max = h->cfg.k_max;
+  g.radius2 = h->cfg.radius2;
+  g.cut_logit = float(std::log(double(h->cfg.score_cut) / (1.0 - double(h->cfg.score_cut))));
+  for (int i = 0; i < 6; ++i) g.fs[i] = h->cfg.feat_scale[i];
+  return g;
+}
+
+bool valid_d(int d) { return (d >= 1 && d <= 8) || d == 16; }
+
+}  // namespace
+
+extern "C" {
+
+void gnntrk_default_cfg(gnntrk_cfg* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->n_embed_layers = 3;
+  c->embed_dims[0] = 3;
+  c->embed_dims[1] = 64;
+  c->embed_dims[2] = 64;
+  c->embed_dims[3] = 4;
+  c->hidden = 32;
+  c->iters = 4;
+  c->n_planes = 26;
+  c->k_max = 64;
+  c->radius2 = 1.0f;
+  c->score_cut = 0.5f;
+  const float fs[6] = {45.f, 3.14159265358979323846f, 750.f, 45.f, 45.f, 750.f};
+  for (int i = 0; i < 6; ++i) c->feat_scale[i] = fs[i];
+  c->precision = GNNTRK_FP32;
+  c->rescore_band = 0.f;
+  c->max_hits = 1 << 20;
+  c->max_events = 4096;
+  c->edges_per_hit = 24;
+  c->use_graph = 0;
+}
+
+gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnntrk_cfg* cfg,
+                            gnntrk_handle** out) {
+  if (!out) return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "cfg is NULL");
+  const gnntrk_cfg& c = *cfg;
+  if (c.n_embed_layers < 1 || c.n_embed_layers > kMaxEmbedLayers || c.embed_dims[0] != 3)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "embedding: 1..8 layers with 3 inputs");
+  for (int l = 1; l <= c.n_embed_layers; ++l)
+    if (c.embed_dims[l] < 1 || c.embed_dims[l] > 256)
+      return fail(nullptr, GNNTRK_ERR_UNSUPPORTED, "embedding widths must be 1..256");
+  if (!valid_d(c.embed_dims[c.n_embed_layers]))
+    return fail(nullptr, GNNTRK_ERR_UNSUPPORTED, "embedding dimension must be 1..8 or 16");
+  if (c.hidden != 32 && c.hidden != 64 && c.hidden != 128)
+    return fail(nullptr, GNNTRK_ERR_UNSUPPORTED, "hidden must be 32, 64 or 128");
+  if (c.iters < 0 || c.iters > kMaxIters)
+    return fail(nullptr, GNNTRK_ERR_UNSUPPORTED, "iters must be 0..16");
+  if (c.n_planes < 2 || c.n_planes > kMaxPlanes)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "n_planes must be 2..64");
+  if (c.k_max < 1) return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "k_max must be >= 1");
+  if (!(c.radius2 > 0.f) || !std::isfinite(c.radius2))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "radius2 must be positive and finite");
+  if (!(c.score_cut > 0.f && c.score_cut < 1.f))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "score_cut must be in (0, 1)");
+  for (int i = 0; i < 6; ++i)
+    if (!(c.feat_scale[i] != 0.f) || !std::isfinite(c.feat_scale[i]))
+      return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "feature scales must be finite and non-zero");
+  if (c.precision < GNNTRK_FP32 || c.precision > GNNTRK_FP8_E4M3)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "unknown precision");
+  if (c.rescore_band < 0.f || c.rescore_band >= 0.5f)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "rescore_band must be in [0, 0.5)");
+  if (c.max_hits < 1 || c.max_hits > (int64_t(1) << 30))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "max_hits must be 1..2^30");
+  if (c.max_events < 1 || c.max_events > 65535)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "max_events must be 1..65535");
+  if (c.edges_per_hit < 1 || int64_t(c.max_hits) * c.edges_per_hit >= (int64_t(1) << 31))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "edge workspace must hold < 2^31 edges");
+
+  std::vector<HostLayer> L;
+  std::string why;
+  if (!parse_weights(weights, weights_bytes, c, L, why))
+    return fail(nullptr, GNNTRK_ERR_WEIGHTS, why);
+
+  gnntrk_handle* h = new gnntrk_handle;
+  h->cfg = c;
+  cudaGetDevice(&h->device);
+  h->n_embed = c.n_embed_layers;
+  h->D = c.embed_dims[c.n_embed_layers];
+  h->h = c.hidden;
+  h->K = c.iters;
+  gnntrk_status st = upload_f32(h, L);
+  if (!st && c.precision != GNNTRK_FP32) st = (gnntrk_status)tc_upload(h->tc, L.data(), int(L.size()), h->n_embed,
+                                                       h->h, h->K, c.precision, &h->d_wtc, h->err);
+  if (!st) st = alloc_workspace(h);
+  if (st) {
+    g_create_error = h->err;
+    gnntrk_destroy(h);
+    return st;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cuda_fail(h, e, "create");
+    g_create_error = h->err;
+    gnntrk_destroy(h);
+    return GNNTRK_ERR_CUDA;
+  }
+  *out = h;
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                                 const float* hits_xyz, const uint8_t* plane,
+                                 const int64_t* offsets, int32_t* out_labels, void* stream) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  const gnntrk_cfg& c = h->cfg;
+  if (n_events < 1 || n_events > c.max_events)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "n_events out of range");
+  if (n_hits < 0 || n_hits > c.max_hits) return fail(h, GNNTRK_ERR_INVALID_ARG, "n_hits out of range");
+  if (n_hits > 0 && (!hits_xyz || !plane || !out_labels))
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "NULL input or output pointer");
+  if (!offsets) return fail(h, GNNTRK_ERR_INVALID_ARG, "offsets is NULL");
+  if ((reinterpret_cast<uintptr_t>(hits_xyz) & 3) || (reinterpret_cast<uintptr_t>(offsets) & 7) ||
+      (reinterpret_cast<uintptr_t>(out_labels) & 3))
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "misaligned pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_events = n_events;
+  h->last_hits = int(n_hits);
+  h->last_stream = s;
+
+  Ws& w = h->ws;
+  Batch b{};
+  b.n_events = n_events;
+  b.n_hits = int(n_hits);
+  b.x = hits_xyz;
+  b.y = hits_xyz + n_hits;
+  b.z = hits_xyz + 2 * n_hits;
+  b.plane = plane;
+  b.offsets = w.ev_off;
+  b.labels = out_labels;
+  const GraphParams g = graph_params(h);
+
+  cudaMemsetAsync(w.counters, 0, C_COUNT * sizeof(int32_t), s);
+  cudaMemcpyAsync(w.ev_off, offsets, sizeof(int64_t) * (n_events + 1), cudaMemcpyDeviceToDevice, s);
+  launch_sort(b, w, c.n_planes, s);
+  const Sel all{nullptr, nullptr, 0};
+  const bool tc = c.precision != GNNTRK_FP32;
+  if (!tc)
+    launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true, all, s);
+  else
+    tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, s);
+  launch_radius(b, w, g, h->D, false, s);
+  launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap, w.scan_blocks, s);
+  launch_radius(b, w, g, h->D, true, s);
+  launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
+              w.scan_blocks, s);
+  launch_csc(b, w, s);
+  if (!tc) {
+    launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s);
+    for (int k = 0; k < h->K; ++k) {
+      launch_node_update_f32(b, w, h->node[k], h->h, all, s);
+      launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                             g.cut_logit, false, 0.f, 0.f, all, s);
+    }
+    if (h->K == 0)  // no message passing: the classifier reads the edge encodings
+      launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f, all, s);
+  } else {
+    tc_gnn(b, w, h->tc, h->h, h->K, g, s);
+    if (c.rescore_band > 0.f) {
+      const double lo = double(c.score_cut) - double(c.rescore_band);
+      const double hi = double(c.score_cut) + double(c.rescore_band);
+      const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
+      const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
+      tc_mark_band(b, w, band_lo, band_hi, s);
+      const Sel sel{w.rerun_list, w.counters + C_RERUN, n_events};
+      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
+                           sel, s);
+      launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s);
+      for (int k = 0; k < h->K; ++k) {
+        launch_node_update_f32(b, w, h->node[k], h->h, sel, s);
+        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                               g.cut_logit, true, band_lo, band_hi, sel, s);
+      }
+      if (h->K == 0)
+        launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
+                               band_hi, sel, s);
+    }
+  }
+  launch_cc(b, w, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  int32_t cnt[C_COUNT];
+  e = cudaMemcpy(cnt, h->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  const int st = cnt[C_STATUS];
+  if (st) {
+    const int32_t zero = 0;
+    cudaMemcpy(h->ws.counters + C_STATUS, &zero, 4, cudaMemcpyHostToDevice);
+  }
+  if (st & ST_INPUT)
+    return fail(h, GNNTRK_ERR_INVALID_ARG,
+                "input out of range (offsets not 0..n_hits non-decreasing, or plane >= n_planes)");
+  if (st & ST_CAPACITY)
+    return fail(h, GNNTRK_ERR_CAPACITY,
+                "graph needs " + std::to_string(cnt[C_EDGES]) + " edges; workspace holds " +
+                    std::to_string(h->ws.e_cap));
+  if (st & ST_TIMEOUT) return fail(h, GNNTRK_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & ST_INTERNAL) return fail(h, GNNTRK_ERR_CUDA, "internal device check failed");
+  h->err.clear();
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out) {
+  if (!h || !out) return GNNTRK_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  int32_t cnt[C_COUNT];
+  e = cudaMemcpy(cnt, h->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stats read");
+  out[0] = cnt[C_EDGES];
+  out[1] = cnt[C_KEPT];
+  out[2] = cnt[C_BAND];
+  out[3] = cnt[C_RERUN];
+  out[4] = h->last_events;
+  out[5] = h->last_hits;
+  out[6] = h->ws.e_cap;
+  out[7] = 0;
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_get_graph(gnntrk_handle* h, int32_t event, int64_t capacity, int32_t* src,
+                               int32_t* dst, float* d2, float* logit, uint8_t* kept,
+                               int64_t* n_edges) {
+  if (!h || !n_edges) return GNNTRK_ERR_INVALID_ARG;
+  if (event < 0 || event >= h->last_events) return fail(h, GNNTRK_ERR_INVALID_ARG, "event out of range");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  const Ws& w = h->ws;
+  int64_t off[2];
+  int32_t cnt[C_COUNT];
+  e = cudaMemcpy(off, w.ev_off + event, sizeof(off), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph read");
+  if (cnt[C_STATUS] & (ST_INPUT | ST_CAPACITY))
+    return fail(h, GNNTRK_ERR_CAPACITY, "the last call failed; no graph");
+  int32_t rp[2];
+  e = cudaMemcpy(&rp[0], w.row_ptr + off[0], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&rp[1], w.row_ptr + off[1], 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph read");
+  const int64_t ne = rp[1] - rp[0];
+  *n_edges = ne;
+  if (capacity < ne) return fail(h, GNNTRK_ERR_CAPACITY, "capacity below the event's edge count");
+  const int64_t nh = off[1] - off[0];
+  std::vector<int32_t> perm(nh), s(ne), d(ne);
+  e = cudaMemcpy(perm.data(), w.perm + off[0], 4 * nh, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(s.data(), w.src + rp[0], 4 * ne, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d.data(), w.col + rp[0], 4 * ne, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && d2) e = cudaMemcpy(d2, w.d2 + rp[0], 4 * ne, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && logit) e = cudaMemcpy(logit, w.logit + rp[0], 4 * ne, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && kept) e = cudaMemcpy(kept, w.keep + rp[0], ne, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph read");
+  for (int64_t i = 0; i < ne; ++i) {
+    if (src) src[i] = perm[s[i] - off[0]] - int32_t(off[0]);
+    if (dst) dst[i] = perm[d[i] - off[0]] - int32_t(off[0]);
+  }
+  return GNNTRK_OK;
+}
+
+const char* gnntrk_last_error(const gnntrk_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void gnntrk_destroy(gnntrk_handle* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+}  // extern "C"

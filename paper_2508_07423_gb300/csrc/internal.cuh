@@ -1,0 +1,201 @@
+// Internal declarations shared by the CUDA translation units of libgnntrk.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace gnntrk {
+
+constexpr int kMaxPlanes = 64;
+constexpr int kMaxEmbedLayers = 8;
+constexpr int kMaxIters = 16;
+constexpr float kLnEps = 1e-5f;
+
+// Bits of the device status word (counters[C_STATUS]).
+enum StatusBits : int {
+  ST_INPUT = 1,     // an input value out of range (plane id, offsets)
+  ST_CAPACITY = 2,  // more edges than the edge workspace
+  ST_TIMEOUT = 4,   // a bounded wait ran out
+  ST_INTERNAL = 8,  // an internal consistency check failed
+};
+
+// Slots of the device counter array.
+enum Counter : int {
+  C_EDGES = 0,     // total edges of the last call (may exceed capacity)
+  C_STATUS = 1,    // status bits
+  C_TICKET = 2,    // last-block ticket of the two-kernel scan
+  C_KEPT = 3,      // kept edges
+  C_BAND = 4,      // edges in the re-score band
+  C_RERUN = 5,     // events re-run in FP32
+  C_SCAN_TOTAL = 6,
+  C_RERUN_EDGES = 7,  // edges of the re-run events
+  C_RERUN_HITS = 8,   // hits of the re-run events
+  C_COUNT = 16
+};
+
+// A layer as parsed from the weight blob (host memory).
+struct HostLayer {
+  int in = 0, out = 0;
+  std::vector<float> W;  // [out][in]
+  std::vector<float> b;  // [out]
+};
+
+// One FP32 linear layer in the SIMT layout: WT[in][ldo] (transposed, output
+// dimension padded to a multiple of 4 with zeros) and b[ldo].
+struct LayerF32 {
+  const float* WT;
+  const float* b;
+  int in, out, ldo;
+};
+
+struct Mlp2F32 {
+  LayerF32 l1, l2;
+};
+
+// One layer packed for tcgen05: B operand (W[out][in], K-major) in the
+// no-swizzle canonical layout of 8x16-byte core matrices, the FP32 bias and,
+// for FP8, the per-output-channel dequantisation scale.
+struct LayerTC {
+  const void* B;       // packed operand image, bytes = out * in * elem_size
+  const float* b;      // [out]
+  const float* scale;  // [out], FP8 only (else nullptr)
+  int in, out;
+};
+
+struct Mlp2TC {
+  LayerTC l1, l2;
+};
+
+// Device workspace of a handle.
+struct Ws {
+  int32_t* perm;        // [H] sorted position -> global input index
+  int32_t* node_event;  // [H] sorted position -> event
+  float4* pos;          // [H] sorted (x, y, z, 0)
+  int32_t* plane_off;   // [max_events][n_planes + 1] sorted offsets (global)
+  float* emb;           // [H][D]
+  int32_t* deg;         // [H] candidates inside the radius (uncapped)
+  int32_t* row_ptr;     // [H + 1]
+  int32_t* col;         // [Ecap] target (sorted position)
+  int32_t* src;         // [Ecap] source (sorted position)
+  float* d2;            // [Ecap]
+  int32_t* in_cnt;      // [H]
+  int32_t* in_ptr;      // [H + 1]
+  int32_t* in_edge;     // [Ecap] edge ids grouped by target, ascending
+  float* hstate;        // [H][h]   FP32 node state (FP32 path and re-score)
+  float* estate;        // [Ecap][h] FP32 edge state
+  __nv_bfloat16* hstate16;  // [H][h]   BF16 node state (tensor-core paths)
+  __nv_bfloat16* estate16;  // [Ecap][h] BF16 edge state
+  float* logit;         // [Ecap]
+  uint8_t* keep;        // [Ecap]
+  int32_t* parent;      // [H] union-find parent over global input indices
+  int32_t* counters;    // [C_COUNT]
+  int32_t* scan_blocks; // block partials of the scan
+  int32_t* ev_flag;     // [max_events] events re-run in FP32
+  int32_t* rerun_list;  // [max_events] compacted list of re-run events
+  int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
+  int64_t h_cap, e_cap;
+};
+
+// The current call.
+struct Batch {
+  int n_events;
+  int n_hits;
+  const float* x;
+  const float* y;
+  const float* z;
+  const uint8_t* plane;
+  const int64_t* offsets;
+  int32_t* labels;
+};
+
+struct GraphParams {
+  int n_planes;
+  int k_max;
+  float radius2;
+  float cut_logit;
+  float fs[6];
+};
+
+// Row selection of a row-parallel kernel: all rows of the batch (list ==
+// nullptr), or only the rows of the events list[0 .. *n_list) (device memory,
+// at most max_list entries; one grid row per list entry).
+struct Sel {
+  const int32_t* list;
+  const int32_t* n_list;
+  int max_list;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (host functions), one per kernel family
+// ---------------------------------------------------------------------------
+void launch_sort(const Batch& b, const Ws& w, int n_planes, cudaStream_t s);
+// embedding (when do_embed) and FP32 node encoder (when do_node_enc)
+void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,
+                          const Mlp2F32& node_enc, int D, int h, const GraphParams& g,
+                          bool do_embed, bool do_node_enc, Sel sel, cudaStream_t s);
+void launch_radius(const Batch& b, const Ws& w, const GraphParams& g, int D, bool fill,
+                   cudaStream_t s);
+// exclusive scan of n entries of `in` (each clamped to clamp_max) into out[0..n],
+// out[n] = total; the total also goes to counters[total_slot] and is checked
+// against `cap` (ST_CAPACITY when above).
+void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t* counters,
+                 int total_slot, int64_t cap, int32_t* blocks, cudaStream_t s);
+void launch_csc(const Batch& b, const Ws& w, cudaStream_t s);
+
+// FP32 SIMT interaction network
+void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
+                         cudaStream_t s);
+void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
+                            cudaStream_t s);
+// last step (cls != nullptr): also runs the classifier and writes logit/keep;
+// with rescore_only, only edges whose current logit lies in (band_lo, band_hi)
+// take the new FP32 logit and decision.
+void launch_edge_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const Mlp2F32* cls,
+                            int h, float cut_logit, bool rescore_only, float band_lo,
+                            float band_hi, Sel sel, cudaStream_t s);
+
+// connected components
+void launch_cc(const Batch& b, const Ws& w, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t* counters, int bits) {
+  atomicOr(&counters[C_STATUS], bits);
+}
+
+__device__ __forceinline__ int clamp_edges(const int32_t* counters, int64_t cap) {
+  int e = counters[C_EDGES];
+  return e < cap ? e : int(cap);
+}
+
+inline int div_up(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+
+// Rows [lo, hi) this block works on under `sel` (false: nothing to do).
+__device__ __forceinline__ bool sel_rows(const Batch& b, const Ws& w, Sel sel, bool edges,
+                                         int& lo, int& hi) {
+  if (sel.list == nullptr) {
+    lo = 0;
+    hi = edges ? clamp_edges(w.counters, w.e_cap) : b.n_hits;
+    return true;
+  }
+  int j = blockIdx.y;
+  if (j >= *sel.n_list) return false;
+  int ev = sel.list[j];
+  int a = int(b.offsets[ev]), c = int(b.offsets[ev + 1]);
+  if (edges) {
+    int ecap = clamp_edges(w.counters, w.e_cap);
+    lo = min(w.row_ptr[a], ecap);
+    hi = min(w.row_ptr[c], ecap);
+  } else {
+    lo = a;
+    hi = c;
+  }
+  return true;
+}
+
+}  // namespace gnntrk

@@ -1,0 +1,435 @@
+// Input staging and rough-graph construction.
+//
+//  k_sort      per event, a stable counting sort of the hits by plane: the
+//              sorted order is (event, plane, input index), so the candidates of
+//              a hit on plane p (planes p+1 and p+2) form one contiguous range.
+//  k_radius    rough graph of Sec. "Hit Embedding and Rough Graph Construction":
+//              hit i on plane p joins hit j on plane p+1 or p+2 when
+//              d^2(i, j) = |e_i - e_j|^2 < d^2_max, keeping at most k_max per i
+//              (the k_max smallest by (d^2, sorted position)). One block per
+//              (event, plane p) stages the candidate embeddings in shared
+//              memory; one warp per query hit tests 32 candidates at a time and
+//              compacts the passing ones with a ballot. A count pass fills the
+//              per-hit candidate count, a scan turns it into CSR row pointers
+//              and a fill pass writes the edges in ascending target order.
+//  k_scan_*    exclusive scan in two kernels (block sums, with the last block
+//              scanning them; then block scans plus the block offset).
+//  k_csc_*     in-edge index: edges grouped by target, ascending edge id, so
+//              that message sums run in a fixed order.
+#include "internal.cuh"
+
+namespace gnntrk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSortThreads = 256;
+constexpr int kRadiusThreads = 256;
+constexpr int kCandSmemBytes = 48 * 1024;
+constexpr int kScanThreads = 512;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+
+__device__ __forceinline__ bool input_bad(const Ws& w) {
+  return (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// stable plane sort, one block per event
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) k_sort(Batch b, Ws w, int P) {
+  __shared__ int cnt[kMaxPlanes];
+  __shared__ int base[kMaxPlanes];
+  __shared__ int wcnt[kSortThreads / 32][kMaxPlanes];
+  __shared__ int ctot[kMaxPlanes];
+  __shared__ int bad;
+  const int ev = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t o0 = b.offsets[ev], o1 = b.offsets[ev + 1];
+  if (tid == 0) {
+    int f = 0;
+    if (o0 < 0 || o1 < o0 || o1 > b.n_hits) f = 1;
+    if (ev == 0 && o0 != 0) f = 1;
+    if (ev == b.n_events - 1 && o1 != b.n_hits) f = 1;
+    if (f) set_status(w.counters, ST_INPUT);
+    bad = f;
+  }
+  for (int i = tid; i < P; i += kSortThreads) cnt[i] = 0;
+  for (int i = tid; i < (kSortThreads / 32) * kMaxPlanes; i += kSortThreads)
+    (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  if (bad) return;
+  const int lo = int(o0), hi = int(o1);
+
+  for (int i = lo + tid; i < hi; i += kSortThreads) {
+    int p = b.plane[i];
+    if (p >= P) {
+      set_status(w.counters, ST_INPUT);
+      p = P - 1;
+    }
+    atomicAdd(&cnt[p], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    int32_t* po = w.plane_off + size_t(ev) * (P + 1);
+    for (int p = 0; p < P; ++p) {
+      base[p] = run;
+      po[p] = lo + run;
+      run += cnt[p];
+    }
+    po[P] = hi;
+  }
+  __syncthreads();
+
+  for (int c0 = lo; c0 < hi; c0 += kSortThreads) {
+    const int i = c0 + tid;
+    const bool valid = i < hi;
+    const int p = valid ? min(int(b.plane[i]), P - 1) : P;
+    const unsigned peers = __match_any_sync(kFull, p);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[warp][p] = __popc(peers);
+    __syncthreads();
+    if (tid < P) {
+      int run = 0;
+      for (int k = 0; k < kSortThreads / 32; ++k) {
+        int t = wcnt[k][tid];
+        wcnt[k][tid] = run;
+        run += t;
+      }
+      ctot[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int d = lo + base[p] + wcnt[warp][p] + rank;
+      w.perm[d] = i;
+      w.node_event[d] = ev;
+      w.pos[d] = make_float4(b.x[i], b.y[i], b.z[i], 0.0f);
+      w.in_cnt[d] = 0;
+      w.deg[d] = 0;
+    }
+    __syncthreads();
+    if (tid < P) base[tid] += ctot[tid];
+    for (int k = tid; k < (kSortThreads / 32) * kMaxPlanes; k += kSortThreads)
+      (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+  }
+  for (int i = lo + tid; i < hi; i += kSortThreads) w.parent[i] = i;
+}
+
+// ---------------------------------------------------------------------------
+// radius search
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ float dist2(const float (&q)[D], const float* c) {
+  float s = 0.0f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const float t = q[d] - c[d];
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
+// number of candidates with key < bound (strict) among those inside the radius
+template <int D>
+__device__ int count_below(const float (&q)[D], const float* ce, int nc, float r2,
+                           unsigned bound, bool inclusive) {
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+  for (int base = 0; base < nc; base += 32) {
+    const int c = base + lane;
+    bool ok = false;
+    if (c < nc) {
+      const float s = dist2<D>(q, ce + size_t(c) * D);
+      const unsigned key = __float_as_uint(s);
+      ok = s < r2 && (inclusive ? key <= bound : key < bound);
+    }
+    n += __popc(__ballot_sync(kFull, ok));
+  }
+  return n;
+}
+
+template <int D, bool FILL>
+__global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphParams g) {
+  extern __shared__ float cand_s[];
+  if (input_bad(w)) return;
+  const int P = g.n_planes;
+  const int ev = blockIdx.x / (P - 1), p = blockIdx.x % (P - 1);
+  const int32_t* po = w.plane_off + size_t(ev) * (P + 1);
+  const int q0 = po[p], q1 = po[p + 1];
+  if (q0 == q1) return;
+  const int c0 = po[p + 1], c1 = po[min(p + 3, P)];
+  const int nc = c1 - c0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const bool staged = size_t(nc) * D * sizeof(float) <= size_t(kCandSmemBytes);
+  const float* ce = staged ? cand_s : w.emb + size_t(c0) * D;
+  if (staged) {
+    for (int k = tid; k < nc * D; k += blockDim.x) cand_s[k] = w.emb[size_t(c0) * D + k];
+    __syncthreads();
+  }
+  const float r2 = g.radius2;
+  for (int q = q0 + warp; q < q1; q += nwarps) {
+    float qe[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+    if (!FILL) {
+      int cnt = 0;
+      for (int base = 0; base < nc; base += 32) {
+        const int c = base + lane;
+        bool ok = false;
+        if (c < nc) ok = dist2<D>(qe, ce + size_t(c) * D) < r2;
+        cnt += __popc(__ballot_sync(kFull, ok));
+      }
+      if (lane == 0) w.deg[q] = cnt;
+      continue;
+    }
+    const int cnt = w.deg[q];
+    const int64_t out0 = w.row_ptr[q];
+    // selection threshold when more than k_max candidates pass: T is the
+    // k_max-th smallest key; keys < T are kept, then the first keys == T
+    unsigned T = 0xffffffffu;
+    int need_eq = 0;
+    const bool capped = cnt > g.k_max;
+    if (capped) {
+      unsigned lo = 0, hi = __float_as_uint(r2);
+      for (int it = 0; it < 40 && lo < hi; ++it) {
+        const unsigned mid = lo + (hi - lo) / 2;
+        if (count_below<D>(qe, ce, nc, r2, mid, true) >= g.k_max)
+          hi = mid;
+        else
+          lo = mid + 1;
+      }
+      T = lo;
+      need_eq = g.k_max - count_below<D>(qe, ce, nc, r2, T, false);
+    }
+    int written = 0, eq_seen = 0;
+    for (int base = 0; base < nc; base += 32) {
+      const int c = base + lane;
+      bool ok = false, eq = false;
+      float s = 0.0f;
+      if (c < nc) {
+        s = dist2<D>(qe, ce + size_t(c) * D);
+        ok = s < r2;
+        if (capped && ok) {
+          const unsigned key = __float_as_uint(s);
+          eq = key == T;
+          ok = key < T;
+        }
+      }
+      if (capped) {
+        const unsigned eqm = __ballot_sync(kFull, eq);
+        const int eq_rank = eq_seen + __popc(eqm & ((1u << lane) - 1u));
+        if (eq && eq_rank < need_eq) ok = true;
+        eq_seen += __popc(eqm);
+      }
+      const unsigned m = __ballot_sync(kFull, ok);
+      if (ok) {
+        const int64_t e = out0 + written + __popc(m & ((1u << lane) - 1u));
+        if (e < w.e_cap) {
+          const int t = c0 + c;
+          w.col[e] = t;
+          w.src[e] = q;
+          w.d2[e] = s;
+          atomicAdd(&w.in_cnt[t], 1);
+        }
+      }
+      written += __popc(m);
+    }
+  }
+}
+
+template <int D>
+void radius_d(const Batch& b, const Ws& w, const GraphParams& g, bool fill, cudaStream_t s) {
+  const int grid = b.n_events * (g.n_planes - 1);
+  if (grid <= 0) return;
+  if (fill) {
+    cudaFuncSetAttribute(k_radius<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCandSmemBytes);
+    k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
+  } else {
+    cudaFuncSetAttribute(k_radius<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCandSmemBytes);
+    k_radius<D, false><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scan
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_s, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_s[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int t = lane < nw ? warp_s[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) warp_s[lane] = t;
+  }
+  __syncthreads();
+  total = warp_s[(blockDim.x >> 5) - 1];
+  const int r = x - v + (warp > 0 ? warp_s[warp - 1] : 0);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* in, int n,
+                                                              int clamp_max, int32_t* blocks,
+                                                              int32_t* counters, int total_slot,
+                                                              int64_t cap) {
+  __shared__ int warp_s[32];
+  __shared__ int is_last;
+  if ((*(volatile int32_t*)&counters[C_STATUS]) & ST_INPUT) return;
+  const int base = blockIdx.x * kScanChunk;
+  int v = 0;
+  for (int k = 0; k < kScanPer; ++k) {
+    const int i = base + k * kScanThreads + threadIdx.x;
+    if (i < n) v += min(in[i], clamp_max);
+  }
+  int total;
+  block_exclusive_scan(v, warp_s, total);
+  if (threadIdx.x == 0) {
+    blocks[blockIdx.x] = total;
+    __threadfence();
+    const int t = atomicAdd(&counters[C_TICKET], 1);
+    is_last = t == int(gridDim.x) - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // the last block scans the block sums
+  long long run = 0;
+  for (int c = 0; c < int(gridDim.x); c += kScanThreads) {
+    const int i = c + threadIdx.x;
+    const int x = i < int(gridDim.x) ? ((volatile int32_t*)blocks)[i] : 0;
+    int tot;
+    const int ex = block_exclusive_scan(x, warp_s, tot);
+    if (i < int(gridDim.x)) blocks[i] = int(run + ex);
+    run += tot;
+  }
+  if (threadIdx.x == 0) {
+    if (run > cap || run > 0x7fffffffLL) set_status(counters, ST_CAPACITY);
+    counters[total_slot] = int(run > 0x7fffffffLL ? 0x7fffffffLL : run);
+    counters[C_TICKET] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* in, int32_t* out,
+                                                             int n, int clamp_max,
+                                                             const int32_t* blocks,
+                                                             const int32_t* counters,
+                                                             int total_slot) {
+  __shared__ int warp_s[32];
+  if ((*(volatile const int32_t*)&counters[C_STATUS]) & ST_INPUT) return;
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    const int i = base + k;
+    v[k] = i < n ? min(in[i], clamp_max) : 0;
+    sum += v[k];
+  }
+  int total;
+  int run = block_exclusive_scan(sum, warp_s, total) + blocks[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    const int i = base + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = counters[total_slot];
+}
+
+// ---------------------------------------------------------------------------
+// in-edge index
+// ---------------------------------------------------------------------------
+__global__ void k_csc_fill(Ws w) {
+  if (input_bad(w)) return;
+  const int E = clamp_edges(w.counters, w.e_cap);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int t = w.col[e];
+    const int k = atomicSub(&w.in_cnt[t], 1) - 1;
+    w.in_edge[w.in_ptr[t] + k] = e;
+  }
+}
+
+__global__ void k_csc_sort(Batch b, Ws w) {
+  if (input_bad(w)) return;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < b.n_hits;
+       v += gridDim.x * blockDim.x) {
+    const int a = w.in_ptr[v], c = w.in_ptr[v + 1];
+    for (int i = a + 1; i < c; ++i) {
+      const int key = w.in_edge[i];
+      int j = i - 1;
+      while (j >= a && w.in_edge[j] > key) {
+        w.in_edge[j + 1] = w.in_edge[j];
+        --j;
+      }
+      w.in_edge[j + 1] = key;
+    }
+  }
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+void launch_sort(const Batch& b, const Ws& w, int n_planes, cudaStream_t s) {
+  if (b.n_events <= 0) return;
+  k_sort<<<b.n_events, kSortThreads, 0, s>>>(b, w, n_planes);
+}
+
+void launch_radius(const Batch& b, const Ws& w, const GraphParams& g, int D, bool fill,
+                   cudaStream_t s) {
+  switch (D) {
+    case 1: radius_d<1>(b, w, g, fill, s); break;
+    case 2: radius_d<2>(b, w, g, fill, s); break;
+    case 3: radius_d<3>(b, w, g, fill, s); break;
+    case 4: radius_d<4>(b, w, g, fill, s); break;
+    case 5: radius_d<5>(b, w, g, fill, s); break;
+    case 6: radius_d<6>(b, w, g, fill, s); break;
+    case 7: radius_d<7>(b, w, g, fill, s); break;
+    case 8: radius_d<8>(b, w, g, fill, s); break;
+    case 16: radius_d<16>(b, w, g, fill, s); break;
+    default: break;
+  }
+}
+
+void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t* counters,
+                 int total_slot, int64_t cap, int32_t* blocks, cudaStream_t s) {
+  const int nb = div_up(n > 0 ? n : 1, kScanChunk);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, clamp_max, blocks, counters, total_slot, cap);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, clamp_max, blocks, counters, total_slot);
+}
+
+void launch_csc(const Batch& b, const Ws& w, cudaStream_t s) {
+  const int grid = num_sms() * 8;
+  k_csc_fill<<<grid, 256, 0, s>>>(w);
+  if (b.n_hits > 0) k_csc_sort<<<div_up(b.n_hits, 256), 256, 0, s>>>(b, w);
+}
+
+int device_sms() { return num_sms(); }
+
+}  // namespace gnntrk

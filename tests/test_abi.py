@@ -1,0 +1,55 @@
+"""The C ABI library loads and exports every entry point its header declares
+(CPU only: no compute call)."""
+import os
+import re
+
+import pytest
+
+import paper_2508_07423_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gnntrk_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_07423_gb300 import build
+    build.build()
+    return pkg.load_library()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = header_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(pkg.EXPORTS) <= declared
+
+
+def test_default_cfg_layout(lib):
+    c = pkg.default_cfg()
+    assert c.n_embed_layers == 3 and list(c.embed_dims[:4]) == [3, 64, 64, 4]
+    assert c.hidden == 32 and c.iters == 4 and c.n_planes == 26 and c.k_max == 64
+    assert abs(c.feat_scale[1] - 3.14159265) < 1e-6
+    assert c.max_hits == 1 << 20 and c.max_events == 4096 and c.edges_per_hit == 24
+
+
+def test_create_rejects_bad_blob_without_gpu_work(lib):
+    # argument and blob checks run before any device call
+    c = pkg.default_cfg()
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.Tracker(b"\x00" * 8, c)
+    assert ei.value.status == 6
+    c.hidden = 48
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.Tracker(b"\x00" * 64, c)
+    assert ei.value.status == 7

@@ -1,0 +1,222 @@
+"""GPU parity: the library's FP32 path against the FP64 oracle, element by
+element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2508_07423_gb300 as pkg
+from paper_2508_07423_gb300 import synth
+from parity import compare_event
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def model_of(wl):
+    sh = synth.shape_of(wl)
+    return oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+
+
+def run_and_compare(tr, batch, wl, model, events=None, k_max=None):
+    labels = pkg.run_batch(tr, batch)
+    fs = pkg.feat_scale_of(tr.cfg)
+    reps = []
+    for e in (range(batch.n_events) if events is None else events):
+        ev = batch.event(e)
+        a = int(batch.offsets[e])
+        g = tr.get_graph(e)
+        reps.append(compare_event(ev, g, labels[a:a + ev.n_hits], model, wl["radius2"],
+                                  k_max or wl["k_max"], wl["model"]["iters"], wl["cut"], fs))
+    return labels, reps
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    wl = synth.workload("cfg1_plain_fp32")
+    return wl, model_of(wl)
+
+
+def test_cfg1_one_event_per_call(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=8192, max_events=8)
+    b = synth.workload_batch(wl, 6)
+    n_exact = 0
+    for e in range(b.n_events):
+        _, reps = run_and_compare(tr, b.event(e), wl, model)
+        n_exact += reps[0].labels_compared and reps[0].labels_equal
+        assert reps[0].edges > 1000
+    assert n_exact >= 5
+
+
+def test_cfg1_batch_equals_one_per_call(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=8192, max_events=8)
+    b = synth.workload_batch(wl, 5, first_event=10)
+    labels_b, _ = run_and_compare(tr, b, wl, model)
+    graphs_b = [tr.get_graph(e) for e in range(b.n_events)]
+    for e in range(b.n_events):
+        ev = b.event(e)
+        lab = pkg.run_batch(tr, ev)
+        a = int(b.offsets[e])
+        assert np.array_equal(lab, labels_b[a:a + ev.n_hits])
+        g = tr.get_graph(0)
+        for k in g:
+            assert np.array_equal(g[k], graphs_b[e][k]), k
+
+
+def test_cfg2_wide_model():
+    wl = synth.workload("cfg2_run3_single")
+    model = model_of(wl)
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=8192, max_events=2)
+    b = synth.workload_batch(wl, 1)
+    _, reps = run_and_compare(tr, b, wl, model)
+    assert reps[0].edges > 10000 and reps[0].scores_compared > 0.9 * reps[0].edges
+
+
+def test_kmax_cap(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, k_max=3, max_hits=8192, max_events=4)
+    b = synth.workload_batch(wl, 2, first_event=20)
+    _, reps = run_and_compare(tr, b, wl, model, k_max=3)
+    for r in reps:
+        assert r.edges > 0
+
+
+def special_events():
+    """Empty, single-hit, one-plane, last-plane-only, dense and large events."""
+    rng = np.random.default_rng(77)
+    z = synth.PLANE_Z
+
+    def mk(x, y, p):
+        p = np.asarray(p, np.uint8)
+        return synth.Batch(np.asarray(x, np.float32), np.asarray(y, np.float32),
+                           z[p].astype(np.float32), p, np.full(len(p), -1, np.int32),
+                           np.array([0, len(p)], np.int64))
+    evs = [mk([], [], []),
+           mk([10.0], [3.0], [4]),
+           mk(rng.uniform(-30, 30, 40), rng.uniform(-30, 30, 40), [7] * 40),
+           mk(rng.uniform(-30, 30, 30), rng.uniform(-30, 30, 30), [25] * 30),
+           synth.gen_batch(1, 99, {"kind": "fixed", "n": 400}, 0.05),
+           synth.gen_batch(1, 98, {"kind": "fixed", "n": 3}, 0.0)]
+    return evs
+
+
+def test_ragged_and_degenerate_events(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=16384, max_events=8)
+    evs = special_events()
+    b = synth.concat(evs)
+    labels, reps = run_and_compare(tr, b, wl, model)
+    # the one-plane events have no edges: every hit is its own component
+    a = int(b.offsets[2])
+    assert np.array_equal(labels[a:a + 40], np.arange(40))
+    assert reps[0].edges == 0 and reps[1].edges == 0
+    assert reps[4].edges > 10000
+
+
+def test_permutation_equivariance(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=8192, max_events=2)
+    ev = synth.workload_batch(wl, 1, first_event=30)
+    lab = pkg.run_batch(tr, ev)
+    g = tr.get_graph(0)
+    # hit s of the permuted event is hit perm[s] of the original one
+    perm = np.random.default_rng(5).permutation(ev.n_hits)
+    pe = synth.Batch(ev.x[perm], ev.y[perm], ev.z[perm], ev.plane[perm], ev.pid[perm],
+                     ev.offsets.copy())
+    lab_p = pkg.run_batch(tr, pe)
+    gp = tr.get_graph(0)
+    # same edges (relabelled) with the same logits
+    a = {(int(perm[s]), int(perm[d])): l for s, d, l in zip(gp["src"], gp["dst"], gp["logit"])}
+    b = {(int(s), int(d)): l for s, d, l in zip(g["src"], g["dst"], g["logit"])}
+    assert a.keys() == b.keys()
+    assert max(abs(a[k] - b[k]) for k in a) < 1e-4
+    # same partition of the hits
+    part = lambda labels, idx: {frozenset(idx[np.nonzero(labels == v)[0]].tolist())
+                                for v in np.unique(labels)}
+    ident = np.arange(ev.n_hits)
+    assert part(lab, ident) == part(lab_p, perm)
+
+
+def test_deterministic_repeat(cfg1):
+    wl, _ = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=65536, max_events=64)
+    b = synth.workload_batch(wl, 40)
+    l1 = pkg.run_batch(tr, b)
+    g1 = [tr.get_graph(e) for e in (0, 17, 39)]
+    l2 = pkg.run_batch(tr, b)
+    g2 = [tr.get_graph(e) for e in (0, 17, 39)]
+    assert np.array_equal(l1, l2)
+    for x, y in zip(g1, g2):
+        for k in x:
+            assert np.array_equal(x[k], y[k])
+
+
+def test_no_message_passing_model():
+    # K = 0: the classifier reads the edge encodings directly
+    shape = synth.ModelShape([3, 16, 4], 32, 0)
+    blob = synth.make_weights(shape, 4242)
+    wl = dict(synth.workload("cfg1_plain_fp32"))
+    wl["model"] = {"embed": [3, 16, 4], "hidden": 32, "iters": 0}
+    model = oracle.Model(blob, shape.embed, 32, 0)
+    # radius from the oracle's own candidate distances: mean degree about 10
+    ev = synth.workload_batch(wl, 1)
+    emb = oracle.embed(model, ev.x, ev.y, ev.z)
+    d2 = np.sort(oracle.candidate_d2(ev.plane, emb))
+    wl["radius2"] = float(np.float32(d2[5 * ev.n_hits]))
+    cfg = pkg.make_cfg(wl["model"], wl["radius2"], max_hits=4096, max_events=2)
+    tr = pkg.Tracker(blob, cfg)
+    _, reps = run_and_compare(tr, ev, wl, model)
+    assert reps[0].scores_compared > 0
+
+
+def test_input_errors_latch_and_recover(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=4096, max_events=4)
+    ev = synth.workload_batch(wl, 1)
+    bad = synth.Batch(ev.x, ev.y, ev.z, ev.plane.copy(), ev.pid, ev.offsets)
+    bad.plane[3] = 26
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.run_batch(tr, bad)
+    assert ei.value.status == 1
+    off = synth.Batch(ev.x, ev.y, ev.z, ev.plane, ev.pid, np.array([0, ev.n_hits - 1]))
+    xyz = torch.from_numpy(off.xyz_soa()).cuda()
+    with pytest.raises(pkg.GnntrkError) as ei:
+        labels = torch.zeros(ev.n_hits, dtype=torch.int32, device="cuda")
+        tr.find_tracks(1, ev.n_hits, xyz, torch.from_numpy(ev.plane).cuda(),
+                       torch.from_numpy(off.offsets).cuda(), labels)
+        tr.sync_status()
+    assert ei.value.status == 1
+    # the handle still works
+    _, reps = run_and_compare(tr, ev, wl, model)
+    assert reps[0].edges > 0
+
+
+def test_capacity_overflow_latches_and_recovers(cfg1):
+    wl, model = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=1024, max_events=4, edges_per_hit=1)
+    ev = synth.workload_batch(wl, 1)
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.run_batch(tr, ev)
+    assert ei.value.status == 4
+    assert "edges" in str(ei.value)
+    # a call that fits works afterwards
+    small = synth.gen_batch(1, 5, {"kind": "fixed", "n": 2}, 0.0)
+    pkg.run_batch(tr, small)
+
+
+def test_cfg3_full_batch_sampled():
+    """The 1000-event batched workload in one call; sampled events vs the oracle
+    and, for a wider sample, labels = components of the kept edges."""
+    wl = synth.workload("cfg3_batched_bf16")
+    model = model_of(wl)
+    b = synth.workload_batch(wl)
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=b.n_hits, max_events=b.n_events)
+    labels, reps = run_and_compare(tr, b, wl, model, events=[0, 499, 999])
+    st = tr.stats()
+    assert st["events"] == 1000 and st["edges"] > 5 * b.n_hits
+    from parity import cc_labels
+    for e in range(0, 1000, 37):
+        g = tr.get_graph(e)
+        a, z = int(b.offsets[e]), int(b.offsets[e + 1])
+        assert np.array_equal(labels[a:z], cc_labels(z - a, g["src"], g["dst"], g["kept"]))
