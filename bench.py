@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Benchmark of the GNN track-finding hot path on one GB300 (or N replicas).
+
+One step = one call of the whole hot path (plane sort, embedding, radius graph,
+interaction network, cut, connected components) over one batch of synthetic
+events of the batched workload (1000 events, tracks Poisson(150) clipped to
+[20, 400], 5 % noise, embed 3-64-64-4, IN h32 K4, mean degree 12). Prints one
+JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32|bf16|fp8] [--workload NAME]
+
+--impl reference times the FP64 CPU oracle on the same workload instead (the
+only other place this file runs the oracle is the cpu_baseline leg).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2508_07423_gb300 import synth  # noqa: E402
+
+METRIC = "events/s and hits/s on 1 GB300 (BF16/FP8 batched vs FP32 plain); p99 latency"
+DEFAULT_WORKLOAD = "cfg3_batched_bf16"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--precision", default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"),
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# roofline of one stage
+# ----------------------------------------------------------------------------
+def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: int, embed):
+    """Algorithmic work of ONE launch of `stage`: (bound, amount, unit-of-amount).
+
+    FP32 SIMT stages are ALU bound (flops); tensor-core and gather stages are
+    HBM bound (bytes). Per-unit figures (per edge / per hit) are the ones in the
+    design notes; amount = figure x units of one launch.
+    """
+    sb = 4 if precision == "fp32" else 2   # state bytes per element
+    if stage in ("edge_update", "gnn_tc"):
+        if precision == "fp32":
+            return "alu", E * 2.0 * (3 * h * h + h * h), "flop"
+        # read e, h_src, h_dst rows; write e
+        return "hbm", E * (4 * h * sb + 8), "byte"
+    if stage == "node_update":
+        if precision == "fp32":
+            return "alu", N * 2.0 * (3 * h * h + h * h), "flop"
+        return "hbm", N * 2 * h * sb + E * 2 * h * sb + E * 8, "byte"
+    if stage in ("radius_count", "radius_fill"):
+        return "hbm", N * D * 4 + N * 4 + (E * 12 if stage == "radius_fill" else 0), "byte"
+    if stage == "components":
+        return "hbm", E * 9 + N * 16, "byte"
+    return "hbm", N * 16, "byte"
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    import torch
+    import paper_2508_07423_gb300 as pkg
+
+    wl = synth.workload(a.workload)
+    precision = a.precision or "fp32"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # each rank processes its own events (replicas over disjoint event ranges)
+    n_ev = wl["n_events"]
+    batch = synth.workload_batch(wl, n_ev, first_event=rank * n_ev)
+    N = batch.n_hits
+    dev = torch.device("cuda", local)
+    xyz = torch.from_numpy(batch.xyz_soa()).to(dev)
+    plane = torch.from_numpy(batch.plane).to(dev)
+    offs = torch.from_numpy(batch.offsets).to(dev)
+    labels = torch.empty(N, dtype=torch.int32, device=dev)
+    tr = pkg.tracker_for_workload(wl, precision=precision, max_hits=N, max_events=n_ev,
+                                  edges_per_hit=16)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+        tr.sync_status(stream)
+    stats = tr.stats()
+
+    # timed region: per-step event pairs, L2 flushed between steps (outside the pairs)
+    tr.set_profiling(True)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(a.steps):
+            flush.fill_(i)
+            ev_s[i].record(stream)
+            step()
+            ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    tr.sync_status(stream)
+    step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
+    stages = tr.stage_times()
+    tr.set_profiling(False)
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_events = n_ev * world
+    value = total_events / (ms / 1e3)
+    hits_total = N * world
+
+    # roofline of the dominant stage
+    pk = peaks()
+    m = wl["model"]
+    E = stats["edges"]
+    dom = max(stages.items(), key=lambda kv: kv[1][0])
+    dname, (dms, druns) = dom
+    bound, amount, _ = stage_work(dname, precision, N, E, m["hidden"], m["iters"],
+                                  m["embed"][-1], m["embed"])
+    launch_ms = dms / max(druns, 1)
+    if bound == "alu":
+        peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        achieved = amount / (launch_ms / 1e3) / 1e12
+        unit = "TFLOP/s"
+    else:
+        peak = pk["hbm_gbs"]
+        achieved = amount / (launch_ms / 1e3) / 1e9
+        unit = "GB/s"
+    roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_src": pk["src"] if bound != "alu" else "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
+            "launch_ms": round(launch_ms, 4),
+            "stage_ms_per_step": {k: round(v[0] / a.steps, 4) for k, v in stages.items()}}
+
+    # end to end through the public call with host buffers
+    e2e = None if a.no_e2e else run_e2e(a, tr, batch, stream, dev, torch)
+
+    # plain FP32 one event per launch (the denominator of the batching target)
+    plain = None if a.no_plain else run_plain(pkg, torch, dev, stream)
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "events/s", "n_gpus": world,
+        "steps": a.steps, "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[precision],
+        "data": "synthetic",
+        "hits_per_s": round(hits_total / (ms / 1e3), 1),
+        "p50_step_ms": round(float(np.percentile(step_ms, 50)), 4),
+        "p99_step_ms": round(float(np.percentile(step_ms, 99)), 4),
+        "config": {"workload": f"{a.workload}: {wl['description']}",
+                   "n_events": n_ev, "hits": N, "edges": E, "kept_edges": stats["kept"],
+                   "net": f"embed {'-'.join(map(str, m['embed']))}, IN h{m['hidden']} K{m['iters']}",
+                   "precision": precision, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (disjoint events, no collective)"},
+        "clocks": clk,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(stats["launches"]) * a.steps,
+        "plain_fp32_one_event_per_launch": plain,
+        "batched_over_plain": (round(value / plain["events_per_s"], 2)
+                               if plain and plain.get("events_per_s") else None),
+        "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, batch, labels.cpu().numpy(), tr, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(a, tr, batch, stream, dev, torch):
+    N, n_ev = batch.n_hits, batch.n_events
+    h_xyz = torch.from_numpy(batch.xyz_soa()).pin_memory()
+    h_plane = torch.from_numpy(batch.plane).pin_memory()
+    h_offs = torch.from_numpy(batch.offsets).pin_memory()
+    h_lab = torch.empty(N, dtype=torch.int32).pin_memory()
+    d_xyz = torch.empty_like(h_xyz, device=dev)
+    d_plane = torch.empty_like(h_plane, device=dev)
+    d_offs = torch.empty_like(h_offs, device=dev)
+    d_lab = torch.empty(N, dtype=torch.int32, device=dev)
+    ms = []
+    with torch.cuda.stream(stream):
+        for i in range(max(a.steps // 2, 3) + 2):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            d_xyz.copy_(h_xyz, non_blocking=True)
+            d_plane.copy_(h_plane, non_blocking=True)
+            d_offs.copy_(h_offs, non_blocking=True)
+            tr.find_tracks(n_ev, N, d_xyz, d_plane, d_offs, d_lab, stream)
+            h_lab.copy_(d_lab, non_blocking=True)
+            e.record(stream)
+            e.synchronize()
+            if i >= 2:
+                ms.append(s.elapsed_time(e))
+    m = float(np.mean(ms))
+    return {"value": round(n_ev / (m / 1e3), 1), "unit": "events/s",
+            "h2d_bytes_per_step": int(h_xyz.numel() * 4 + h_plane.numel() + h_offs.numel() * 8),
+            "d2h_bytes_per_step": int(N * 4), "ms_per_step": round(m, 4)}
+
+
+def run_plain(pkg, torch, dev, stream):
+    """cfg1: 100 distinct 40-track events, FP32, one event per call."""
+    try:
+        wl = synth.workload("cfg1_plain_fp32")
+        b = synth.workload_batch(wl)
+        tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=8192, max_events=1)
+        evs = []
+        for e in range(b.n_events):
+            ev = b.event(e)
+            evs.append((ev.n_hits, torch.from_numpy(ev.xyz_soa()).to(dev),
+                        torch.from_numpy(ev.plane).to(dev), torch.from_numpy(ev.offsets).to(dev),
+                        torch.empty(ev.n_hits, dtype=torch.int32, device=dev)))
+        for n, x, p, o, l in evs[:5]:
+            tr.find_tracks(1, n, x, p, o, l, stream)
+        tr.sync_status(stream)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        with torch.cuda.stream(stream):
+            s.record(stream)
+            for _ in range(reps):
+                for n, x, p, o, l in evs:
+                    tr.find_tracks(1, n, x, p, o, l, stream)
+            e.record(stream)
+        e.synchronize()
+        tr.sync_status(stream)
+        ms = s.elapsed_time(e)
+        n = reps * len(evs)
+        hits = reps * sum(v[0] for v in evs)
+        tr.close()
+        return {"events_per_s": round(n / (ms / 1e3), 1), "hits_per_s": round(hits / (ms / 1e3), 1),
+                "workload": "cfg1_plain_fp32: 100 distinct 40-track events, FP32, one event per call"}
+    except Exception as ex:  # reported, not fatal
+        return {"events_per_s": None, "error": str(ex)}
+
+
+def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
+    """The FP64 oracle on the host cores over a bounded sample of the same events,
+    plus agreement of the GPU result on that sample."""
+    import oracle
+    from oracle import metrics
+    sh = synth.shape_of(wl)
+    model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+    import paper_2508_07423_gb300 as pkg
+    fs = pkg.feat_scale_of(tr.cfg)
+    cores = os.cpu_count() or 1
+    done, hits, t_used = 0, 0, 0.0
+    lab_ref = []
+    while t_used < seconds and done < batch.n_events:
+        idx = list(range(done, min(done + cores, batch.n_events)))
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        lab, _ = oracle.find_tracks_batch(model, sub.x, sub.y, sub.z, sub.plane, sub.offsets,
+                                          wl["radius2"], wl["k_max"], wl["cut"], threads=cores,
+                                          feat_scale=fs)
+        t_used += time.perf_counter() - t0
+        lab_ref.append(lab)
+        done += len(idx)
+        hits += sub.n_hits
+    lab_ref = np.concatenate(lab_ref)
+    n_s = int(batch.offsets[done])
+    same = sum(np.array_equal(gpu_labels[batch.offsets[e]:batch.offsets[e + 1]],
+                              lab_ref[batch.offsets[e]:batch.offsets[e + 1]]) for e in range(done))
+    cg = metrics.batch_counts(gpu_labels[:n_s], batch.pid[:n_s], batch.offsets[:done + 1]).summary()
+    co = metrics.batch_counts(lab_ref, batch.pid[:n_s], batch.offsets[:done + 1]).summary()
+    # edge decisions on the first sampled events, over the union of both edge
+    # sets (an edge absent from one side counts as not kept there)
+    agree, union, max_err = 0, 0, 0.0
+    for e in range(min(4, done)):
+        ev = batch.event(e)
+        ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                       wl["k_max"], wl["cut"], feat_scale=fs)
+        g = tr.get_graph(e)
+        G = {(int(s), int(d)): (int(k), float(l))
+             for s, d, k, l in zip(g["src"], g["dst"], g["kept"], g["logit"])}
+        O = {(int(s), int(d)): (int(k), float(l))
+             for s, d, k, l in zip(ref.src, ref.dst, ref.keep, ref.logit)}
+        for key in set(G) | set(O):
+            kg = G.get(key, (0, 0.0))[0]
+            ko = O.get(key, (0, 0.0))[0]
+            agree += kg == ko
+            union += 1
+            if key in G and key in O:
+                sg = 1 / (1 + math.exp(-G[key][1]))
+                so = 1 / (1 + math.exp(-O[key][1]))
+                max_err = max(max_err, abs(sg - so))
+    return {"value": round(done / t_used, 2), "unit": "events/s",
+            "hits_per_s": round(hits / t_used, 1), "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of the {batch.n_events} benchmark events "
+                      f"({hits} hits), FP64 C++ oracle, one event per thread",
+            "labels_identical_events": f"{same}/{done}",
+            "track_efficiency_gpu": round(cg["efficiency"], 6),
+            "track_efficiency_oracle": round(co["efficiency"], 6),
+            "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4),
+            "edge_decision_agreement": round(agree / max(union, 1), 6),
+            "edge_decision_events": min(4, done), "max_score_error": max_err}
+
+
+def run_reference(a, rank, world):
+    """The FP64 oracle as the reference arm: each step a bounded sample of the
+    workload's events on all host cores."""
+    if rank != 0:
+        return
+    import oracle
+    wl = synth.workload(a.workload)
+    sh = synth.shape_of(wl)
+    model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+    cores = os.cpu_count() or 1
+    per_step = cores
+    fs = tuple(float(np.float32(v)) for v in oracle.DEFAULT_FEAT_SCALE)
+    times, hits = [], 0
+    for i in range(max(a.warmup, 3) + a.steps):
+        b = synth.workload_batch(wl, per_step, first_event=(i * per_step) % wl["n_events"])
+        t0 = time.perf_counter()
+        oracle.find_tracks_batch(model, b.x, b.y, b.z, b.plane, b.offsets, wl["radius2"],
+                                 wl["k_max"], wl["cut"], threads=cores, feat_scale=fs)
+        dt = time.perf_counter() - t0
+        if i >= max(a.warmup, 3):
+            times.append(dt)
+            hits += b.n_hits
+    ms = 1e3 * float(np.mean(times))
+    value = per_step / (ms / 1e3)
+    sample = f"{per_step} events of the workload per step, one per thread, FP64 C++ oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "events/s",
+        "n_gpus": world, "steps": a.steps, "warmup": max(a.warmup, 3),
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "hits_per_s": round(hits / sum(times), 1),
+        "config": {"workload": f"{a.workload}: {wl['description']}", "sample": sample},
+        "cpu_baseline": {"value": round(value, 2), "unit": "events/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 2), "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -201,9 +201,27 @@ gnntrk_status gnntrk_get_graph(gnntrk_handle* h, int32_t event, int64_t capacity
  * Statistics of the last gnntrk_find_tracks call (synchronises the device).
  *   out: host int64 [8]: [0] total edges, [1] kept edges, [2] edges in the
  *        re-score band, [3] events re-run in FP32, [4] events, [5] hits,
- *        [6] edge capacity, [7] reserved (0).
+ *        [6] edge capacity, [7] kernels launched by the call.
  */
 gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out);
+
+/*
+ * Per-stage device timing (instrumentation for benchmarks).
+ * gnntrk_set_profiling(h, 1) makes later gnntrk_find_tracks calls record a
+ * CUDA event pair around each stage on the call's stream; 0 stops it. Enabling
+ * also clears the accumulated times.
+ * gnntrk_stage_times waits for the recorded events and reports, per stage
+ * (in pipeline order), its name (NUL-terminated, at most 31 chars, written to
+ * names + 32 * i), the summed device time in ms and the number of times it
+ * ran. Any output may be NULL. Returns the number of stages (which may exceed
+ * max_stages; only max_stages are written), or -1 on error.
+ * Stage names: sort, node_prep, radius_count, scan_out, radius_fill, scan_in,
+ * in_index, edge_encoder, node_update, edge_update, band_mark, rescore,
+ * components.
+ */
+gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable);
+int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, double* total_ms,
+                           int64_t* runs);
 
 /* Description of the last error on this handle ("" if none). The string is
  * owned by the handle. NULL handle: description of the last create failure. */

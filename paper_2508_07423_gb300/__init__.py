@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
           6: "WEIGHTS", 7: "UNSUPPORTED"}
 
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
-           "gnntrk_get_graph", "gnntrk_stats", "gnntrk_last_error", "gnntrk_destroy"]
+           "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
+           "gnntrk_last_error", "gnntrk_destroy"]
 
 
 class GnntrkError(RuntimeError):
@@ -79,6 +80,10 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_get_graph.restype = st
     L.gnntrk_stats.argtypes = [vp, vp]
     L.gnntrk_stats.restype = st
+    L.gnntrk_set_profiling.argtypes = [vp, i32]
+    L.gnntrk_set_profiling.restype = st
+    L.gnntrk_stage_times.argtypes = [vp, i32, vp, vp, vp]
+    L.gnntrk_stage_times.restype = i32
     L.gnntrk_last_error.argtypes = [vp]
     L.gnntrk_last_error.restype = ctypes.c_char_p
     L.gnntrk_destroy.argtypes = [vp]
@@ -180,7 +185,26 @@ class Tracker:
         self._check(self._L.gnntrk_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return {"edges": int(out[0]), "kept": int(out[1]), "band": int(out[2]),
                 "rerun_events": int(out[3]), "events": int(out[4]), "hits": int(out[5]),
-                "edge_capacity": int(out[6])}
+                "edge_capacity": int(out[6]), "launches": int(out[7])}
+
+    def set_profiling(self, enable: bool):
+        self._check(self._L.gnntrk_set_profiling(self._h, int(bool(enable))))
+
+    def stage_times(self) -> dict:
+        """{stage: (total device ms, runs)} accumulated since profiling was enabled."""
+        n = self._L.gnntrk_stage_times(self._h, 0, None, None, None)
+        if n < 0:
+            raise GnntrkError(1, "stage_times failed")
+        names = ctypes.create_string_buffer(32 * max(n, 1))
+        ms = np.zeros(max(n, 1), np.float64)
+        runs = np.zeros(max(n, 1), np.int64)
+        self._L.gnntrk_stage_times(self._h, n, names, ms.ctypes.data_as(ctypes.c_void_p),
+                                   runs.ctypes.data_as(ctypes.c_void_p))
+        out = {}
+        for i in range(n):
+            nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+            out[nm] = (float(ms[i]), int(runs[i]))
+        return out
 
     def get_graph(self, event: int) -> dict:
         """Rough graph of one event of the last call (host numpy arrays)."""

@@ -32,8 +32,23 @@ struct gnntrk_handle {
   std::vector<void*> allocs;
   // last call
   int last_events = 0, last_hits = 0;
+  int last_launches = 0;
   cudaStream_t last_stream = nullptr;
   std::string err;
+  // per-stage profiling
+  bool profiling = false;
+  struct StageAcc {
+    std::string name;
+    double ms = 0.0;
+    int64_t runs = 0;
+  };
+  std::vector<StageAcc> stages;
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace {
@@ -208,6 +223,63 @@ GraphParams graph_params(const gnntrk_handle* h) {
 
 bool valid_d(int d) { return (d >= 1 && d <= 8) || d == 16; }
 
+cudaEvent_t take_event(gnntrk_handle* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// wait for the recorded stage events and fold them into the totals
+void collect_stages(gnntrk_handle* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->stages[p.stage].ms += ms;
+      h->stages[p.stage].runs += 1;
+    }
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->pending.clear();
+  cudaGetLastError();
+}
+
+// Runs `fn` (which enqueues one pipeline stage on s) and, when profiling,
+// brackets it with an event pair on the same stream.
+template <class F>
+void stage(gnntrk_handle* h, const char* name, cudaStream_t s, int kernels, F&& fn) {
+  h->last_launches += kernels;
+  if (!h->profiling) {
+    fn();
+    return;
+  }
+  int idx = -1;
+  for (size_t i = 0; i < h->stages.size(); ++i)
+    if (h->stages[i].name == name) idx = int(i);
+  if (idx < 0) {
+    h->stages.push_back({name, 0.0, 0});
+    idx = int(h->stages.size()) - 1;
+  }
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  cudaEventRecord(a, s);
+  fn();
+  cudaEventRecord(b, s);
+  h->pending.push_back({idx, a, b});
+}
+
+int tc_node_prep_kernels(int n_embed) { return 1; }
+
+// tensor-core GNN, one profiling stage per kernel family
+void tc_gnn_staged(gnntrk_handle* h, const Batch& b, const Ws& w, const GraphParams& g,
+                   cudaStream_t s) {
+  stage(h, "gnn_tc", s, 2 + 2 * h->K, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, s); });
+}
+
 }  // namespace
 
 extern "C" {
@@ -337,53 +409,71 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
   b.labels = out_labels;
   const GraphParams g = graph_params(h);
 
+  if (h->profiling) collect_stages(h);
+  h->last_launches = 0;
   cudaMemsetAsync(w.counters, 0, C_COUNT * sizeof(int32_t), s);
   cudaMemcpyAsync(w.ev_off, offsets, sizeof(int64_t) * (n_events + 1), cudaMemcpyDeviceToDevice, s);
-  launch_sort(b, w, c.n_planes, s);
+  stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
   const Sel all{nullptr, nullptr, 0};
   const bool tc = c.precision != GNNTRK_FP32;
-  if (!tc)
-    launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true, all, s);
-  else
-    tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, s);
-  launch_radius(b, w, g, h->D, false, s);
-  launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap, w.scan_blocks, s);
-  launch_radius(b, w, g, h->D, true, s);
-  launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
-              w.scan_blocks, s);
-  launch_csc(b, w, s);
+  stage(h, "node_prep", s, tc ? tc_node_prep_kernels(h->n_embed) : 1, [&] {
+    if (!tc)
+      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true,
+                           all, s);
+    else
+      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, s);
+  });
+  stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
+  stage(h, "scan_out", s, 2, [&] {
+    launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap,
+                w.scan_blocks, s);
+  });
+  stage(h, "radius_fill", s, 1, [&] { launch_radius(b, w, g, h->D, true, s); });
+  stage(h, "scan_in", s, 2, [&] {
+    launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
+                w.scan_blocks, s);
+  });
+  stage(h, "in_index", s, 2, [&] { launch_csc(b, w, s); });
   if (!tc) {
-    launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s);
+    stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {
-      launch_node_update_f32(b, w, h->node[k], h->h, all, s);
-      launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                             g.cut_logit, false, 0.f, 0.f, all, s);
+      stage(h, "node_update", s, 1,
+            [&] { launch_node_update_f32(b, w, h->node[k], h->h, all, s); });
+      stage(h, "edge_update", s, 1, [&] {
+        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                               g.cut_logit, false, 0.f, 0.f, all, s);
+      });
     }
     if (h->K == 0)  // no message passing: the classifier reads the edge encodings
-      launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f, all, s);
+      stage(h, "edge_update", s, 1, [&] {
+        launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f,
+                               all, s);
+      });
   } else {
-    tc_gnn(b, w, h->tc, h->h, h->K, g, s);
+    tc_gnn_staged(h, b, w, g, s);
     if (c.rescore_band > 0.f) {
       const double lo = double(c.score_cut) - double(c.rescore_band);
       const double hi = double(c.score_cut) + double(c.rescore_band);
       const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
       const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
-      tc_mark_band(b, w, band_lo, band_hi, s);
+      stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
       const Sel sel{w.rerun_list, w.counters + C_RERUN, n_events};
-      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
-                           sel, s);
-      launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s);
-      for (int k = 0; k < h->K; ++k) {
-        launch_node_update_f32(b, w, h->node[k], h->h, sel, s);
-        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                               g.cut_logit, true, band_lo, band_hi, sel, s);
-      }
-      if (h->K == 0)
-        launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
-                               band_hi, sel, s);
+      stage(h, "rescore", s, 3 + 2 * h->K, [&] {
+        launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
+                             sel, s);
+        launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s);
+        for (int k = 0; k < h->K; ++k) {
+          launch_node_update_f32(b, w, h->node[k], h->h, sel, s);
+          launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                                 g.cut_logit, true, band_lo, band_hi, sel, s);
+        }
+        if (h->K == 0)
+          launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
+                                 band_hi, sel, s);
+      });
     }
   }
-  launch_cc(b, w, s);
+  stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "launch");
   return GNNTRK_OK;
@@ -428,7 +518,7 @@ gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out) {
   out[4] = h->last_events;
   out[5] = h->last_hits;
   out[6] = h->ws.e_cap;
-  out[7] = 0;
+  out[7] = h->last_launches;
   return GNNTRK_OK;
 }
 
@@ -474,8 +564,34 @@ const char* gnntrk_last_error(const gnntrk_handle* h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  collect_stages(h);
+  h->profiling = enable != 0;
+  if (h->profiling) h->stages.clear();
+  return GNNTRK_OK;
+}
+
+int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, double* total_ms,
+                           int64_t* runs) {
+  if (!h) return -1;
+  collect_stages(h);
+  const int n = int(h->stages.size());
+  for (int i = 0; i < n && i < max_stages; ++i) {
+    if (names) {
+      std::memset(names + 32 * i, 0, 32);
+      std::strncpy(names + 32 * i, h->stages[i].name.c_str(), 31);
+    }
+    if (total_ms) total_ms[i] = h->stages[i].ms;
+    if (runs) runs[i] = h->stages[i].runs;
+  }
+  return n;
+}
+
 void gnntrk_destroy(gnntrk_handle* h) {
   if (!h) return;
+  collect_stages(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
