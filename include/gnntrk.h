@@ -223,8 +223,47 @@ gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable);
 int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, double* total_ms,
                            int64_t* runs);
 
+/*
+ * Connected-component labels of one graph, WITHOUT allocating any memory.
+ * The thesis has no counterpart of this call; it is here for callers that
+ * cannot allocate device memory -- code running under another framework's
+ * memory manager (a trigger application that hands out all device memory
+ * itself and forbids allocations inside its algorithms), or a real-time path
+ * that may not pay for cudaMalloc. It makes no allocation of any kind.
+ *
+ *   n_hits:  number of vertices, 0..GNNTRK_NOALLOC_MAX_HITS.
+ *   n_edges: number of edges, 0..2^31-1.
+ *   src, dst: device int32 [n_edges]; vertex indices in [0, n_hits).
+ *   kept:    device uint8 [n_edges], or NULL for "all edges"; edge e joins
+ *            its vertices iff kept[e] != 0.
+ *   out_labels: device int32 [n_hits]; receives for each vertex the smallest
+ *            vertex index of its weakly connected component. Given one event's
+ *            graph from gnntrk_get_graph (src, dst, kept), these are the labels
+ *            gnntrk_find_tracks wrote for that event.
+ * Scratch: one fixed device array of 4 * (GNNTRK_NOALLOC_MAX_HITS + 64) bytes
+ *   (4 MiB + 256 B), part of the library image: every GPU on which the library
+ *   is loaded holds it until the process exits.
+ * Set-up: the first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ * Sharing: every call on a device uses the same array, which keeps the last
+ *   call's contents (each call rewrites what it reads first). Calls whose work
+ *   overlaps on the GPU -- on different streams or from different host threads
+ *   -- race on it and give undefined labels: keep them on one stream.
+ * Errors: INVALID_ARG (synchronous, nothing launched) when n_hits exceeds
+ *   GNNTRK_NOALLOC_MAX_HITS, n_edges is out of range or a needed pointer is
+ *   NULL; CUDA when a launch fails. gnntrk_last_error(NULL) describes it. An
+ *   edge index outside [0, n_hits) is detected on the device: every label of
+ *   that call is then -1.
+ * Asynchronous on `stream`.
+ */
+#define GNNTRK_NOALLOC_MAX_HITS (1 << 20)
+gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edges, const int32_t* src,
+                                        const int32_t* dst, const uint8_t* kept,
+                                        int32_t* out_labels, void* stream);
+
 /* Description of the last error on this handle ("" if none). The string is
- * owned by the handle. NULL handle: description of the last create failure. */
+ * owned by the handle. NULL handle: description of the last failure of
+ * gnntrk_create or gnntrk_components_noalloc. */
 const char* gnntrk_last_error(const gnntrk_handle* h);
 
 /* Release the handle's device memory, CUDA graphs and streams. NULL is a no-op.

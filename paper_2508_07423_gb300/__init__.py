@@ -25,7 +25,9 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
-           "gnntrk_last_error", "gnntrk_destroy"]
+           "gnntrk_components_noalloc", "gnntrk_last_error", "gnntrk_destroy"]
+
+NOALLOC_MAX_HITS = 1 << 20
 
 
 class GnntrkError(RuntimeError):
@@ -84,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_set_profiling.restype = st
     L.gnntrk_stage_times.argtypes = [vp, i32, vp, vp, vp]
     L.gnntrk_stage_times.restype = i32
+    L.gnntrk_components_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp]
+    L.gnntrk_components_noalloc.restype = st
     L.gnntrk_last_error.argtypes = [vp]
     L.gnntrk_last_error.restype = ctypes.c_char_p
     L.gnntrk_destroy.argtypes = [vp]
@@ -247,6 +251,17 @@ def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
     args.update(kw)
     cfg = make_cfg(wl["model"], wl["radius2"], **args)
     return Tracker(synth.workload_weights(wl), cfg)
+
+
+def components_noalloc(n_hits: int, src, dst, kept, out_labels, stream=None):
+    """Component labels of one graph with no allocation (CUDA tensors in/out);
+    see gnntrk_components_noalloc in include/gnntrk.h."""
+    L = load_library()
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    st = L.gnntrk_components_noalloc(n_hits, 0 if src is None else src.numel(), _ptr(src),
+                                     _ptr(dst), _ptr(kept), _ptr(out_labels), ctypes.c_void_p(s))
+    if st != 0:
+        raise GnntrkError(st, L.gnntrk_last_error(None).decode())
 
 
 def cut_logit(score_cut: float) -> float:

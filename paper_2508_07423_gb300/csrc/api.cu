@@ -282,6 +282,11 @@ void tc_gnn_staged(gnntrk_handle* h, const Batch& b, const Ws& w, const GraphPar
 
 }  // namespace
 
+namespace gnntrk {
+// failure text of handle-less calls, returned by gnntrk_last_error(NULL)
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace gnntrk
+
 extern "C" {
 
 void gnntrk_default_cfg(gnntrk_cfg* c) {

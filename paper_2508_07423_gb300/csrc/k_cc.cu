@@ -9,6 +9,9 @@
 //     ancestor, which keeps parent[i] <= i).
 // A label is the root minus the event's first index: the smallest event-local
 // input index of the component.
+#include <mutex>
+
+#include "../../include/gnntrk.h"
 #include "internal.cuh"
 
 namespace gnntrk {
@@ -71,7 +74,72 @@ __global__ void k_cc_label(Batch b, Ws w) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Component labelling without allocation (gnntrk_components_noalloc).
+//
+// For callers that may not allocate device memory, the union-find parents live
+// in one file-scope device array of fixed size instead of a handle's
+// workspace. The array exists on every device that loads the library and
+// stays until the process exits. Every call on a device reuses it, so each
+// call first rewrites the part it needs (status word and parents); calls whose
+// work overlaps on the GPU would race on it.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocHeader = 64;  // ints: [C_STATUS] status word, rest padding
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocHeader + GNNTRK_NOALLOC_MAX_HITS];
+
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_ptr[kMaxDevices] = {};
+
+__global__ void k_na_init(int32_t* scratch, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kNoAllocHeader) scratch[t] = 0;
+  int32_t* P = scratch + kNoAllocHeader;
+  for (int v = t; v < n; v += gridDim.x * blockDim.x) P[v] = v;
+}
+
+__global__ void k_na_union(int32_t* scratch, int n, int ne, const int32_t* src,
+                           const int32_t* dst, const uint8_t* kept) {
+  int32_t* P = scratch + kNoAllocHeader;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    if (kept != nullptr && !kept[e]) continue;
+    const int a = src[e], b = dst[e];
+    if (a < 0 || a >= n || b < 0 || b >= n) {
+      set_status(scratch, ST_INPUT);
+      continue;
+    }
+    uf_union(P, a, b, scratch);
+  }
+}
+
+__global__ void k_na_label(const int32_t* scratch, int n, int32_t* labels) {
+  const bool bad = *(volatile const int32_t*)&scratch[C_STATUS] != 0;
+  int32_t* P = const_cast<int32_t*>(scratch) + kNoAllocHeader;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    labels[v] = bad ? -1 : uf_find(P, v);
+}
+
 }  // namespace
+
+void set_global_error(const std::string& msg);
+
+// Device address of the scratch array on the current device; looked up once
+// per device (with that device current) and cached.
+static cudaError_t noalloc_scratch(int32_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    int32_t* p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
 
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s) {
   k_cc_union<<<device_sms() * 8, 256, 0, s>>>(w);
@@ -79,3 +147,43 @@ void launch_cc(const Batch& b, const Ws& w, cudaStream_t s) {
 }
 
 }  // namespace gnntrk
+
+extern "C" gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edges,
+                                                   const int32_t* src, const int32_t* dst,
+                                                   const uint8_t* kept, int32_t* out_labels,
+                                                   void* stream) {
+  using namespace gnntrk;
+  if (n_hits < 0 || n_hits > GNNTRK_NOALLOC_MAX_HITS) {
+    set_global_error("gnntrk_components_noalloc: n_hits " + std::to_string(n_hits) +
+                     " outside 0.." + std::to_string(GNNTRK_NOALLOC_MAX_HITS) +
+                     " (the fixed scratch array holds at most that many vertices)");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  if (n_edges < 0 || n_edges > 0x7fffffffLL) {
+    set_global_error("gnntrk_components_noalloc: n_edges outside 0..2^31-1");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  if ((n_hits > 0 && out_labels == nullptr) || (n_edges > 0 && (src == nullptr || dst == nullptr))) {
+    set_global_error("gnntrk_components_noalloc: NULL pointer");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  if (n_hits == 0) return GNNTRK_OK;
+  int32_t* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("gnntrk_components_noalloc: scratch address: ") +
+                     cudaGetErrorString(e));
+    return GNNTRK_ERR_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = int(n_hits), ne = int(n_edges);
+  k_na_init<<<div_up(n > kNoAllocHeader ? n : kNoAllocHeader, 256), 256, 0, s>>>(scratch, n);
+  if (ne > 0) k_na_union<<<device_sms() * 8, 256, 0, s>>>(scratch, n, ne, src, dst, kept);
+  k_na_label<<<div_up(n, 256), 256, 0, s>>>(scratch, n, out_labels);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("gnntrk_components_noalloc: launch: ") + cudaGetErrorString(e));
+    return GNNTRK_ERR_CUDA;
+  }
+  return GNNTRK_OK;
+}
