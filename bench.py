@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--precision", default=None)
+    p.add_argument("--band", type=float, default=None,
+                   help="re-score band |s - cut| in score units (default: the workload's)")
+    p.add_argument("--events", type=int, default=None,
+                   help="events per step (default: the workload's; smaller for profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
@@ -159,7 +163,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # each rank processes its own events (replicas over disjoint event ranges)
-    n_ev = wl["n_events"]
+    n_ev = a.events or wl["n_events"]
     batch = synth.workload_batch(wl, n_ev, first_event=rank * n_ev)
     N = batch.n_hits
     dev = torch.device("cuda", local)
@@ -167,8 +171,10 @@ def main():
     plane = torch.from_numpy(batch.plane).to(dev)
     offs = torch.from_numpy(batch.offsets).to(dev)
     labels = torch.empty(N, dtype=torch.int32, device=dev)
+    kw = {} if a.band is None else {"rescore_band": a.band}
     tr = pkg.tracker_for_workload(wl, precision=precision, max_hits=N, max_events=n_ev,
-                                  edges_per_hit=16)
+                                  edges_per_hit=16, **kw)
+    band = tr.cfg.rescore_band
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
@@ -256,7 +262,9 @@ def main():
         "config": {"workload": f"{a.workload}: {wl['description']}",
                    "n_events": n_ev, "hits": N, "edges": E, "kept_edges": stats["kept"],
                    "net": f"embed {'-'.join(map(str, m['embed']))}, IN h{m['hidden']} K{m['iters']}",
-                   "precision": precision, "l2": "flushed between steps (256 MiB write)",
+                   "precision": precision, "rescore_band": round(float(band), 6),
+                   "band_edges": stats["band"], "rerun_events": stats["rerun_events"],
+                   "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (disjoint events, no collective)"},
         "clocks": clk,
         "roofline": roof,

@@ -243,10 +243,8 @@ def run_batch(tracker: Tracker, batch, device="cuda", stream=None, check=True):
 def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
     """A Tracker for a workload of workloads.json (weights from its seed)."""
     from . import synth
-    band = 0.0
     prec = precision if precision is not None else wl.get("precision", "fp32")
-    if prec != "fp32":
-        band = float(wl.get("rescore_band_score", 0.0))
+    band = float(wl.get("rescore_band_score", 0.0)) if prec != "fp32" else 0.0
     args = dict(k_max=wl["k_max"], score_cut=wl["cut"], precision=prec, rescore_band=band)
     args.update(kw)
     cfg = make_cfg(wl["model"], wl["radius2"], **args)

@@ -272,14 +272,6 @@ void stage(gnntrk_handle* h, const char* name, cudaStream_t s, int kernels, F&& 
   h->pending.push_back({idx, a, b});
 }
 
-int tc_node_prep_kernels(int n_embed) { return 1; }
-
-// tensor-core GNN, one profiling stage per kernel family
-void tc_gnn_staged(gnntrk_handle* h, const Batch& b, const Ws& w, const GraphParams& g,
-                   cudaStream_t s) {
-  stage(h, "gnn_tc", s, 2 + 2 * h->K, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, s); });
-}
-
 }  // namespace
 
 namespace gnntrk {
@@ -421,12 +413,12 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
   stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
   const Sel all{nullptr, nullptr, 0};
   const bool tc = c.precision != GNNTRK_FP32;
-  stage(h, "node_prep", s, tc ? tc_node_prep_kernels(h->n_embed) : 1, [&] {
+  stage(h, "node_prep", s, tc ? 2 : 1, [&] {
     if (!tc)
       launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true,
                            all, s);
     else
-      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, s);
+      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s);
   });
   stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
   stage(h, "scan_out", s, 2, [&] {
@@ -455,7 +447,17 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
                                all, s);
       });
   } else {
-    tc_gnn_staged(h, b, w, g, s);
+    const bool fused = tc_cls_fused(h->h, c.precision);
+    stage(h, "edge_encoder", s, 1,
+          [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
+    for (int k = 0; k < h->K; ++k) {
+      stage(h, "node_update", s, 1,
+            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
+      stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
+            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k); });
+    }
+    if (h->K == 0)
+      stage(h, "edge_update", s, 1, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1); });
     if (c.rescore_band > 0.f) {
       const double lo = double(c.score_cut) - double(c.rescore_band);
       const double hi = double(c.score_cut) + double(c.rescore_band);
@@ -598,6 +600,7 @@ void gnntrk_destroy(gnntrk_handle* h) {
   collect_stages(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->d_wtc) cudaFree(h->d_wtc);
   delete h;
 }
 

@@ -243,15 +243,18 @@ template <int D>
 void radius_d(const Batch& b, const Ws& w, const GraphParams& g, bool fill, cudaStream_t s) {
   const int grid = b.n_events * (g.n_planes - 1);
   if (grid <= 0) return;
-  if (fill) {
+  static bool attr = false;
+  if (!attr) {
     cudaFuncSetAttribute(k_radius<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kCandSmemBytes);
-    k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
-  } else {
     cudaFuncSetAttribute(k_radius<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kCandSmemBytes);
-    k_radius<D, false><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
+    attr = true;
   }
+  if (fill)
+    k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
+  else
+    k_radius<D, false><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
 }
 
 // ---------------------------------------------------------------------------

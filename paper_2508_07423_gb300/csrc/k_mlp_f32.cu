@@ -244,10 +244,28 @@ __global__ void k_edge_upd_f32(Batch b, Ws w, Mlp2F32 m, Mlp2F32 cls, int has_cl
   }
 }
 
+// occupancy of (kernel, block size, shared memory), queried once and cached
 int blocks_per_sm(const void* fn, int threads, size_t smem) {
+  struct Entry {
+    const void* fn;
+    int threads;
+    size_t smem;
+    int n;
+  };
+  static Entry cache[32];
+  static int used = 0;
+  for (int i = 0; i < used; ++i)
+    if (cache[i].fn == fn && cache[i].threads == threads && cache[i].smem == smem) return cache[i].n;
   int n = 0;
+  // the attribute is an upper bound: set it once to the device maximum, so a
+  // later configuration with less shared memory never lowers it
+  bool seen = false;
+  for (int i = 0; i < used; ++i) seen = seen || cache[i].fn == fn;
+  if (!seen) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
-  return n > 0 ? n : 1;
+  n = n > 0 ? n : 1;
+  if (used < 32) cache[used++] = Entry{fn, threads, smem, n};
+  return n;
 }
 
 // rows per block and shared memory of the interaction-network kernels
@@ -276,7 +294,6 @@ void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, in
   width = max(width, h);
   const int stride = width | 1;
   const size_t smem = size_t(2) * kPrepThreads * stride * sizeof(float);
-  cudaFuncSetAttribute(k_node_prep_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const dim3 grid = grid_for((const void*)k_node_prep_f32, kPrepThreads, smem, sel, b.n_hits);
   k_node_prep_f32<<<grid, kPrepThreads, smem, s>>>(b, w, em, n_embed, node_enc, D, h, g, stride,
                                                    do_embed, do_node_enc, sel);
@@ -287,7 +304,6 @@ void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, S
   const int T = gnn_threads(h);
   const int stride = (3 * h + 2) | 1;
   const size_t smem = size_t(T) * stride * sizeof(float);
-  cudaFuncSetAttribute(k_edge_enc_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const dim3 grid = grid_for((const void*)k_edge_enc_f32, T, smem, sel, -1);
   k_edge_enc_f32<<<grid, T, smem, s>>>(b, w, m, h, stride, sel);
 }
@@ -298,7 +314,6 @@ void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h
   const int T = gnn_threads(h);
   const int stride = (4 * h + 2) | 1;
   const size_t smem = size_t(T) * stride * sizeof(float);
-  cudaFuncSetAttribute(k_node_upd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const dim3 grid = grid_for((const void*)k_node_upd_f32, T, smem, sel, b.n_hits);
   k_node_upd_f32<<<grid, T, smem, s>>>(b, w, m, h, stride, sel);
 }
@@ -309,7 +324,6 @@ void launch_edge_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const
   const int T = gnn_threads(h);
   const int stride = (4 * h + 2) | 1;
   const size_t smem = size_t(T) * stride * sizeof(float);
-  cudaFuncSetAttribute(k_edge_upd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const dim3 grid = grid_for((const void*)k_edge_upd_f32, T, smem, sel, -1);
   Mlp2F32 c{};
   if (cls) c = *cls;

@@ -1,16 +1,1052 @@
-// Tensor-core path (placeholder until the tcgen05 kernels land).
+// Tensor-core (tcgen05) kernels of the interaction network: BF16 or FP8-E4M3
+// operands, FP32 accumulation in tensor memory.
+//
+// One CTA of 128 threads works on tiles of 128 rows (edges or hits); thread t
+// owns row t of the tile and TMEM lane t (warp w reads lanes 32w..32w+31). Per
+// tile:
+//   1. gather: each thread copies the pieces of its input row ([e, h_src,
+//      h_dst], [h, sum_out e, sum_in e], ...) from global memory into the A
+//      tile in shared memory, laid out as 8-row x 16-byte core matrices
+//      (K-major, no swizzle: row r, 16-byte chunk c at
+//      ((r/8) * (K/epc) + c) * 128 + (r%8) * 16);
+//   2. one thread issues the layer-1 MMAs (weights resident in shared memory,
+//      loaded once per CTA by cp.async.bulk) and commits them to an mbarrier;
+//   3. every thread reads its row of the accumulator back with tcgen05.ld,
+//      adds the bias, applies LayerNorm and ReLU and writes the hidden row as
+//      the next A tile; layer 2 follows the same way;
+//   4. the epilogue adds the residual and stores the new state (BF16); at the
+//      last step the edge classifier (a third MMA, LayerNorm, ReLU and a dot
+//      product) and the cut run instead of the store.
+// FP8: each input segment of layer 1 (e.g. e, h_src, h_dst) is quantised with
+// its own per-row scale amax/448 and accumulated in its own TMEM block, so the
+// epilogue can apply the scales; weights carry per-output-channel scales
+// amax/448. Hidden rows are quantised per row as well. The K = 3 first layer of
+// the node encoder and the 1-unit last layer of the classifier stay FP32.
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
 #include "../../include/gnntrk.h"
 #include "tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace gnntrk {
 
-int tc_upload(TcModel&, const HostLayer*, int, int, int, int, int, void**, std::string& err) {
-  err = "BF16/FP8 tensor-core path not built yet";
-  return GNNTRK_ERR_UNSUPPORTED;
+int device_sms();
+
+namespace {
+
+using namespace tc;
+
+constexpr int kRows = 128;       // rows per tile = threads per CTA = TMEM lanes
+constexpr long long kWaitCycles = 4000000000LL;  // bounded waits: about 2 s
+
+enum Mode : int { M_NODE_ENC = 0, M_EDGE_ENC = 1, M_NODE_UPD = 2, M_EDGE_UPD = 3,
+                  M_EDGE_UPD_CLS = 4, M_CLS = 5 };
+
+struct TcArgs {
+  Batch b;
+  Ws w;
+  const uint8_t* W1;  // layer-1 operand image (classifier layer 1 in M_CLS)
+  const uint8_t* W2;  // layer-2 operand image
+  const uint8_t* Wc;  // classifier layer-1 image (M_EDGE_UPD_CLS)
+  const float* b1;
+  const float* b2;
+  const float* bc1;
+  const float* s1;    // FP8 per-output-channel weight scales
+  const float* s2;
+  const float* sc;
+  LayerF32 ne1;       // node encoder layer 1 (FP32, M_NODE_ENC)
+  LayerF32 c2;        // classifier layer 2 (FP32, h -> 1)
+  float fs[6];
+  float cut;
+};
+
+__host__ __device__ constexpr int n_seg(int mode) {
+  return mode == M_EDGE_ENC ? 2 : ((mode == M_NODE_UPD || mode == M_EDGE_UPD || mode == M_EDGE_UPD_CLS) ? 3 : 1);
 }
-void tc_node_prep(const Batch&, const Ws&, const TcModel&, const LayerF32*, int, int, int,
-                  const GraphParams&, cudaStream_t) {}
-void tc_gnn(const Batch&, const Ws&, const TcModel&, int, int, const GraphParams&, cudaStream_t) {}
-void tc_mark_band(const Batch&, const Ws&, float, float, cudaStream_t) {}
+__host__ __device__ constexpr int align1k(int x) { return (x + 1023) & ~1023; }
+__host__ __device__ constexpr int pow2_cols(int x) {
+  return x <= 32 ? 32 : (x <= 64 ? 64 : (x <= 128 ? 128 : (x <= 256 ? 256 : 512)));
+}
+
+// Shared-memory layout of one CTA (byte offsets).
+template <int H, bool FP8, int MODE>
+struct Layout {
+  static constexpr int ESZ = FP8 ? 1 : 2;
+  static constexpr int NSEG = n_seg(MODE);
+  static constexpr int K1 = (MODE == M_NODE_ENC) ? H : NSEG * H;
+  static constexpr bool HAS_W1 = MODE != M_NODE_ENC;
+  static constexpr bool HAS_W2 = MODE != M_CLS;
+  static constexpr bool HAS_WC = MODE == M_EDGE_UPD_CLS;
+  static constexpr int W1 = 0;
+  static constexpr int W1_BYTES = HAS_W1 ? H * K1 * ESZ : 0;
+  static constexpr int W2 = align1k(W1 + W1_BYTES);
+  static constexpr int W2_BYTES = HAS_W2 ? H * H * ESZ : 0;
+  static constexpr int WC = align1k(W2 + W2_BYTES);
+  static constexpr int WC_BYTES = HAS_WC ? H * H * ESZ : 0;
+  static constexpr int A = align1k(WC + WC_BYTES);
+  static constexpr int A_BYTES = kRows * (K1 > H ? K1 : H) * ESZ;
+  static constexpr int PAR = align1k(A + A_BYTES);
+  // fp32 parameters: b1, b2, bc1, s1, s2, sc, c2 weights, ne1 (3 x H + H)
+  static constexpr int PAR_FLOATS = 7 * H + 4 * H + 8;
+  static constexpr int BAR = PAR + PAR_FLOATS * 4;
+  static constexpr int TOTAL = BAR + 64;
+  static constexpr int TMEM_COLS = FP8 ? pow2_cols(NSEG * H) : pow2_cols(H);
+};
+
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+// byte offset of (row, 16-byte chunk) in a canonical tile with `kchunks`
+// chunks per row
+__device__ __forceinline__ uint32_t tile_off(int row, int chunk, int kchunks) {
+  return uint32_t(((row >> 3) * kchunks + chunk) * 128 + (row & 7) * 16);
+}
+
+// Write `n` (multiple of 16 for FP8, of 8 for BF16) FP32 values of this
+// thread's row into the A tile starting at element k0, scaled by `inv` for FP8.
+template <bool FP8>
+__device__ __forceinline__ void put_row_f32(uint8_t* tile, int row, int kchunks, int k0,
+                                            const float* v, int n, float inv) {
+  if constexpr (FP8) {
+    for (int c = 0; c < n / 16; ++c) {
+      const float* q = v + 16 * c;
+      uint4 u;
+      u.x = pack_e4m3x4(q[0] * inv, q[1] * inv, q[2] * inv, q[3] * inv);
+      u.y = pack_e4m3x4(q[4] * inv, q[5] * inv, q[6] * inv, q[7] * inv);
+      u.z = pack_e4m3x4(q[8] * inv, q[9] * inv, q[10] * inv, q[11] * inv);
+      u.w = pack_e4m3x4(q[12] * inv, q[13] * inv, q[14] * inv, q[15] * inv);
+      *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 4) + c, kchunks)) = u;
+    }
+  } else {
+    for (int c = 0; c < n / 8; ++c) {
+      const float* q = v + 8 * c;
+      uint4 u;
+      u.x = pack_bf16(q[0], q[1]);
+      u.y = pack_bf16(q[2], q[3]);
+      u.z = pack_bf16(q[4], q[5]);
+      u.w = pack_bf16(q[6], q[7]);
+      *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 3) + c, kchunks)) = u;
+    }
+  }
+}
+
+// Copy one BF16 row of H values from global memory into the A tile (BF16) or
+// quantise it (FP8, per-row scale returned). `keep` receives the raw row when
+// not null.
+template <int H, bool FP8>
+__device__ __forceinline__ float put_row_bf16(uint8_t* tile, int row, int kchunks, int k0,
+                                              const __nv_bfloat16* src, uint4* keep) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  if constexpr (!FP8) {
+#pragma unroll
+    for (int c = 0; c < H / 8; ++c) {
+      const uint4 u = s4[c];
+      if (keep) keep[c] = u;
+      *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 3) + c, kchunks)) = u;
+    }
+    return 1.0f;
+  } else {
+    uint4 r[H / 8];
+    float amax = 0.f;
+#pragma unroll
+    for (int c = 0; c < H / 8; ++c) {
+      r[c] = s4[c];
+      if (keep) keep[c] = r[c];
+      const uint32_t q[4] = {r[c].x, r[c].y, r[c].z, r[c].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        amax = fmaxf(amax, fmaxf(fabsf(bf16_lo(q[j])), fabsf(bf16_hi(q[j]))));
+    }
+    const float scale = amax > 0.f ? amax / 448.f : 1.f;
+    const float inv = amax > 0.f ? 448.f / amax : 1.f;
+#pragma unroll
+    for (int c = 0; c < H / 16; ++c) {
+      const uint4 a = r[2 * c], b = r[2 * c + 1];
+      uint4 u;
+      u.x = pack_e4m3x4(bf16_lo(a.x) * inv, bf16_hi(a.x) * inv, bf16_lo(a.y) * inv, bf16_hi(a.y) * inv);
+      u.y = pack_e4m3x4(bf16_lo(a.z) * inv, bf16_hi(a.z) * inv, bf16_lo(a.w) * inv, bf16_hi(a.w) * inv);
+      u.z = pack_e4m3x4(bf16_lo(b.x) * inv, bf16_hi(b.x) * inv, bf16_lo(b.y) * inv, bf16_hi(b.y) * inv);
+      u.w = pack_e4m3x4(bf16_lo(b.z) * inv, bf16_hi(b.z) * inv, bf16_lo(b.w) * inv, bf16_hi(b.w) * inv);
+      *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 4) + c, kchunks)) = u;
+    }
+    return scale;
+  }
+}
+
+template <int H>
+__device__ __forceinline__ void add_bf16_row(float* acc, const __nv_bfloat16* src) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int c = 0; c < H / 8; ++c) {
+    const uint4 u = s4[c];
+    acc[8 * c + 0] += bf16_lo(u.x);
+    acc[8 * c + 1] += bf16_hi(u.x);
+    acc[8 * c + 2] += bf16_lo(u.y);
+    acc[8 * c + 3] += bf16_hi(u.y);
+    acc[8 * c + 4] += bf16_lo(u.z);
+    acc[8 * c + 5] += bf16_hi(u.z);
+    acc[8 * c + 6] += bf16_lo(u.w);
+    acc[8 * c + 7] += bf16_hi(u.w);
+  }
+}
+
+// Issue the MMAs of one layer: A tile (kchunks 16-byte chunks per row) times
+// the weight image (H rows) over K elements. FP8 with segments: segment s
+// (H columns of K) accumulates into TMEM columns [s*H, (s+1)*H).
+template <int H, bool FP8>
+__device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, const uint8_t* W,
+                                            int K, int nseg_sep) {
+  constexpr int ESZ = FP8 ? 1 : 2;
+  constexpr int KSTEP = FP8 ? 32 : 16;
+  constexpr uint32_t IDESC = FP8 ? idesc_e4m3(kRows, H) : idesc_bf16(kRows, H);
+  const int kchunks = K * ESZ / 16;
+  const uint32_t sbo = uint32_t(kchunks) * 128;
+  const uint32_t a0 = smem_u32(A), w0 = smem_u32(W);
+  const int seg_len = nseg_sep > 1 ? K / nseg_sep : K;
+  for (int k = 0; k < K; k += KSTEP) {
+    const int seg = k / seg_len;
+    const uint32_t byte_k = uint32_t(k * ESZ / 16) * 128;  // chunk index * 128
+    const uint64_t ad = smem_desc(a0 + byte_k, 128, sbo);
+    const uint64_t bd = smem_desc(w0 + byte_k, 128, sbo);
+    const uint32_t d = tmem + uint32_t(nseg_sep > 1 ? seg * H : 0);
+    const uint32_t acc = (k % seg_len) != 0;
+    if constexpr (FP8)
+      mma_e4m3(d, ad, bd, IDESC, acc);
+    else
+      mma_bf16(d, ad, bd, IDESC, acc);
+  }
+}
+
+template <int H, bool FP8, int MODE>
+__global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
+  using L = Layout<H, FP8, MODE>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sW1 = smem + L::W1;
+  uint8_t* sW2 = smem + L::W2;
+  uint8_t* sWC = smem + L::WC;
+  uint8_t* sA = smem + L::A;
+  float* par = reinterpret_cast<float*>(smem + L::PAR);
+  float* pb1 = par;
+  float* pb2 = par + H;
+  float* pbc = par + 2 * H;
+  float* ps1 = par + 3 * H;
+  float* ps2 = par + 4 * H;
+  float* psc = par + 5 * H;
+  float* pc2 = par + 6 * H;      // classifier layer 2 weights [H] + bias
+  float* pne = par + 7 * H + 4;  // node encoder layer 1: W[3][H], b[H]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] mma
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::BAR + 16);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const Ws& w = p.w;
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+
+  // ---- set-up: barriers, TMEM, weights --------------------------------------
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, L::TMEM_COLS);
+    tmem_relinquish();
+  }
+  for (int i = tid; i < H; i += kRows) {
+    pb1[i] = MODE == M_NODE_ENC ? p.ne1.b[i] : (MODE == M_CLS ? p.bc1[i] : p.b1[i]);
+    pb2[i] = MODE == M_CLS ? 0.f : p.b2[i];
+    pbc[i] = (MODE == M_EDGE_UPD_CLS) ? p.bc1[i] : 0.f;
+    if constexpr (FP8) {
+      ps1[i] = MODE == M_NODE_ENC ? 1.f : (MODE == M_CLS ? p.sc[i] : p.s1[i]);
+      ps2[i] = MODE == M_CLS ? 1.f : p.s2[i];
+      psc[i] = (MODE == M_EDGE_UPD_CLS) ? p.sc[i] : 1.f;
+    }
+    if (MODE == M_EDGE_UPD_CLS || MODE == M_CLS) pc2[i] = p.c2.WT[i * p.c2.ldo];
+    if (MODE == M_NODE_ENC) {
+      for (int j = 0; j < 3; ++j) pne[j * H + i] = p.ne1.WT[j * p.ne1.ldo + i];
+      pne[3 * H + i] = p.ne1.b[i];
+    }
+  }
+  if (tid == 0 && (MODE == M_EDGE_UPD_CLS || MODE == M_CLS)) pc2[H] = p.c2.b[0];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const uint32_t tmem_lane = tmem_base + (uint32_t(warp * 32) << 16);
+
+  if (tid == 0) {
+    uint32_t bytes = uint32_t(L::W1_BYTES + L::W2_BYTES + L::WC_BYTES);
+    mbar_expect_tx(&bar[0], bytes);
+    if (L::HAS_W1) bulk_g2s(sW1, MODE == M_CLS ? p.Wc : p.W1, L::W1_BYTES, &bar[0]);
+    if (L::HAS_W2) bulk_g2s(sW2, p.W2, L::W2_BYTES, &bar[0]);
+    if (L::HAS_WC) bulk_g2s(sWC, p.Wc, L::WC_BYTES, &bar[0]);
+  }
+  bool ok = mbar_wait_bounded(&bar[0], 0, kWaitCycles);
+  uint32_t mma_phase = 0;
+  bool mma_pending = false;  // an MMA commit not yet waited for
+  const bool weights_late = __syncthreads_or(!ok);
+  bool aborted = weights_late;
+
+  const bool edge_rows = MODE != M_NODE_ENC && MODE != M_NODE_UPD;
+  int lo = 0, hi = 0;
+  {
+    const Batch& b = p.b;
+    hi = edge_rows ? clamp_edges(w.counters, w.e_cap) : b.n_hits;
+  }
+  const int n_tiles = (hi - lo + kRows - 1) / kRows;
+  constexpr int K1 = L::K1;
+  constexpr int KCH1 = K1 * L::ESZ / 16;  // 16-byte chunks per A row, layer 1
+  constexpr int KCHH = H * L::ESZ / 16;   // 16-byte chunks per A row, K = H
+
+  // wait for the MMAs committed so far; false on timeout (uniform across CTA)
+  auto wait_mma = [&]() -> bool {
+    mma_pending = true;
+    bool good = mbar_wait_bounded(&bar[1], mma_phase, kWaitCycles);
+    tc_fence_after();
+    if (__syncthreads_or(!good)) return false;
+    mma_phase ^= 1;
+    mma_pending = false;
+    return true;
+  };
+
+  for (int t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
+    const int r = lo + t * kRows + tid;
+    const bool valid = r < hi;
+    float sa[3] = {1.f, 1.f, 1.f};  // FP8 per-row scales of the layer-1 segments
+    uint4 keep_row[(H <= 64) ? H / 8 : 1];
+    (void)keep_row;
+
+    // ---- 1. gather ---------------------------------------------------------
+    if constexpr (MODE == M_NODE_ENC) {
+      // FP32 first layer (K = 3) in registers, then LayerNorm + ReLU into A
+      float hid[H];
+      if (valid) {
+        const float4 q = w.pos[r];
+        const float f0 = q.x / p.fs[3], f1 = q.y / p.fs[4], f2 = q.z / p.fs[5];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          float a = pne[3 * H + i];
+          a = fmaf(f0, pne[i], a);
+          a = fmaf(f1, pne[H + i], a);
+          a = fmaf(f2, pne[2 * H + i], a);
+          hid[i] = a;
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) s += hid[i];
+        const float mean = s / float(H);
+        float v = 0.f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          const float d = hid[i] - mean;
+          v = fmaf(d, d, v);
+        }
+        const float inv = 1.0f / sqrtf(v / float(H) + kLnEps);
+        float amax = 0.f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          hid[i] = fmaxf((hid[i] - mean) * inv, 0.f);
+          amax = fmaxf(amax, hid[i]);
+        }
+        sa[0] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
+        put_row_f32<FP8>(sA, tid, KCHH, 0, hid, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < H; ++i) hid[i] = 0.f;
+        put_row_f32<FP8>(sA, tid, KCHH, 0, hid, H, 1.f);
+      }
+    } else if constexpr (MODE == M_NODE_UPD) {
+      if (valid) {
+        sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.hstate16 + size_t(r) * H,
+                                     H <= 64 ? keep_row : nullptr);
+        const int E = clamp_edges(w.counters, w.e_cap);
+        float acc[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) acc[i] = 0.f;
+        const int a = min(w.row_ptr[r], E), z = min(w.row_ptr[r + 1], E);
+        for (int e = a; e < z; ++e) add_bf16_row<H>(acc, w.estate16 + size_t(e) * H);
+        float amax = 0.f;
+        if constexpr (FP8) {
+#pragma unroll
+          for (int i = 0; i < H; ++i) amax = fmaxf(amax, fabsf(acc[i]));
+        }
+        sa[1] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
+        put_row_f32<FP8>(sA, tid, KCH1, H, acc, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
+#pragma unroll
+        for (int i = 0; i < H; ++i) acc[i] = 0.f;
+        const int ia = w.in_ptr[r], iz = w.in_ptr[r + 1];
+        for (int k = ia; k < iz; ++k) add_bf16_row<H>(acc, w.estate16 + size_t(w.in_edge[k]) * H);
+        amax = 0.f;
+        if constexpr (FP8) {
+#pragma unroll
+          for (int i = 0; i < H; ++i) amax = fmaxf(amax, fabsf(acc[i]));
+        }
+        sa[2] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
+        put_row_f32<FP8>(sA, tid, KCH1, 2 * H, acc, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
+      } else {
+        float z[16] = {};
+        for (int k = 0; k < K1; k += 16) put_row_f32<FP8>(sA, tid, KCH1, k, z, 16, 1.f);
+      }
+    } else {
+      // edge rows: [e], [h_src, h_dst], [e, h_src, h_dst]
+      if (valid) {
+        int seg = 0;
+        if constexpr (MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS || MODE == M_CLS) {
+          sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.estate16 + size_t(r) * H,
+                                       (H <= 64 && MODE != M_CLS) ? keep_row : nullptr);
+          seg = 1;
+        }
+        if constexpr (MODE != M_CLS) {
+          sa[seg] = put_row_bf16<H, FP8>(sA, tid, KCH1, seg * H, w.hstate16 + size_t(w.src[r]) * H,
+                                         nullptr);
+          sa[seg + 1] = put_row_bf16<H, FP8>(sA, tid, KCH1, (seg + 1) * H,
+                                             w.hstate16 + size_t(w.col[r]) * H, nullptr);
+        }
+      } else {
+        float z[16] = {};
+        for (int k = 0; k < K1; k += 16) put_row_f32<FP8>(sA, tid, KCH1, k, z, 16, 1.f);
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+
+    float hid_scale = 1.f;  // FP8 per-row scale of the layer-2 input
+    if constexpr (MODE != M_NODE_ENC) {
+      // ---- 2. layer 1 ------------------------------------------------------
+      if (tid == 0) {
+        tc_fence_after();
+        issue_layer<H, FP8>(tmem_base, sA, sW1, K1, FP8 ? L::NSEG : 1);
+        mma_commit(&bar[1]);
+      }
+      if (!wait_mma()) {
+        aborted = true;
+        break;
+      }
+      // ---- 3. bias + LayerNorm + ReLU (-> A as the next operand, or the
+      //         classifier output for M_CLS) -------------------------------
+      // x[n] = s_w[n] * sum_seg s_a[seg] * acc_seg[n] + b[n]  (FP8)
+      //      = acc[n] + b[n]                                   (BF16)
+      auto xval = [&](int c, float (&x)[32]) {
+        float v[32];
+        tmem_ld32(tmem_lane + uint32_t(c * 32), v);
+        if constexpr (FP8) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= sa[0];
+#pragma unroll
+          for (int s = 1; s < L::NSEG; ++s) {
+            float u[32];
+            tmem_ld32(tmem_lane + uint32_t(s * H + c * 32), u);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = fmaf(u[j], sa[s], v[j]);
+          }
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = c * 32 + j;
+          x[j] = FP8 ? fmaf(v[j], ps1[n], pb1[n]) : v[j] + pb1[n];
+        }
+      };
+      float sum = 0.f, xmax = -INFINITY;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        xval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          sum += x[j];
+          xmax = fmaxf(xmax, x[j]);
+        }
+      }
+      const float mean = sum / float(H);
+      float var = 0.f;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        xval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float d = x[j] - mean;
+          var = fmaf(d, d, var);
+        }
+      }
+      const float inv = 1.0f / sqrtf(var / float(H) + kLnEps);
+      if constexpr (MODE == M_CLS) {
+        float logit = pc2[H];
+#pragma unroll
+        for (int c = 0; c < H / 32; ++c) {
+          float x[32];
+          xval(c, x);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) logit = fmaf(fmaxf((x[j] - mean) * inv, 0.f), pc2[c * 32 + j], logit);
+        }
+        if (valid) {
+          w.logit[r] = logit;
+          w.keep[r] = logit >= p.cut ? 1 : 0;
+        }
+        tc_fence_before();
+        continue;
+      }
+      const float hmax = fmaxf((xmax - mean) * inv, 0.f);
+      hid_scale = FP8 ? (hmax > 0.f ? hmax / 448.f : 1.f) : 1.f;
+      const float hinv = FP8 ? (hmax > 0.f ? 448.f / hmax : 1.f) : 1.f;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        xval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = fmaxf((x[j] - mean) * inv, 0.f);
+        put_row_f32<FP8>(sA, tid, KCHH, c * 32, x, 32, hinv);
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+    } else {
+      hid_scale = sa[0];
+    }
+
+    // ---- 4. layer 2 ----------------------------------------------------------
+    if (tid == 0) {
+      tc_fence_after();
+      issue_layer<H, FP8>(tmem_base, sA, sW2, H, 1);
+      mma_commit(&bar[1]);
+    }
+    if (!wait_mma()) {
+      aborted = true;
+      break;
+    }
+    // z[n] = s_w2[n] * s_h * acc[n] + b2[n] (FP8) or acc[n] + b2[n]
+    auto zval = [&](int c, float (&z)[32]) {
+      float v[32];
+      tmem_ld32(tmem_lane + uint32_t(c * 32), v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = c * 32 + j;
+        z[j] = FP8 ? fmaf(v[j] * hid_scale, ps2[n], pb2[n]) : v[j] + pb2[n];
+      }
+    };
+    // residual input row (BF16) for the update modes
+    auto resid = [&](int c, float (&z)[32]) {
+      if constexpr (MODE == M_NODE_UPD || MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS) {
+        const __nv_bfloat16* rowp = (MODE == M_NODE_UPD ? w.hstate16 : w.estate16) + size_t(r) * H;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 u = (H <= 64) ? keep_row[c * 4 + q]
+                                    : reinterpret_cast<const uint4*>(rowp)[c * 4 + q];
+          z[8 * q + 0] += bf16_lo(u.x);
+          z[8 * q + 1] += bf16_hi(u.x);
+          z[8 * q + 2] += bf16_lo(u.y);
+          z[8 * q + 3] += bf16_hi(u.y);
+          z[8 * q + 4] += bf16_lo(u.z);
+          z[8 * q + 5] += bf16_hi(u.z);
+          z[8 * q + 6] += bf16_lo(u.w);
+          z[8 * q + 7] += bf16_hi(u.w);
+        }
+      }
+    };
+
+    if constexpr (MODE != M_EDGE_UPD_CLS) {
+      // ---- 5. store the new state (BF16) -----------------------------------
+      __nv_bfloat16* dst = (MODE == M_NODE_ENC || MODE == M_NODE_UPD ? w.hstate16 : w.estate16) +
+                           size_t(r) * H;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float z[32];
+        zval(c, z);
+        if (valid) {
+          resid(c, z);
+          uint4* d4 = reinterpret_cast<uint4*>(dst) + c * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            d4[q] = make_uint4(pack_bf16(z[8 * q], z[8 * q + 1]), pack_bf16(z[8 * q + 2], z[8 * q + 3]),
+                               pack_bf16(z[8 * q + 4], z[8 * q + 5]), pack_bf16(z[8 * q + 6], z[8 * q + 7]));
+        }
+      }
+      tc_fence_before();
+    } else {
+      // ---- 5'. classifier on the new edge state, then the cut ---------------
+      float emax = 0.f;
+      if constexpr (FP8) {
+#pragma unroll
+        for (int c = 0; c < H / 32; ++c) {
+          float z[32];
+          zval(c, z);
+          resid(c, z);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) emax = fmaxf(emax, fabsf(z[j]));
+        }
+      }
+      const float es = FP8 ? (emax > 0.f ? emax / 448.f : 1.f) : 1.f;
+      const float einv = FP8 ? (emax > 0.f ? 448.f / emax : 1.f) : 1.f;
+      // the new state is rounded to BF16 as it would be stored, then fed on
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float z[32];
+        zval(c, z);
+        resid(c, z);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = __bfloat162float(__float2bfloat16_rn(z[j]));
+        put_row_f32<FP8>(sA, tid, KCHH, c * 32, z, 32, einv);
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        issue_layer<H, FP8>(tmem_base, sA, sWC, H, 1);
+        mma_commit(&bar[1]);
+      }
+      if (!wait_mma()) {
+        aborted = true;
+        break;
+      }
+      auto cval = [&](int c, float (&x)[32]) {
+        float v[32];
+        tmem_ld32(tmem_lane + uint32_t(c * 32), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = c * 32 + j;
+          x[j] = FP8 ? fmaf(v[j] * es, psc[n], pbc[n]) : v[j] + pbc[n];
+        }
+      };
+      float sum = 0.f;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        cval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum += x[j];
+      }
+      const float mean = sum / float(H);
+      float var = 0.f;
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        cval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float d = x[j] - mean;
+          var = fmaf(d, d, var);
+        }
+      }
+      const float inv = 1.0f / sqrtf(var / float(H) + kLnEps);
+      float logit = pc2[H];
+#pragma unroll
+      for (int c = 0; c < H / 32; ++c) {
+        float x[32];
+        cval(c, x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) logit = fmaf(fmaxf((x[j] - mean) * inv, 0.f), pc2[c * 32 + j], logit);
+      }
+      if (valid) {
+        w.logit[r] = logit;
+        w.keep[r] = logit >= p.cut ? 1 : 0;
+      }
+      tc_fence_before();
+    }
+  }
+
+  // ---- clean-up: on a timeout, give the outstanding MMAs one more bounded
+  //      wait, then free the tensor memory -----------------------------------
+  if (aborted) {
+    if (tid == 0) set_status(w.counters, ST_TIMEOUT);
+    if (weights_late) mbar_wait_bounded(&bar[0], 0, kWaitCycles);
+    if (mma_pending) mbar_wait_bounded(&bar[1], mma_phase, kWaitCycles);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, L::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// near-cut band: count band edges and list the events that hold one
+// ---------------------------------------------------------------------------
+__global__ void k_band_flag(Ws w, float lo, float hi) {
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+  const int E = clamp_edges(w.counters, w.e_cap);
+  for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
+    const int e = base + threadIdx.x;
+    bool in = false;
+    if (e < E) {
+      const float l = w.logit[e];
+      in = l > lo && l < hi;
+      if (in) w.ev_flag[w.node_event[w.src[e]]] = 1;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&w.counters[C_BAND], __popc(m));
+  }
+}
+
+__global__ void k_band_list(Ws w, int n_events) {
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c = 0; c < n_events; c += blockDim.x) {
+    const int ev = c + threadIdx.x;
+    const bool f = ev < n_events && w.ev_flag[ev] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) wsum[wp] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int k = 0; k < wp; ++k) off += wsum[k];
+    if (f) w.rerun_list[off + __popc(m & ((1u << lane) - 1u))] = ev;
+    if (ev < n_events) w.ev_flag[ev] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int k = 0; k < int(blockDim.x >> 5); ++k) base += wsum[k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w.counters[C_RERUN] = base;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+// CTAs per SM of one kernel: the occupancy query, capped so that the CTAs of an
+// SM fit in its 512 tensor-memory columns; computed once per instantiation.
+template <int H, bool FP8, int MODE>
+int tc_blocks_per_sm() {
+  using L = Layout<H, FP8, MODE>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc<H, FP8, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc<H, FP8, MODE>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int n = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tc<H, FP8, MODE>, kRows, L::TOTAL);
+    // the same bound from the kernel's resources: registers (allocated per warp
+    // in units of 256), shared memory (228 KB per SM, 1 KB reserved per CTA),
+    // 2048 threads per SM. CTAs never wait on one another, so a bound above
+    // what fits only queues CTAs.
+    cudaFuncAttributes fa{};
+    int est = 16;
+    if (cudaFuncGetAttributes(&fa, k_tc<H, FP8, MODE>) == cudaSuccess && fa.numRegs > 0) {
+      const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+      est = std::min(est, 65536 / (regs_warp * (kRows / 32)));
+    }
+    est = std::min(est, 233472 / (L::TOTAL + 1024));
+    if (e != cudaSuccess) cudaGetLastError();
+    if (getenv("GNNTRK_VERBOSE"))
+      fprintf(stderr, "gnntrk: k_tc<%d,%d,%d> occupancy query %d (%s), resource bound %d\n", H,
+              int(FP8), MODE, n, cudaGetErrorString(e), est);
+    n = std::max(n, est);
+    n = n < 1 ? 1 : n;
+    while (n > 1 && n * L::TMEM_COLS > 512) --n;
+    if (getenv("GNNTRK_VERBOSE"))
+      fprintf(stderr, "gnntrk: k_tc<%d,%d,%d> smem %d B, %d CTAs/SM\n", H, int(FP8), MODE,
+              L::TOTAL, n);
+    per_sm = n;
+  }
+  return per_sm;
+}
+
+template <int H, bool FP8, int MODE>
+void launch_mode(const TcArgs& a, cudaStream_t s, int rows_hint) {
+  using L = Layout<H, FP8, MODE>;
+  int grid = device_sms() * tc_blocks_per_sm<H, FP8, MODE>();
+  if (rows_hint >= 0) grid = rows_hint == 0 ? 1 : min(grid, div_up(rows_hint, kRows));
+  k_tc<H, FP8, MODE><<<grid, kRows, L::TOTAL, s>>>(a);
+}
+
+template <int H, bool FP8>
+void launch_h(int mode, const TcArgs& a, cudaStream_t s, int rows_hint) {
+  switch (mode) {
+    case M_NODE_ENC: launch_mode<H, FP8, M_NODE_ENC>(a, s, rows_hint); break;
+    case M_EDGE_ENC: launch_mode<H, FP8, M_EDGE_ENC>(a, s, rows_hint); break;
+    case M_NODE_UPD: launch_mode<H, FP8, M_NODE_UPD>(a, s, rows_hint); break;
+    case M_EDGE_UPD: launch_mode<H, FP8, M_EDGE_UPD>(a, s, rows_hint); break;
+    case M_EDGE_UPD_CLS: launch_mode<H, FP8, M_EDGE_UPD_CLS>(a, s, rows_hint); break;
+    case M_CLS: launch_mode<H, FP8, M_CLS>(a, s, rows_hint); break;
+  }
+}
+
+template <bool FP8>
+constexpr int smem_total(int H, int mode) {
+#define GNNTRK_LT(HH)                                                                 \
+  (mode == M_NODE_ENC ? Layout<HH, FP8, M_NODE_ENC>::TOTAL                            \
+   : mode == M_EDGE_ENC ? Layout<HH, FP8, M_EDGE_ENC>::TOTAL                          \
+   : mode == M_NODE_UPD ? Layout<HH, FP8, M_NODE_UPD>::TOTAL                          \
+   : mode == M_EDGE_UPD ? Layout<HH, FP8, M_EDGE_UPD>::TOTAL                          \
+   : mode == M_EDGE_UPD_CLS ? Layout<HH, FP8, M_EDGE_UPD_CLS>::TOTAL                  \
+                            : Layout<HH, FP8, M_CLS>::TOTAL)
+  return H == 32 ? GNNTRK_LT(32) : (H == 64 ? GNNTRK_LT(64) : GNNTRK_LT(128));
+#undef GNNTRK_LT
+}
+
+void launch_any(int H, bool fp8, int mode, const TcArgs& a, cudaStream_t s, int rows_hint) {
+  if (fp8) {
+    if (H == 32) launch_h<32, true>(mode, a, s, rows_hint);
+    else if (H == 64) launch_h<64, true>(mode, a, s, rows_hint);
+    else launch_h<128, true>(mode, a, s, rows_hint);
+  } else {
+    if (H == 32) launch_h<32, false>(mode, a, s, rows_hint);
+    else if (H == 64) launch_h<64, false>(mode, a, s, rows_hint);
+    else launch_h<128, false>(mode, a, s, rows_hint);
+  }
+}
+
+constexpr int kMaxSmem = 232448;  // 227 KB of dynamic shared memory per CTA
+
+// ---------------------------------------------------------------------------
+// host: weight packing
+// ---------------------------------------------------------------------------
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return uint16_t((u >> 16) | 0x40);  // quiet NaN
+  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+  return uint16_t(u >> 16);
+}
+
+}  // namespace
+
+// E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no infinities,
+// largest finite 448) of a float, rounding to nearest even and saturating to
+// +-448; NaN maps to 0x7F.
+uint8_t e4m3_from_float(float f) {
+  if (std::isnan(f)) return 0x7f;
+  const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+  double a = std::fabs(double(f));
+  if (a >= 448.0) return sign | 0x7e;
+  // candidates: subnormals k * 2^-9 (k = 0..7), normals (1 + m/8) * 2^(e-7)
+  int e = 0;
+  if (a < std::ldexp(1.0, -6)) {
+    double k = a / std::ldexp(1.0, -9);
+    double fl = std::floor(k), r = k - fl;
+    int q = int(fl);
+    if (r > 0.5 || (r == 0.5 && (q & 1))) ++q;
+    return sign | uint8_t(q);  // q == 8 is the smallest normal (0x08)
+  }
+  std::frexp(a, &e);  // a = f * 2^e, f in [0.5, 1)
+  int E = e - 1;      // a in [2^E, 2^(E+1))
+  double m = a / std::ldexp(1.0, E) - 1.0;  // [0, 1)
+  double k = m * 8.0;
+  double fl = std::floor(k), r = k - fl;
+  int q = int(fl);
+  if (r > 0.5 || (r == 0.5 && (q & 1))) ++q;
+  if (q == 8) {
+    q = 0;
+    ++E;
+  }
+  int be = E + 7;
+  uint8_t code = uint8_t((be << 3) | q);
+  if (code > 0x7e) code = 0x7e;
+  return sign | code;
+}
+
+float e4m3_to_float(uint8_t c) {
+  const float s = (c & 0x80) ? -1.f : 1.f;
+  const int be = (c >> 3) & 0xf, m = c & 7;
+  if (be == 0xf && m == 7) return NAN;
+  if (be == 0) return s * std::ldexp(float(m), -9);
+  return s * std::ldexp(1.f + float(m) / 8.f, be - 7);
+}
+
+namespace {
+
+// Operand image of W[out][in] for the tensor cores: K-major rows of `out`,
+// core matrices of 8 rows x 16 bytes, chunks of a row contiguous per 8-row
+// group. FP8: per-output-channel scale amax/448 applied before encoding.
+void pack_layer(const HostLayer& l, bool fp8, std::vector<uint8_t>& img, std::vector<float>& scale) {
+  const int N = l.out, K = l.in;
+  const int esz = fp8 ? 1 : 2, epc = 16 / esz;
+  const int kch = K / epc;
+  img.assign(size_t(N) * K * esz, 0);
+  scale.assign(N, 1.f);
+  for (int n = 0; n < N; ++n) {
+    float amax = 0.f;
+    for (int k = 0; k < K; ++k) amax = std::max(amax, std::fabs(l.W[size_t(n) * K + k]));
+    if (fp8) scale[n] = amax > 0.f ? amax / 448.f : 1.f;
+    for (int k = 0; k < K; ++k) {
+      const size_t off = size_t((n / 8) * kch + k / epc) * 128 + (n % 8) * 16 + (k % epc) * esz;
+      const float v = l.W[size_t(n) * K + k];
+      if (fp8) {
+        img[off] = e4m3_from_float(v / scale[n]);
+      } else {
+        const uint16_t b = bf16_bits(v);
+        img[off] = uint8_t(b & 0xff);
+        img[off + 1] = uint8_t(b >> 8);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, int K,
+              int precision, void** dmem, std::string& err) {
+  const bool fp8 = precision == GNNTRK_FP8_E4M3;
+  // which layers: node enc l2, edge enc l1/l2, per step node l1/l2 edge l1/l2, cls l1
+  struct Item {
+    int layer;
+    LayerTC* dst;
+  };
+  std::vector<Item> items;
+  int c = n_embed;
+  items.push_back({c + 1, &m.node_enc.l2});
+  items.push_back({c + 2, &m.edge_enc.l1});
+  items.push_back({c + 3, &m.edge_enc.l2});
+  c += 4;
+  for (int k = 0; k < K; ++k) {
+    items.push_back({c, &m.node[k].l1});
+    items.push_back({c + 1, &m.node[k].l2});
+    items.push_back({c + 2, &m.edge[k].l1});
+    items.push_back({c + 3, &m.edge[k].l2});
+    c += 4;
+  }
+  items.push_back({c, &m.cls.l1});
+  if (c + 2 != n_layers) {
+    err = "tensor-core packing: unexpected layer count";
+    return GNNTRK_ERR_WEIGHTS;
+  }
+  // shared-memory budget of the largest kernel
+  for (int mode : {M_EDGE_UPD, M_NODE_UPD})
+    if ((fp8 ? smem_total<true>(h, mode) : smem_total<false>(h, mode)) > kMaxSmem) {
+      err = "tensor-core kernels do not fit shared memory at this hidden size";
+      return GNNTRK_ERR_UNSUPPORTED;
+    }
+  std::vector<uint8_t> blob;
+  std::vector<size_t> off_img(items.size()), off_b(items.size()), off_s(items.size());
+  auto align = [&](size_t a) { blob.resize((blob.size() + a - 1) / a * a, 0); };
+  for (size_t i = 0; i < items.size(); ++i) {
+    std::vector<uint8_t> img;
+    std::vector<float> sc;
+    pack_layer(L[items[i].layer], fp8, img, sc);
+    align(1024);
+    off_img[i] = blob.size();
+    blob.insert(blob.end(), img.begin(), img.end());
+    align(16);
+    off_b[i] = blob.size();
+    const auto& bb = L[items[i].layer].b;
+    blob.resize(blob.size() + 4 * bb.size());
+    std::memcpy(blob.data() + off_b[i], bb.data(), 4 * bb.size());
+    align(16);
+    off_s[i] = blob.size();
+    blob.resize(blob.size() + 4 * sc.size());
+    std::memcpy(blob.data() + off_s[i], sc.data(), 4 * sc.size());
+  }
+  void* d = nullptr;
+  if (cudaMalloc(&d, blob.size()) != cudaSuccess) {
+    cudaGetLastError();
+    err = "cudaMalloc of the tensor-core weights failed";
+    return GNNTRK_ERR_OOM;
+  }
+  if (cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    err = "tensor-core weight upload failed";
+    return GNNTRK_ERR_CUDA;
+  }
+  *dmem = d;
+  const uint8_t* base = static_cast<const uint8_t*>(d);
+  for (size_t i = 0; i < items.size(); ++i) {
+    const HostLayer& l = L[items[i].layer];
+    *items[i].dst = LayerTC{base + off_img[i], reinterpret_cast<const float*>(base + off_b[i]),
+                            reinterpret_cast<const float*>(base + off_s[i]), l.in, l.out};
+  }
+  m.precision = precision;
+  m.h = h;
+  m.K = K;
+  m.n_embed = n_embed;
+  return GNNTRK_OK;
+}
+
+namespace {
+TcArgs base_args(const Batch& b, const Ws& w, const GraphParams& g) {
+  TcArgs a{};
+  a.b = b;
+  a.w = w;
+  for (int i = 0; i < 6; ++i) a.fs[i] = g.fs[i];
+  a.cut = g.cut_logit;
+  return a;
+}
+}  // namespace
+
+void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32* embed_f32,
+                  int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
+                  cudaStream_t s) {
+  // embedding in FP32: its output feeds the threshold d^2 < r^2
+  const Sel all{nullptr, nullptr, 0};
+  launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, D, h, g, true, false, all, s);
+  TcArgs a = base_args(b, w, g);
+  a.ne1 = ne1_f32;
+  a.W2 = static_cast<const uint8_t*>(m.node_enc.l2.B);
+  a.b2 = m.node_enc.l2.b;
+  a.s2 = m.node_enc.l2.scale;
+  launch_any(h, m.precision == GNNTRK_FP8_E4M3, M_NODE_ENC, a, s, b.n_hits);
+}
+
+void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
+            const LayerF32& cls2_f32, cudaStream_t s, int stage) {
+  const bool fp8 = m.precision == GNNTRK_FP8_E4M3;
+  TcArgs a = base_args(b, w, g);
+  a.c2 = cls2_f32;
+  a.Wc = static_cast<const uint8_t*>(m.cls.l1.B);
+  a.bc1 = m.cls.l1.b;
+  a.sc = m.cls.l1.scale;
+  const bool fuse = (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
+  auto set = [&](const Mlp2TC& mm) {
+    a.W1 = static_cast<const uint8_t*>(mm.l1.B);
+    a.b1 = mm.l1.b;
+    a.s1 = mm.l1.scale;
+    a.W2 = static_cast<const uint8_t*>(mm.l2.B);
+    a.b2 = mm.l2.b;
+    a.s2 = mm.l2.scale;
+  };
+  // stage < 0: everything; otherwise 0 = edge encoder, 1 + 2k = node step k,
+  // 2 + 2k = edge step k (with the classifier at the last step)
+  if (stage < 0 || stage == 0) {
+    set(m.edge_enc);
+    launch_any(h, fp8, M_EDGE_ENC, a, s, -1);
+  }
+  for (int k = 0; k < K; ++k) {
+    if (stage < 0 || stage == 1 + 2 * k) {
+      set(m.node[k]);
+      launch_any(h, fp8, M_NODE_UPD, a, s, b.n_hits);
+    }
+    if (stage < 0 || stage == 2 + 2 * k) {
+      set(m.edge[k]);
+      const bool last = k + 1 == K;
+      launch_any(h, fp8, last && fuse ? M_EDGE_UPD_CLS : M_EDGE_UPD, a, s, -1);
+      if (last && !fuse) launch_any(h, fp8, M_CLS, a, s, -1);
+    }
+  }
+  if (K == 0 && (stage < 0 || stage == 1)) launch_any(h, fp8, M_CLS, a, s, -1);
+}
+
+bool tc_cls_fused(int h, int precision) {
+  const bool fp8 = precision == GNNTRK_FP8_E4M3;
+  return (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
+}
+
+void tc_mark_band(const Batch& b, const Ws& w, float band_lo, float band_hi, cudaStream_t s) {
+  cudaMemsetAsync(w.ev_flag, 0, sizeof(int32_t) * b.n_events, s);
+  k_band_flag<<<device_sms() * 8, 256, 0, s>>>(w, band_lo, band_hi);
+  k_band_list<<<1, 1024, 0, s>>>(w, b.n_events);
+}
 
 }  // namespace gnntrk

@@ -19,15 +19,26 @@ struct TcModel {
 int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, int K,
               int precision, void** dmem, std::string& err);
 
-// Embedding (FP32 first layer, tensor-core hidden layers) and node encoder;
-// writes w.emb (FP32) and w.hstate16.
+// FP32 embedding (its output feeds the radius test) and the node encoder
+// (FP32 K = 3 first layer, tensor-core second layer); writes w.emb and
+// w.hstate16.
 void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32* embed_f32,
-                  int n_embed, int D, int h, const GraphParams& g, cudaStream_t s);
+                  int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
+                  cudaStream_t s);
 
 // Edge encoder, K message-passing steps and the classifier with the cut;
-// writes w.logit and w.keep.
+// writes w.logit and w.keep. stage < 0 runs everything; otherwise only
+// stage 0 (edge encoder), 1 + 2k (node step k) or 2 + 2k (edge step k, with
+// the classifier at the last step; stage 1 is the classifier when K = 0).
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
-            cudaStream_t s);
+            const LayerF32& cls2_f32, cudaStream_t s, int stage);
+
+// Whether the classifier runs inside the last edge step (shared memory fits).
+bool tc_cls_fused(int h, int precision);
+
+// Host reference codec of E4M3 (used to pack weights).
+uint8_t e4m3_from_float(float f);
+float e4m3_to_float(uint8_t c);
 
 // Count the edges whose logit lies in (band_lo, band_hi) and list the events
 // holding one (w.rerun_list, count in counters[C_RERUN]).
