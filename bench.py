@@ -127,7 +127,9 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     design notes; amount = figure x units of one launch.
     """
     sb = 4 if precision == "fp32" else 2   # state bytes per element
-    if stage in ("edge_update", "gnn_tc"):
+    if stage.startswith("rescore_"):  # the FP32 re-run (same kernels as the FP32 path)
+        precision, stage = "fp32", stage[len("rescore_"):]
+    if stage == "edge_update":
         if precision == "fp32":
             return "alu", E * 2.0 * (3 * h * h + h * h), "flop"
         # read e, h_src, h_dst rows; write e

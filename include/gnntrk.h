@@ -216,8 +216,9 @@ gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out);
  * ran. Any output may be NULL. Returns the number of stages (which may exceed
  * max_stages; only max_stages are written), or -1 on error.
  * Stage names: sort, node_prep, radius_count, scan_out, radius_fill, scan_in,
- * in_index, edge_encoder, node_update, edge_update, band_mark, rescore,
- * components.
+ * in_index, edge_encoder, node_update, edge_update, band_mark,
+ * rescore_node_prep, rescore_edge_encoder, rescore_node_update,
+ * rescore_edge_update, components.
  */
 gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable);
 int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, double* total_ms,

@@ -465,19 +465,25 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
       const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
       stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
       const Sel sel{w.rerun_list, w.counters + C_RERUN, n_events};
-      stage(h, "rescore", s, 3 + 2 * h->K, [&] {
+      stage(h, "rescore_node_prep", s, 1, [&] {
         launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
                              sel, s);
-        launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s);
-        for (int k = 0; k < h->K; ++k) {
-          launch_node_update_f32(b, w, h->node[k], h->h, sel, s);
+      });
+      stage(h, "rescore_edge_encoder", s, 1,
+            [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s); });
+      for (int k = 0; k < h->K; ++k) {
+        stage(h, "rescore_node_update", s, 1,
+              [&] { launch_node_update_f32(b, w, h->node[k], h->h, sel, s); });
+        stage(h, "rescore_edge_update", s, 1, [&] {
           launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
                                  g.cut_logit, true, band_lo, band_hi, sel, s);
-        }
-        if (h->K == 0)
+        });
+      }
+      if (h->K == 0)
+        stage(h, "rescore_edge_update", s, 1, [&] {
           launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
                                  band_hi, sel, s);
-      });
+        });
     }
   }
   stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });

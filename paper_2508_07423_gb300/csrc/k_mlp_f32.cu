@@ -1,22 +1,26 @@
 // FP32 SIMT kernels of the embedding MLP and the interaction network.
 //
-// One thread owns one row (a hit or an edge). Its input row, hidden row and
-// output live in thread-private rows of shared memory (odd strides, so the 32
-// rows a warp touches at one column fall in 32 different banks); the weights
-// are read through the read-only cache as float4 (every thread of a warp reads
-// the same address, one transaction). Each layer accumulates 32 outputs at a
-// time in registers, adding inputs in increasing index order.
+// Work is cut into tiles of TM rows (hits or edges). A block of 256 threads
+// stages the tile's input rows TRANSPOSED in shared memory (As[k][row], so a
+// warp reading one k for 32 row groups touches consecutive words) and computes
+// each layer as a register-tiled product: thread (lane, warp) owns RM rows x CW
+// columns of the output, reads RM inputs per k with one vector shared-memory
+// load and CW weights with CW/4 warp-uniform float4 loads through the
+// read-only cache, and keeps RM x CW FP32 accumulators in registers (inputs are
+// added in increasing k order). A hidden layer is written back transposed; one
+// thread per row then applies LayerNorm + ReLU over it in place.
 //
-//  k_node_prep_f32   embedding MLP (Sec. "Hit Embedding and Rough Graph
-//                    Construction") on (r/s0, phi/s1, z/s2) and the node encoder
-//                    on (x/s3, y/s4, z/s5) (Sec. "Graph Neural Network and
-//                    Classifiers").
-//  k_edge_enc_f32    edge encoder on [h_src, h_dst].
-//  k_node_upd_f32    message m_l = [sum of outgoing e, sum of incoming e]
-//                    (Eq. of m^k_l) and h_l <- h_l + N_k([h_l, m_l]).
-//  k_edge_upd_f32    e_ij <- e_ij + E_k([e_ij, h_i, h_j]) with the updated h;
-//                    at the last step also the edge classifier and the cut.
-// Sub-networks are Linear -> LayerNorm -> ReLU -> Linear.
+//  k_embed_f32     embedding MLP (Sec. "Hit Embedding and Rough Graph
+//                  Construction") on (r/s0, phi/s1, z/s2), ReLU between layers
+//  k_gnn_f32<MODE> node encoder on (x/s3, y/s4, z/s5); edge encoder on
+//                  [h_src, h_dst]; node step: m = [sum_out e, sum_in e]
+//                  (Eq. of m^k_l), h <- h + N_k([h, m]); edge step:
+//                  e <- e + E_k([e, h_src, h_dst]) with the updated h, and at
+//                  the last step the classifier and the cut (Sec. "Graph Neural
+//                  Network and Classifiers"). Sub-networks are
+//                  Linear -> LayerNorm -> ReLU -> Linear.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gnntrk {
@@ -25,222 +29,345 @@ int device_sms();
 
 namespace {
 
-constexpr int kPrepThreads = 64;
+constexpr int kThreads = 256;
+constexpr int kRowGroups = 32;                     // lanes of a warp
+constexpr int kColGroups = kThreads / kRowGroups;  // warps of a block
+
+enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
+                   G_EDGE_UPD_CLS = 4, G_CLS = 5 };
 
 __device__ __forceinline__ bool input_bad(const Ws& w) {
   return (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) != 0;
 }
 
-// out[o] = b[o] + sum_i in[i] * W[o][i] for o < ldo (padding columns give 0)
-__device__ __forceinline__ void row_linear(const float* in, const LayerF32& L, float* out,
-                                           bool relu) {
-  for (int o0 = 0; o0 < L.ldo; o0 += 32) {
-    const int nv = min(8, (L.ldo - o0) >> 2);
-    float acc[32];
+// acc[i][j] = b[c0 + j] + sum_k A[k][r0 + i] * W[k][c0 + j]
+// A: shared [K][TM]; W: global [K][ldo] (transposed weights)
+template <int RM, int CW, int TM>
+__device__ __forceinline__ void tile_layer(const float* As, int K, const LayerF32& L, int r0,
+                                           int c0, float (&acc)[RM][CW]) {
+  static_assert(CW % 4 == 0 && (RM == 2 || RM == 4), "tile shape");
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < nv) bb = __ldg(reinterpret_cast<const float4*>(L.b + o0) + j);
-      acc[4 * j] = bb.x;
-      acc[4 * j + 1] = bb.y;
-      acc[4 * j + 2] = bb.z;
-      acc[4 * j + 3] = bb.w;
+  for (int j = 0; j < CW; j += 4) {
+    const float4 bb = __ldg(reinterpret_cast<const float4*>(L.b + c0 + j));
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+      acc[i][j] = bb.x;
+      acc[i][j + 1] = bb.y;
+      acc[i][j + 2] = bb.z;
+      acc[i][j + 3] = bb.w;
     }
-    const float* wrow = L.WT + o0;
-    for (int i = 0; i < L.in; ++i) {
-      const float a = in[i];
-      const float4* wv = reinterpret_cast<const float4*>(wrow + size_t(i) * L.ldo);
+  }
+  const float* wp = L.WT + c0;
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    float a[RM];
+    if constexpr (RM == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(As + k * TM + r0);
+      a[0] = v.x;
+      a[1] = v.y;
+      a[2] = v.z;
+      a[3] = v.w;
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(As + k * TM + r0);
+      a[0] = v.x;
+      a[1] = v.y;
+    }
+    const float4* w4 = reinterpret_cast<const float4*>(wp + size_t(k) * L.ldo);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (j < nv) {
-          const float4 q = __ldg(wv + j);
-          acc[4 * j] = fmaf(a, q.x, acc[4 * j]);
-          acc[4 * j + 1] = fmaf(a, q.y, acc[4 * j + 1]);
-          acc[4 * j + 2] = fmaf(a, q.z, acc[4 * j + 2]);
-          acc[4 * j + 3] = fmaf(a, q.w, acc[4 * j + 3]);
-        }
+    for (int j = 0; j < CW; j += 4) {
+      const float4 q = __ldg(w4 + j / 4);
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        acc[i][j] = fmaf(a[i], q.x, acc[i][j]);
+        acc[i][j + 1] = fmaf(a[i], q.y, acc[i][j + 1]);
+        acc[i][j + 2] = fmaf(a[i], q.z, acc[i][j + 2]);
+        acc[i][j + 3] = fmaf(a[i], q.w, acc[i][j + 3]);
       }
     }
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if ((j >> 2) < nv) out[o0 + j] = relu ? fmaxf(acc[j], 0.f) : acc[j];
   }
 }
 
-// in place: v <- ReLU((v - mean) / sqrt(var + eps)), biased variance
-__device__ __forceinline__ void row_ln_relu(float* v, int n) {
+// store acc transposed into S[c][row] (one vector store per column)
+template <int RM, int CW, int TM>
+__device__ __forceinline__ void tile_store_t(float* S, int r0, int c0, const float (&acc)[RM][CW],
+                                             bool relu) {
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    float v[RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) v[i] = relu ? fmaxf(acc[i][j], 0.f) : acc[i][j];
+    if constexpr (RM == 4)
+      *reinterpret_cast<float4*>(S + (c0 + j) * TM + r0) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+      *reinterpret_cast<float2*>(S + (c0 + j) * TM + r0) = make_float2(v[0], v[1]);
+  }
+}
+
+// in place over column r of S[n][TM]: ReLU((v - mean) / sqrt(var + eps))
+template <int TM>
+__device__ __forceinline__ void col_ln_relu(float* S, int n, int r) {
   float s = 0.f;
-  for (int i = 0; i < n; ++i) s += v[i];
+  for (int i = 0; i < n; ++i) s += S[i * TM + r];
   const float mean = s / float(n);
   float q = 0.f;
   for (int i = 0; i < n; ++i) {
-    const float t = v[i] - mean;
+    const float t = S[i * TM + r] - mean;
     q = fmaf(t, t, q);
   }
   const float inv = 1.0f / sqrtf(q / float(n) + kLnEps);
-  for (int i = 0; i < n; ++i) v[i] = fmaxf((v[i] - mean) * inv, 0.f);
+  for (int i = 0; i < n; ++i) S[i * TM + r] = fmaxf((S[i * TM + r] - mean) * inv, 0.f);
 }
 
-// Linear -> LayerNorm -> ReLU -> Linear
-__device__ __forceinline__ void row_mlp2(const float* in, const Mlp2F32& m, float* hid,
-                                         float* out) {
-  row_linear(in, m.l1, hid, false);
-  row_ln_relu(hid, m.l1.out);
-  row_linear(hid, m.l2, out, false);
-}
-
-__device__ __forceinline__ void load_row(float* dst, const float* src, int h) {
+// copy an h-float global row into column `row` of S[k0 .. k0+h)[TM]
+template <int TM>
+__device__ __forceinline__ void put_col(float* S, int k0, int row, const float* src, int h) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int c = 0; c < (h >> 2); ++c) {
+  for (int c = 0; c < h / 4; ++c) {
     const float4 v = s4[c];
-    dst[4 * c] = v.x;
-    dst[4 * c + 1] = v.y;
-    dst[4 * c + 2] = v.z;
-    dst[4 * c + 3] = v.w;
+    S[(k0 + 4 * c) * TM + row] = v.x;
+    S[(k0 + 4 * c + 1) * TM + row] = v.y;
+    S[(k0 + 4 * c + 2) * TM + row] = v.z;
+    S[(k0 + 4 * c + 3) * TM + row] = v.w;
   }
 }
 
-__device__ __forceinline__ void add_row(float* dst, const float* src, int h) {
+template <int TM>
+__device__ __forceinline__ void add_col(float* S, int k0, int row, const float* src, int h) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int c = 0; c < (h >> 2); ++c) {
+  for (int c = 0; c < h / 4; ++c) {
     const float4 v = s4[c];
-    dst[4 * c] += v.x;
-    dst[4 * c + 1] += v.y;
-    dst[4 * c + 2] += v.z;
-    dst[4 * c + 3] += v.w;
+    S[(k0 + 4 * c) * TM + row] += v.x;
+    S[(k0 + 4 * c + 1) * TM + row] += v.y;
+    S[(k0 + 4 * c + 2) * TM + row] += v.z;
+    S[(k0 + 4 * c + 3) * TM + row] += v.w;
   }
 }
 
 // ---------------------------------------------------------------------------
-// embedding and node encoder
+// interaction network, one kernel per mode
+// ---------------------------------------------------------------------------
+struct GnnArgs {
+  Batch b;
+  Ws w;
+  Mlp2F32 m;    // the sub-network of this kernel
+  Mlp2F32 cls;  // classifier (G_EDGE_UPD_CLS, G_CLS)
+  float fs[6];
+  float cut;
+  int rescore_only;
+  float band_lo, band_hi;
+  Sel sel;
+};
+
+__host__ __device__ constexpr int g_nseg(int mode) {
+  return mode == G_NODE_ENC ? 0 : (mode == G_EDGE_ENC ? 2 : (mode == G_CLS ? 1 : 3));
+}
+
+template <int H, int TM, int MODE>
+__global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
+  constexpr int RM = TM / kRowGroups;
+  constexpr int CW = H / kColGroups;
+  constexpr int NSEG = g_nseg(MODE);
+  constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
+  constexpr int KA = K1 > 4 ? K1 : 4;
+  extern __shared__ __align__(16) float sm[];
+  float* As = sm;            // [KA][TM] input rows, transposed
+  float* Hs = sm + KA * TM;  // [H][TM] hidden rows, transposed
+  const Ws& w = p.w;
+  if (input_bad(w)) return;
+  int lo, hi;
+  if (!sel_rows(p.b, w, p.sel, MODE != G_NODE_ENC && MODE != G_NODE_UPD, lo, hi)) return;
+  const int tid = threadIdx.x;
+  const int r0 = (tid % kRowGroups) * RM;
+  const int c0 = (tid / kRowGroups) * CW;
+  const int E = clamp_edges(w.counters, w.e_cap);
+
+  for (int base = lo + blockIdx.x * TM; base < hi; base += gridDim.x * TM) {
+    // ---- gather: task t = (segment t / TM, row t % TM) --------------------
+    if constexpr (MODE == G_NODE_ENC) {
+      for (int r = tid; r < TM; r += kThreads) {
+        const int v = base + r;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        if (v < hi) {
+          const float4 q = w.pos[v];
+          f0 = q.x / p.fs[3];
+          f1 = q.y / p.fs[4];
+          f2 = q.z / p.fs[5];
+        }
+        As[r] = f0;
+        As[TM + r] = f1;
+        As[2 * TM + r] = f2;
+      }
+    } else {
+      for (int t = tid; t < NSEG * TM; t += kThreads) {
+        const int seg = t / TM, r = t % TM, row = base + r;
+        const int k0 = seg * H;
+        if (row >= hi) {
+          for (int k = 0; k < H; ++k) As[(k0 + k) * TM + r] = 0.f;
+          continue;
+        }
+        if constexpr (MODE == G_NODE_UPD) {
+          if (seg == 0) {
+            put_col<TM>(As, k0, r, w.hstate + size_t(row) * H, H);
+          } else {
+            for (int k = 0; k < H; ++k) As[(k0 + k) * TM + r] = 0.f;
+            if (seg == 1) {
+              const int a = min(w.row_ptr[row], E), z = min(w.row_ptr[row + 1], E);
+              for (int e = a; e < z; ++e) add_col<TM>(As, k0, r, w.estate + size_t(e) * H, H);
+            } else {
+              const int a = w.in_ptr[row], z = w.in_ptr[row + 1];
+              for (int q = a; q < z; ++q)
+                add_col<TM>(As, k0, r, w.estate + size_t(w.in_edge[q]) * H, H);
+            }
+          }
+        } else if constexpr (MODE == G_EDGE_ENC) {
+          put_col<TM>(As, k0, r, w.hstate + size_t(seg == 0 ? w.src[row] : w.col[row]) * H, H);
+        } else if constexpr (MODE == G_CLS) {
+          put_col<TM>(As, k0, r, w.estate + size_t(row) * H, H);
+        } else {  // edge step: [e, h_src, h_dst]
+          const float* src = seg == 0 ? w.estate + size_t(row) * H
+                                      : w.hstate + size_t(seg == 1 ? w.src[row] : w.col[row]) * H;
+          put_col<TM>(As, k0, r, src, H);
+        }
+      }
+    }
+    __syncthreads();
+
+    float acc[RM][CW];
+    if constexpr (MODE != G_CLS) {
+      // ---- layer 1 -> LayerNorm -> ReLU -------------------------------------
+      tile_layer<RM, CW, TM>(As, K1, p.m.l1, r0, c0, acc);
+      tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
+      __syncthreads();
+      for (int r = tid; r < TM; r += kThreads) col_ln_relu<TM>(Hs, H, r);
+      __syncthreads();
+      // ---- layer 2 + residual ---------------------------------------------
+      tile_layer<RM, CW, TM>(Hs, H, p.m.l2, r0, c0, acc);
+      if constexpr (MODE == G_NODE_UPD || MODE == G_EDGE_UPD || MODE == G_EDGE_UPD_CLS) {
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < CW; ++j) acc[i][j] += As[(c0 + j) * TM + r0 + i];
+      }
+    }
+    if constexpr (MODE == G_EDGE_UPD_CLS || MODE == G_CLS) {
+      // ---- classifier: Linear -> LayerNorm -> ReLU -> dot, then the cut ------
+      if constexpr (MODE == G_EDGE_UPD_CLS) {
+        // the new edge state becomes segment 0 of As (each element is read and
+        // written by the same thread)
+        tile_store_t<RM, CW, TM>(As, r0, c0, acc, false);
+        __syncthreads();
+      }
+      tile_layer<RM, CW, TM>(As, H, p.cls.l1, r0, c0, acc);
+      __syncthreads();  // everyone is done reading Hs (layer 2 above)
+      tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
+      __syncthreads();
+      for (int r = tid; r < TM; r += kThreads) {
+        col_ln_relu<TM>(Hs, H, r);
+        const int row = base + r;
+        if (row < hi) {
+          float lg = p.cls.l2.b[0];
+          for (int k = 0; k < H; ++k) lg = fmaf(Hs[k * TM + r], p.cls.l2.WT[k * p.cls.l2.ldo], lg);
+          bool write = true;
+          if (p.rescore_only) {
+            const float old = w.logit[row];
+            write = old > p.band_lo && old < p.band_hi;
+          }
+          if (write) {
+            w.logit[row] = lg;
+            w.keep[row] = lg >= p.cut ? 1 : 0;
+          }
+        }
+      }
+    } else {
+      // ---- store the new state ---------------------------------------------
+      float* dst = (MODE == G_NODE_ENC || MODE == G_NODE_UPD) ? w.hstate : w.estate;
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        const int row = base + r0 + i;
+        if (row < hi) {
+          float4* d4 = reinterpret_cast<float4*>(dst + size_t(row) * H + c0);
+#pragma unroll
+          for (int j = 0; j < CW; j += 4)
+            d4[j / 4] = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// embedding MLP
 // ---------------------------------------------------------------------------
 struct EmbedLayers {
   LayerF32 l[kMaxEmbedLayers];
 };
 
-__global__ void __launch_bounds__(kPrepThreads) k_node_prep_f32(Batch b, Ws w, EmbedLayers em,
-                                                                int n_embed, Mlp2F32 ne, int D,
-                                                                int h, GraphParams g,
-                                                                int stride, int do_embed,
-                                                                int do_node_enc, Sel sel) {
-  extern __shared__ float smem[];
+constexpr int kEmbedTM = 128;
+
+template <int CW>
+__device__ __forceinline__ void embed_layer_tiled(const float* X, float* Y, const LayerF32& L,
+                                                  int tid, bool relu) {
+  float acc[4][CW];
+  const int r0 = (tid % kRowGroups) * 4, c0 = (tid / kRowGroups) * CW;
+  tile_layer<4, CW, kEmbedTM>(X, L.in, L, r0, c0, acc);
+  tile_store_t<4, CW, kEmbedTM>(Y, r0, c0, acc, relu);
+}
+
+__global__ void __launch_bounds__(kThreads) k_embed_f32(Batch b, Ws w, EmbedLayers em,
+                                                        int n_embed, int D, GraphParams g,
+                                                        int maxw) {
+  extern __shared__ __align__(16) float sm[];
   if (input_bad(w)) return;
-  int lo, hi;
-  if (!sel_rows(b, w, sel, false, lo, hi)) return;
-  float* A = smem + threadIdx.x * stride;
-  float* B = smem + (blockDim.x + threadIdx.x) * stride;
-  for (int v = lo + blockIdx.x * blockDim.x + threadIdx.x; v < hi;
-       v += gridDim.x * blockDim.x) {
-    const float4 p = w.pos[v];
-    if (do_embed) {
-      A[0] = sqrtf(p.x * p.x + p.y * p.y) / g.fs[0];
-      A[1] = atan2f(p.y, p.x) / g.fs[1];
-      A[2] = p.z / g.fs[2];
-      float* in = A;
-      float* out = B;
-      for (int l = 0; l < n_embed; ++l) {
-        row_linear(in, em.l[l], out, l + 1 < n_embed);
-        float* t = in;
-        in = out;
-        out = t;
+  const int tid = threadIdx.x;
+  for (int base = blockIdx.x * kEmbedTM; base < b.n_hits; base += gridDim.x * kEmbedTM) {
+    float* X = sm;
+    float* Y = sm + maxw * kEmbedTM;
+    for (int r = tid; r < kEmbedTM; r += kThreads) {
+      const int v = base + r;
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+      if (v < b.n_hits) {
+        const float4 p = w.pos[v];
+        f0 = sqrtf(p.x * p.x + p.y * p.y) / g.fs[0];
+        f1 = atan2f(p.y, p.x) / g.fs[1];
+        f2 = p.z / g.fs[2];
       }
-      for (int d = 0; d < D; ++d) w.emb[size_t(v) * D + d] = in[d];
+      X[r] = f0;
+      X[kEmbedTM + r] = f1;
+      X[2 * kEmbedTM + r] = f2;
     }
-    if (do_node_enc) {
-      A[0] = p.x / g.fs[3];
-      A[1] = p.y / g.fs[4];
-      A[2] = p.z / g.fs[5];
-      row_mlp2(A, ne, B, A);
-      float4* dst = reinterpret_cast<float4*>(w.hstate + size_t(v) * h);
-      for (int c = 0; c < (h >> 2); ++c)
-        dst[c] = make_float4(A[4 * c], A[4 * c + 1], A[4 * c + 2], A[4 * c + 3]);
+    __syncthreads();
+    for (int l = 0; l < n_embed; ++l) {
+      const LayerF32& L = em.l[l];
+      const bool relu = l + 1 < n_embed;
+      const int cw = L.ldo / kColGroups;
+      if (L.ldo % 32 == 0 && (cw == 4 || cw == 8 || cw == 16)) {
+        // register-tiled: 32 row groups x 8 column groups of ldo/8 columns
+        if (cw == 4)
+          embed_layer_tiled<4>(X, Y, L, tid, relu);
+        else if (cw == 8)
+          embed_layer_tiled<8>(X, Y, L, tid, relu);
+        else
+          embed_layer_tiled<16>(X, Y, L, tid, relu);
+      } else {
+        // any other width (the D-wide output): one thread per (row, output)
+        for (int t = tid; t < kEmbedTM * L.out; t += kThreads) {
+          const int r = t % kEmbedTM, o = t / kEmbedTM;
+          float a = L.b[o];
+          for (int k = 0; k < L.in; ++k) a = fmaf(X[k * kEmbedTM + r], L.WT[k * L.ldo + o], a);
+          Y[o * kEmbedTM + r] = relu ? fmaxf(a, 0.f) : a;
+        }
+      }
+      __syncthreads();
+      float* t = X;
+      X = Y;
+      Y = t;
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// edge encoder: e0 = EE([h_src, h_dst])
-// ---------------------------------------------------------------------------
-__global__ void k_edge_enc_f32(Batch b, Ws w, Mlp2F32 m, int h, int stride, Sel sel) {
-  extern __shared__ float smem[];
-  if (input_bad(w)) return;
-  int lo, hi;
-  if (!sel_rows(b, w, sel, true, lo, hi)) return;
-  float* R = smem + threadIdx.x * stride;  // [2h] input, then output
-  float* H = R + 2 * h + 1;                // [h] hidden (stride includes it)
-  for (int e = lo + blockIdx.x * blockDim.x + threadIdx.x; e < hi;
-       e += gridDim.x * blockDim.x) {
-    load_row(R, w.hstate + size_t(w.src[e]) * h, h);
-    load_row(R + h, w.hstate + size_t(w.col[e]) * h, h);
-    row_mlp2(R, m, H, R);
-    float4* dst = reinterpret_cast<float4*>(w.estate + size_t(e) * h);
-    for (int c = 0; c < (h >> 2); ++c)
-      dst[c] = make_float4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// node update: h <- h + N_k([h, sum_out e, sum_in e])
-// ---------------------------------------------------------------------------
-__global__ void k_node_upd_f32(Batch b, Ws w, Mlp2F32 m, int h, int stride, Sel sel) {
-  extern __shared__ float smem[];
-  if (input_bad(w)) return;
-  int lo, hi;
-  if (!sel_rows(b, w, sel, false, lo, hi)) return;
-  const int E = clamp_edges(w.counters, w.e_cap);
-  float* R = smem + threadIdx.x * stride;  // [3h] input
-  float* H = R + 3 * h + 1;                // [h] hidden
-  for (int v = lo + blockIdx.x * blockDim.x + threadIdx.x; v < hi;
-       v += gridDim.x * blockDim.x) {
-    load_row(R, w.hstate + size_t(v) * h, h);
-    for (int c = 0; c < 2 * h; ++c) R[h + c] = 0.f;
-    const int a = min(w.row_ptr[v], E), z = min(w.row_ptr[v + 1], E);
-    for (int e = a; e < z; ++e) add_row(R + h, w.estate + size_t(e) * h, h);
-    const int ia = w.in_ptr[v], iz = w.in_ptr[v + 1];
-    for (int k = ia; k < iz; ++k) add_row(R + 2 * h, w.estate + size_t(w.in_edge[k]) * h, h);
-    row_mlp2(R, m, H, R + h);
-    float4* dst = reinterpret_cast<float4*>(w.hstate + size_t(v) * h);
-    for (int c = 0; c < (h >> 2); ++c)
-      dst[c] = make_float4(R[4 * c] + R[h + 4 * c], R[4 * c + 1] + R[h + 4 * c + 1],
-                           R[4 * c + 2] + R[h + 4 * c + 2], R[4 * c + 3] + R[h + 4 * c + 3]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// edge update: e <- e + E_k([e, h_src, h_dst]); last step: classifier + cut
-// ---------------------------------------------------------------------------
-__global__ void k_edge_upd_f32(Batch b, Ws w, Mlp2F32 m, Mlp2F32 cls, int has_cls, int h,
-                               int stride, float cut, int rescore_only, float band_lo,
-                               float band_hi, Sel sel) {
-  extern __shared__ float smem[];
-  if (input_bad(w)) return;
-  int lo, hi;
-  if (!sel_rows(b, w, sel, true, lo, hi)) return;
-  float* R = smem + threadIdx.x * stride;  // [3h] input
-  float* H = R + 3 * h + 1;                // [h] hidden
-  for (int e = lo + blockIdx.x * blockDim.x + threadIdx.x; e < hi;
-       e += gridDim.x * blockDim.x) {
-    load_row(R, w.estate + size_t(e) * h, h);
-    if (m.l1.WT != nullptr) {
-      load_row(R + h, w.hstate + size_t(w.src[e]) * h, h);
-      load_row(R + 2 * h, w.hstate + size_t(w.col[e]) * h, h);
-      row_mlp2(R, m, H, R + h);
-      for (int c = 0; c < h; ++c) R[c] += R[h + c];
+    for (int t = tid; t < kEmbedTM * D; t += kThreads) {
+      const int r = t / D, d = t % D, v = base + r;
+      if (v < b.n_hits) w.emb[size_t(v) * D + d] = X[d * kEmbedTM + r];
     }
-    if (!has_cls) {
-      float4* dst = reinterpret_cast<float4*>(w.estate + size_t(e) * h);
-      for (int c = 0; c < (h >> 2); ++c)
-        dst[c] = make_float4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
-      continue;
-    }
-    row_mlp2(R, cls, H, R + h);
-    const float lg = R[h];
-    if (rescore_only) {
-      const float old = w.logit[e];
-      if (!(old > band_lo && old < band_hi)) continue;
-    }
-    w.logit[e] = lg;
-    w.keep[e] = lg >= cut ? 1 : 0;
+    __syncthreads();
   }
 }
 
@@ -252,7 +379,7 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
     size_t smem;
     int n;
   };
-  static Entry cache[32];
+  static Entry cache[64];
   static int used = 0;
   for (int i = 0; i < used; ++i)
     if (cache[i].fn == fn && cache[i].threads == threads && cache[i].smem == smem) return cache[i].n;
@@ -264,19 +391,63 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   if (!seen) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
   n = n > 0 ? n : 1;
-  if (used < 32) cache[used++] = Entry{fn, threads, smem, n};
+  if (used < 64) cache[used++] = Entry{fn, threads, smem, n};
   return n;
 }
 
-// rows per block and shared memory of the interaction-network kernels
-int gnn_threads(int h) { return h <= 32 ? 128 : (h <= 64 ? 64 : 32); }
+template <int H>
+constexpr int tile_rows() {
+  return H <= 32 ? 128 : 64;
+}
 
-dim3 grid_for(const void* fn, int threads, size_t smem, Sel sel, int64_t rows_hint) {
-  const int full = device_sms() * blocks_per_sm(fn, threads, smem);
-  if (sel.list != nullptr) return dim3(4, sel.max_list > 0 ? sel.max_list : 1);
-  int g = full;
-  if (rows_hint >= 0) g = max(1, min(full, div_up(rows_hint, threads)));
-  return dim3(g, 1);
+template <int H, int MODE>
+size_t gnn_smem() {
+  constexpr int TM = tile_rows<H>();
+  constexpr int NSEG = g_nseg(MODE);
+  constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
+  return size_t((K1 > 4 ? K1 : 4) + H) * TM * sizeof(float);
+}
+
+template <int H, int MODE>
+void launch_gnn(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
+  constexpr int TM = tile_rows<H>();
+  const size_t smem = gnn_smem<H, MODE>();
+  const void* fn = (const void*)k_gnn_f32<H, TM, MODE>;
+  const int full = device_sms() * blocks_per_sm(fn, kThreads, smem);
+  dim3 grid(full, 1);
+  if (a.sel.list != nullptr)
+    grid = dim3(8, a.sel.max_list > 0 ? a.sel.max_list : 1);
+  else if (rows_hint >= 0)
+    grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, TM)));
+  k_gnn_f32<H, TM, MODE><<<grid, kThreads, smem, s>>>(a);
+}
+
+void launch_gnn_any(int h, int mode, const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
+#define GNNTRK_M(HH)                                                                \
+  switch (mode) {                                                                   \
+    case G_NODE_ENC: launch_gnn<HH, G_NODE_ENC>(a, rows_hint, s); break;            \
+    case G_EDGE_ENC: launch_gnn<HH, G_EDGE_ENC>(a, rows_hint, s); break;            \
+    case G_NODE_UPD: launch_gnn<HH, G_NODE_UPD>(a, rows_hint, s); break;            \
+    case G_EDGE_UPD: launch_gnn<HH, G_EDGE_UPD>(a, rows_hint, s); break;            \
+    case G_EDGE_UPD_CLS: launch_gnn<HH, G_EDGE_UPD_CLS>(a, rows_hint, s); break;    \
+    case G_CLS: launch_gnn<HH, G_CLS>(a, rows_hint, s); break;                      \
+  }
+  if (h == 32) {
+    GNNTRK_M(32)
+  } else if (h == 64) {
+    GNNTRK_M(64)
+  } else {
+    GNNTRK_M(128)
+  }
+#undef GNNTRK_M
+}
+
+GnnArgs gnn_args(const Batch& b, const Ws& w, Sel sel) {
+  GnnArgs a{};
+  a.b = b;
+  a.w = w;
+  a.sel = sel;
+  return a;
 }
 
 }  // namespace
@@ -285,50 +456,53 @@ void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, in
                           const Mlp2F32& node_enc, int D, int h, const GraphParams& g,
                           bool do_embed, bool do_node_enc, Sel sel, cudaStream_t s) {
   if (b.n_hits <= 0) return;
-  EmbedLayers em{};
-  int width = 3;
-  for (int l = 0; l < n_embed; ++l) {
-    em.l[l] = embed[l];
-    width = max(width, embed[l].ldo);
+  if (do_embed) {
+    EmbedLayers em{};
+    int maxw = 4;
+    for (int l = 0; l < n_embed; ++l) {
+      em.l[l] = embed[l];
+      maxw = std::max(maxw, embed[l].ldo);
+    }
+    const size_t smem = size_t(2) * maxw * kEmbedTM * sizeof(float);
+    const int full = device_sms() * blocks_per_sm((const void*)k_embed_f32, kThreads, smem);
+    const int grid = std::max(1, std::min(full, div_up(b.n_hits, kEmbedTM)));
+    k_embed_f32<<<grid, kThreads, smem, s>>>(b, w, em, n_embed, D, g, maxw);
   }
-  width = max(width, h);
-  const int stride = width | 1;
-  const size_t smem = size_t(2) * kPrepThreads * stride * sizeof(float);
-  const dim3 grid = grid_for((const void*)k_node_prep_f32, kPrepThreads, smem, sel, b.n_hits);
-  k_node_prep_f32<<<grid, kPrepThreads, smem, s>>>(b, w, em, n_embed, node_enc, D, h, g, stride,
-                                                   do_embed, do_node_enc, sel);
+  if (do_node_enc) {
+    GnnArgs a = gnn_args(b, w, sel);
+    a.m = node_enc;
+    for (int i = 0; i < 6; ++i) a.fs[i] = g.fs[i];
+    launch_gnn_any(h, G_NODE_ENC, a, b.n_hits, s);
+  }
 }
 
 void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
                          cudaStream_t s) {
-  const int T = gnn_threads(h);
-  const int stride = (3 * h + 2) | 1;
-  const size_t smem = size_t(T) * stride * sizeof(float);
-  const dim3 grid = grid_for((const void*)k_edge_enc_f32, T, smem, sel, -1);
-  k_edge_enc_f32<<<grid, T, smem, s>>>(b, w, m, h, stride, sel);
+  GnnArgs a = gnn_args(b, w, sel);
+  a.m = m;
+  launch_gnn_any(h, G_EDGE_ENC, a, -1, s);
 }
 
 void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
                             cudaStream_t s) {
   if (b.n_hits <= 0) return;
-  const int T = gnn_threads(h);
-  const int stride = (4 * h + 2) | 1;
-  const size_t smem = size_t(T) * stride * sizeof(float);
-  const dim3 grid = grid_for((const void*)k_node_upd_f32, T, smem, sel, b.n_hits);
-  k_node_upd_f32<<<grid, T, smem, s>>>(b, w, m, h, stride, sel);
+  GnnArgs a = gnn_args(b, w, sel);
+  a.m = m;
+  launch_gnn_any(h, G_NODE_UPD, a, b.n_hits, s);
 }
 
 void launch_edge_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const Mlp2F32* cls,
                             int h, float cut_logit, bool rescore_only, float band_lo,
                             float band_hi, Sel sel, cudaStream_t s) {
-  const int T = gnn_threads(h);
-  const int stride = (4 * h + 2) | 1;
-  const size_t smem = size_t(T) * stride * sizeof(float);
-  const dim3 grid = grid_for((const void*)k_edge_upd_f32, T, smem, sel, -1);
-  Mlp2F32 c{};
-  if (cls) c = *cls;
-  k_edge_upd_f32<<<grid, T, smem, s>>>(b, w, m, c, cls != nullptr, h, stride, cut_logit,
-                                       rescore_only, band_lo, band_hi, sel);
+  GnnArgs a = gnn_args(b, w, sel);
+  a.m = m;
+  if (cls) a.cls = *cls;
+  a.cut = cut_logit;
+  a.rescore_only = rescore_only;
+  a.band_lo = band_lo;
+  a.band_hi = band_hi;
+  const int mode = cls == nullptr ? G_EDGE_UPD : (m.l1.WT == nullptr ? G_CLS : G_EDGE_UPD_CLS);
+  launch_gnn_any(h, mode, a, -1, s);
 }
 
 }  // namespace gnntrk
