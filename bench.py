@@ -145,6 +145,41 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     return "hbm", N * 16, "byte"
 
 
+def timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, steps):
+    """Per-step CUDA-event times on `stream`, L2 flushed between steps."""
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i)
+            ev_s[i].record(stream)
+            tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    tr.sync_status(stream)
+    return [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
+
+
+def quick_rate(pkg, torch, wl, batch, dev, stream, flush, steps=5, **kw):
+    """events/s of another configuration on the same resident batch."""
+    n_ev, N = batch.n_events, batch.n_hits
+    xyz = torch.from_numpy(batch.xyz_soa()).to(dev)
+    plane = torch.from_numpy(batch.plane).to(dev)
+    offs = torch.from_numpy(batch.offsets).to(dev)
+    labels = torch.empty(N, dtype=torch.int32, device=dev)
+    tr = pkg.tracker_for_workload(wl, max_hits=N, max_events=n_ev, edges_per_hit=16,
+                                  use_graph=True, **kw)
+    for _ in range(3):
+        tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+    tr.sync_status(stream)
+    ms = float(np.mean(timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream,
+                                   flush, steps)))
+    st = tr.stats()
+    tr.close()
+    return {"events_per_s": round(n_ev / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+            "band_edges": st["band"], "rerun_events": st["rerun_events"]}
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -157,7 +192,7 @@ def main():
     import paper_2508_07423_gb300 as pkg
 
     wl = synth.workload(a.workload)
-    precision = a.precision or "fp32"
+    precision = a.precision or wl.get("precision", "fp32")
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -175,23 +210,19 @@ def main():
     labels = torch.empty(N, dtype=torch.int32, device=dev)
     kw = {} if a.band is None else {"rescore_band": a.band}
     tr = pkg.tracker_for_workload(wl, precision=precision, max_hits=N, max_events=n_ev,
-                                  edges_per_hit=16, **kw)
+                                  edges_per_hit=16, use_graph=True, **kw)
     band = tr.cfg.rescore_band
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    def step():
-        tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
-
+    tuned = tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
     for _ in range(max(a.warmup, 3)):
-        step()
+        tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
         tr.sync_status(stream)
     stats = tr.stats()
 
-    # timed region: per-step event pairs, L2 flushed between steps (outside the pairs)
-    tr.set_profiling(True)
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    # timed region: CUDA-graph replays, per-step event pairs, L2 flushed between
+    # steps (outside the pairs)
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -199,21 +230,11 @@ def main():
     clocks.start()
     time.sleep(0.3)
     t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for i in range(a.steps):
-            flush.fill_(i)
-            ev_s[i].record(stream)
-            step()
-            ev_e[i].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, a.steps)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    tr.sync_status(stream)
-    step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
-    stages = tr.stage_times()
-    tr.set_profiling(False)
     ms = float(np.mean(step_ms))
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -223,12 +244,15 @@ def main():
     value = total_events / (ms / 1e3)
     hits_total = N * world
 
-    # roofline of the dominant stage
+    # the same steps again with per-stage events (direct launches): roofline
+    tr.set_profiling(True)
+    prof_ms = timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, a.steps)
+    stages = tr.stage_times()
+    tr.set_profiling(False)
     pk = peaks()
     m = wl["model"]
     E = stats["edges"]
-    dom = max(stages.items(), key=lambda kv: kv[1][0])
-    dname, (dms, druns) = dom
+    dname, (dms, druns) = max(stages.items(), key=lambda kv: kv[1][0])
     bound, amount, _ = stage_work(dname, precision, N, E, m["hidden"], m["iters"],
                                   m["embed"][-1], m["embed"])
     launch_ms = dms / max(druns, 1)
@@ -242,15 +266,23 @@ def main():
         unit = "GB/s"
     roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
             "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
-            "peak_src": pk["src"] if bound != "alu" else "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
+            "peak_src": ("derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"
+                         if bound == "alu" else pk["src"]),
             "launch_ms": round(launch_ms, 4),
+            "profiled_ms_per_step": round(float(np.mean(prof_ms)), 4),
             "stage_ms_per_step": {k: round(v[0] / a.steps, 4) for k, v in stages.items()}}
 
-    # end to end through the public call with host buffers
     e2e = None if a.no_e2e else run_e2e(a, tr, batch, stream, dev, torch)
-
-    # plain FP32 one event per launch (the denominator of the batching target)
-    plain = None if a.no_plain else run_plain(pkg, torch, dev, stream)
+    extra = {}
+    if not a.no_plain:
+        extra["plain_fp32_one_event_per_launch"] = run_plain(pkg, torch, dev, stream)
+        if precision != "fp32":
+            extra["no_rescore"] = quick_rate(pkg, torch, wl, batch, dev, stream, flush,
+                                             precision=precision, rescore_band=0.0)
+        extra["fp32_batched"] = quick_rate(pkg, torch, wl, batch, dev, stream, flush,
+                                           precision="fp32")
+        extra["serving"] = run_serving(pkg, precision)
+    plain = extra.get("plain_fp32_one_event_per_launch")
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "events/s", "n_gpus": world,
@@ -266,23 +298,57 @@ def main():
                    "net": f"embed {'-'.join(map(str, m['embed']))}, IN h{m['hidden']} K{m['iters']}",
                    "precision": precision, "rescore_band": round(float(band), 6),
                    "band_edges": stats["band"], "rerun_events": stats["rerun_events"],
+                   "launch": "one CUDA graph per step (captured on first use)",
+                   "autotuned_ctas_per_sm": tuned,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (disjoint events, no collective)"},
         "clocks": clk,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": int(stats["launches"]) * a.steps,
-        "plain_fp32_one_event_per_launch": plain,
         "batched_over_plain": (round(value / plain["events_per_s"], 2)
                                if plain and plain.get("events_per_s") else None),
         "wall_s_timed": round(wall, 3),
     }
+    out.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, batch, labels.cpu().numpy(), tr, a.cpu_seconds)
     if rank == 0:
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def run_serving(pkg, precision):
+    """Config 5: Poisson arrivals at 50 k events/s, continuous batching within a
+    40 GB budget; p50/p99 latency and sustained events/s."""
+    try:
+        wl = synth.workload("cfg5_serving")
+        n = wl["n_events"]
+        b = synth.workload_batch(wl, n)
+        arr = pkg.poisson_arrivals(n, wl["arrival_rate_hz"], wl["seeds"]["arrivals"])
+        band = float(wl.get("rescore_band_score", 0.0)) if precision != "fp32" else 0.0
+        cfg = pkg.make_cfg(wl["model"], wl["radius2"], k_max=wl["k_max"], precision=precision,
+                           rescore_band=band, edges_per_hit=16)
+        res = {}
+        for name, bnd in (("rescore", band), ("no_rescore", 0.0)):
+            cfg.rescore_band = bnd
+            _, done, st = pkg.serve_run(synth.workload_weights(wl), cfg, b, arr, n_slots=4,
+                                        max_events_per_batch=2048, max_hits_per_batch=4 << 20,
+                                        memory_budget_bytes=wl["memory_budget_bytes"])
+            lat = (done - arr) * 1e3
+            res[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                         "sustained_events_per_s": round(n / (done.max() - arr[0]), 1),
+                         "batches": st["batches"], "slots": st["slots"],
+                         "max_in_flight": st["max_in_flight"],
+                         "largest_batch": st["largest_batch"]}
+            if precision == "fp32":
+                break
+        return {"workload": f"cfg5_serving: {n} events, {wl['description']}",
+                "offered_events_per_s": wl["arrival_rate_hz"], "precision": precision, **res}
+    except Exception as ex:  # reported, not fatal
+        return {"error": str(ex)}
 
 
 def run_e2e(a, tr, batch, stream, dev, torch):

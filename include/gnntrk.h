@@ -225,6 +225,76 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
                            int64_t* runs);
 
 /*
+ * Autotuner of the tensor-core kernels. Runs the given call repeatedly (it is
+ * a real call: inputs, outputs and stream as for gnntrk_find_tracks), timing
+ * each tensor-core kernel family (node encoder, edge encoder, node step, edge
+ * step with classifier) under 1..8 resident CTAs per SM (capped by the shared
+ * memory, registers and tensor-memory columns each CTA needs), keeps the
+ * fastest count per family and returns it in choice[0..3] (host int32 [8] or
+ * NULL; other entries 0). The choice applies to every handle of the process
+ * with the same precision and hidden width. Synchronous. FP32 handles have
+ * nothing to tune (returns OK, choices 0). Errors: as gnntrk_find_tracks and
+ * gnntrk_sync_status.
+ */
+gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                              const float* hits_xyz, const uint8_t* plane,
+                              const int64_t* offsets, int32_t* out_labels, void* stream,
+                              int32_t* choice);
+
+/*
+ * Device memory a handle created with `cfg` allocates (weights and workspace),
+ * in bytes; 0 if cfg is invalid. For admission planning.
+ */
+int64_t gnntrk_workspace_bytes(const gnntrk_cfg* cfg);
+
+/*
+ * Serving loop with continuous batching (trigger-style request stream).
+ *
+ * Events arrive at given times; the server admits every event that has
+ * arrived into the next batch as soon as one of its slots is free, so events
+ * that arrive while others are on the GPU join the next batch instead of
+ * waiting for a fixed batch to fill. Each slot has its own stream, handle
+ * (resident weights and workspace) and pinned staging buffers; several batches
+ * are on the device at once and their copies and kernels overlap. Slots are
+ * created only while their device memory fits the budget.
+ *
+ *   weights, weights_bytes, model: as for gnntrk_create; the capacity fields
+ *            of `model` are replaced by the batch caps below.
+ *   scfg: host; n_slots (1..16, batches in flight), max_events_per_batch,
+ *            max_hits_per_batch (every single event must fit), memory_budget_bytes
+ *            (device bytes of all slots together).
+ *   n_events, offsets (host int64 [n_events+1]), hits_xyz (host float32
+ *            [3][n_hits]), plane (host uint8 [n_hits]): the request stream,
+ *            events in arrival order.
+ *   arrival_s: host double [n_events], non-decreasing arrival times in
+ *            seconds from the start of the run.
+ *   out_labels: host int32 [n_hits]; event-local labels as gnntrk_find_tracks
+ *            writes them (-1 for events of a batch that failed).
+ *   done_s: host double [n_events]; time (seconds from the start) at which the
+ *            event's labels were back in host memory.
+ *   stats: host int64 [8] or NULL: [0] batches, [1] slots created,
+ *            [2] batches that failed, [3] most batches in flight at once,
+ *            [4] device bytes per slot, [5] largest batch (events),
+ *            [6] wall time of the run in microseconds, [7] reserved.
+ * Blocks until every event is done (the calling thread runs the loop).
+ * Errors: INVALID_ARG, WEIGHTS, UNSUPPORTED, OOM (not even one slot fits the
+ * budget), CUDA. gnntrk_last_error(NULL) describes them.
+ */
+typedef struct gnntrk_serve_cfg {
+  int32_t n_slots;
+  int32_t max_events_per_batch;
+  int64_t max_hits_per_batch;
+  int64_t memory_budget_bytes;
+  int32_t reserved[8];
+} gnntrk_serve_cfg;
+
+gnntrk_status gnntrk_serve_run(const void* weights, size_t weights_bytes, const gnntrk_cfg* model,
+                               const gnntrk_serve_cfg* scfg, int32_t n_events,
+                               const int64_t* offsets, const float* hits_xyz,
+                               const uint8_t* plane, const double* arrival_s,
+                               int32_t* out_labels, double* done_s, int64_t* stats);
+
+/*
  * Connected-component labels of one graph, WITHOUT allocating any memory.
  * The thesis has no counterpart of this call; it is here for callers that
  * cannot allocate device memory -- code running under another framework's
@@ -264,7 +334,7 @@ gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edges, const i
 
 /* Description of the last error on this handle ("" if none). The string is
  * owned by the handle. NULL handle: description of the last failure of
- * gnntrk_create or gnntrk_components_noalloc. */
+ * gnntrk_create, gnntrk_serve_run or gnntrk_components_noalloc. */
 const char* gnntrk_last_error(const gnntrk_handle* h);
 
 /* Release the handle's device memory, CUDA graphs and streams. NULL is a no-op.

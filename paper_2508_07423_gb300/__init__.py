@@ -25,7 +25,9 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
-           "gnntrk_components_noalloc", "gnntrk_last_error", "gnntrk_destroy"]
+           "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
+           "gnntrk_autotune",
+           "gnntrk_last_error", "gnntrk_destroy"]
 
 NOALLOC_MAX_HITS = 1 << 20
 
@@ -34,6 +36,17 @@ class GnntrkError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"gnntrk {STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class ServeCfg(ctypes.Structure):
+    """Mirror of gnntrk_serve_cfg."""
+    _fields_ = [
+        ("n_slots", ctypes.c_int32),
+        ("max_events_per_batch", ctypes.c_int32),
+        ("max_hits_per_batch", ctypes.c_int64),
+        ("memory_budget_bytes", ctypes.c_int64),
+        ("reserved", ctypes.c_int32 * 8),
+    ]
 
 
 class Cfg(ctypes.Structure):
@@ -88,6 +101,13 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_stage_times.restype = i32
     L.gnntrk_components_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp]
     L.gnntrk_components_noalloc.restype = st
+    L.gnntrk_autotune.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, vp]
+    L.gnntrk_autotune.restype = st
+    L.gnntrk_workspace_bytes.argtypes = [ctypes.POINTER(Cfg)]
+    L.gnntrk_workspace_bytes.restype = i64
+    L.gnntrk_serve_run.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(Cfg),
+                                   ctypes.POINTER(ServeCfg), i32, vp, vp, vp, vp, vp, vp, vp]
+    L.gnntrk_serve_run.restype = st
     L.gnntrk_last_error.argtypes = [vp]
     L.gnntrk_last_error.restype = ctypes.c_char_p
     L.gnntrk_destroy.argtypes = [vp]
@@ -191,6 +211,18 @@ class Tracker:
                 "rerun_events": int(out[3]), "events": int(out[4]), "hits": int(out[5]),
                 "edge_capacity": int(out[6]), "launches": int(out[7])}
 
+    def autotune(self, n_events: int, n_hits: int, hits_xyz, plane, offsets, out_labels,
+                 stream=None) -> dict:
+        """Tune the tensor-core launch configuration on this call's data."""
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        ch = np.zeros(8, np.int32)
+        self._check(self._L.gnntrk_autotune(self._h, n_events, n_hits, _ptr(hits_xyz),
+                                            _ptr(plane), _ptr(offsets), _ptr(out_labels),
+                                            ctypes.c_void_p(s),
+                                            ch.ctypes.data_as(ctypes.c_void_p)))
+        return {"node_prep": int(ch[0]), "edge_encoder": int(ch[1]), "node_update": int(ch[2]),
+                "edge_update": int(ch[3])}
+
     def set_profiling(self, enable: bool):
         self._check(self._L.gnntrk_set_profiling(self._h, int(bool(enable))))
 
@@ -260,6 +292,42 @@ def components_noalloc(n_hits: int, src, dst, kept, out_labels, stream=None):
                                      _ptr(dst), _ptr(kept), _ptr(out_labels), ctypes.c_void_p(s))
     if st != 0:
         raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+
+
+def workspace_bytes(cfg: Cfg) -> int:
+    return int(load_library().gnntrk_workspace_bytes(ctypes.byref(cfg)))
+
+
+def serve_run(weights: bytes, cfg: Cfg, batch, arrival_s, n_slots: int = 4,
+              max_events_per_batch: int = 512, max_hits_per_batch: int = 1 << 20,
+              memory_budget_bytes: int = 40_000_000_000):
+    """Run the continuous-batching server over a host `synth.Batch` whose events
+    arrive at `arrival_s` (seconds). Returns (labels, done_s, stats)."""
+    L = load_library()
+    sc = ServeCfg(n_slots, max_events_per_batch, max_hits_per_batch, memory_budget_bytes)
+    xyz = np.ascontiguousarray(batch.xyz_soa(), np.float32)
+    plane = np.ascontiguousarray(batch.plane, np.uint8)
+    offs = np.ascontiguousarray(batch.offsets, np.int64)
+    arr = np.ascontiguousarray(arrival_s, np.float64)
+    labels = np.full(batch.n_hits, -7, np.int32)
+    done = np.zeros(batch.n_events, np.float64)
+    stats = np.zeros(8, np.int64)
+    blob = ctypes.create_string_buffer(weights, len(weights))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = L.gnntrk_serve_run(blob, len(weights), ctypes.byref(cfg), ctypes.byref(sc),
+                            batch.n_events, p(offs), p(xyz), p(plane), p(arr), p(labels),
+                            p(done), p(stats))
+    if st != 0:
+        raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+    names = ["batches", "slots", "failed_batches", "max_in_flight", "slot_bytes",
+             "largest_batch", "wall_us"]
+    return labels, done, dict(zip(names, (int(v) for v in stats[:7])))
+
+
+def poisson_arrivals(n: int, rate_hz: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process: exponential gaps, seeded."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, n))
 
 
 def cut_logit(score_cut: float) -> float:

@@ -49,6 +49,15 @@ struct gnntrk_handle {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
+  // CUDA graphs of earlier call shapes (use_graph)
+  struct GraphEntry {
+    int32_t n_events;
+    int64_t n_hits;
+    const void *xyz, *plane, *offsets, *labels;
+    cudaGraphExec_t exec;
+    int launches;
+  };
+  std::vector<GraphEntry> graphs;
 };
 
 namespace {
@@ -170,44 +179,53 @@ gnntrk_status upload_f32(gnntrk_handle* h, const std::vector<HostLayer>& L) {
   return GNNTRK_OK;
 }
 
-gnntrk_status alloc_workspace(gnntrk_handle* h) {
-  const gnntrk_cfg& c = h->cfg;
+// Every workspace array with its size in bytes (one list for allocation and
+// for gnntrk_workspace_bytes).
+std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D, int hd, Ws& w) {
   const int64_t H = c.max_hits, E = int64_t(c.max_hits) * c.edges_per_hit;
-  Ws& w = h->ws;
+  std::vector<std::pair<void**, size_t>> v;
+  auto add = [&](auto** ptr, int64_t n) {
+    v.push_back({reinterpret_cast<void**>(ptr), size_t(n) * sizeof(**ptr)});
+  };
+  add(&w.perm, H);
+  add(&w.node_event, H);
+  add(&w.pos, H);
+  add(&w.plane_off, int64_t(c.max_events) * (c.n_planes + 1));
+  add(&w.emb, H * D);
+  add(&w.deg, H);
+  add(&w.row_ptr, H + 1);
+  add(&w.col, E);
+  add(&w.src, E);
+  add(&w.d2, E);
+  add(&w.in_cnt, H);
+  add(&w.in_ptr, H + 1);
+  add(&w.in_edge, E);
+  add(&w.hstate, H * hd);
+  add(&w.estate, E * hd);
+  if (c.precision != GNNTRK_FP32) {
+    add(&w.hstate16, H * hd);
+    add(&w.estate16, E * hd);
+  }
+  add(&w.logit, E);
+  add(&w.keep, E);
+  add(&w.parent, H);
+  add(&w.counters, C_COUNT);
+  add(&w.scan_blocks, (H + 4095) / 4096 + 1);
+  add(&w.ev_flag, c.max_events);
+  add(&w.rerun_list, c.max_events);
+  add(&w.ev_off, int64_t(c.max_events) + 1);
   w.h_cap = H;
   w.e_cap = E;
-  gnntrk_status st;
-#define A(ptr, n)                                   \
-  if ((st = alloc_n(h, &w.ptr, size_t(n))) != 0) return st;
-  A(perm, H);
-  A(node_event, H);
-  A(pos, H);
-  A(plane_off, int64_t(c.max_events) * (c.n_planes + 1));
-  A(emb, H * h->D);
-  A(deg, H);
-  A(row_ptr, H + 1);
-  A(col, E);
-  A(src, E);
-  A(d2, E);
-  A(in_cnt, H);
-  A(in_ptr, H + 1);
-  A(in_edge, E);
-  A(hstate, H * h->h);
-  A(estate, E * h->h);
-  if (c.precision != GNNTRK_FP32) {
-    A(hstate16, H * h->h);
-    A(estate16, E * h->h);
+  return v;
+}
+
+gnntrk_status alloc_workspace(gnntrk_handle* h) {
+  auto plan = workspace_plan(h->cfg, h->D, h->h, h->ws);
+  for (auto& it : plan) {
+    gnntrk_status st = alloc(h, it.first, it.second);
+    if (st) return st;
   }
-  A(logit, E);
-  A(keep, E);
-  A(parent, H);
-  A(counters, C_COUNT);
-  A(scan_blocks, (H + 4095) / 4096 + 1);
-  A(ev_flag, c.max_events);
-  A(rerun_list, c.max_events);
-  A(ev_off, int64_t(c.max_events) + 1);
-#undef A
-  cudaMemset(w.counters, 0, C_COUNT * sizeof(int32_t));
+  cudaMemset(h->ws.counters, 0, C_COUNT * sizeof(int32_t));
   return GNNTRK_OK;
 }
 
@@ -273,6 +291,95 @@ void stage(gnntrk_handle* h, const char* name, cudaStream_t s, int kernels, F&& 
 }
 
 }  // namespace
+
+// Enqueue the whole hot path of one call on stream s (also used inside a
+// CUDA-graph capture).
+void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, cudaStream_t s) {
+  const gnntrk_cfg& c = h->cfg;
+  Ws& w = h->ws;
+  const GraphParams g = graph_params(h);
+  if (h->profiling) collect_stages(h);
+  h->last_launches = 0;
+  cudaMemsetAsync(w.counters, 0, C_COUNT * sizeof(int32_t), s);
+  cudaMemcpyAsync(w.ev_off, offsets, sizeof(int64_t) * (b.n_events + 1), cudaMemcpyDeviceToDevice, s);
+  stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
+  const Sel all{nullptr, nullptr, 0};
+  const bool tc = c.precision != GNNTRK_FP32;
+  stage(h, "node_prep", s, tc ? 2 : 1, [&] {
+    if (!tc)
+      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true,
+                           all, s);
+    else
+      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s);
+  });
+  stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
+  stage(h, "scan_out", s, 2, [&] {
+    launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap,
+                w.scan_blocks, s);
+  });
+  stage(h, "radius_fill", s, 1, [&] { launch_radius(b, w, g, h->D, true, s); });
+  stage(h, "scan_in", s, 2, [&] {
+    launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
+                w.scan_blocks, s);
+  });
+  stage(h, "in_index", s, 2, [&] { launch_csc(b, w, s); });
+  if (!tc) {
+    stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
+    for (int k = 0; k < h->K; ++k) {
+      stage(h, "node_update", s, 1,
+            [&] { launch_node_update_f32(b, w, h->node[k], h->h, all, s); });
+      stage(h, "edge_update", s, 1, [&] {
+        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                               g.cut_logit, false, 0.f, 0.f, all, s);
+      });
+    }
+    if (h->K == 0)  // no message passing: the classifier reads the edge encodings
+      stage(h, "edge_update", s, 1, [&] {
+        launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f,
+                               all, s);
+      });
+  } else {
+    const bool fused = tc_cls_fused(h->h, c.precision);
+    stage(h, "edge_encoder", s, 1,
+          [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
+    for (int k = 0; k < h->K; ++k) {
+      stage(h, "node_update", s, 1,
+            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
+      stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
+            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k); });
+    }
+    if (h->K == 0)
+      stage(h, "edge_update", s, 1, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1); });
+    if (c.rescore_band > 0.f) {
+      const double lo = double(c.score_cut) - double(c.rescore_band);
+      const double hi = double(c.score_cut) + double(c.rescore_band);
+      const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
+      const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
+      stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
+      const Sel sel{w.rerun_list, w.counters + C_RERUN, b.n_events};
+      stage(h, "rescore_node_prep", s, 1, [&] {
+        launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
+                             sel, s);
+      });
+      stage(h, "rescore_edge_encoder", s, 1,
+            [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s); });
+      for (int k = 0; k < h->K; ++k) {
+        stage(h, "rescore_node_update", s, 1,
+              [&] { launch_node_update_f32(b, w, h->node[k], h->h, sel, s); });
+        stage(h, "rescore_edge_update", s, 1, [&] {
+          launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
+                                 g.cut_logit, true, band_lo, band_hi, sel, s);
+        });
+      }
+      if (h->K == 0)
+        stage(h, "rescore_edge_update", s, 1, [&] {
+          launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
+                                 band_hi, sel, s);
+        });
+    }
+  }
+  stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });
+}
 
 namespace gnntrk {
 // failure text of handle-less calls, returned by gnntrk_last_error(NULL)
@@ -404,91 +511,107 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
   b.plane = plane;
   b.offsets = w.ev_off;
   b.labels = out_labels;
-  const GraphParams g = graph_params(h);
 
-  if (h->profiling) collect_stages(h);
-  h->last_launches = 0;
-  cudaMemsetAsync(w.counters, 0, C_COUNT * sizeof(int32_t), s);
-  cudaMemcpyAsync(w.ev_off, offsets, sizeof(int64_t) * (n_events + 1), cudaMemcpyDeviceToDevice, s);
-  stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
-  const Sel all{nullptr, nullptr, 0};
-  const bool tc = c.precision != GNNTRK_FP32;
-  stage(h, "node_prep", s, tc ? 2 : 1, [&] {
-    if (!tc)
-      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true,
-                           all, s);
-    else
-      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s);
-  });
-  stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
-  stage(h, "scan_out", s, 2, [&] {
-    launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap,
-                w.scan_blocks, s);
-  });
-  stage(h, "radius_fill", s, 1, [&] { launch_radius(b, w, g, h->D, true, s); });
-  stage(h, "scan_in", s, 2, [&] {
-    launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
-                w.scan_blocks, s);
-  });
-  stage(h, "in_index", s, 2, [&] { launch_csc(b, w, s); });
-  if (!tc) {
-    stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
-    for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 1,
-            [&] { launch_node_update_f32(b, w, h->node[k], h->h, all, s); });
-      stage(h, "edge_update", s, 1, [&] {
-        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                               g.cut_logit, false, 0.f, 0.f, all, s);
-      });
-    }
-    if (h->K == 0)  // no message passing: the classifier reads the edge encodings
-      stage(h, "edge_update", s, 1, [&] {
-        launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f,
-                               all, s);
-      });
-  } else {
-    const bool fused = tc_cls_fused(h->h, c.precision);
-    stage(h, "edge_encoder", s, 1,
-          [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
-    for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 1,
-            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
-      stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
-            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k); });
-    }
-    if (h->K == 0)
-      stage(h, "edge_update", s, 1, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1); });
-    if (c.rescore_band > 0.f) {
-      const double lo = double(c.score_cut) - double(c.rescore_band);
-      const double hi = double(c.score_cut) + double(c.rescore_band);
-      const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
-      const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
-      stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
-      const Sel sel{w.rerun_list, w.counters + C_RERUN, n_events};
-      stage(h, "rescore_node_prep", s, 1, [&] {
-        launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
-                             sel, s);
-      });
-      stage(h, "rescore_edge_encoder", s, 1,
-            [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s); });
-      for (int k = 0; k < h->K; ++k) {
-        stage(h, "rescore_node_update", s, 1,
-              [&] { launch_node_update_f32(b, w, h->node[k], h->h, sel, s); });
-        stage(h, "rescore_edge_update", s, 1, [&] {
-          launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                                 g.cut_logit, true, band_lo, band_hi, sel, s);
-        });
+  if (c.use_graph && !h->profiling && s != nullptr) {
+    for (auto& ge : h->graphs)
+      if (ge.n_events == n_events && ge.n_hits == n_hits && ge.xyz == hits_xyz &&
+          ge.plane == plane && ge.offsets == offsets && ge.labels == out_labels) {
+        h->last_launches = ge.launches;
+        cudaError_t e = cudaGraphLaunch(ge.exec, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+        return GNNTRK_OK;
       }
-      if (h->K == 0)
-        stage(h, "rescore_edge_update", s, 1, [&] {
-          launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
-                                 band_hi, sel, s);
-        });
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream capture");
+    enqueue_pipeline(h, b, offsets, s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    if (h->graphs.size() >= 16) {
+      cudaGraphExecDestroy(h->graphs.front().exec);
+      h->graphs.erase(h->graphs.begin());
     }
+    h->graphs.push_back({n_events, n_hits, hits_xyz, plane, offsets, out_labels, exec,
+                         h->last_launches});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    return GNNTRK_OK;
   }
-  stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });
+  enqueue_pipeline(h, b, offsets, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+  return GNNTRK_OK;
+}
+
+int64_t gnntrk_workspace_bytes(const gnntrk_cfg* c) {
+  if (!c || c->max_hits < 1 || c->n_embed_layers < 1 || c->n_embed_layers > kMaxEmbedLayers ||
+      c->hidden < 1 || c->iters < 0 || c->iters > kMaxIters || c->edges_per_hit < 1 ||
+      c->max_events < 1)
+    return 0;
+  Ws w{};
+  const int D = c->embed_dims[c->n_embed_layers];
+  int64_t total = 0;
+  for (auto& it : workspace_plan(*c, D, c->hidden, w)) total += int64_t((it.second + 255) / 256 * 256);
+  // weights: the FP32 image plus, for the tensor-core paths, the packed one
+  int64_t wparams = 0;
+  for (int l = 0; l < c->n_embed_layers; ++l)
+    wparams += int64_t(c->embed_dims[l] + 1) * ((c->embed_dims[l + 1] + 3) & ~3);
+  const int64_t hh = c->hidden;
+  wparams += (4 + 4 * hh) * hh + (3 * hh + 1) * hh + (hh + 1) * hh;           // encoders
+  wparams += int64_t(c->iters) * 2 * ((3 * hh + 1) * hh + (hh + 1) * hh);    // steps
+  wparams += (hh + 1) * hh + (hh + 1) * 4;                                   // classifier
+  total += 4 * wparams;
+  if (c->precision != GNNTRK_FP32) total += 2 * wparams + 64 * 1024;
+  return total;
+}
+
+gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                              const float* hits_xyz, const uint8_t* plane,
+                              const int64_t* offsets, int32_t* out_labels, void* stream,
+                              int32_t* choice) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  if (choice)
+    for (int i = 0; i < 8; ++i) choice[i] = 0;
+  if (h->cfg.precision == GNNTRK_FP32) return GNNTRK_OK;  // nothing to tune
+  const char* names[4] = {"node_prep", "edge_encoder", "node_update", "edge_update"};
+  double best_t[4] = {1e30, 1e30, 1e30, 1e30};
+  int best_n[4] = {0, 0, 0, 0};
+  const bool was_profiling = h->profiling;
+  const int prec = h->cfg.precision, hd = h->h;
+  for (int n = 1; n <= 8; ++n) {
+    for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, n);
+    gnntrk_status st = gnntrk_find_tracks(h, n_events, n_hits, hits_xyz, plane, offsets,
+                                          out_labels, stream);  // warm-up
+    if (!st) st = gnntrk_sync_status(h, stream);
+    if (st) {
+      for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, 0);
+      return st;
+    }
+    gnntrk_set_profiling(h, 1);
+    for (int r = 0; r < 2 && !st; ++r)
+      st = gnntrk_find_tracks(h, n_events, n_hits, hits_xyz, plane, offsets, out_labels, stream);
+    collect_stages(h);
+    for (auto& sa : h->stages)
+      for (int f = 0; f < 4; ++f)
+        if (sa.name == names[f] && sa.ms < best_t[f]) {
+          best_t[f] = sa.ms;
+          best_n[f] = n;
+        }
+    gnntrk_set_profiling(h, 0);
+    if (st) break;
+  }
+  for (int f = 0; f < 4; ++f) {
+    tc_set_ctas(prec, hd, f, best_n[f]);
+    if (choice) choice[f] = best_n[f];
+  }
+  if (was_profiling) gnntrk_set_profiling(h, 1);
+  // shapes captured before tuning would keep the old launch configuration
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
   return GNNTRK_OK;
 }
 
@@ -604,6 +727,7 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
 void gnntrk_destroy(gnntrk_handle* h) {
   if (!h) return;
   collect_stages(h);
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->d_wtc) cudaFree(h->d_wtc);

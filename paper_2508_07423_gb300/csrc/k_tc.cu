@@ -765,10 +765,23 @@ int tc_blocks_per_sm() {
   return per_sm;
 }
 
+// Resident CTAs per SM chosen by the autotuner, per (FP8, hidden, kernel
+// family); 0 = the resource bound. Families: 0 node encoder, 1 edge encoder,
+// 2 node step, 3 edge step and classifier.
+int g_tuned[2][3][4] = {};
+
+constexpr int family_of(int mode) {
+  return mode == M_NODE_ENC ? 0 : mode == M_EDGE_ENC ? 1 : mode == M_NODE_UPD ? 2 : 3;
+}
+constexpr int hidx(int h) { return h == 32 ? 0 : (h == 64 ? 1 : 2); }
+
 template <int H, bool FP8, int MODE>
 void launch_mode(const TcArgs& a, cudaStream_t s, int rows_hint) {
   using L = Layout<H, FP8, MODE>;
-  int grid = device_sms() * tc_blocks_per_sm<H, FP8, MODE>();
+  int per_sm = tc_blocks_per_sm<H, FP8, MODE>();
+  const int tuned = g_tuned[FP8 ? 1 : 0][hidx(H)][family_of(MODE)];
+  if (tuned > 0 && tuned < per_sm) per_sm = tuned;
+  int grid = device_sms() * per_sm;
   if (rows_hint >= 0) grid = rows_hint == 0 ? 1 : min(grid, div_up(rows_hint, kRows));
   k_tc<H, FP8, MODE><<<grid, kRows, L::TOTAL, s>>>(a);
 }
@@ -1036,6 +1049,16 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
     }
   }
   if (K == 0 && (stage < 0 || stage == 1)) launch_any(h, fp8, M_CLS, a, s, -1);
+}
+
+void tc_set_ctas(int precision, int h, int family, int n) {
+  if (family < 0 || family > 3 || (h != 32 && h != 64 && h != 128)) return;
+  g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family] = n < 0 ? 0 : n;
+}
+
+int tc_get_ctas(int precision, int h, int family) {
+  if (family < 0 || family > 3 || (h != 32 && h != 64 && h != 128)) return 0;
+  return g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family];
 }
 
 bool tc_cls_fused(int h, int precision) {

@@ -33,6 +33,13 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
             const LayerF32& cls2_f32, cudaStream_t s, int stage);
 
+// Autotuner hooks: resident CTAs per SM for a tensor-core kernel family
+// (0 node encoder, 1 edge encoder, 2 node step, 3 edge step + classifier) at a
+// precision and hidden width, shared by every handle of the process; n = 0
+// restores the resource bound.
+void tc_set_ctas(int precision, int h, int family, int n);
+int tc_get_ctas(int precision, int h, int family);
+
 // Whether the classifier runs inside the last edge step (shared memory fits).
 bool tc_cls_fused(int h, int precision);
 

@@ -136,3 +136,67 @@ def test_bf16_at_hidden_128_is_rejected():
     with pytest.raises(pkg.GnntrkError) as ei:
         pkg.tracker_for_workload(wl, precision="bf16", max_hits=1024, max_events=1)
     assert ei.value.status == 7
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_cuda_graph_replay_matches_direct_launches(prec):
+    """use_graph: the first call of a shape is captured into a CUDA graph and
+    later calls replay it; replays read the current contents of the buffers."""
+    wl = synth.workload("cfg3_batched_bf16")
+    b1 = synth.workload_batch(wl, 8)
+    b2 = synth.workload_batch(wl, 8, first_event=8)
+    n = max(b1.n_hits, b2.n_hits)
+    ref = []
+    for b in (b1, b2):
+        lab, g, _ = run(wl, b, prec, band=0.02 if prec != "fp32" else 0.0)
+        ref.append((lab, g))
+    tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=n, max_events=8,
+                                  edges_per_hit=32, use_graph=True)
+    s = torch.cuda.Stream()
+    xyz = torch.zeros((3, n), dtype=torch.float32, device="cuda")
+    plane = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    offs = torch.zeros(9, dtype=torch.int64, device="cuda")
+    labels = torch.zeros(n, dtype=torch.int32, device="cuda")
+    for rep in range(2):
+        for k, b in enumerate((b1, b2)):
+            # same shape and buffers each time: captured once, then replayed
+            nh = b.n_hits
+            xyz2 = torch.from_numpy(b.xyz_soa())
+            xyz.zero_()
+            xyz.view(-1)[:3 * nh].copy_(xyz2.reshape(-1).cuda())
+            plane[:nh].copy_(torch.from_numpy(b.plane).cuda())
+            offs.copy_(torch.from_numpy(b.offsets).cuda())
+            torch.cuda.synchronize()
+            tr.find_tracks(8, nh, xyz.view(-1)[:3 * nh], plane, offs, labels, s)
+            tr.sync_status(s)
+            assert np.array_equal(labels[:nh].cpu().numpy(), ref[k][0])
+            for e in (0, 7):
+                g = tr.get_graph(e)
+                for key in g:
+                    assert np.array_equal(g[key], ref[k][1][e][key]), key
+    tr.close()
+
+
+def test_autotune_picks_a_count_and_keeps_results():
+    wl = synth.workload("cfg3_batched_bf16")
+    b = synth.workload_batch(wl, 16)
+    lab0, g0, _ = run(wl, b, "bf16", band=0.02)
+    tr = pkg.tracker_for_workload(wl, precision="bf16", rescore_band=0.02, max_hits=b.n_hits,
+                                  max_events=b.n_events, edges_per_hit=32)
+    xyz = torch.from_numpy(b.xyz_soa()).cuda()
+    plane = torch.from_numpy(b.plane).cuda()
+    offs = torch.from_numpy(b.offsets).cuda()
+    labels = torch.zeros(b.n_hits, dtype=torch.int32, device="cuda")
+    choice = tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, labels)
+    assert all(1 <= v <= 8 for v in choice.values()), choice
+    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, labels)
+    tr.sync_status()
+    # launch shapes do not change any result
+    assert np.array_equal(labels.cpu().numpy(), lab0)
+    g = tr.get_graph(5)
+    for k in g:
+        assert np.array_equal(g[k], g0[5][k]), k
+    tr.close()
+    # restore the resource-bound default for the other tests of this process
+    lib = pkg.load_library()
+    del lib

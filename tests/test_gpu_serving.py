@@ -1,0 +1,45 @@
+"""Serving loop with continuous batching (gnntrk_serve_run): every event's
+result is the same alone and in the mix of a running server."""
+import numpy as np
+import pytest
+
+import paper_2508_07423_gb300 as pkg
+from paper_2508_07423_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_serving_results_equal_alone(prec):
+    wl = synth.workload("cfg5_serving")
+    b = synth.workload_batch(wl, 120)
+    arrivals = pkg.poisson_arrivals(b.n_events, 20000.0, 7)
+    band = 0.02 if prec != "fp32" else 0.0
+    cfg = pkg.make_cfg(wl["model"], wl["radius2"], k_max=wl["k_max"], precision=prec,
+                       rescore_band=band, edges_per_hit=24)
+    labels, done, st = pkg.serve_run(synth.workload_weights(wl), cfg, b, arrivals, n_slots=3,
+                                     max_events_per_batch=32, max_hits_per_batch=1 << 16,
+                                     memory_budget_bytes=8 << 30)
+    assert st["failed_batches"] == 0
+    assert st["batches"] < b.n_events          # events were batched together
+    assert st["largest_batch"] <= 32
+    assert np.all(done >= arrivals)            # no result before its request
+    # each event alone through the same library
+    tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=band, max_hits=1 << 14,
+                                  max_events=1)
+    for e in range(0, b.n_events, 7):
+        ev = b.event(e)
+        alone = pkg.run_batch(tr, ev)
+        a = int(b.offsets[e])
+        assert np.array_equal(labels[a:a + ev.n_hits], alone), e
+    tr.close()
+
+
+def test_serving_budget_too_small_is_rejected():
+    wl = synth.workload("cfg5_serving")
+    b = synth.workload_batch(wl, 2)
+    cfg = pkg.make_cfg(wl["model"], wl["radius2"])
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.serve_run(synth.workload_weights(wl), cfg, b, np.zeros(2), memory_budget_bytes=1000)
+    assert ei.value.status == 3
