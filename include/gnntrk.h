@@ -225,15 +225,17 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
                            int64_t* runs);
 
 /*
- * Autotuner of the tensor-core kernels. Runs the given call repeatedly (it is
- * a real call: inputs, outputs and stream as for gnntrk_find_tracks), timing
- * each tensor-core kernel family (node encoder, edge encoder, node step, edge
- * step with classifier) under 1..8 resident CTAs per SM (capped by the shared
- * memory, registers and tensor-memory columns each CTA needs), keeps the
- * fastest count per family and returns it in choice[0..3] (host int32 [8] or
- * NULL; other entries 0). The choice applies to every handle of the process
- * with the same precision and hidden width. Synchronous. FP32 handles have
- * nothing to tune (returns OK, choices 0). Errors: as gnntrk_find_tracks and
+ * Autotuner. Runs the given call repeatedly (a real call: inputs, outputs and
+ * stream as for gnntrk_find_tracks) and times, per kernel family:
+ *   - tensor-core kernels (BF16/FP8 handles): 1..8 resident CTAs per SM, capped
+ *     by the shared memory, registers and tensor-memory columns each CTA needs;
+ *     choice[0..3] = node encoder, edge encoder, node step, edge step;
+ *   - FP32 SIMT kernels (FP32 handles, and the FP32 re-score of BF16/FP8 handles
+ *     with a re-score band): tile-shape variant 0 or 1 (rows per tile, threads,
+ *     columns per thread); choice[4..6] = encoders, node step, edge step.
+ * The fastest setting of each family is kept and applies to every handle of
+ * the process with the same precision and hidden width. choice: host int32 [8]
+ * or NULL (entry 7 is 0). Synchronous. Errors: as gnntrk_find_tracks and
  * gnntrk_sync_status.
  */
 gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits,

@@ -220,8 +220,10 @@ class Tracker:
                                             _ptr(plane), _ptr(offsets), _ptr(out_labels),
                                             ctypes.c_void_p(s),
                                             ch.ctypes.data_as(ctypes.c_void_p)))
-        return {"node_prep": int(ch[0]), "edge_encoder": int(ch[1]), "node_update": int(ch[2]),
-                "edge_update": int(ch[3])}
+        return {"tc_node_prep": int(ch[0]), "tc_edge_encoder": int(ch[1]),
+                "tc_node_update": int(ch[2]), "tc_edge_update": int(ch[3]),
+                "f32_encoders": int(ch[4]), "f32_node_update": int(ch[5]),
+                "f32_edge_update": int(ch[6])}
 
     def set_profiling(self, enable: bool):
         self._check(self._L.gnntrk_set_profiling(self._h, int(bool(enable))))

@@ -576,43 +576,83 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
   if (!h) return GNNTRK_ERR_INVALID_ARG;
   if (choice)
     for (int i = 0; i < 8; ++i) choice[i] = 0;
-  if (h->cfg.precision == GNNTRK_FP32) return GNNTRK_OK;  // nothing to tune
-  const char* names[4] = {"node_prep", "edge_encoder", "node_update", "edge_update"};
-  double best_t[4] = {1e30, 1e30, 1e30, 1e30};
-  int best_n[4] = {0, 0, 0, 0};
-  const bool was_profiling = h->profiling;
+  const bool tc = h->cfg.precision != GNNTRK_FP32;
   const int prec = h->cfg.precision, hd = h->h;
-  for (int n = 1; n <= 8; ++n) {
-    for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, n);
+  const bool was_profiling = h->profiling;
+  // time one candidate: warm-up call, then two profiled calls; stage times
+  auto trial = [&](std::vector<std::pair<std::string, double>>& out) -> gnntrk_status {
+    gnntrk_set_profiling(h, 0);
     gnntrk_status st = gnntrk_find_tracks(h, n_events, n_hits, hits_xyz, plane, offsets,
-                                          out_labels, stream);  // warm-up
+                                          out_labels, stream);
     if (!st) st = gnntrk_sync_status(h, stream);
-    if (st) {
-      for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, 0);
-      return st;
-    }
+    if (st) return st;
     gnntrk_set_profiling(h, 1);
     for (int r = 0; r < 2 && !st; ++r)
       st = gnntrk_find_tracks(h, n_events, n_hits, hits_xyz, plane, offsets, out_labels, stream);
     collect_stages(h);
-    for (auto& sa : h->stages)
-      for (int f = 0; f < 4; ++f)
-        if (sa.name == names[f] && sa.ms < best_t[f]) {
-          best_t[f] = sa.ms;
+    out.clear();
+    for (auto& sa : h->stages) out.push_back({sa.name, sa.ms});
+    gnntrk_set_profiling(h, 0);
+    return st;
+  };
+  auto stage_ms = [](const std::vector<std::pair<std::string, double>>& v, const char* n) {
+    for (auto& p : v)
+      if (p.first == n) return p.second;
+    return 1e30;
+  };
+  std::vector<std::pair<std::string, double>> t;
+  gnntrk_status st = GNNTRK_OK;
+  // 1. tensor-core kernels: resident CTAs per SM (choice[0..3])
+  if (tc) {
+    const char* names[4] = {"node_prep", "edge_encoder", "node_update", "edge_update"};
+    double best_t[4] = {1e30, 1e30, 1e30, 1e30};
+    int best_n[4] = {0, 0, 0, 0};
+    for (int n = 1; n <= 8 && !st; ++n) {
+      for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, n);
+      st = trial(t);
+      for (int f = 0; f < 4; ++f) {
+        const double v = stage_ms(t, names[f]);
+        if (v < best_t[f]) {
+          best_t[f] = v;
           best_n[f] = n;
         }
-    gnntrk_set_profiling(h, 0);
-    if (st) break;
+      }
+    }
+    for (int f = 0; f < 4; ++f) {
+      tc_set_ctas(prec, hd, f, best_n[f]);
+      if (choice) choice[f] = best_n[f];
+    }
   }
-  for (int f = 0; f < 4; ++f) {
-    tc_set_ctas(prec, hd, f, best_n[f]);
-    if (choice) choice[f] = best_n[f];
+  // 2. FP32 kernels (the FP32 path, or the re-score of a tensor-core path):
+  //    tile-shape variant per family (choice[4..6])
+  const bool fp32_runs = !tc || h->cfg.rescore_band > 0.f;
+  if (fp32_runs && !st) {
+    const char* n32[3][2] = {{"edge_encoder", "rescore_edge_encoder"},
+                             {"node_update", "rescore_node_update"},
+                             {"edge_update", "rescore_edge_update"}};
+    double best_t[3] = {1e30, 1e30, 1e30};
+    int best_v[3] = {0, 0, 0};
+    for (int v = 0; v < 2 && !st; ++v) {
+      for (int f = 0; f < 3; ++f) f32_set_variant(hd, f, v);
+      st = trial(t);
+      for (int f = 0; f < 3; ++f) {
+        const double ms = stage_ms(t, n32[f][tc ? 1 : 0]);
+        if (ms < best_t[f]) {
+          best_t[f] = ms;
+          best_v[f] = v;
+        }
+      }
+    }
+    for (int f = 0; f < 3; ++f) {
+      f32_set_variant(hd, f, best_v[f]);
+      if (choice) choice[4 + f] = best_v[f];
+    }
   }
   if (was_profiling) gnntrk_set_profiling(h, 1);
   // shapes captured before tuning would keep the old launch configuration
   for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
   h->graphs.clear();
-  return GNNTRK_OK;
+  return st;
 }
 
 gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream) {

@@ -158,6 +158,11 @@ void launch_edge_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const
                             int h, float cut_logit, bool rescore_only, float band_lo,
                             float band_hi, Sel sel, cudaStream_t s);
 
+// FP32 tile-shape variant (0 or 1) per kernel family (0 encoders, 1 node step,
+// 2 edge step + classifier), process wide; chosen by the autotuner.
+void f32_set_variant(int h, int family, int v);
+int f32_get_variant(int h, int family);
+
 // connected components
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s);
 

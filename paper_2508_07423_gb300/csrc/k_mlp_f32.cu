@@ -29,9 +29,45 @@ int device_sms();
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;                      // embedding kernel
 constexpr int kRowGroups = 32;                     // lanes of a warp
-constexpr int kColGroups = kThreads / kRowGroups;  // warps of a block
+constexpr int kColGroups = kThreads / kRowGroups;  // warps of the embedding block
+
+// Interaction-network tile shape per hidden width: NT threads in NCG column
+// groups (warps w with the same w % NCG share columns), TM rows. Per k a warp
+// reads RM rows of A (RM wavefronts) and CW weights (CW/4 uniform loads) for
+// RM x CW FMAs per lane, so RM * CW / 4 FMA cycles per RM + CW / 4 wavefronts.
+// Two variants per width; the autotuner picks one per kernel family.
+template <int H, int V>
+struct Shape;
+template <>
+struct Shape<32, 0> {
+  static constexpr int NT = 256, NCG = 8, TM = 128;  // RM 4, CW 4
+};
+template <>
+struct Shape<32, 1> {
+  static constexpr int NT = 256, NCG = 4, TM = 128;  // RM 2, CW 8
+};
+template <>
+struct Shape<64, 0> {
+  static constexpr int NT = 256, NCG = 8, TM = 64;   // RM 2, CW 8
+};
+template <>
+struct Shape<64, 1> {
+  static constexpr int NT = 128, NCG = 4, TM = 64;   // RM 2, CW 16
+};
+template <>
+struct Shape<128, 0> {
+  static constexpr int NT = 256, NCG = 8, TM = 64;   // RM 2, CW 16
+};
+template <>
+struct Shape<128, 1> {
+  static constexpr int NT = 128, NCG = 4, TM = 64;   // RM 2, CW 32
+};
+
+// Variant chosen per (hidden index, kernel family: 0 encoders, 1 node step,
+// 2 edge step and classifier); set by the autotuner, process wide.
+int g_f32_variant[3][3] = {};
 
 enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
                    G_EDGE_UPD_CLS = 4, G_CLS = 5 };
@@ -162,10 +198,11 @@ __host__ __device__ constexpr int g_nseg(int mode) {
   return mode == G_NODE_ENC ? 0 : (mode == G_EDGE_ENC ? 2 : (mode == G_CLS ? 1 : 3));
 }
 
-template <int H, int TM, int MODE>
-__global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
-  constexpr int RM = TM / kRowGroups;
-  constexpr int CW = H / kColGroups;
+template <int H, int MODE, int V>
+__global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
+  constexpr int NT = Shape<H, V>::NT, NCG = Shape<H, V>::NCG, TM = Shape<H, V>::TM;
+  constexpr int RM = TM / (NT / NCG);
+  constexpr int CW = H / NCG;
   constexpr int NSEG = g_nseg(MODE);
   constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
   constexpr int KA = K1 > 4 ? K1 : 4;
@@ -176,15 +213,15 @@ __global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
   if (input_bad(w)) return;
   int lo, hi;
   if (!sel_rows(p.b, w, p.sel, MODE != G_NODE_ENC && MODE != G_NODE_UPD, lo, hi)) return;
-  const int tid = threadIdx.x;
-  const int r0 = (tid % kRowGroups) * RM;
-  const int c0 = (tid / kRowGroups) * CW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = ((warp / NCG) * 32 + lane) * RM;
+  const int c0 = (warp % NCG) * CW;
   const int E = clamp_edges(w.counters, w.e_cap);
 
   for (int base = lo + blockIdx.x * TM; base < hi; base += gridDim.x * TM) {
     // ---- gather: task t = (segment t / TM, row t % TM) --------------------
     if constexpr (MODE == G_NODE_ENC) {
-      for (int r = tid; r < TM; r += kThreads) {
+      for (int r = tid; r < TM; r += NT) {
         const int v = base + r;
         float f0 = 0.f, f1 = 0.f, f2 = 0.f;
         if (v < hi) {
@@ -198,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
         As[2 * TM + r] = f2;
       }
     } else {
-      for (int t = tid; t < NSEG * TM; t += kThreads) {
+      for (int t = tid; t < NSEG * TM; t += NT) {
         const int seg = t / TM, r = t % TM, row = base + r;
         const int k0 = seg * H;
         if (row >= hi) {
@@ -238,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
       tile_layer<RM, CW, TM>(As, K1, p.m.l1, r0, c0, acc);
       tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
       __syncthreads();
-      for (int r = tid; r < TM; r += kThreads) col_ln_relu<TM>(Hs, H, r);
+      for (int r = tid; r < TM; r += NT) col_ln_relu<TM>(Hs, H, r);
       __syncthreads();
       // ---- layer 2 + residual ---------------------------------------------
       tile_layer<RM, CW, TM>(Hs, H, p.m.l2, r0, c0, acc);
@@ -261,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) k_gnn_f32(const GnnArgs p) {
       __syncthreads();  // everyone is done reading Hs (layer 2 above)
       tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
       __syncthreads();
-      for (int r = tid; r < TM; r += kThreads) {
+      for (int r = tid; r < TM; r += NT) {
         col_ln_relu<TM>(Hs, H, r);
         const int row = base + r;
         if (row < hi) {
@@ -395,31 +432,39 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   return n;
 }
 
-template <int H>
-constexpr int tile_rows() {
-  return H <= 32 ? 128 : 64;
-}
-
-template <int H, int MODE>
+template <int H, int MODE, int V>
 size_t gnn_smem() {
-  constexpr int TM = tile_rows<H>();
+  constexpr int TM = Shape<H, V>::TM;
   constexpr int NSEG = g_nseg(MODE);
   constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
   return size_t((K1 > 4 ? K1 : 4) + H) * TM * sizeof(float);
 }
 
-template <int H, int MODE>
-void launch_gnn(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
-  constexpr int TM = tile_rows<H>();
-  const size_t smem = gnn_smem<H, MODE>();
-  const void* fn = (const void*)k_gnn_f32<H, TM, MODE>;
-  const int full = device_sms() * blocks_per_sm(fn, kThreads, smem);
+template <int H, int MODE, int V>
+void launch_gnn_v(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
+  constexpr int TM = Shape<H, V>::TM, NT = Shape<H, V>::NT;
+  const size_t smem = gnn_smem<H, MODE, V>();
+  const void* fn = (const void*)k_gnn_f32<H, MODE, V>;
+  const int full = device_sms() * blocks_per_sm(fn, NT, smem);
   dim3 grid(full, 1);
   if (a.sel.list != nullptr)
     grid = dim3(8, a.sel.max_list > 0 ? a.sel.max_list : 1);
   else if (rows_hint >= 0)
     grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, TM)));
-  k_gnn_f32<H, TM, MODE><<<grid, kThreads, smem, s>>>(a);
+  k_gnn_f32<H, MODE, V><<<grid, NT, smem, s>>>(a);
+}
+
+constexpr int f32_family(int mode) {
+  return (mode == G_NODE_ENC || mode == G_EDGE_ENC) ? 0 : (mode == G_NODE_UPD ? 1 : 2);
+}
+
+template <int H, int MODE>
+void launch_gnn(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
+  const int v = g_f32_variant[H == 32 ? 0 : (H == 64 ? 1 : 2)][f32_family(MODE)];
+  if (v == 1)
+    launch_gnn_v<H, MODE, 1>(a, rows_hint, s);
+  else
+    launch_gnn_v<H, MODE, 0>(a, rows_hint, s);
 }
 
 void launch_gnn_any(int h, int mode, const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
@@ -451,6 +496,16 @@ GnnArgs gnn_args(const Batch& b, const Ws& w, Sel sel) {
 }
 
 }  // namespace
+
+void f32_set_variant(int h, int family, int v) {
+  if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return;
+  g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family] = (v == 1) ? 1 : 0;
+}
+
+int f32_get_variant(int h, int family) {
+  if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return 0;
+  return g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family];
+}
 
 void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,
                           const Mlp2F32& node_enc, int D, int h, const GraphParams& g,
