@@ -313,6 +313,8 @@ def main():
     out.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, batch, labels.cpu().numpy(), tr, a.cpu_seconds)
+        if not a.no_plain:
+            out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -476,6 +478,105 @@ def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
             "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4),
             "edge_decision_agreement": round(agree / max(union, 1), 6),
             "edge_decision_events": min(4, done), "max_score_error": max_err}
+
+
+def fp8_report(pkg, torch, dev, stream, chunk=1000):
+    """Config 4: FP8-E4M3 (per-channel weight scales, per-row activation
+    scales, FP32 accumulate), config-1 model at hidden 128, 10000 events of
+    200 tracks. Throughput over all events; agreement with the FP32 path on all
+    events; score error, decision agreement and track efficiency against the
+    FP64 oracle on a sample (one event per host core)."""
+    try:
+        import oracle
+        from oracle import metrics
+        wl = synth.workload("cfg4_batched_fp8")
+        n = wl["n_events"]
+        chunks = [synth.workload_batch(wl, chunk, first_event=c) for c in range(0, n, chunk)]
+        maxh = max(b.n_hits for b in chunks)
+        res = {}
+        graphs = {}
+        for prec in ("fp8", "fp32"):
+            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=maxh, max_events=chunk,
+                                          edges_per_hit=16, use_graph=True)
+            ms, agree_n, edges_n, kept = 0.0, 0, 0, []
+            for ci, b in enumerate(chunks):
+                xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+                plane = torch.from_numpy(b.plane).to(dev)
+                offs = torch.from_numpy(b.offsets).to(dev)
+                lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+                tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+                tr.sync_status(stream)
+                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    s_.record(stream)
+                    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+                    e_.record(stream)
+                e_.synchronize()
+                tr.sync_status(stream)
+                ms += s_.elapsed_time(e_)
+                if ci == 0:
+                    graphs[prec] = [tr.get_graph(e) for e in range(b.n_events)]
+                    res[prec + "_labels0"] = lab.cpu().numpy()
+            res[prec] = {"events_per_s": round(n / (ms / 1e3), 1), "ms_per_1000_events": round(ms / len(chunks), 3)}
+            tr.close()
+        # FP8 vs FP32 on the first chunk (same graph: the embedding is FP32 in both)
+        g8, g32 = graphs["fp8"], graphs["fp32"]
+        d = np.concatenate([np.abs(1 / (1 + np.exp(-a["logit"].astype(np.float64))) -
+                                   1 / (1 + np.exp(-b["logit"].astype(np.float64))))
+                            for a, b in zip(g8, g32)])
+        agree32 = np.mean(np.concatenate([a["kept"] == b["kept"] for a, b in zip(g8, g32)]))
+        # against the FP64 oracle on a sample
+        sh = synth.shape_of(wl)
+        model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+        fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+        cores = os.cpu_count() or 1
+        b0 = chunks[0]
+        sample = list(range(min(cores, b0.n_events)))
+        sub = b0.subset(sample)
+        t0 = time.perf_counter()
+        lab_ref, _ = oracle.find_tracks_batch(model, sub.x, sub.y, sub.z, sub.plane, sub.offsets,
+                                              wl["radius2"], wl["k_max"], wl["cut"],
+                                              threads=cores, feat_scale=fs)
+        t_oracle = time.perf_counter() - t0
+        agree = union = 0
+        errs = []
+        import concurrent.futures as cf
+
+        def one(e):  # the oracle call releases the GIL (ctypes)
+            ev = b0.event(e)
+            return e, oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                               wl["k_max"], wl["cut"], feat_scale=fs)
+        with cf.ThreadPoolExecutor(4) as ex:
+            refs = list(ex.map(one, sample[:4]))
+        for e, ref in refs:
+            O = {(int(x), int(y)): (int(k), float(l)) for x, y, k, l in zip(ref.src, ref.dst, ref.keep, ref.logit)}
+            G = {(int(x), int(y)): (int(k), float(l)) for x, y, k, l in
+                 zip(g8[e]["src"], g8[e]["dst"], g8[e]["kept"], g8[e]["logit"])}
+            for key in set(O) | set(G):
+                agree += O.get(key, (0, 0))[0] == G.get(key, (0, 0))[0]
+                union += 1
+                if key in O and key in G:
+                    errs.append(abs(1 / (1 + math.exp(-O[key][1])) - 1 / (1 + math.exp(-G[key][1]))))
+        nh = int(sub.n_hits)
+        lab8 = res["fp8_labels0"][:nh]
+        c8 = metrics.batch_counts(lab8, sub.pid, sub.offsets).summary()
+        co = metrics.batch_counts(lab_ref, sub.pid, sub.offsets).summary()
+        return {"workload": f"cfg4_batched_fp8: {n} events, {wl['description']}",
+                "fp8": res["fp8"], "fp32": res["fp32"],
+                "vs_fp32_first_1000_events": {"max_score_error": round(float(d.max()), 5),
+                                              "mean_score_error": round(float(d.mean()), 6),
+                                              "edge_decision_agreement": round(float(agree32), 6)},
+                "vs_fp64_oracle": {"events": len(sample),
+                                   "edge_decision_agreement (4 events)": round(agree / max(union, 1), 6),
+                                   "max_score_error (4 events)": round(max(errs), 5) if errs else None,
+                                   "mean_score_error (4 events)": round(float(np.mean(errs)), 6) if errs else None,
+                                   "track_efficiency_fp8": round(c8["efficiency"], 6),
+                                   "track_efficiency_oracle": round(co["efficiency"], 6),
+                                   "track_efficiency_delta_pp": round(100 * abs(c8["efficiency"] - co["efficiency"]), 4),
+                                   "oracle_seconds": round(t_oracle, 2), "oracle_cores": cores}}
+    except Exception as ex:  # reported, not fatal
+        import traceback
+        return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
 
 
 def run_reference(a, rank, world):
