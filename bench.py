@@ -131,13 +131,18 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
         precision, stage = "fp32", stage[len("rescore_"):]
     if stage == "edge_update":
         if precision == "fp32":
-            return "alu", E * 2.0 * (3 * h * h + h * h), "flop"
+            # W_e e (h x h) and the second layer (h x h); the h_src / h_dst
+            # products come precomputed per hit from the node step
+            return "alu", E * 2.0 * (h * h + h * h), "flop"
         # read e, h_src, h_dst rows; write e
         return "hbm", E * (4 * h * sb + 8), "byte"
     if stage == "node_update":
         if precision == "fp32":
-            return "alu", N * 2.0 * (3 * h * h + h * h), "flop"
+            # node network (3h x h, h x h) and the two projections (2 x h x h)
+            return "alu", N * 2.0 * (3 * h * h + h * h + 2 * h * h), "flop"
         return "hbm", N * 2 * h * sb + E * 2 * h * sb + E * 8, "byte"
+    if stage == "edge_encoder" and precision == "fp32":
+        return "alu", E * 2.0 * h * h, "flop"
     if stage in ("radius_count", "radius_fill"):
         return "hbm", N * D * 4 + N * 4 + (E * 12 if stage == "radius_fill" else 0), "byte"
     if stage == "components":

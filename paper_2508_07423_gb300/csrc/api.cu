@@ -24,6 +24,7 @@ struct gnntrk_handle {
   float* d_wf32 = nullptr;
   LayerF32 embed[kMaxEmbedLayers]{};
   Mlp2F32 node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
+  EdgeProj enc_proj{}, step_proj[kMaxIters]{};  // h_src / h_dst column blocks
   // tensor-core weights (BF16 / FP8 packed operands)
   TcModel tc{};
   void* d_wtc = nullptr;
@@ -157,6 +158,9 @@ gnntrk_status upload_f32(gnntrk_handle* h, const std::vector<HostLayer>& L) {
     img.resize(img.size() + ldo[l], 0.f);
     for (int o = 0; o < L[l].out; ++o) img[bofs[l] + o] = L[l].b[o];
   }
+  // a zero bias for the projection views
+  const size_t zofs = img.size();
+  img.resize(img.size() + size_t((h->h + 3) & ~3) + 4, 0.f);
   gnntrk_status st = alloc_n(h, &h->d_wf32, img.size());
   if (st) return st;
   cudaError_t e = cudaMemcpy(h->d_wf32, img.data(), img.size() * 4, cudaMemcpyHostToDevice);
@@ -176,6 +180,13 @@ gnntrk_status upload_f32(gnntrk_handle* h, const std::vector<HostLayer>& L) {
     c += 4;
   }
   h->cls = {lay(c), lay(c + 1)};
+  // projection views: rows [k0, k0 + h) of a transposed first layer
+  const float* zero = h->d_wf32 + zofs;
+  auto view = [&](const LayerF32& l1, int k0) {
+    return LayerF32{l1.WT + size_t(k0) * l1.ldo, zero, h->h, l1.out, l1.ldo};
+  };
+  h->enc_proj = {view(h->edge_enc.l1, 0), view(h->edge_enc.l1, h->h)};
+  for (int k = 0; k < h->K; ++k) h->step_proj[k] = {view(h->edge[k].l1, h->h), view(h->edge[k].l1, 2 * h->h)};
   return GNNTRK_OK;
 }
 
@@ -202,6 +213,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.in_edge, E);
   add(&w.hstate, H * hd);
   add(&w.estate, E * hd);
+  add(&w.pstate, H * 2 * hd);
   if (c.precision != GNNTRK_FP32) {
     add(&w.hstate16, H * hd);
     add(&w.estate16, E * hd);
@@ -307,8 +319,8 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   const bool tc = c.precision != GNNTRK_FP32;
   stage(h, "node_prep", s, tc ? 2 : 1, [&] {
     if (!tc)
-      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, true, true,
-                           all, s);
+      launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
+                           true, true, all, s);
     else
       tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s);
   });
@@ -327,7 +339,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {
       stage(h, "node_update", s, 1,
-            [&] { launch_node_update_f32(b, w, h->node[k], h->h, all, s); });
+            [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, all, s); });
       stage(h, "edge_update", s, 1, [&] {
         launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
                                g.cut_logit, false, 0.f, 0.f, all, s);
@@ -358,14 +370,14 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
       const Sel sel{w.rerun_list, w.counters + C_RERUN, b.n_events};
       stage(h, "rescore_node_prep", s, 1, [&] {
-        launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->D, h->h, g, false, true,
-                             sel, s);
+        launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
+                             false, true, sel, s);
       });
       stage(h, "rescore_edge_encoder", s, 1,
             [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s); });
       for (int k = 0; k < h->K; ++k) {
         stage(h, "rescore_node_update", s, 1,
-              [&] { launch_node_update_f32(b, w, h->node[k], h->h, sel, s); });
+              [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, sel, s); });
         stage(h, "rescore_edge_update", s, 1, [&] {
           launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
                                  g.cut_logit, true, band_lo, band_hi, sel, s);

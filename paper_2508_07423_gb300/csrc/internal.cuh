@@ -87,6 +87,7 @@ struct Ws {
   int32_t* in_edge;     // [Ecap] edge ids grouped by target, ascending
   float* hstate;        // [H][h]   FP32 node state (FP32 path and re-score)
   float* estate;        // [Ecap][h] FP32 edge state
+  float* pstate;        // [H][2h]  FP32 node projections for the next edge layer
   __nv_bfloat16* hstate16;  // [H][h]   BF16 node state (tensor-core paths)
   __nv_bfloat16* estate16;  // [Ecap][h] BF16 edge state
   float* logit;         // [Ecap]
@@ -133,10 +134,20 @@ struct Sel {
 // launchers (host functions), one per kernel family
 // ---------------------------------------------------------------------------
 void launch_sort(const Batch& b, const Ws& w, int n_planes, cudaStream_t s);
-// embedding (when do_embed) and FP32 node encoder (when do_node_enc)
+// Column blocks of an edge layer's first Linear for the inputs h_src and
+// h_dst (views into its transposed weights, zero bias): the node kernels
+// project each node once, P[v] = [W_src h_v, W_dst h_v], and the edge kernels
+// gather P[src] and P[dst] instead of multiplying h_src and h_dst per edge.
+struct EdgeProj {
+  LayerF32 src, dst;
+};
+
+// embedding (when do_embed) and FP32 node encoder (when do_node_enc), the
+// encoder also writing the projections for the edge encoder
 void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,
-                          const Mlp2F32& node_enc, int D, int h, const GraphParams& g,
-                          bool do_embed, bool do_node_enc, Sel sel, cudaStream_t s);
+                          const Mlp2F32& node_enc, const EdgeProj& proj, int D, int h,
+                          const GraphParams& g, bool do_embed, bool do_node_enc, Sel sel,
+                          cudaStream_t s);
 void launch_radius(const Batch& b, const Ws& w, const GraphParams& g, int D, bool fill,
                    cudaStream_t s);
 // exclusive scan of n entries of `in` (each clamped to clamp_max) into out[0..n],
@@ -149,8 +160,9 @@ void launch_csc(const Batch& b, const Ws& w, cudaStream_t s);
 // FP32 SIMT interaction network
 void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
                          cudaStream_t s);
-void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
-                            cudaStream_t s);
+// node step, also writing the projections for the edge step that follows
+void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const EdgeProj& proj,
+                            int h, Sel sel, cudaStream_t s);
 // last step (cls != nullptr): also runs the classifier and writes logit/keep;
 // with rescore_only, only edges whose current logit lies in (band_lo, band_hi)
 // take the new FP32 logit and decision.

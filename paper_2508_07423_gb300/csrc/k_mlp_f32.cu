@@ -185,6 +185,7 @@ __device__ __forceinline__ void add_col(float* S, int k0, int row, const float* 
 struct GnnArgs {
   Batch b;
   Ws w;
+  EdgeProj proj;  // node kernels: projections for the next edge layer
   Mlp2F32 m;    // the sub-network of this kernel
   Mlp2F32 cls;  // classifier (G_EDGE_UPD_CLS, G_CLS)
   float fs[6];
@@ -257,12 +258,15 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
             }
           }
         } else if constexpr (MODE == G_EDGE_ENC) {
-          put_col<TM>(As, k0, r, w.hstate + size_t(seg == 0 ? w.src[row] : w.col[row]) * H, H);
+          // projections: W_src h_src (first half of P[src]), W_dst h_dst (second half of P[dst])
+          put_col<TM>(As, k0, r,
+                      w.pstate + size_t(seg == 0 ? w.src[row] : w.col[row]) * 2 * H + seg * H, H);
         } else if constexpr (MODE == G_CLS) {
           put_col<TM>(As, k0, r, w.estate + size_t(row) * H, H);
-        } else {  // edge step: [e, h_src, h_dst]
-          const float* src = seg == 0 ? w.estate + size_t(row) * H
-                                      : w.hstate + size_t(seg == 1 ? w.src[row] : w.col[row]) * H;
+        } else {  // edge step: [e, W_src h_src, W_dst h_dst]
+          const float* src =
+              seg == 0 ? w.estate + size_t(row) * H
+                       : w.pstate + size_t(seg == 1 ? w.src[row] : w.col[row]) * 2 * H + (seg - 1) * H;
           put_col<TM>(As, k0, r, src, H);
         }
       }
@@ -272,7 +276,28 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
     float acc[RM][CW];
     if constexpr (MODE != G_CLS) {
       // ---- layer 1 -> LayerNorm -> ReLU -------------------------------------
-      tile_layer<RM, CW, TM>(As, K1, p.m.l1, r0, c0, acc);
+      if constexpr (MODE == G_EDGE_ENC) {
+        // b + W_src h_src + W_dst h_dst: the products come projected
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          const float bj = p.m.l1.b[c0 + j];
+#pragma unroll
+          for (int i = 0; i < RM; ++i)
+            acc[i][j] = bj + As[(c0 + j) * TM + r0 + i] + As[(H + c0 + j) * TM + r0 + i];
+        }
+      } else if constexpr (MODE == G_EDGE_UPD || MODE == G_EDGE_UPD_CLS) {
+        // b + W_e e over the e block, plus the gathered projections
+        LayerF32 le = p.m.l1;
+        le.in = H;
+        tile_layer<RM, CW, TM>(As, H, le, r0, c0, acc);
+#pragma unroll
+        for (int j = 0; j < CW; ++j)
+#pragma unroll
+          for (int i = 0; i < RM; ++i)
+            acc[i][j] += As[(H + c0 + j) * TM + r0 + i] + As[(2 * H + c0 + j) * TM + r0 + i];
+      } else {
+        tile_layer<RM, CW, TM>(As, K1, p.m.l1, r0, c0, acc);
+      }
       tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
       __syncthreads();
       for (int r = tid; r < TM; r += NT) col_ln_relu<TM>(Hs, H, r);
@@ -326,6 +351,25 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
 #pragma unroll
           for (int j = 0; j < CW; j += 4)
             d4[j / 4] = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+        }
+      }
+      if constexpr (MODE == G_NODE_ENC || MODE == G_NODE_UPD) {
+        // ---- projections of the new node state for the next edge layer -----
+        __syncthreads();  // everyone is done reading Hs (layer 2 above)
+        tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
+        __syncthreads();
+        for (int half = 0; half < 2; ++half) {
+          tile_layer<RM, CW, TM>(Hs, H, half == 0 ? p.proj.src : p.proj.dst, r0, c0, acc);
+#pragma unroll
+          for (int i = 0; i < RM; ++i) {
+            const int row = base + r0 + i;
+            if (row < hi) {
+              float4* d4 = reinterpret_cast<float4*>(w.pstate + size_t(row) * 2 * H + half * H + c0);
+#pragma unroll
+              for (int j = 0; j < CW; j += 4)
+                d4[j / 4] = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+            }
+          }
         }
       }
     }
@@ -508,8 +552,9 @@ int f32_get_variant(int h, int family) {
 }
 
 void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,
-                          const Mlp2F32& node_enc, int D, int h, const GraphParams& g,
-                          bool do_embed, bool do_node_enc, Sel sel, cudaStream_t s) {
+                          const Mlp2F32& node_enc, const EdgeProj& proj, int D, int h,
+                          const GraphParams& g, bool do_embed, bool do_node_enc, Sel sel,
+                          cudaStream_t s) {
   if (b.n_hits <= 0) return;
   if (do_embed) {
     EmbedLayers em{};
@@ -526,6 +571,7 @@ void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, in
   if (do_node_enc) {
     GnnArgs a = gnn_args(b, w, sel);
     a.m = node_enc;
+    a.proj = proj;
     for (int i = 0; i < 6; ++i) a.fs[i] = g.fs[i];
     launch_gnn_any(h, G_NODE_ENC, a, b.n_hits, s);
   }
@@ -538,11 +584,12 @@ void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, S
   launch_gnn_any(h, G_EDGE_ENC, a, -1, s);
 }
 
-void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
-                            cudaStream_t s) {
+void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const EdgeProj& proj,
+                            int h, Sel sel, cudaStream_t s) {
   if (b.n_hits <= 0) return;
   GnnArgs a = gnn_args(b, w, sel);
   a.m = m;
+  a.proj = proj;
   launch_gnn_any(h, G_NODE_UPD, a, b.n_hits, s);
 }
 

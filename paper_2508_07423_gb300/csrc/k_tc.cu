@@ -1004,7 +1004,8 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
                   cudaStream_t s) {
   // embedding in FP32: its output feeds the threshold d^2 < r^2
   const Sel all{nullptr, nullptr, 0};
-  launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, D, h, g, true, false, all, s);
+  launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, EdgeProj{}, D, h, g, true, false, all,
+                       s);
   TcArgs a = base_args(b, w, g);
   a.ne1 = ne1_f32;
   a.W2 = static_cast<const uint8_t*>(m.node_enc.l2.B);
