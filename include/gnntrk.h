@@ -199,11 +199,29 @@ gnntrk_status gnntrk_get_graph(gnntrk_handle* h, int32_t event, int64_t capacity
 
 /*
  * Statistics of the last gnntrk_find_tracks call (synchronises the device).
- *   out: host int64 [8]: [0] total edges, [1] kept edges, [2] edges in the
- *        re-score band, [3] events re-run in FP32, [4] events, [5] hits,
- *        [6] edge capacity, [7] kernels launched by the call.
+ *   out: host int64 [10]: [0] total edges, [1] kept edges, [2] edges in the
+ *        re-score band, [3] events holding a band edge, [4] events, [5] hits,
+ *        [6] edge capacity, [7] kernels launched by the call, [8] edges and
+ *        [9] hits recomputed in FP32 by the re-score (the receptive field of
+ *        the band edges; 0 without a re-score).
  */
 gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out);
+
+/*
+ * Rows recomputed by the FP32 re-score of the last gnntrk_find_tracks call,
+ * per message-passing step (synchronises the device). The logit of an edge
+ * after K steps of the interaction network (Sec. 3.3) depends only on its
+ * K-hop neighbourhood, so the re-score evaluates, per step, only the rows in
+ * the receptive field of the band edges.
+ *   n:     length of both arrays (K + 1 entries are meaningful).
+ *   edges: host int64 [n]: edges[0] rows of the edge encoder, edges[k + 1]
+ *          rows of edge step k (edges[K] = the band edges).
+ *   hits:  host int64 [n]: hits[0] rows of the node encoder, hits[k + 1] rows
+ *          of node step k.
+ * All zero without a re-score (FP32 precision or band 0). Errors:
+ * INVALID_ARG for NULL arrays or n < 1.
+ */
+gnntrk_status gnntrk_rescore_rows(gnntrk_handle* h, int32_t n, int64_t* edges, int64_t* hits);
 
 /*
  * Per-stage device timing (instrumentation for benchmarks).

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
-           "gnntrk_autotune",
+           "gnntrk_autotune", "gnntrk_rescore_rows",
            "gnntrk_last_error", "gnntrk_destroy"]
 
 NOALLOC_MAX_HITS = 1 << 20
@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_get_graph.restype = st
     L.gnntrk_stats.argtypes = [vp, vp]
     L.gnntrk_stats.restype = st
+    L.gnntrk_rescore_rows.argtypes = [vp, i32, vp, vp]
+    L.gnntrk_rescore_rows.restype = st
     L.gnntrk_set_profiling.argtypes = [vp, i32]
     L.gnntrk_set_profiling.restype = st
     L.gnntrk_stage_times.argtypes = [vp, i32, vp, vp, vp]
@@ -205,11 +207,23 @@ class Tracker:
         self._check(self._L.gnntrk_sync_status(self._h, ctypes.c_void_p(s)))
 
     def stats(self) -> dict:
-        out = np.zeros(8, np.int64)
+        out = np.zeros(10, np.int64)
         self._check(self._L.gnntrk_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return {"edges": int(out[0]), "kept": int(out[1]), "band": int(out[2]),
                 "rerun_events": int(out[3]), "events": int(out[4]), "hits": int(out[5]),
-                "edge_capacity": int(out[6]), "launches": int(out[7])}
+                "edge_capacity": int(out[6]), "launches": int(out[7]),
+                "rescore_edges": int(out[8]), "rescore_hits": int(out[9])}
+
+    def rescore_rows(self) -> dict:
+        """Rows the FP32 re-score recomputed, per step: 'edges'[0] / 'hits'[0]
+        the encoders, [k + 1] message-passing step k."""
+        n = 18
+        e = np.zeros(n, np.int64)
+        v = np.zeros(n, np.int64)
+        self._check(self._L.gnntrk_rescore_rows(self._h, n, e.ctypes.data_as(ctypes.c_void_p),
+                                                v.ctypes.data_as(ctypes.c_void_p)))
+        k = self.cfg.iters
+        return {"edges": e[:k + 1].tolist(), "hits": v[:k + 1].tolist()}
 
     def autotune(self, n_events: int, n_hits: int, hits_xyz, plane, offsets, out_labels,
                  stream=None) -> dict:

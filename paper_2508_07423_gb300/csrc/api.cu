@@ -226,6 +226,13 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.ev_flag, c.max_events);
   add(&w.rerun_list, c.max_events);
   add(&w.ev_off, int64_t(c.max_events) + 1);
+  if (c.precision != GNNTRK_FP32) {
+    add(&w.rs_elev, E);
+    add(&w.rs_nlev, H);
+    add(&w.rs_elist, E);
+    add(&w.rs_nlist, H);
+    add(&w.rs_counts, 6 * (kMaxIters + 2));
+  }
   w.h_cap = H;
   w.e_cap = E;
   return v;
@@ -315,7 +322,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   cudaMemsetAsync(w.counters, 0, C_COUNT * sizeof(int32_t), s);
   cudaMemcpyAsync(w.ev_off, offsets, sizeof(int64_t) * (b.n_events + 1), cudaMemcpyDeviceToDevice, s);
   stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
-  const Sel all{nullptr, nullptr, 0};
+  const Sel all{nullptr, nullptr};
   const bool tc = c.precision != GNNTRK_FP32;
   stage(h, "node_prep", s, tc ? 2 : 1, [&] {
     if (!tc)
@@ -367,26 +374,37 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       const double hi = double(c.score_cut) + double(c.rescore_band);
       const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
       const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
-      stage(h, "band_mark", s, 2, [&] { tc_mark_band(b, w, band_lo, band_hi, s); });
-      const Sel sel{w.rerun_list, w.counters + C_RERUN, b.n_events};
+      // exact receptive field of the band edges, then FP32 over those rows only
+      int mk = 0;
+      stage(h, "band_mark", s, 0, [&] {
+        mk = launch_rescore_sets(b, w, band_lo, band_hi, h->K, s);
+        tc_count_band_events(b, w, s);
+      });
+      h->last_launches += mk + 1;
+      const int NL = kMaxIters + 2;
+      const int32_t* cge_e = w.rs_counts + 2 * NL;  // [k + 1]: edges of step k
+      const int32_t* cge_n = w.rs_counts + 5 * NL;  // [k + 1]: hits of step k
+      auto esel = [&](int k) { return Sel{w.rs_elist, cge_e + k + 1}; };
+      auto nsel = [&](int k) { return Sel{w.rs_nlist, cge_n + k + 1}; };
       stage(h, "rescore_node_prep", s, 1, [&] {
         launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
-                             false, true, sel, s);
+                             false, true, nsel(-1), s);
       });
       stage(h, "rescore_edge_encoder", s, 1,
-            [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, sel, s); });
+            [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, esel(-1), s); });
       for (int k = 0; k < h->K; ++k) {
-        stage(h, "rescore_node_update", s, 1,
-              [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, sel, s); });
+        stage(h, "rescore_node_update", s, 1, [&] {
+          launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, nsel(k), s);
+        });
         stage(h, "rescore_edge_update", s, 1, [&] {
           launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                                 g.cut_logit, true, band_lo, band_hi, sel, s);
+                                 g.cut_logit, true, band_lo, band_hi, esel(k), s);
         });
       }
       if (h->K == 0)
         stage(h, "rescore_edge_update", s, 1, [&] {
           launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, true, band_lo,
-                                 band_hi, sel, s);
+                                 band_hi, esel(-1), s);
         });
     }
   }
@@ -707,6 +725,25 @@ gnntrk_status gnntrk_stats(gnntrk_handle* h, int64_t* out) {
   out[5] = h->last_hits;
   out[6] = h->ws.e_cap;
   out[7] = h->last_launches;
+  out[8] = cnt[C_RERUN_EDGES];
+  out[9] = cnt[C_RERUN_HITS];
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_rescore_rows(gnntrk_handle* h, int32_t n, int64_t* edges, int64_t* hits) {
+  if (!h || !edges || !hits || n < 1) return GNNTRK_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) edges[i] = hits[i] = 0;
+  if (h->cfg.precision == GNNTRK_FP32 || h->cfg.rescore_band <= 0.f) return GNNTRK_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  const int NL = kMaxIters + 2;
+  int32_t rs[6 * NL];
+  e = cudaMemcpy(rs, h->ws.rs_counts, sizeof(rs), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "re-score counts read");
+  for (int i = 0; i < n && i <= h->K; ++i) {
+    edges[i] = rs[2 * NL + i];
+    hits[i] = rs[5 * NL + i];
+  }
   return GNNTRK_OK;
 }
 

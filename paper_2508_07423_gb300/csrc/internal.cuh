@@ -96,7 +96,12 @@ struct Ws {
   int32_t* counters;    // [C_COUNT]
   int32_t* scan_blocks; // block partials of the scan
   int32_t* ev_flag;     // [max_events] events re-run in FP32
-  int32_t* rerun_list;  // [max_events] compacted list of re-run events
+  int32_t* rerun_list;  // [max_events] (unused)
+  int32_t* rs_elev;     // [Ecap] re-score level of each edge (-2 none)
+  int32_t* rs_nlev;     // [H]    re-score level of each hit (-2 none)
+  int32_t* rs_elist;    // [Ecap] edges by level, descending
+  int32_t* rs_nlist;    // [H]    hits by level, descending
+  int32_t* rs_counts;   // [6][kMaxIters + 2] histograms, cursors, rows with level >= k
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
   int64_t h_cap, e_cap;
 };
@@ -121,14 +126,20 @@ struct GraphParams {
   float fs[6];
 };
 
-// Row selection of a row-parallel kernel: all rows of the batch (list ==
-// nullptr), or only the rows of the events list[0 .. *n_list) (device memory,
-// at most max_list entries; one grid row per list entry).
+// Row selection of a row-parallel kernel: all rows of the batch (rows ==
+// nullptr), or the rows rows[0 .. *n_rows) (device memory).
 struct Sel {
-  const int32_t* list;
-  const int32_t* n_list;
-  int max_list;
+  const int32_t* rows;
+  const int32_t* n_rows;
 };
+
+// Levels of the FP32 re-score (exact receptive field of the edges whose logit
+// lies in (band_lo, band_hi)); afterwards rs_elist / rs_nlist prefixes of
+// rs_counts[2 * (kMaxIters + 2) + k + 1] (edges) and
+// rs_counts[5 * (kMaxIters + 2) + k + 1] (hits) are the rows of step k
+// (k = -1: the encoders). Returns the number of kernels launched.
+int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
+                        cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (host functions), one per kernel family
@@ -192,27 +203,18 @@ __device__ __forceinline__ int clamp_edges(const int32_t* counters, int64_t cap)
 
 inline int div_up(int64_t a, int64_t b) { return int((a + b - 1) / b); }
 
-// Rows [lo, hi) this block works on under `sel` (false: nothing to do).
+// Positions [lo, hi) this kernel works on under `sel` (false: nothing to do);
+// position i is row sel_row(sel, i).
 __device__ __forceinline__ bool sel_rows(const Batch& b, const Ws& w, Sel sel, bool edges,
                                          int& lo, int& hi) {
-  if (sel.list == nullptr) {
-    lo = 0;
-    hi = edges ? clamp_edges(w.counters, w.e_cap) : b.n_hits;
-    return true;
-  }
-  int j = blockIdx.y;
-  if (j >= *sel.n_list) return false;
-  int ev = sel.list[j];
-  int a = int(b.offsets[ev]), c = int(b.offsets[ev + 1]);
-  if (edges) {
-    int ecap = clamp_edges(w.counters, w.e_cap);
-    lo = min(w.row_ptr[a], ecap);
-    hi = min(w.row_ptr[c], ecap);
-  } else {
-    lo = a;
-    hi = c;
-  }
-  return true;
+  lo = 0;
+  hi = edges ? clamp_edges(w.counters, w.e_cap) : b.n_hits;
+  if (sel.rows != nullptr) hi = min(hi, *sel.n_rows);
+  return hi > 0;
+}
+
+__device__ __forceinline__ int sel_row(Sel sel, int pos) {
+  return sel.rows != nullptr ? sel.rows[pos] : pos;
 }
 
 }  // namespace gnntrk

@@ -223,10 +223,10 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
     // ---- gather: task t = (segment t / TM, row t % TM) --------------------
     if constexpr (MODE == G_NODE_ENC) {
       for (int r = tid; r < TM; r += NT) {
-        const int v = base + r;
+        const int pos = base + r;
         float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-        if (v < hi) {
-          const float4 q = w.pos[v];
+        if (pos < hi) {
+          const float4 q = w.pos[sel_row(p.sel, pos)];
           f0 = q.x / p.fs[3];
           f1 = q.y / p.fs[4];
           f2 = q.z / p.fs[5];
@@ -237,12 +237,13 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
       }
     } else {
       for (int t = tid; t < NSEG * TM; t += NT) {
-        const int seg = t / TM, r = t % TM, row = base + r;
+        const int seg = t / TM, r = t % TM, pos = base + r;
         const int k0 = seg * H;
-        if (row >= hi) {
+        if (pos >= hi) {
           for (int k = 0; k < H; ++k) As[(k0 + k) * TM + r] = 0.f;
           continue;
         }
+        const int row = sel_row(p.sel, pos);
         if constexpr (MODE == G_NODE_UPD) {
           if (seg == 0) {
             put_col<TM>(As, k0, r, w.hstate + size_t(row) * H, H);
@@ -325,8 +326,8 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
       __syncthreads();
       for (int r = tid; r < TM; r += NT) {
         col_ln_relu<TM>(Hs, H, r);
-        const int row = base + r;
-        if (row < hi) {
+        if (base + r < hi) {
+          const int row = sel_row(p.sel, base + r);
           float lg = p.cls.l2.b[0];
           for (int k = 0; k < H; ++k) lg = fmaf(Hs[k * TM + r], p.cls.l2.WT[k * p.cls.l2.ldo], lg);
           bool write = true;
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
       float* dst = (MODE == G_NODE_ENC || MODE == G_NODE_UPD) ? w.hstate : w.estate;
 #pragma unroll
       for (int i = 0; i < RM; ++i) {
-        const int row = base + r0 + i;
-        if (row < hi) {
+        if (base + r0 + i < hi) {
+          const int row = sel_row(p.sel, base + r0 + i);
           float4* d4 = reinterpret_cast<float4*>(dst + size_t(row) * H + c0);
 #pragma unroll
           for (int j = 0; j < CW; j += 4)
@@ -362,8 +363,8 @@ __global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
           tile_layer<RM, CW, TM>(Hs, H, half == 0 ? p.proj.src : p.proj.dst, r0, c0, acc);
 #pragma unroll
           for (int i = 0; i < RM; ++i) {
-            const int row = base + r0 + i;
-            if (row < hi) {
+            if (base + r0 + i < hi) {
+              const int row = sel_row(p.sel, base + r0 + i);
               float4* d4 = reinterpret_cast<float4*>(w.pstate + size_t(row) * 2 * H + half * H + c0);
 #pragma unroll
               for (int j = 0; j < CW; j += 4)
@@ -491,9 +492,7 @@ void launch_gnn_v(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
   const void* fn = (const void*)k_gnn_f32<H, MODE, V>;
   const int full = device_sms() * blocks_per_sm(fn, NT, smem);
   dim3 grid(full, 1);
-  if (a.sel.list != nullptr)
-    grid = dim3(8, a.sel.max_list > 0 ? a.sel.max_list : 1);
-  else if (rows_hint >= 0)
+  if (a.sel.rows == nullptr && rows_hint >= 0)
     grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, TM)));
   k_gnn_f32<H, MODE, V><<<grid, NT, smem, s>>>(a);
 }

@@ -679,24 +679,9 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 }
 
 // ---------------------------------------------------------------------------
-// near-cut band: count band edges and list the events that hold one
+// events holding a near-cut edge (flags set by the re-score marking): count
+// them into counters[C_RERUN] and clear the flags
 // ---------------------------------------------------------------------------
-__global__ void k_band_flag(Ws w, float lo, float hi) {
-  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
-  const int E = clamp_edges(w.counters, w.e_cap);
-  for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
-    const int e = base + threadIdx.x;
-    bool in = false;
-    if (e < E) {
-      const float l = w.logit[e];
-      in = l > lo && l < hi;
-      if (in) w.ev_flag[w.node_event[w.src[e]]] = 1;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&w.counters[C_BAND], __popc(m));
-  }
-}
-
 __global__ void k_band_list(Ws w, int n_events) {
   __shared__ int base;
   if (threadIdx.x == 0) base = 0;
@@ -1003,7 +988,7 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
                   int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
                   cudaStream_t s) {
   // embedding in FP32: its output feeds the threshold d^2 < r^2
-  const Sel all{nullptr, nullptr, 0};
+  const Sel all{nullptr, nullptr};
   launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, EdgeProj{}, D, h, g, true, false, all,
                        s);
   TcArgs a = base_args(b, w, g);
@@ -1067,9 +1052,7 @@ bool tc_cls_fused(int h, int precision) {
   return (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
 }
 
-void tc_mark_band(const Batch& b, const Ws& w, float band_lo, float band_hi, cudaStream_t s) {
-  cudaMemsetAsync(w.ev_flag, 0, sizeof(int32_t) * b.n_events, s);
-  k_band_flag<<<device_sms() * 8, 256, 0, s>>>(w, band_lo, band_hi);
+void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s) {
   k_band_list<<<1, 1024, 0, s>>>(w, b.n_events);
 }
 

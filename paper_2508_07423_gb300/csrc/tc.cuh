@@ -47,8 +47,8 @@ bool tc_cls_fused(int h, int precision);
 uint8_t e4m3_from_float(float f);
 float e4m3_to_float(uint8_t c);
 
-// Count the edges whose logit lies in (band_lo, band_hi) and list the events
-// holding one (w.rerun_list, count in counters[C_RERUN]).
-void tc_mark_band(const Batch& b, const Ws& w, float band_lo, float band_hi, cudaStream_t s);
+// Count the events flagged in w.ev_flag (those holding a near-cut edge) into
+// counters[C_RERUN] and clear the flags.
+void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s);
 
 }  // namespace gnntrk

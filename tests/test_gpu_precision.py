@@ -29,6 +29,9 @@ def sigmoid(v):
     return 1.0 / (1.0 + np.exp(-np.asarray(v, np.float64)))
 
 
+TRACKER_ROWS = {}
+
+
 def run(wl, batch, precision, band=0.0, **kw):
     tr = pkg.tracker_for_workload(wl, precision=precision, rescore_band=band,
                                   max_hits=batch.n_hits, max_events=batch.n_events,
@@ -36,6 +39,7 @@ def run(wl, batch, precision, band=0.0, **kw):
     labels = pkg.run_batch(tr, batch)
     graphs = [tr.get_graph(e) for e in range(batch.n_events)]
     st = tr.stats()
+    TRACKER_ROWS["rows"] = tr.rescore_rows()
     tr.close()
     return labels, graphs, st
 
@@ -82,6 +86,38 @@ def test_rescore_band_takes_fp32_decisions(cfg1):
     assert np.array_equal(l1[~inband], l0[~inband])
     # every BF16 error is inside the band here, so decisions match FP32
     assert np.mean(cat(g1, "kept") == cat(ref[1], "kept")) >= 0.9999
+    # only the receptive field of the band edges was recomputed, step by step
+    re, rv = receptive_field(g0, band, synth.shape_of(wl).iters, b)
+    rows = TRACKER_ROWS["rows"]
+    assert rows == {"edges": re, "hits": rv}, (rows, re, rv)
+    assert (st["rescore_edges"], st["rescore_hits"]) == (re[0], rv[0])
+    assert re[-1] == st["band"] and 0 < re[0] < st["edges"]
+
+
+def receptive_field(graphs, band, K, batch):
+    """Rows an FP32 re-score of the band edges needs per step, found by walking
+    the message passing backwards on the host: edge step K - 1 needs the band
+    edges; node step k the endpoints of the edges of edge step k (and the hits
+    of node step k + 1); edge step k - 1 every edge touching a hit of node
+    step k; the encoders the endpoints of the first step's edges.
+    Returns (edges, hits), index 0 the encoders, k + 1 step k."""
+    edges = [0] * (K + 1)
+    hits = [0] * (K + 1)
+    for e, g in enumerate(graphs):
+        src, dst = g["src"].astype(np.int64), g["dst"].astype(np.int64)
+        E = np.abs(sigmoid(g["logit"]) - 0.5) < band
+        V = np.zeros(batch.event(e).n_hits, bool)
+        edges[K] += int(E.sum())
+        for k in range(K - 1, -1, -1):
+            V[src[E]] = True
+            V[dst[E]] = True
+            hits[k + 1] += int(V.sum())
+            E = E | V[src] | V[dst]
+            edges[k] += int(E.sum())
+        V[src[E]] = True
+        V[dst[E]] = True
+        hits[0] += int(V.sum())
+    return edges, hits
 
 
 def test_bf16_rescored_agrees_with_oracle(cfg1):
