@@ -232,6 +232,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
     add(&w.rs_elist, E);
     add(&w.rs_nlist, H);
     add(&w.rs_counts, 6 * (kMaxIters + 2));
+    add(&w.rs_blk, 2 * (kMaxIters + 2) * kRsMaxBlocks);
   }
   w.h_cap = H;
   w.e_cap = E;

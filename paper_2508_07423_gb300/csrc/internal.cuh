@@ -13,6 +13,7 @@ namespace gnntrk {
 constexpr int kMaxPlanes = 64;
 constexpr int kMaxEmbedLayers = 8;
 constexpr int kMaxIters = 16;
+constexpr int kRsMaxBlocks = 1024;  // blocks of the re-score level sort (at most)
 constexpr float kLnEps = 1e-5f;
 
 // Bits of the device status word (counters[C_STATUS]).
@@ -96,12 +97,13 @@ struct Ws {
   int32_t* counters;    // [C_COUNT]
   int32_t* scan_blocks; // block partials of the scan
   int32_t* ev_flag;     // [max_events] events re-run in FP32
-  int32_t* rerun_list;  // [max_events] (unused)
-  int32_t* rs_elev;     // [Ecap] re-score level of each edge (-2 none)
-  int32_t* rs_nlev;     // [H]    re-score level of each hit (-2 none)
+  int32_t* rerun_list;  // [max_events] events holding a near-cut edge
+  int8_t* rs_elev;      // [Ecap] re-score level of each edge + 2 (0 none)
+  int8_t* rs_nlev;      // [H]    re-score level of each hit + 2 (0 none)
   int32_t* rs_elist;    // [Ecap] edges by level, descending
   int32_t* rs_nlist;    // [H]    hits by level, descending
-  int32_t* rs_counts;   // [6][kMaxIters + 2] histograms, cursors, rows with level >= k
+  int32_t* rs_counts;   // [6][kMaxIters + 2]: [2] and [5] rows with level >= k (edges, hits)
+  int32_t* rs_blk;      // [2][kMaxIters + 2][kRsMaxBlocks] per-block offsets of the level sort
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
   int64_t h_cap, e_cap;
 };

@@ -9,9 +9,14 @@
 //   edge step k-1 : E_{k-1} = edges incident to V_k       (their e^k feeds the sums)
 //   node encoder  : V_{-1} = V_0 + endpoints(E_{-1}); edge encoder: E_{-1}
 // Recomputing exactly these rows in FP32 gives the band edges the same logits
-// as an FP32 run of the whole event. A counting sort by level (descending)
-// turns the levels into one row list whose prefix [0, cnt_ge[k]) is the set of
-// step k.
+// as an FP32 run of the whole event. A stable counting sort by level
+// (descending) turns the levels into one row list whose prefix [0, cnt_ge[k])
+// is the set of step k, rows in index order within a level.
+//
+// Levels are stored as int8 shifted by +2 (0 = not needed, 1 = encoders only,
+// k + 2 = up to step k), so a memset clears them.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gnntrk {
@@ -20,128 +25,213 @@ int device_sms();
 
 namespace {
 
-__device__ __forceinline__ bool input_bad(const Ws& w) {
-  return (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) != 0;
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+
+__device__ __forceinline__ bool input_bad(const int32_t* counters) {
+  return (*(volatile const int32_t*)&counters[C_STATUS] & ST_INPUT) != 0;
 }
 
-// band edges get level K-1 (or -1 when K = 0), all others -2; nodes -2
-__global__ void k_rs_init(Batch b, Ws w, float lo, float hi, int K) {
-  if (input_bad(w)) return;
+// E_{K-1} = band edges, V_{K-1} = their endpoints; flags the events.
+__global__ void k_rs_init(Ws w, float lo, float hi, int K) {
+  if (input_bad(w.counters)) return;
   const int E = clamp_edges(w.counters, w.e_cap);
-  const int n = max(E, b.n_hits);
-  const int top = K > 0 ? K - 1 : -1;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int i = base + threadIdx.x;
+  const int8_t top = int8_t((K > 0 ? K - 1 : -1) + 2);
+  for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
+    const int e = base + threadIdx.x;
     bool in = false;
-    if (i < E) {
-      const float l = w.logit[i];
+    if (e < E) {
+      const float l = w.logit[e];
       in = l > lo && l < hi;
-      w.rs_elev[i] = in ? top : -2;
-      if (in) w.ev_flag[w.node_event[w.src[i]]] = 1;
+      if (in) {
+        w.rs_elev[e] = top;
+        const int a = w.src[e], c = w.col[e];
+        w.rs_nlev[a] = top;  // every writer stores the same value
+        w.rs_nlev[c] = top;
+        w.ev_flag[w.node_event[a]] = 1;
+      }
     }
-    if (i < b.n_hits) w.rs_nlev[i] = -2;
     const unsigned m = __ballot_sync(0xffffffffu, in);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&w.counters[C_BAND], __popc(m));
   }
 }
 
-// V_k grows by the endpoints of E_k (edges with level >= k)
-__global__ void k_rs_nodes(Ws w, int k) {
-  if (input_bad(w)) return;
+// One backward step k (K-1 .. 0), both set updates fused:
+//   E_{k-1} = E_k + edges touching V_k        (nodes at level >= k)
+//   V_{k-1} = V_k + endpoints(E_{k-1})        (stores of level k-1)
+// The stores of level k-1 only replace levels below k-1, so they never change
+// which nodes read as >= k in the same pass; concurrent writers store the same
+// value.
+__global__ void k_rs_step(Ws w, int k) {
+  if (input_bad(w.counters)) return;
   const int E = clamp_edges(w.counters, w.e_cap);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
-    if (w.rs_elev[e] >= k) {
-      atomicMax(&w.rs_nlev[w.src[e]], k);
-      atomicMax(&w.rs_nlev[w.col[e]], k);
+  const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    int8_t L = w.rs_elev[e];
+    const int a = w.src[e], c = w.col[e];
+    const int8_t la = w.rs_nlev[a], lc = w.rs_nlev[c];
+    if (L < km1 && (la >= ge_k || lc >= ge_k)) {
+      L = km1;
+      w.rs_elev[e] = L;
     }
+    if (L >= km1) {
+      if (la < km1) w.rs_nlev[a] = km1;
+      if (lc < km1) w.rs_nlev[c] = km1;
+    }
+  }
 }
 
-// E_{k-1}: edges incident to a node of V_k (level >= k)
-__global__ void k_rs_edges(Ws w, int k) {
-  if (input_bad(w)) return;
-  const int E = clamp_edges(w.counters, w.e_cap);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
-    if (w.rs_elev[e] < k - 1 && (w.rs_nlev[w.src[e]] >= k || w.rs_nlev[w.col[e]] >= k))
-      w.rs_elev[e] = k - 1;
+// Stable counting sort of the levels. Bucket = top - shifted level (bucket 0
+// holds the highest level); rows at level 0 (not needed) are dropped.
+struct SortSide {
+  const int8_t* lev;
+  int32_t* list;
+  int32_t* blk_cnt;      // [nb][gridDim.x] rows per bucket per block, then block offsets
+  const int32_t* n_ptr;  // row count on the device (edges) or null
+  int n_fixed;
+  int32_t* cge;          // [K + 1]: rows with level >= k at [k + 1]
+  int counter;           // counters index receiving the total
+};
+
+__device__ __forceinline__ void chunk_of(int n, int& lo, int& hi) {
+  const int per = (((n + gridDim.x - 1) / gridDim.x) + kRsThreads - 1) / kRsThreads * kRsThreads;
+  lo = min(n, int(blockIdx.x) * per);
+  hi = min(n, lo + per);
 }
 
-// histogram of levels -1 .. K-1 into buckets K-1-level (so bucket 0 = top)
-__global__ void k_rs_count(const int32_t* lev, const int32_t* n_ptr, int n_fixed, int32_t* hist,
-                           int K, const int32_t* counters) {
-  __shared__ int h[kMaxIters + 2];
-  if ((*(volatile const int32_t*)&counters[C_STATUS]) & ST_INPUT) return;
+__device__ __forceinline__ int side_rows(const SortSide& sd) {
+  return sd.n_ptr ? min(*sd.n_ptr, sd.n_fixed) : sd.n_fixed;
+}
+
+// per block and bucket, the number of rows (ballot counts, no atomics)
+__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int K,
+                                                         const int32_t* counters) {
+  if (input_bad(counters)) return;
+  const SortSide& sd = blockIdx.y == 0 ? se : sn;
+  const int nb = K + 1, top = K + 1;
+  __shared__ int cnt[kRsWarps][kMaxIters + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int mine = 0;  // lane j of each warp counts bucket j
+  int lo, hi;
+  chunk_of(side_rows(sd), lo, hi);
+  for (int base = lo; base < hi; base += kRsThreads) {
+    const int i = base + threadIdx.x;
+    const int bk = i < hi ? top - sd.lev[i] : -1;  // level 0 -> bucket K + 1 (dropped)
+    for (int j = 0; j < nb; ++j) {
+      const int c = __popc(__ballot_sync(0xffffffffu, bk == j));
+      if (lane == j) mine += c;
+    }
+  }
+  if (lane < nb) cnt[warp][lane] = mine;
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    int t = 0;
+    for (int q = 0; q < kRsWarps; ++q) t += cnt[q][threadIdx.x];
+    sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// exclusive offsets per (bucket, block) in bucket-major order; one block per side
+__global__ void __launch_bounds__(1024) k_rs_offsets(SortSide se, SortSide sn, int K, int nblk,
+                                                     int32_t* counters) {
+  if (input_bad(counters)) return;
+  const SortSide& sd = blockIdx.x == 0 ? se : sn;
   const int nb = K + 1;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
-  __syncthreads();
-  const int n = n_ptr ? min(*n_ptr, n_fixed) : n_fixed;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int l = lev[i];
-    if (l >= -1) atomicAdd(&h[K - 1 - l], 1);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nb; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-// cursors (exclusive prefix over buckets) and cnt_ge[k + 1] = rows with
-// level >= k, for k = -1 .. K-1
-__global__ void k_rs_offsets(int32_t* rs, int K, int32_t* counters) {
-  if ((*(volatile int32_t*)&counters[C_STATUS]) & ST_INPUT) return;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int NL = kMaxIters + 2;
-  for (int side = 0; side < 2; ++side) {  // 0 edges, 1 nodes
-    int32_t* hist = rs + side * 3 * NL;
-    int32_t* cur = hist + NL;
-    int32_t* cge = hist + 2 * NL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int tot[kMaxIters + 2];
+  // warp j scans bucket j over the blocks
+  if (warp < nb) {
+    int32_t* row = sd.blk_cnt + warp * nblk;
     int run = 0;
-    for (int bkt = 0; bkt <= K; ++bkt) {  // level K-1-bkt
-      cur[bkt] = run;
-      run += hist[bkt];
-      cge[K - 1 - bkt + 1] = run;  // rows with level >= K-1-bkt
+    for (int b0 = 0; b0 < nblk; b0 += 32) {
+      const int v = b0 + lane < nblk ? row[b0 + lane] : 0;
+      int x = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+      }
+      if (b0 + lane < nblk) row[b0 + lane] = run + x - v;
+      run += __shfl_sync(0xffffffffu, x, 31);
     }
-    counters[side == 0 ? C_RERUN_EDGES : C_RERUN_HITS] = run;
+    if (lane == 0) tot[warp] = run;
   }
+  __syncthreads();
+  __shared__ int base[kMaxIters + 2];
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int j = 0; j < nb; ++j) {  // bucket j = level K-1-j
+      base[j] = run;
+      run += tot[j];
+      sd.cge[K - 1 - j + 1] = run;  // rows with level >= K-1-j
+    }
+    counters[sd.counter] = run;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) sd.blk_cnt[j * nblk + b] += base[j];
 }
 
-__global__ void k_rs_scatter(const int32_t* lev, const int32_t* n_ptr, int n_fixed, int32_t* cur,
-                             int32_t* list, int K, const int32_t* counters) {
-  if ((*(volatile const int32_t*)&counters[C_STATUS]) & ST_INPUT) return;
-  const int n = n_ptr ? min(*n_ptr, n_fixed) : n_fixed;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int l = lev[i];
-    if (l >= -1) list[atomicAdd(&cur[K - 1 - l], 1)] = i;
+// scatter in the same chunk and tile order as the count: stable
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int K,
+                                                           const int32_t* counters) {
+  if (input_bad(counters)) return;
+  const SortSide& sd = blockIdx.y == 0 ? se : sn;
+  const int nb = K + 1, top = K + 1;
+  __shared__ int wtot[kRsWarps][kMaxIters + 2];
+  __shared__ int run[kMaxIters + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x < nb) run[threadIdx.x] = sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x];
+  int lo, hi;
+  chunk_of(side_rows(sd), lo, hi);
+  for (int base = lo; base < hi; base += kRsThreads) {
+    const int i = base + threadIdx.x;
+    const int bk = i < hi ? top - sd.lev[i] : -1;
+    int rank = 0;
+    for (int j = 0; j < nb; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, bk == j);
+      if (bk == j) rank = __popc(m & lt);
+      if (lane == 0) wtot[warp][j] = __popc(m);
+    }
+    __syncthreads();
+    if (bk >= 0 && bk < nb) {
+      int off = run[bk];
+      for (int q = 0; q < warp; ++q) off += wtot[q][bk];
+      sd.list[off + rank] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      int t = 0;
+      for (int q = 0; q < kRsWarps; ++q) t += wtot[q][threadIdx.x];
+      run[threadIdx.x] += t;
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
+int rescore_sort_blocks() { return std::min(device_sms() * 4, kRsMaxBlocks); }
+
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s) {
   const int NL = kMaxIters + 2;
   const int grid = device_sms() * 8;
-  int launches = 0;
+  const int nblk = rescore_sort_blocks();
   cudaMemsetAsync(w.ev_flag, 0, sizeof(int32_t) * b.n_events, s);
   cudaMemsetAsync(w.rs_counts, 0, sizeof(int32_t) * 6 * NL, s);
-  k_rs_init<<<grid, 256, 0, s>>>(b, w, band_lo, band_hi, K);
-  ++launches;
-  for (int k = K - 1; k >= 0; --k) {
-    k_rs_nodes<<<grid, 256, 0, s>>>(w, k);
-    k_rs_edges<<<grid, 256, 0, s>>>(w, k);
-    launches += 2;
-  }
-  k_rs_nodes<<<grid, 256, 0, s>>>(w, -1);
-  ++launches;
-  int32_t* he = w.rs_counts;
-  int32_t* hn = w.rs_counts + 3 * NL;
-  k_rs_count<<<grid, 256, 0, s>>>(w.rs_elev, w.counters + C_EDGES, int(w.e_cap), he, K, w.counters);
-  k_rs_count<<<grid, 256, 0, s>>>(w.rs_nlev, nullptr, b.n_hits, hn, K, w.counters);
-  k_rs_offsets<<<1, 32, 0, s>>>(w.rs_counts, K, w.counters);
-  k_rs_scatter<<<grid, 256, 0, s>>>(w.rs_elev, w.counters + C_EDGES, int(w.e_cap), he + NL,
-                                    w.rs_elist, K, w.counters);
-  k_rs_scatter<<<grid, 256, 0, s>>>(w.rs_nlev, nullptr, b.n_hits, hn + NL, w.rs_nlist, K,
-                                    w.counters);
-  launches += 5;
-  return launches;
+  cudaMemsetAsync(w.rs_elev, 0, size_t(w.e_cap), s);
+  cudaMemsetAsync(w.rs_nlev, 0, size_t(b.n_hits), s);
+  k_rs_init<<<grid, kRsThreads, 0, s>>>(w, band_lo, band_hi, K);
+  for (int k = K - 1; k >= 0; --k) k_rs_step<<<grid, kRsThreads, 0, s>>>(w, k);
+  SortSide se{w.rs_elev, w.rs_elist, w.rs_blk, w.counters + C_EDGES, int(w.e_cap),
+              w.rs_counts + 2 * NL, C_RERUN_EDGES};
+  SortSide sn{w.rs_nlev, w.rs_nlist, w.rs_blk + NL * nblk, nullptr, b.n_hits,
+              w.rs_counts + 5 * NL, C_RERUN_HITS};
+  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
+  k_rs_offsets<<<2, 1024, 0, s>>>(se, sn, K, nblk, w.counters);
+  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
+  return 1 + K + 3;
 }
 
 }  // namespace gnntrk
