@@ -346,7 +346,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   if (!tc) {
     stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 1,
+      stage(h, "node_update", s, 2,
             [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, all, s); });
       stage(h, "edge_update", s, 1, [&] {
         launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
@@ -394,7 +394,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       stage(h, "rescore_edge_encoder", s, 1,
             [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, esel(-1), s); });
       for (int k = 0; k < h->K; ++k) {
-        stage(h, "rescore_node_update", s, 1, [&] {
+        stage(h, "rescore_node_update", s, 2, [&] {
           launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, nsel(k), s);
         });
         stage(h, "rescore_edge_update", s, 1, [&] {

@@ -33,36 +33,27 @@ constexpr int kThreads = 256;                      // embedding kernel
 constexpr int kRowGroups = 32;                     // lanes of a warp
 constexpr int kColGroups = kThreads / kRowGroups;  // warps of the embedding block
 
-// Interaction-network tile shape per hidden width: NT threads in NCG column
-// groups (warps w with the same w % NCG share columns), TM rows. Per k a warp
-// reads RM rows of A (RM wavefronts) and CW weights (CW/4 uniform loads) for
-// RM x CW FMAs per lane, so RM * CW / 4 FMA cycles per RM + CW / 4 wavefronts.
-// Two variants per width; the autotuner picks one per kernel family.
-template <int H, int V>
-struct Shape;
-template <>
-struct Shape<32, 0> {
-  static constexpr int NT = 256, NCG = 8, TM = 128;  // RM 4, CW 4
+// Interaction network: every warp owns whole rows. Lane (rg = lane / 8,
+// cg = lane % 8) holds RM rows (rg + 4 i) x CW columns (32 j + 4 cg + u) of a
+// layer's output in registers (RM x CW = 32 accumulators); a warp covers
+// WR = 4 RM rows and all H columns, so a row's LayerNorm is a reduction over
+// the 8 lanes of its row group and no block-wide barrier is needed. Inputs are
+// staged row-major in the warp's own shared-memory slice with a row stride of
+// H + 4 floats: the four rows a warp reads at one k fall in distinct bank
+// quads, and the eight lanes of a row group read the same address (broadcast).
+template <int H>
+struct WarpTile {
+  static constexpr int CW = H / 8;    // columns per lane
+  static constexpr int RM = 256 / H;  // rows per lane
+  static constexpr int WR = 4 * RM;   // rows per warp
+  static constexpr int NJ = CW / 4;   // float4 column chunks per lane
+  static constexpr int LDH = H + 4;   // row stride of staged rows (floats)
 };
-template <>
-struct Shape<32, 1> {
-  static constexpr int NT = 256, NCG = 4, TM = 128;  // RM 2, CW 8
-};
-template <>
-struct Shape<64, 0> {
-  static constexpr int NT = 256, NCG = 8, TM = 64;   // RM 2, CW 8
-};
-template <>
-struct Shape<64, 1> {
-  static constexpr int NT = 128, NCG = 4, TM = 64;   // RM 2, CW 16
-};
-template <>
-struct Shape<128, 0> {
-  static constexpr int NT = 256, NCG = 8, TM = 64;   // RM 2, CW 16
-};
-template <>
-struct Shape<128, 1> {
-  static constexpr int NT = 128, NCG = 4, TM = 64;   // RM 2, CW 32
+
+// Warps per block, per variant (the autotuner picks one per kernel family).
+template <int V>
+struct Warps {
+  static constexpr int NW = V == 0 ? 4 : 8;
 };
 
 // Variant chosen per (hidden index, kernel family: 0 encoders, 1 node step,
@@ -76,6 +67,414 @@ __device__ __forceinline__ bool input_bad(const Ws& w) {
   return (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) != 0;
 }
 
+// acc[i][4j+u] (+)= sum_{k < KV} A[rg + 4i][k] * WT[(k_off + k) * ldo + 32j + 4cg + u],
+// k ascending; A row-major with stride LDA (K a multiple of 4, KV <= K valid)
+template <int H, int K, int KV, int LDA>
+__device__ __forceinline__ void warp_layer(const float* A, const LayerF32& L, int k_off, int rg,
+                                           int cg, float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+  constexpr int RM = WarpTile<H>::RM, NJ = WarpTile<H>::NJ;
+  const float* wp = L.WT + size_t(k_off) * L.ldo + 4 * cg;
+#pragma unroll 2
+  for (int k4 = 0; k4 < K; k4 += 4) {
+    float4 a[RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+      a[i] = *reinterpret_cast<const float4*>(A + (rg + 4 * i) * LDA + k4);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (KV < K && k4 + t >= KV) break;
+      float4 q[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        q[j] = __ldg(reinterpret_cast<const float4*>(wp + size_t(k4 + t) * L.ldo + 32 * j));
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        const float av = t == 0 ? a[i].x : (t == 1 ? a[i].y : (t == 2 ? a[i].z : a[i].w));
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          acc[i][4 * j] = fmaf(av, q[j].x, acc[i][4 * j]);
+          acc[i][4 * j + 1] = fmaf(av, q[j].y, acc[i][4 * j + 1]);
+          acc[i][4 * j + 2] = fmaf(av, q[j].z, acc[i][4 * j + 2]);
+          acc[i][4 * j + 3] = fmaf(av, q[j].w, acc[i][4 * j + 3]);
+        }
+      }
+    }
+  }
+}
+
+template <int H>
+__device__ __forceinline__ void acc_bias(const float* b, int cg,
+                                         float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+#pragma unroll
+  for (int j = 0; j < WarpTile<H>::NJ; ++j) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(b + 32 * j + 4 * cg));
+#pragma unroll
+    for (int i = 0; i < WarpTile<H>::RM; ++i) {
+      acc[i][4 * j] = v.x;
+      acc[i][4 * j + 1] = v.y;
+      acc[i][4 * j + 2] = v.z;
+      acc[i][4 * j + 3] = v.w;
+    }
+  }
+}
+
+// acc += S[rg + 4i][32j + 4cg + u] (each lane reads only its own elements)
+template <int H>
+__device__ __forceinline__ void acc_add_smem(const float* S, int rg, int cg,
+                                             float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+  constexpr int LD = WarpTile<H>::LDH;
+#pragma unroll
+  for (int i = 0; i < WarpTile<H>::RM; ++i)
+#pragma unroll
+    for (int j = 0; j < WarpTile<H>::NJ; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(S + (rg + 4 * i) * LD + 32 * j + 4 * cg);
+      acc[i][4 * j] += v.x;
+      acc[i][4 * j + 1] += v.y;
+      acc[i][4 * j + 2] += v.z;
+      acc[i][4 * j + 3] += v.w;
+    }
+}
+
+template <int H>
+__device__ __forceinline__ void acc_store_smem(float* S, int rg, int cg,
+                                               const float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+  constexpr int LD = WarpTile<H>::LDH;
+#pragma unroll
+  for (int i = 0; i < WarpTile<H>::RM; ++i)
+#pragma unroll
+    for (int j = 0; j < WarpTile<H>::NJ; ++j)
+      *reinterpret_cast<float4*>(S + (rg + 4 * i) * LD + 32 * j + 4 * cg) =
+          make_float4(acc[i][4 * j], acc[i][4 * j + 1], acc[i][4 * j + 2], acc[i][4 * j + 3]);
+}
+
+// rows of the warp to global: dst[rows[r] * ld + off + col] (rows < 0 skipped)
+template <int H>
+__device__ __forceinline__ void acc_store_rows(float* dst, int64_t ld, int off, const int* rows,
+                                               int rg, int cg,
+                                               const float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+#pragma unroll
+  for (int i = 0; i < WarpTile<H>::RM; ++i) {
+    const int row = rows[rg + 4 * i];
+    if (row < 0) continue;
+    float* d = dst + size_t(row) * ld + off + 4 * cg;
+#pragma unroll
+    for (int j = 0; j < WarpTile<H>::NJ; ++j)
+      *reinterpret_cast<float4*>(d + 32 * j) =
+          make_float4(acc[i][4 * j], acc[i][4 * j + 1], acc[i][4 * j + 2], acc[i][4 * j + 3]);
+  }
+}
+
+// sum over the 8 lanes of a row group (lane bits 0..2)
+__device__ __forceinline__ float row_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+// per row: ReLU((v - mean) / sqrt(var + eps)) over the H columns
+template <int H>
+__device__ __forceinline__ void acc_ln_relu(float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
+  constexpr int CW = WarpTile<H>::CW;
+#pragma unroll
+  for (int i = 0; i < WarpTile<H>::RM; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) s += acc[i][c];
+    const float mean = row_sum(s) / float(H);
+    float q = 0.f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      const float t = acc[i][c] - mean;
+      q = fmaf(t, t, q);
+    }
+    const float inv = 1.0f / sqrtf(row_sum(q) / float(H) + kLnEps);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[i][c] = fmaxf((acc[i][c] - mean) * inv, 0.f);
+  }
+}
+
+// S[r][col] = X[rows[r]][off + col] (+ Y[rows2[r]][off2 + col]), zero for rows < 0;
+// 8 lanes per row, one float4 column chunk each, four rows per instruction.
+// Loads are unconditional (row 0 stands in for a missing row, its value is
+// then dropped) so that all of a lane's loads are in flight together.
+template <int H, bool TWO>
+__device__ __forceinline__ void stage_rows(float* S, const int* rows, const float* X, int64_t ldx,
+                                           int offx, const int* rows2, const float* Y,
+                                           int64_t ldy, int offy, int lane) {
+  constexpr int RM = WarpTile<H>::RM, NJ = WarpTile<H>::NJ, LD = WarpTile<H>::LDH;
+  const int gr = lane >> 3, q = lane & 7;
+  float4 v[RM][NJ];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int row = rows[gr + 4 * i];
+    const int rx = max(row, 0);
+    const int ry = TWO ? (row >= 0 ? rows2[gr + 4 * i] : 0) : 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      v[i][j] = __ldg(reinterpret_cast<const float4*>(X + size_t(rx) * ldx + offx + 32 * j + 4 * q));
+      if (TWO) {
+        const float4 y =
+            __ldg(reinterpret_cast<const float4*>(Y + size_t(ry) * ldy + offy + 32 * j + 4 * q));
+        v[i][j].x += y.x;
+        v[i][j].y += y.y;
+        v[i][j].z += y.z;
+        v[i][j].w += y.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const bool ok = rows[gr + 4 * i] >= 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+      *reinterpret_cast<float4*>(S + (gr + 4 * i) * LD + 32 * j + 4 * q) =
+          ok ? v[i][j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// interaction network, one kernel per mode
+// ---------------------------------------------------------------------------
+struct GnnArgs {
+  Batch b;
+  Ws w;
+  EdgeProj proj;  // node kernels: projections for the next edge layer
+  Mlp2F32 m;    // the sub-network of this kernel
+  Mlp2F32 cls;  // classifier (G_EDGE_UPD_CLS, G_CLS)
+  float fs[6];
+  float cut;
+  int rescore_only;
+  float band_lo, band_hi;
+  Sel sel;
+};
+
+template <int H, int MODE>
+__host__ __device__ constexpr int g_lda() {
+  return MODE == G_NODE_ENC ? 8 : WarpTile<H>::LDH;
+}
+
+// shared memory of one warp (floats): staged input A, hidden Hs, row ids and,
+// for the node step, a third row buffer Bs
+template <int H, int MODE>
+__host__ __device__ constexpr int g_warp_floats() {
+  return WarpTile<H>::WR * (g_lda<H, MODE>() + WarpTile<H>::LDH) + 4 * WarpTile<H>::WR +
+         (MODE == G_NODE_UPD ? WarpTile<H>::WR * WarpTile<H>::LDH : 0);
+}
+
+template <int H, int MODE, int NW>
+__global__ void __launch_bounds__(NW * 32) k_gnn_f32(const GnnArgs p) {
+  using T = WarpTile<H>;
+  constexpr int RM = T::RM, CW = T::CW, WR = T::WR;
+  constexpr int LDA = g_lda<H, MODE>();
+  constexpr bool EDGE_ROWS = MODE != G_NODE_ENC && MODE != G_NODE_UPD;
+  extern __shared__ __align__(16) float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* As = sm + warp * g_warp_floats<H, MODE>();  // [WR][LDA]
+  float* Hs = As + WR * LDA;                          // [WR][H + 4]
+  int* rows = reinterpret_cast<int*>(Hs + WR * T::LDH);
+  int* srcs = rows + WR;
+  int* dsts = srcs + WR;
+  const Ws& w = p.w;
+  if (input_bad(w)) return;
+  int lo, hi;
+  if (!sel_rows(p.b, w, p.sel, EDGE_ROWS, lo, hi)) return;
+  const int rg = lane >> 3, cg = lane & 7;
+  const int E = clamp_edges(w.counters, w.e_cap);
+
+  for (int base = lo + (blockIdx.x * NW + warp) * WR; base < hi; base += gridDim.x * NW * WR) {
+    // ---- rows of this warp -----------------------------------------------
+    if (lane < WR) {
+      const int pos = base + lane;
+      int row = -1, a = 0, c = 0;
+      if (pos < hi) {
+        row = sel_row(p.sel, pos);
+        if (EDGE_ROWS) {
+          a = w.src[row];
+          c = w.col[row];
+        }
+      }
+      rows[lane] = row;
+      srcs[lane] = a;
+      dsts[lane] = c;
+    }
+    __syncwarp();
+    float acc[RM][CW];
+
+    if constexpr (MODE == G_NODE_ENC || MODE == G_NODE_UPD) {
+      if constexpr (MODE == G_NODE_ENC) {
+        // features (x/s3, y/s4, z/s5) of each hit, column 3 zero
+        if (lane < WR) {
+          const int row = rows[lane];
+          float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row >= 0) {
+            const float4 q = w.pos[row];
+            f = make_float4(q.x / p.fs[3], q.y / p.fs[4], q.z / p.fs[5], 0.f);
+          }
+          *reinterpret_cast<float4*>(As + lane * LDA) = f;
+        }
+        __syncwarp();
+        acc_bias<H>(p.m.l1.b, cg, acc);
+        warp_layer<H, 4, 3, LDA>(As, p.m.l1, 0, rg, cg, acc);
+        acc_ln_relu<H>(acc);
+        acc_store_smem<H>(Hs, rg, cg, acc);
+        __syncwarp();
+        acc_bias<H>(p.m.l2.b, cg, acc);
+        warp_layer<H, H, H, T::LDH>(Hs, p.m.l2, 0, rg, cg, acc);
+        __syncwarp();  // all lanes are done reading Hs
+      } else {
+        // [h, sum_out e, sum_in e]: h in Hs, the two sums (written into the
+        // node's projection row by k_msg_f32) in As and Bs
+        float* Bs = Hs + WR * T::LDH + 4 * WR;
+        stage_rows<H, false>(Hs, rows, w.hstate, H, 0, nullptr, nullptr, 0, 0, lane);
+        stage_rows<H, false>(As, rows, w.pstate, 2 * H, 0, nullptr, nullptr, 0, 0, lane);
+        stage_rows<H, false>(Bs, rows, w.pstate, 2 * H, H, nullptr, nullptr, 0, 0, lane);
+        __syncwarp();
+        acc_bias<H>(p.m.l1.b, cg, acc);
+        warp_layer<H, H, H, T::LDH>(Hs, p.m.l1, 0, rg, cg, acc);
+        warp_layer<H, H, H, LDA>(As, p.m.l1, H, rg, cg, acc);
+        warp_layer<H, H, H, T::LDH>(Bs, p.m.l1, 2 * H, rg, cg, acc);
+        acc_ln_relu<H>(acc);
+        __syncwarp();  // all lanes are done reading As
+        acc_store_smem<H>(As, rg, cg, acc);
+        __syncwarp();
+        acc_bias<H>(p.m.l2.b, cg, acc);
+        warp_layer<H, H, H, LDA>(As, p.m.l2, 0, rg, cg, acc);
+        acc_add_smem<H>(Hs, rg, cg, acc);  // residual h
+      }
+      acc_store_rows<H>(w.hstate, H, 0, rows, rg, cg, acc);
+      // ---- projections of the new node state for the next edge layer -------
+      acc_store_smem<H>(Hs, rg, cg, acc);
+      __syncwarp();
+      acc_bias<H>(p.proj.src.b, cg, acc);
+      warp_layer<H, H, H, T::LDH>(Hs, p.proj.src, 0, rg, cg, acc);
+      acc_store_rows<H>(w.pstate, 2 * H, 0, rows, rg, cg, acc);
+      acc_bias<H>(p.proj.dst.b, cg, acc);
+      warp_layer<H, H, H, T::LDH>(Hs, p.proj.dst, 0, rg, cg, acc);
+      acc_store_rows<H>(w.pstate, 2 * H, H, rows, rg, cg, acc);
+    } else {
+      if constexpr (MODE != G_CLS) {
+        // ---- layer 1: b + W_e e + (W_src h_src + W_dst h_dst, projected) ----
+        stage_rows<H, true>(Hs, srcs, w.pstate, 2 * H, 0, dsts, w.pstate, 2 * H, H, lane);
+        if constexpr (MODE != G_EDGE_ENC)
+          stage_rows<H, false>(As, rows, w.estate, H, 0, nullptr, nullptr, 0, 0, lane);
+        __syncwarp();
+        acc_bias<H>(p.m.l1.b, cg, acc);
+        if constexpr (MODE != G_EDGE_ENC) warp_layer<H, H, H, LDA>(As, p.m.l1, 0, rg, cg, acc);
+        acc_add_smem<H>(Hs, rg, cg, acc);
+        acc_ln_relu<H>(acc);
+        acc_store_smem<H>(Hs, rg, cg, acc);  // own elements only
+        __syncwarp();
+        // ---- layer 2 (+ residual e) -----------------------------------------
+        acc_bias<H>(p.m.l2.b, cg, acc);
+        warp_layer<H, H, H, T::LDH>(Hs, p.m.l2, 0, rg, cg, acc);
+        if constexpr (MODE != G_EDGE_ENC) acc_add_smem<H>(As, rg, cg, acc);
+        if constexpr (MODE != G_EDGE_UPD_CLS) acc_store_rows<H>(w.estate, H, 0, rows, rg, cg, acc);
+        if constexpr (MODE == G_EDGE_UPD_CLS) {
+          acc_store_smem<H>(As, rg, cg, acc);  // own elements only
+        }
+      } else {
+        stage_rows<H, false>(As, rows, w.estate, H, 0, nullptr, nullptr, 0, 0, lane);
+      }
+      if constexpr (MODE == G_EDGE_UPD_CLS || MODE == G_CLS) {
+        // ---- classifier: Linear -> LayerNorm -> ReLU -> dot, then the cut ----
+        __syncwarp();
+        acc_bias<H>(p.cls.l1.b, cg, acc);
+        warp_layer<H, H, H, LDA>(As, p.cls.l1, 0, rg, cg, acc);
+        acc_ln_relu<H>(acc);
+        const LayerF32& l2 = p.cls.l2;
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+          float part = 0.f;
+#pragma unroll
+          for (int j = 0; j < T::NJ; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              part = fmaf(acc[i][4 * j + u], __ldg(l2.WT + size_t(32 * j + 4 * cg + u) * l2.ldo), part);
+          const float lg = l2.b[0] + row_sum(part);
+          const int row = rows[rg + 4 * i];
+          if (cg == 0 && row >= 0) {
+            bool write = true;
+            if (p.rescore_only) {
+              const float old = w.logit[row];
+              write = old > p.band_lo && old < p.band_hi;
+            }
+            if (write) {
+              w.logit[row] = lg;
+              w.keep[row] = lg >= p.cut ? 1 : 0;
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();  // the next tile overwrites this warp's shared memory
+  }
+}
+
+// ---------------------------------------------------------------------------
+// messages of the node step: m_v = [sum of e over v's out edges, sum over its
+// in edges], each sum in increasing list order starting from zero, written to
+// the node's projection row P[v] = [m_out | m_in] (the node step reads it
+// there and then overwrites the row with the new projections). One group of
+// 8 lanes per node, one float4 column chunk per lane; U list entries per
+// round are loaded together (entries past the end reload a valid row and are
+// dropped), so each lane keeps U loads in flight.
+// ---------------------------------------------------------------------------
+template <int H>
+__global__ void __launch_bounds__(256) k_msg_f32(Batch b, Ws w, Sel sel) {
+  constexpr int NJ = H / 32, U = 8 / NJ;
+  if (input_bad(w)) return;
+  int lo, hi;
+  if (!sel_rows(b, w, sel, false, lo, hi)) return;
+  const int E = clamp_edges(w.counters, w.e_cap);
+  const int q = threadIdx.x & 7;
+  const int groups = gridDim.x * (blockDim.x >> 3);
+  for (int pos = lo + blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3); pos < hi; pos += groups) {
+    const int row = sel_row(sel, pos);
+    float* out = w.pstate + size_t(row) * 2 * H + 4 * q;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      int a, n;
+      if (side == 0) {
+        a = min(w.row_ptr[row], E);
+        n = min(w.row_ptr[row + 1], E) - a;
+      } else {
+        a = w.in_ptr[row];
+        n = w.in_ptr[row + 1] - a;
+      }
+      float4 s[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) s[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int t0 = 0; t0 < n; t0 += U) {
+        float4 v[U][NJ];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int at = a + min(t0 + u, n - 1);
+          const int e = side == 0 ? at : __ldg(w.in_edge + at);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            v[u][j] = __ldg(reinterpret_cast<const float4*>(w.estate + size_t(e) * H + 32 * j + 4 * q));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (t0 + u < n) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              s[j].x += v[u][j].x;
+              s[j].y += v[u][j].y;
+              s[j].z += v[u][j].z;
+              s[j].w += v[u][j].w;
+            }
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        *reinterpret_cast<float4*>(out + side * H + 32 * j) = s[j];
+    }
+  }
+}
+
+// ---- transposed register tiles of the embedding MLP -------------------------
 // acc[i][j] = b[c0 + j] + sum_k A[k][r0 + i] * W[k][c0 + j]
 // A: shared [K][TM]; W: global [K][ldo] (transposed weights)
 template <int RM, int CW, int TM>
@@ -136,245 +535,6 @@ __device__ __forceinline__ void tile_store_t(float* S, int r0, int c0, const flo
       *reinterpret_cast<float4*>(S + (c0 + j) * TM + r0) = make_float4(v[0], v[1], v[2], v[3]);
     else
       *reinterpret_cast<float2*>(S + (c0 + j) * TM + r0) = make_float2(v[0], v[1]);
-  }
-}
-
-// in place over column r of S[n][TM]: ReLU((v - mean) / sqrt(var + eps))
-template <int TM>
-__device__ __forceinline__ void col_ln_relu(float* S, int n, int r) {
-  float s = 0.f;
-  for (int i = 0; i < n; ++i) s += S[i * TM + r];
-  const float mean = s / float(n);
-  float q = 0.f;
-  for (int i = 0; i < n; ++i) {
-    const float t = S[i * TM + r] - mean;
-    q = fmaf(t, t, q);
-  }
-  const float inv = 1.0f / sqrtf(q / float(n) + kLnEps);
-  for (int i = 0; i < n; ++i) S[i * TM + r] = fmaxf((S[i * TM + r] - mean) * inv, 0.f);
-}
-
-// copy an h-float global row into column `row` of S[k0 .. k0+h)[TM]
-template <int TM>
-__device__ __forceinline__ void put_col(float* S, int k0, int row, const float* src, int h) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int c = 0; c < h / 4; ++c) {
-    const float4 v = s4[c];
-    S[(k0 + 4 * c) * TM + row] = v.x;
-    S[(k0 + 4 * c + 1) * TM + row] = v.y;
-    S[(k0 + 4 * c + 2) * TM + row] = v.z;
-    S[(k0 + 4 * c + 3) * TM + row] = v.w;
-  }
-}
-
-template <int TM>
-__device__ __forceinline__ void add_col(float* S, int k0, int row, const float* src, int h) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int c = 0; c < h / 4; ++c) {
-    const float4 v = s4[c];
-    S[(k0 + 4 * c) * TM + row] += v.x;
-    S[(k0 + 4 * c + 1) * TM + row] += v.y;
-    S[(k0 + 4 * c + 2) * TM + row] += v.z;
-    S[(k0 + 4 * c + 3) * TM + row] += v.w;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// interaction network, one kernel per mode
-// ---------------------------------------------------------------------------
-struct GnnArgs {
-  Batch b;
-  Ws w;
-  EdgeProj proj;  // node kernels: projections for the next edge layer
-  Mlp2F32 m;    // the sub-network of this kernel
-  Mlp2F32 cls;  // classifier (G_EDGE_UPD_CLS, G_CLS)
-  float fs[6];
-  float cut;
-  int rescore_only;
-  float band_lo, band_hi;
-  Sel sel;
-};
-
-__host__ __device__ constexpr int g_nseg(int mode) {
-  return mode == G_NODE_ENC ? 0 : (mode == G_EDGE_ENC ? 2 : (mode == G_CLS ? 1 : 3));
-}
-
-template <int H, int MODE, int V>
-__global__ void __launch_bounds__(Shape<H, V>::NT) k_gnn_f32(const GnnArgs p) {
-  constexpr int NT = Shape<H, V>::NT, NCG = Shape<H, V>::NCG, TM = Shape<H, V>::TM;
-  constexpr int RM = TM / (NT / NCG);
-  constexpr int CW = H / NCG;
-  constexpr int NSEG = g_nseg(MODE);
-  constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
-  constexpr int KA = K1 > 4 ? K1 : 4;
-  extern __shared__ __align__(16) float sm[];
-  float* As = sm;            // [KA][TM] input rows, transposed
-  float* Hs = sm + KA * TM;  // [H][TM] hidden rows, transposed
-  const Ws& w = p.w;
-  if (input_bad(w)) return;
-  int lo, hi;
-  if (!sel_rows(p.b, w, p.sel, MODE != G_NODE_ENC && MODE != G_NODE_UPD, lo, hi)) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int r0 = ((warp / NCG) * 32 + lane) * RM;
-  const int c0 = (warp % NCG) * CW;
-  const int E = clamp_edges(w.counters, w.e_cap);
-
-  for (int base = lo + blockIdx.x * TM; base < hi; base += gridDim.x * TM) {
-    // ---- gather: task t = (segment t / TM, row t % TM) --------------------
-    if constexpr (MODE == G_NODE_ENC) {
-      for (int r = tid; r < TM; r += NT) {
-        const int pos = base + r;
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-        if (pos < hi) {
-          const float4 q = w.pos[sel_row(p.sel, pos)];
-          f0 = q.x / p.fs[3];
-          f1 = q.y / p.fs[4];
-          f2 = q.z / p.fs[5];
-        }
-        As[r] = f0;
-        As[TM + r] = f1;
-        As[2 * TM + r] = f2;
-      }
-    } else {
-      for (int t = tid; t < NSEG * TM; t += NT) {
-        const int seg = t / TM, r = t % TM, pos = base + r;
-        const int k0 = seg * H;
-        if (pos >= hi) {
-          for (int k = 0; k < H; ++k) As[(k0 + k) * TM + r] = 0.f;
-          continue;
-        }
-        const int row = sel_row(p.sel, pos);
-        if constexpr (MODE == G_NODE_UPD) {
-          if (seg == 0) {
-            put_col<TM>(As, k0, r, w.hstate + size_t(row) * H, H);
-          } else {
-            for (int k = 0; k < H; ++k) As[(k0 + k) * TM + r] = 0.f;
-            if (seg == 1) {
-              const int a = min(w.row_ptr[row], E), z = min(w.row_ptr[row + 1], E);
-              for (int e = a; e < z; ++e) add_col<TM>(As, k0, r, w.estate + size_t(e) * H, H);
-            } else {
-              const int a = w.in_ptr[row], z = w.in_ptr[row + 1];
-              for (int q = a; q < z; ++q)
-                add_col<TM>(As, k0, r, w.estate + size_t(w.in_edge[q]) * H, H);
-            }
-          }
-        } else if constexpr (MODE == G_EDGE_ENC) {
-          // projections: W_src h_src (first half of P[src]), W_dst h_dst (second half of P[dst])
-          put_col<TM>(As, k0, r,
-                      w.pstate + size_t(seg == 0 ? w.src[row] : w.col[row]) * 2 * H + seg * H, H);
-        } else if constexpr (MODE == G_CLS) {
-          put_col<TM>(As, k0, r, w.estate + size_t(row) * H, H);
-        } else {  // edge step: [e, W_src h_src, W_dst h_dst]
-          const float* src =
-              seg == 0 ? w.estate + size_t(row) * H
-                       : w.pstate + size_t(seg == 1 ? w.src[row] : w.col[row]) * 2 * H + (seg - 1) * H;
-          put_col<TM>(As, k0, r, src, H);
-        }
-      }
-    }
-    __syncthreads();
-
-    float acc[RM][CW];
-    if constexpr (MODE != G_CLS) {
-      // ---- layer 1 -> LayerNorm -> ReLU -------------------------------------
-      if constexpr (MODE == G_EDGE_ENC) {
-        // b + W_src h_src + W_dst h_dst: the products come projected
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-          const float bj = p.m.l1.b[c0 + j];
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-            acc[i][j] = bj + As[(c0 + j) * TM + r0 + i] + As[(H + c0 + j) * TM + r0 + i];
-        }
-      } else if constexpr (MODE == G_EDGE_UPD || MODE == G_EDGE_UPD_CLS) {
-        // b + W_e e over the e block, plus the gathered projections
-        LayerF32 le = p.m.l1;
-        le.in = H;
-        tile_layer<RM, CW, TM>(As, H, le, r0, c0, acc);
-#pragma unroll
-        for (int j = 0; j < CW; ++j)
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-            acc[i][j] += As[(H + c0 + j) * TM + r0 + i] + As[(2 * H + c0 + j) * TM + r0 + i];
-      } else {
-        tile_layer<RM, CW, TM>(As, K1, p.m.l1, r0, c0, acc);
-      }
-      tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
-      __syncthreads();
-      for (int r = tid; r < TM; r += NT) col_ln_relu<TM>(Hs, H, r);
-      __syncthreads();
-      // ---- layer 2 + residual ---------------------------------------------
-      tile_layer<RM, CW, TM>(Hs, H, p.m.l2, r0, c0, acc);
-      if constexpr (MODE == G_NODE_UPD || MODE == G_EDGE_UPD || MODE == G_EDGE_UPD_CLS) {
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < CW; ++j) acc[i][j] += As[(c0 + j) * TM + r0 + i];
-      }
-    }
-    if constexpr (MODE == G_EDGE_UPD_CLS || MODE == G_CLS) {
-      // ---- classifier: Linear -> LayerNorm -> ReLU -> dot, then the cut ------
-      if constexpr (MODE == G_EDGE_UPD_CLS) {
-        // the new edge state becomes segment 0 of As (each element is read and
-        // written by the same thread)
-        tile_store_t<RM, CW, TM>(As, r0, c0, acc, false);
-        __syncthreads();
-      }
-      tile_layer<RM, CW, TM>(As, H, p.cls.l1, r0, c0, acc);
-      __syncthreads();  // everyone is done reading Hs (layer 2 above)
-      tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
-      __syncthreads();
-      for (int r = tid; r < TM; r += NT) {
-        col_ln_relu<TM>(Hs, H, r);
-        if (base + r < hi) {
-          const int row = sel_row(p.sel, base + r);
-          float lg = p.cls.l2.b[0];
-          for (int k = 0; k < H; ++k) lg = fmaf(Hs[k * TM + r], p.cls.l2.WT[k * p.cls.l2.ldo], lg);
-          bool write = true;
-          if (p.rescore_only) {
-            const float old = w.logit[row];
-            write = old > p.band_lo && old < p.band_hi;
-          }
-          if (write) {
-            w.logit[row] = lg;
-            w.keep[row] = lg >= p.cut ? 1 : 0;
-          }
-        }
-      }
-    } else {
-      // ---- store the new state ---------------------------------------------
-      float* dst = (MODE == G_NODE_ENC || MODE == G_NODE_UPD) ? w.hstate : w.estate;
-#pragma unroll
-      for (int i = 0; i < RM; ++i) {
-        if (base + r0 + i < hi) {
-          const int row = sel_row(p.sel, base + r0 + i);
-          float4* d4 = reinterpret_cast<float4*>(dst + size_t(row) * H + c0);
-#pragma unroll
-          for (int j = 0; j < CW; j += 4)
-            d4[j / 4] = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
-        }
-      }
-      if constexpr (MODE == G_NODE_ENC || MODE == G_NODE_UPD) {
-        // ---- projections of the new node state for the next edge layer -----
-        __syncthreads();  // everyone is done reading Hs (layer 2 above)
-        tile_store_t<RM, CW, TM>(Hs, r0, c0, acc, false);
-        __syncthreads();
-        for (int half = 0; half < 2; ++half) {
-          tile_layer<RM, CW, TM>(Hs, H, half == 0 ? p.proj.src : p.proj.dst, r0, c0, acc);
-#pragma unroll
-          for (int i = 0; i < RM; ++i) {
-            if (base + r0 + i < hi) {
-              const int row = sel_row(p.sel, base + r0 + i);
-              float4* d4 = reinterpret_cast<float4*>(w.pstate + size_t(row) * 2 * H + half * H + c0);
-#pragma unroll
-              for (int j = 0; j < CW; j += 4)
-                d4[j / 4] = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -478,23 +638,15 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
 }
 
 template <int H, int MODE, int V>
-size_t gnn_smem() {
-  constexpr int TM = Shape<H, V>::TM;
-  constexpr int NSEG = g_nseg(MODE);
-  constexpr int K1 = MODE == G_NODE_ENC ? 3 : NSEG * H;
-  return size_t((K1 > 4 ? K1 : 4) + H) * TM * sizeof(float);
-}
-
-template <int H, int MODE, int V>
 void launch_gnn_v(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
-  constexpr int TM = Shape<H, V>::TM, NT = Shape<H, V>::NT;
-  const size_t smem = gnn_smem<H, MODE, V>();
-  const void* fn = (const void*)k_gnn_f32<H, MODE, V>;
-  const int full = device_sms() * blocks_per_sm(fn, NT, smem);
+  constexpr int NW = Warps<V>::NW, WR = WarpTile<H>::WR;
+  const size_t smem = size_t(NW) * g_warp_floats<H, MODE>() * sizeof(float);
+  const void* fn = (const void*)k_gnn_f32<H, MODE, NW>;
+  const int full = device_sms() * blocks_per_sm(fn, NW * 32, smem);
   dim3 grid(full, 1);
   if (a.sel.rows == nullptr && rows_hint >= 0)
-    grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, TM)));
-  k_gnn_f32<H, MODE, V><<<grid, NT, smem, s>>>(a);
+    grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, NW * WR)));
+  k_gnn_f32<H, MODE, NW><<<grid, NW * 32, smem, s>>>(a);
 }
 
 constexpr int f32_family(int mode) {
@@ -586,6 +738,16 @@ void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, S
 void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const EdgeProj& proj,
                             int h, Sel sel, cudaStream_t s) {
   if (b.n_hits <= 0) return;
+  {
+    const int full = device_sms() * 8;
+    const int grid = sel.rows ? full : std::max(1, std::min(full, div_up(b.n_hits, 32)));
+    if (h == 32)
+      k_msg_f32<32><<<grid, 256, 0, s>>>(b, w, sel);
+    else if (h == 64)
+      k_msg_f32<64><<<grid, 256, 0, s>>>(b, w, sel);
+    else
+      k_msg_f32<128><<<grid, 256, 0, s>>>(b, w, sel);
+  }
   GnnArgs a = gnn_args(b, w, sel);
   a.m = m;
   a.proj = proj;
