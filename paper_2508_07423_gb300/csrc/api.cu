@@ -363,7 +363,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     stage(h, "edge_encoder", s, 1,
           [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
     for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 1,
+      stage(h, "node_update", s, 2,
             [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
       stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
             [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k); });

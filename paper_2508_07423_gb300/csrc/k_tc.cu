@@ -373,30 +373,29 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       if (valid) {
         sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.hstate16 + size_t(r) * H,
                                      H <= 64 ? keep_row : nullptr);
-        const int E = clamp_edges(w.counters, w.e_cap);
-        float acc[H];
+        // the message sums [sum_out e, sum_in e] (FP32, written by k_msg_bf16
+        // into the node's projection row)
+        const float4* m4 = reinterpret_cast<const float4*>(w.pstate + size_t(r) * 2 * H);
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          float acc[H];
 #pragma unroll
-        for (int i = 0; i < H; ++i) acc[i] = 0.f;
-        const int a = min(w.row_ptr[r], E), z = min(w.row_ptr[r + 1], E);
-        for (int e = a; e < z; ++e) add_bf16_row<H>(acc, w.estate16 + size_t(e) * H);
-        float amax = 0.f;
-        if constexpr (FP8) {
+          for (int i = 0; i < H / 4; ++i) {
+            const float4 v = m4[side * (H / 4) + i];
+            acc[4 * i] = v.x;
+            acc[4 * i + 1] = v.y;
+            acc[4 * i + 2] = v.z;
+            acc[4 * i + 3] = v.w;
+          }
+          float amax = 0.f;
+          if constexpr (FP8) {
 #pragma unroll
-          for (int i = 0; i < H; ++i) amax = fmaxf(amax, fabsf(acc[i]));
+            for (int i = 0; i < H; ++i) amax = fmaxf(amax, fabsf(acc[i]));
+          }
+          sa[1 + side] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
+          put_row_f32<FP8>(sA, tid, KCH1, (1 + side) * H, acc, H,
+                           FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
         }
-        sa[1] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
-        put_row_f32<FP8>(sA, tid, KCH1, H, acc, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
-#pragma unroll
-        for (int i = 0; i < H; ++i) acc[i] = 0.f;
-        const int ia = w.in_ptr[r], iz = w.in_ptr[r + 1];
-        for (int k = ia; k < iz; ++k) add_bf16_row<H>(acc, w.estate16 + size_t(w.in_edge[k]) * H);
-        amax = 0.f;
-        if constexpr (FP8) {
-#pragma unroll
-          for (int i = 0; i < H; ++i) amax = fmaxf(amax, fabsf(acc[i]));
-        }
-        sa[2] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
-        put_row_f32<FP8>(sA, tid, KCH1, 2 * H, acc, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
       } else {
         float z[16] = {};
         for (int k = 0; k < K1; k += 16) put_row_f32<FP8>(sA, tid, KCH1, k, z, 16, 1.f);
@@ -675,6 +674,76 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem_base, L::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// messages of the node step from the BF16 edge states: P[v] = [sum of e over
+// v's out edges | sum over its in edges], FP32 sums in increasing list order
+// starting from zero. One group of 8 lanes per node, H/8 columns per lane;
+// U list entries per round are loaded together (entries past the end reload
+// a valid row and are dropped).
+// ---------------------------------------------------------------------------
+template <int H>
+__global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
+  constexpr int CPL = H / 8;                 // columns per lane
+  constexpr int NV = CPL / 8 > 0 ? CPL / 8 : 1;  // uint4 loads per lane (CPL >= 8)
+  constexpr int U = 8;
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+  const int E = clamp_edges(w.counters, w.e_cap);
+  const int q = threadIdx.x & 7;
+  const int groups = gridDim.x * (blockDim.x >> 3);
+  for (int row = blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3); row < b.n_hits; row += groups) {
+    float* out = w.pstate + size_t(row) * 2 * H + q * CPL;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      int a, n;
+      if (side == 0) {
+        a = min(w.row_ptr[row], E);
+        n = min(w.row_ptr[row + 1], E) - a;
+      } else {
+        a = w.in_ptr[row];
+        n = w.in_ptr[row + 1] - a;
+      }
+      float s[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) s[c] = 0.f;
+      for (int t0 = 0; t0 < n; t0 += U) {
+        uint32_t v[U][CPL / 2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int at = a + min(t0 + u, n - 1);
+          const int e = side == 0 ? at : __ldg(w.in_edge + at);
+          const __nv_bfloat16* ep = w.estate16 + size_t(e) * H + q * CPL;
+          if constexpr (CPL == 4) {
+            const uint2 x = __ldg(reinterpret_cast<const uint2*>(ep));
+            v[u][0] = x.x;
+            v[u][1] = x.y;
+          } else {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              const uint4 x = __ldg(reinterpret_cast<const uint4*>(ep) + k);
+              v[u][4 * k] = x.x;
+              v[u][4 * k + 1] = x.y;
+              v[u][4 * k + 2] = x.z;
+              v[u][4 * k + 3] = x.w;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (t0 + u < n) {
+#pragma unroll
+            for (int c = 0; c < CPL / 2; ++c) {
+              s[2 * c] += bf16_lo(v[u][c]);
+              s[2 * c + 1] += bf16_hi(v[u][c]);
+            }
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < CPL; c += 4)
+        *reinterpret_cast<float4*>(out + side * H + c) = make_float4(s[c], s[c + 1], s[c + 2], s[c + 3]);
+    }
   }
 }
 
@@ -1025,6 +1094,13 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
   for (int k = 0; k < K; ++k) {
     if (stage < 0 || stage == 1 + 2 * k) {
       set(m.node[k]);
+      const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 32)));
+      if (h == 32)
+        k_msg_bf16<32><<<grid, 256, 0, s>>>(b, w);
+      else if (h == 64)
+        k_msg_bf16<64><<<grid, 256, 0, s>>>(b, w);
+      else
+        k_msg_bf16<128><<<grid, 256, 0, s>>>(b, w);
       launch_any(h, fp8, M_NODE_UPD, a, s, b.n_hits);
     }
     if (stage < 0 || stage == 2 + 2 * k) {
