@@ -90,12 +90,18 @@ __device__ __forceinline__ void warp_layer(const float* A, const LayerF32& L, in
 #pragma unroll
       for (int i = 0; i < RM; ++i) {
         const float av = t == 0 ? a[i].x : (t == 1 ? a[i].y : (t == 2 ? a[i].z : a[i].w));
+        const float2 a2 = make_float2(av, av);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-          acc[i][4 * j] = fmaf(av, q[j].x, acc[i][4 * j]);
-          acc[i][4 * j + 1] = fmaf(av, q[j].y, acc[i][4 * j + 1]);
-          acc[i][4 * j + 2] = fmaf(av, q[j].z, acc[i][4 * j + 2]);
-          acc[i][4 * j + 3] = fmaf(av, q[j].w, acc[i][4 * j + 3]);
+          // two columns per packed FMA (each lane rounds like fmaf)
+          float2 c01 = __ffma2_rn(a2, make_float2(q[j].x, q[j].y),
+                                  make_float2(acc[i][4 * j], acc[i][4 * j + 1]));
+          float2 c23 = __ffma2_rn(a2, make_float2(q[j].z, q[j].w),
+                                  make_float2(acc[i][4 * j + 2], acc[i][4 * j + 3]));
+          acc[i][4 * j] = c01.x;
+          acc[i][4 * j + 1] = c01.y;
+          acc[i][4 * j + 2] = c23.x;
+          acc[i][4 * j + 3] = c23.y;
         }
       }
     }
@@ -460,10 +466,9 @@ __global__ void __launch_bounds__(256) k_msg_f32(Batch b, Ws w, Sel sel) {
           if (t0 + u < n) {
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
-              s[j].x += v[u][j].x;
-              s[j].y += v[u][j].y;
-              s[j].z += v[u][j].z;
-              s[j].w += v[u][j].w;
+              const float2 lo = __fadd2_rn(make_float2(s[j].x, s[j].y), make_float2(v[u][j].x, v[u][j].y));
+              const float2 hi = __fadd2_rn(make_float2(s[j].z, s[j].w), make_float2(v[u][j].z, v[u][j].w));
+              s[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
             }
           }
       }

@@ -735,8 +735,10 @@ __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
           if (t0 + u < n) {
 #pragma unroll
             for (int c = 0; c < CPL / 2; ++c) {
-              s[2 * c] += bf16_lo(v[u][c]);
-              s[2 * c + 1] += bf16_hi(v[u][c]);
+              const float2 r = __fadd2_rn(make_float2(s[2 * c], s[2 * c + 1]),
+                                          make_float2(bf16_lo(v[u][c]), bf16_hi(v[u][c])));
+              s[2 * c] = r.x;
+              s[2 * c + 1] = r.y;
             }
           }
       }
