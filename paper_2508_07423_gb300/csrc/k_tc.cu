@@ -89,9 +89,21 @@ struct Layout {
   static constexpr int W2_BYTES = HAS_W2 ? H * H * ESZ : 0;
   static constexpr int WC = align1k(W2 + W2_BYTES);
   static constexpr int WC_BYTES = HAS_WC ? H * H * ESZ : 0;
+  // BF16 node-step tiles ([h, m_out, m_in], contiguous rows) are gathered by
+  // coalesced cp.async copies; with PREFETCH into two alternating layer-1
+  // input buffers (tile t + 1 loads while tile t computes). Edge tiles keep
+  // the per-row copies, whose h_src / h_dst loads hit L1 for edges sharing a
+  // hit (measured faster than both cp.async forms on 1000 events).
+  static constexpr bool PIPE = !FP8 && MODE == M_NODE_UPD;
+  static constexpr bool PREFETCH = false;
   static constexpr int A = align1k(WC + WC_BYTES);
-  static constexpr int A_BYTES = kRows * (K1 > H ? K1 : H) * ESZ;
-  static constexpr int PAR = align1k(A + A_BYTES);
+  static constexpr int A_BYTES = MODE == M_NODE_ENC ? 0 : kRows * K1 * ESZ;
+  static constexpr int NBUF = PIPE && PREFETCH ? 2 : 1;
+  // hidden / classifier input: its own tile with two input buffers, else it
+  // overwrites the layer-1 input once the layer-1 MMAs are done
+  static constexpr int HA = NBUF == 2 || MODE == M_NODE_ENC ? align1k(A + NBUF * A_BYTES) : A;
+  static constexpr int HA_BYTES = NBUF == 2 || MODE == M_NODE_ENC ? kRows * H * ESZ : 0;
+  static constexpr int PAR = align1k(HA_BYTES > 0 ? HA + HA_BYTES : A + NBUF * A_BYTES);
   // fp32 parameters: b1, b2, bc1, s1, s2, sc, c2 weights, ne1 (3 x H + H)
   static constexpr int PAR_FLOATS = 7 * H + 4 * H + 8;
   static constexpr int BAR = PAR + PAR_FLOATS * 4;
@@ -232,6 +244,44 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, con
   }
 }
 
+// Issue the cp.async copies of one BF16 tile's layer-1 input (rows row0 ..
+// row0 + 127; rows at or past `hi` are zero-filled): segment s of row r, chunk
+// c (16 bytes) lands at tile_off(r, s * H/8 + c). Consecutive threads take the
+// chunks of one row, so a warp reads 8 rows x H*2 bytes per segment.
+template <int H, int MODE>
+__device__ __forceinline__ void gather_async(uint8_t* dst, const TcArgs& p, int row0, int hi,
+                                             int tid) {
+  constexpr int CH = H / 8;
+  constexpr int NSEG = n_seg(MODE);
+  constexpr int KCH = NSEG * CH;
+  const Ws& w = p.w;
+  const __nv_bfloat16* msg16 = reinterpret_cast<const __nv_bfloat16*>(w.pstate);
+#pragma unroll
+  for (int L = tid; L < kRows * CH; L += kRows) {
+    const int rr = L / CH, c = L % CH;
+    const int r = row0 + rr;
+    const uint32_t n = r < hi ? 16u : 0u;
+    const int rs = r < hi ? r : 0;
+    const __nv_bfloat16* src[3];
+    if constexpr (MODE == M_NODE_UPD) {
+      src[0] = w.hstate16 + size_t(rs) * H;
+      src[1] = msg16 + size_t(rs) * 2 * H;
+      src[2] = src[1] + H;
+    } else if constexpr (MODE == M_EDGE_ENC) {
+      src[0] = w.hstate16 + size_t(w.src[rs]) * H;
+      src[1] = w.hstate16 + size_t(w.col[rs]) * H;
+    } else if constexpr (MODE == M_CLS) {
+      src[0] = w.estate16 + size_t(rs) * H;
+    } else {
+      src[0] = w.estate16 + size_t(rs) * H;
+      src[1] = w.hstate16 + size_t(w.src[rs]) * H;
+      src[2] = w.hstate16 + size_t(w.col[rs]) * H;
+    }
+#pragma unroll
+    for (int sg = 0; sg < NSEG; ++sg) cp_async16(dst + tile_off(rr, sg * CH + c, KCH), src[sg] + 8 * c, n);
+  }
+}
+
 template <int H, bool FP8, int MODE>
 __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   using L = Layout<H, FP8, MODE>;
@@ -239,7 +289,6 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   uint8_t* sW1 = smem + L::W1;
   uint8_t* sW2 = smem + L::W2;
   uint8_t* sWC = smem + L::WC;
-  uint8_t* sA = smem + L::A;
   float* par = reinterpret_cast<float*>(smem + L::PAR);
   float* pb1 = par;
   float* pb2 = par + H;
@@ -323,15 +372,37 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
     return true;
   };
 
-  for (int t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
+  if constexpr (L::PIPE && L::PREFETCH) {
+    if (int(blockIdx.x) < n_tiles && !aborted)
+      gather_async<H, MODE>(smem + L::A, p, lo + int(blockIdx.x) * kRows, hi, tid);
+    cp_async_commit();
+  }
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x, ++it) {
     const int r = lo + t * kRows + tid;
     const bool valid = r < hi;
+    uint8_t* sA = smem + L::A + (L::NBUF == 2 ? (it & 1) * L::A_BYTES : 0);
+    uint8_t* sHA = L::HA == L::A ? sA : smem + L::HA;  // layer-2 input and classifier input
     float sa[3] = {1.f, 1.f, 1.f};  // FP8 per-row scales of the layer-1 segments
     uint4 keep_row[(H <= 64) ? H / 8 : 1];
     (void)keep_row;
 
     // ---- 1. gather ---------------------------------------------------------
-    if constexpr (MODE == M_NODE_ENC) {
+    if constexpr (L::PIPE && L::PREFETCH) {
+      // every thread is done with the other buffer (tile it - 1): fill it with
+      // the next tile, then wait for this tile's copies
+      __syncthreads();
+      const int tn = t + int(gridDim.x);
+      if (tn < n_tiles)
+        gather_async<H, MODE>(smem + L::A + ((it + 1) & 1) * L::A_BYTES, p, lo + tn * kRows, hi, tid);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else if constexpr (L::PIPE) {
+      __syncthreads();  // every thread is done with the buffer (tile it - 1)
+      gather_async<H, MODE>(sA, p, lo + t * kRows, hi, tid);
+      cp_async_commit();
+      cp_async_wait<0>();
+    } else if constexpr (MODE == M_NODE_ENC) {
       // FP32 first layer (K = 3) in registers, then LayerNorm + ReLU into A
       float hid[H];
       if (valid) {
@@ -363,11 +434,11 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           amax = fmaxf(amax, hid[i]);
         }
         sa[0] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
-        put_row_f32<FP8>(sA, tid, KCHH, 0, hid, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
+        put_row_f32<FP8>(sHA, tid, KCHH, 0, hid, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
       } else {
 #pragma unroll
         for (int i = 0; i < H; ++i) hid[i] = 0.f;
-        put_row_f32<FP8>(sA, tid, KCHH, 0, hid, H, 1.f);
+        put_row_f32<FP8>(sHA, tid, KCHH, 0, hid, H, 1.f);
       }
     } else if constexpr (MODE == M_NODE_UPD) {
       if (valid) {
@@ -435,6 +506,16 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       if (!wait_mma()) {
         aborted = true;
         break;
+      }
+      if constexpr (L::PIPE && L::HA == L::A) {
+        // the hidden tile overwrites the layer-1 input: keep this row's
+        // residual segment in registers first
+        if constexpr (MODE == M_NODE_UPD || MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS) {
+#pragma unroll
+          for (int c = 0; c < H / 8; ++c)
+            keep_row[c] = *reinterpret_cast<const uint4*>(sA + tile_off(tid, c, KCH1));
+        }
+        __syncthreads();
       }
       // ---- 3. bias + LayerNorm + ReLU (-> A as the next operand, or the
       //         classifier output for M_CLS) -------------------------------
@@ -510,7 +591,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         xval(c, x);
 #pragma unroll
         for (int j = 0; j < 32; ++j) x[j] = fmaxf((x[j] - mean) * inv, 0.f);
-        put_row_f32<FP8>(sA, tid, KCHH, c * 32, x, 32, hinv);
+        put_row_f32<FP8>(sHA, tid, KCHH, c * 32, x, 32, hinv);
       }
       fence_proxy_async();
       tc_fence_before();
@@ -522,7 +603,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
     // ---- 4. layer 2 ----------------------------------------------------------
     if (tid == 0) {
       tc_fence_after();
-      issue_layer<H, FP8>(tmem_base, sA, sW2, H, 1);
+      issue_layer<H, FP8>(tmem_base, sHA, sW2, H, 1);
       mma_commit(&bar[1]);
     }
     if (!wait_mma()) {
@@ -546,8 +627,10 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         const __nv_bfloat16* rowp = (MODE == M_NODE_UPD ? w.hstate16 : w.estate16) + size_t(r) * H;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint4 u = (H <= 64) ? keep_row[c * 4 + q]
-                                    : reinterpret_cast<const uint4*>(rowp)[c * 4 + q];
+          const uint4 u = (L::PIPE && L::HA != L::A)
+                              ? *reinterpret_cast<const uint4*>(sA + tile_off(tid, c * 4 + q, KCH1))
+                          : (H <= 64) ? keep_row[c * 4 + q]
+                                      : reinterpret_cast<const uint4*>(rowp)[c * 4 + q];
           z[8 * q + 0] += bf16_lo(u.x);
           z[8 * q + 1] += bf16_hi(u.x);
           z[8 * q + 2] += bf16_lo(u.y);
@@ -601,14 +684,14 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         resid(c, z);
 #pragma unroll
         for (int j = 0; j < 32; ++j) z[j] = __bfloat162float(__float2bfloat16_rn(z[j]));
-        put_row_f32<FP8>(sA, tid, KCHH, c * 32, z, 32, einv);
+        put_row_f32<FP8>(sHA, tid, KCHH, c * 32, z, 32, einv);
       }
       fence_proxy_async();
       tc_fence_before();
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        issue_layer<H, FP8>(tmem_base, sA, sWC, H, 1);
+        issue_layer<H, FP8>(tmem_base, sHA, sWC, H, 1);
         mma_commit(&bar[1]);
       }
       if (!wait_mma()) {
@@ -664,6 +747,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 
   // ---- clean-up: on a timeout, give the outstanding MMAs one more bounded
   //      wait, then free the tensor memory -----------------------------------
+  if constexpr (L::PIPE) cp_async_wait<0>();  // no copy may land after the exit
   if (aborted) {
     if (tid == 0) set_status(w.counters, ST_TIMEOUT);
     if (weights_late) mbar_wait_bounded(&bar[0], 0, kWaitCycles);
@@ -680,11 +764,13 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 // ---------------------------------------------------------------------------
 // messages of the node step from the BF16 edge states: P[v] = [sum of e over
 // v's out edges | sum over its in edges], FP32 sums in increasing list order
-// starting from zero. One group of 8 lanes per node, H/8 columns per lane;
-// U list entries per round are loaded together (entries past the end reload
-// a valid row and are dropped).
+// starting from zero, stored as FP32 (FP8 path: the node step quantises them
+// with a per-row scale) or rounded to BF16 (BF16 path: the layer-1 operand
+// as the node step would round it). One group of 8 lanes per node, H/8
+// columns per lane; U list entries per round are loaded together (entries
+// past the end reload a valid row and are dropped).
 // ---------------------------------------------------------------------------
-template <int H>
+template <int H, bool OUT16>
 __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
   constexpr int CPL = H / 8;                 // columns per lane
   constexpr int NV = CPL / 8 > 0 ? CPL / 8 : 1;  // uint4 loads per lane (CPL >= 8)
@@ -742,9 +828,18 @@ __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
             }
           }
       }
+      if constexpr (OUT16) {
+        __nv_bfloat16* o16 = reinterpret_cast<__nv_bfloat16*>(w.pstate) + size_t(row) * 2 * H +
+                             side * H + q * CPL;
 #pragma unroll
-      for (int c = 0; c < CPL; c += 4)
-        *reinterpret_cast<float4*>(out + side * H + c) = make_float4(s[c], s[c + 1], s[c + 2], s[c + 3]);
+        for (int c = 0; c < CPL; c += 4)
+          *reinterpret_cast<uint2*>(o16 + c) =
+              make_uint2(pack_bf16(s[c], s[c + 1]), pack_bf16(s[c + 2], s[c + 3]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPL; c += 4)
+          *reinterpret_cast<float4*>(out + side * H + c) = make_float4(s[c], s[c + 1], s[c + 2], s[c + 3]);
+      }
     }
   }
 }
@@ -1098,11 +1193,11 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
       set(m.node[k]);
       const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 32)));
       if (h == 32)
-        k_msg_bf16<32><<<grid, 256, 0, s>>>(b, w);
+        fp8 ? k_msg_bf16<32, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<32, true><<<grid, 256, 0, s>>>(b, w);
       else if (h == 64)
-        k_msg_bf16<64><<<grid, 256, 0, s>>>(b, w);
+        fp8 ? k_msg_bf16<64, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<64, true><<<grid, 256, 0, s>>>(b, w);
       else
-        k_msg_bf16<128><<<grid, 256, 0, s>>>(b, w);
+        fp8 ? k_msg_bf16<128, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<128, true><<<grid, 256, 0, s>>>(b, w);
       launch_any(h, fp8, M_NODE_UPD, a, s, b.n_hits);
     }
     if (stage < 0 || stage == 2 + 2 * k) {
