@@ -268,8 +268,17 @@ __host__ __device__ constexpr int g_warp_floats() {
          (MODE == G_NODE_UPD ? WarpTile<H>::WR * WarpTile<H>::LDH : 0);
 }
 
+// Resident blocks per SM the register budget is sized for: at h = 32 the
+// 4-warp edge kernels fit 5 blocks of shared memory per SM, so their
+// registers are capped to let 5 blocks (20 warps) reside; elsewhere the
+// compiler's choice stands.
 template <int H, int MODE, int NW>
-__global__ void __launch_bounds__(NW * 32) k_gnn_f32(const GnnArgs p) {
+__host__ __device__ constexpr int g_min_blocks() {
+  return (H == 32 && NW == 4 && MODE != G_NODE_ENC && MODE != G_NODE_UPD) ? 5 : 1;
+}
+
+template <int H, int MODE, int NW>
+__global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_f32(const GnnArgs p) {
   using T = WarpTile<H>;
   constexpr int RM = T::RM, CW = T::CW, WR = T::WR;
   constexpr int LDA = g_lda<H, MODE>();
