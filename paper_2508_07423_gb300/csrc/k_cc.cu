@@ -9,6 +9,7 @@
 //     ancestor, which keeps parent[i] <= i).
 // A label is the root minus the event's first index: the smallest event-local
 // input index of the component.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/gnntrk.h"
@@ -119,6 +120,45 @@ __global__ void k_na_label(const int32_t* scratch, int n, int32_t* labels) {
     labels[v] = bad ? -1 : uf_find(P, v);
 }
 
+// ---------------------------------------------------------------------------
+// One block per event: events are independent and their hits and edges are
+// contiguous (sorted positions are event-major, edges are CSR rows), so the
+// union-find runs in shared memory over event-local input indices, with the
+// same hooking rule. An event with more than kCcSmemHits hits runs the same
+// steps on its slice of the global parent array.
+// ---------------------------------------------------------------------------
+constexpr int kCcThreads = 256;
+constexpr int kCcSmemHits = 8192;
+
+__global__ void __launch_bounds__(kCcThreads) k_cc_event(Batch b, Ws w) {
+  extern __shared__ int32_t sP[];
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+  const int E = clamp_edges(w.counters, w.e_cap);
+  int kept = 0;
+  for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
+    const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
+    const int n = v1 - v0;
+    const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
+    int32_t* P = n <= kCcSmemHits ? sP : w.parent + v0;  // local index -> parent
+    for (int i = threadIdx.x; i < n; i += kCcThreads) P[i] = i;
+    __syncthreads();
+    for (int e = e0 + threadIdx.x; e < e1; e += kCcThreads) {
+      if (!w.keep[e]) continue;
+      ++kept;
+      uf_union(P, w.perm[w.src[e]] - v0, w.perm[w.col[e]] - v0, w.counters);
+    }
+    __syncthreads();
+    for (int v = v0 + threadIdx.x; v < v1; v += kCcThreads) {
+      const int i = w.perm[v];
+      b.labels[i] = uf_find(P, i - v0);
+    }
+    __syncthreads();  // P is reused by the next event
+  }
+  // kept-edge count
+  for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&w.counters[C_KEPT], kept);
+}
+
 }  // namespace
 
 void set_global_error(const std::string& msg);
@@ -142,8 +182,18 @@ static cudaError_t noalloc_scratch(int32_t** out) {
 }
 
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s) {
-  k_cc_union<<<device_sms() * 8, 256, 0, s>>>(w);
-  if (b.n_hits > 0) k_cc_label<<<div_up(b.n_hits, 256), 256, 0, s>>>(b, w);
+  if (b.n_events <= 0 || b.n_hits <= 0) {
+    k_cc_union<<<device_sms() * 8, 256, 0, s>>>(w);
+    return;
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_cc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCcSmemHits * int(sizeof(int32_t)));
+    attr_set = true;
+  }
+  k_cc_event<<<std::min(b.n_events, device_sms() * 16), kCcThreads,
+               kCcSmemHits * sizeof(int32_t), s>>>(b, w);
 }
 
 }  // namespace gnntrk
