@@ -127,11 +127,13 @@ __global__ void k_na_label(const int32_t* scratch, int n, int32_t* labels) {
 // same hooking rule. An event with more than kCcSmemHits hits runs the same
 // steps on its slice of the global parent array.
 // ---------------------------------------------------------------------------
-constexpr int kCcThreads = 256;
-constexpr int kCcSmemHits = 8192;
+constexpr int kCcThreads = 512;
+constexpr int kCcSmemHits = 6144;
 
 __global__ void __launch_bounds__(kCcThreads) k_cc_event(Batch b, Ws w) {
-  extern __shared__ int32_t sP[];
+  extern __shared__ int32_t sm_cc[];
+  int32_t* sP = sm_cc;                // [kCcSmemHits] parents (event-local input index)
+  int32_t* sL = sm_cc + kCcSmemHits;  // [kCcSmemHits] local input index of sorted position
   if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
   const int E = clamp_edges(w.counters, w.e_cap);
   int kept = 0;
@@ -139,20 +141,26 @@ __global__ void __launch_bounds__(kCcThreads) k_cc_event(Batch b, Ws w) {
     const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
     const int n = v1 - v0;
     const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
-    int32_t* P = n <= kCcSmemHits ? sP : w.parent + v0;  // local index -> parent
-    for (int i = threadIdx.x; i < n; i += kCcThreads) P[i] = i;
+    const bool small = n <= kCcSmemHits;
+    int32_t* P = small ? sP : w.parent + v0;  // local index -> parent
+    for (int i = threadIdx.x; i < n; i += kCcThreads) {
+      P[i] = i;
+      if (small) sL[i] = w.perm[v0 + i] - v0;
+    }
     __syncthreads();
     for (int e = e0 + threadIdx.x; e < e1; e += kCcThreads) {
       if (!w.keep[e]) continue;
       ++kept;
-      uf_union(P, w.perm[w.src[e]] - v0, w.perm[w.col[e]] - v0, w.counters);
+      const int a = w.src[e] - v0, c = w.col[e] - v0;
+      uf_union(P, small ? sL[a] : w.perm[v0 + a] - v0, small ? sL[c] : w.perm[v0 + c] - v0,
+               w.counters);
     }
     __syncthreads();
-    for (int v = v0 + threadIdx.x; v < v1; v += kCcThreads) {
-      const int i = w.perm[v];
-      b.labels[i] = uf_find(P, i - v0);
+    for (int i = threadIdx.x; i < n; i += kCcThreads) {
+      const int li = small ? sL[i] : w.perm[v0 + i] - v0;
+      b.labels[v0 + li] = uf_find(P, li);
     }
-    __syncthreads();  // P is reused by the next event
+    __syncthreads();  // P and L are reused by the next event
   }
   // kept-edge count
   for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
@@ -189,11 +197,11 @@ void launch_cc(const Batch& b, const Ws& w, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_cc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kCcSmemHits * int(sizeof(int32_t)));
+                         2 * kCcSmemHits * int(sizeof(int32_t)));
     attr_set = true;
   }
   k_cc_event<<<std::min(b.n_events, device_sms() * 16), kCcThreads,
-               kCcSmemHits * sizeof(int32_t), s>>>(b, w);
+               2 * kCcSmemHits * sizeof(int32_t), s>>>(b, w);
 }
 
 }  // namespace gnntrk
