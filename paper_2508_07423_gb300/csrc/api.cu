@@ -338,11 +338,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
                 w.scan_blocks, s);
   });
   stage(h, "radius_fill", s, 1, [&] { launch_radius(b, w, g, h->D, true, s); });
-  stage(h, "scan_in", s, 2, [&] {
-    launch_scan(w.in_cnt, w.in_ptr, b.n_hits, 0x7fffffff, w.counters, C_SCAN_TOTAL, w.e_cap,
-                w.scan_blocks, s);
-  });
-  stage(h, "in_index", s, 2, [&] { launch_csc(b, w, s); });
+  stage(h, "in_index", s, 1, [&] { launch_csc(b, w, s); });
   if (!tc) {
     stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {

@@ -16,6 +16,8 @@
 //              scanning them; then block scans plus the block offset).
 //  k_csc_*     in-edge index: edges grouped by target, ascending edge id, so
 //              that message sums run in a fixed order.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gnntrk {
@@ -25,7 +27,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSortThreads = 256;
 constexpr int kRadiusThreads = 256;
-constexpr int kCandSmemBytes = 48 * 1024;
+constexpr int kCandSmemBytes = 12 * 1024;  // staged candidates (about 2-6 KB needed); 8 blocks per SM
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
 constexpr int kScanChunk = kScanThreads * kScanPer;
@@ -231,7 +233,6 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
           w.col[e] = t;
           w.src[e] = q;
           w.d2[e] = s;
-          atomicAdd(&w.in_cnt[t], 1);
         }
       }
       written += __popc(m);
@@ -358,30 +359,72 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* in, 
 // ---------------------------------------------------------------------------
 // in-edge index
 // ---------------------------------------------------------------------------
-__global__ void k_csc_fill(Ws w) {
+// In-edge index, one block per event: an event's edges are the contiguous
+// range [row_ptr[v0], row_ptr[v1]) and its in-edges are among them, so its
+// in_ptr / in_edge slice is built locally: in-degrees by shared-memory atomics,
+// a block-wide exclusive scan, placement by cursors, then each target's list
+// sorted by edge id (ascending, so the message sums have a fixed order). An
+// event with more than kCscSmemHits hits counts in its slice of in_cnt.
+constexpr int kCscThreads = 512;
+constexpr int kCscSmemHits = 8192;
+
+__global__ void __launch_bounds__(kCscThreads) k_csc_event(Batch b, Ws w) {
+  extern __shared__ int32_t sm_csc[];
+  __shared__ int wsum[kCscThreads / 32];
   if (input_bad(w)) return;
   const int E = clamp_edges(w.counters, w.e_cap);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-    const int t = w.col[e];
-    const int k = atomicSub(&w.in_cnt[t], 1) - 1;
-    w.in_edge[w.in_ptr[t] + k] = e;
-  }
-}
-
-__global__ void k_csc_sort(Batch b, Ws w) {
-  if (input_bad(w)) return;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < b.n_hits;
-       v += gridDim.x * blockDim.x) {
-    const int a = w.in_ptr[v], c = w.in_ptr[v + 1];
-    for (int i = a + 1; i < c; ++i) {
-      const int key = w.in_edge[i];
-      int j = i - 1;
-      while (j >= a && w.in_edge[j] > key) {
-        w.in_edge[j + 1] = w.in_edge[j];
-        --j;
-      }
-      w.in_edge[j + 1] = key;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
+    const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
+    const int n = v1 - v0;
+    const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
+    int32_t* C = n <= kCscSmemHits ? sm_csc : w.in_cnt + v0;
+    for (int i = tid; i < n; i += kCscThreads) C[i] = 0;
+    __syncthreads();
+    for (int e = e0 + tid; e < e1; e += kCscThreads) atomicAdd(&C[w.col[e] - v0], 1);
+    __syncthreads();
+    // exclusive scan: thread t owns the consecutive counts [t*per, (t+1)*per)
+    const int per = (n + kCscThreads - 1) / kCscThreads;
+    const int a = min(n, tid * per), z = min(n, a + per);
+    int sum = 0;
+    for (int i = a; i < z; ++i) sum += C[i];
+    int x = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, d);
+      if (lane >= d) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < warp; ++k) before += wsum[k];
+    int run = before + x - sum;
+    for (int i = a; i < z; ++i) {
+      const int c = C[i];
+      C[i] = run;  // cursor
+      w.in_ptr[v0 + i] = e0 + run;
+      run += c;
+    }
+    if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
+    __syncthreads();
+    for (int e = e0 + tid; e < e1; e += kCscThreads) {
+      const int k = atomicAdd(&C[w.col[e] - v0], 1);
+      w.in_edge[e0 + k] = e;
+    }
+    __syncthreads();
+    // C[i] is now the end of target i's list
+    for (int i = tid; i < n; i += kCscThreads) {
+      const int lo = w.in_ptr[v0 + i], hi = e0 + C[i];
+      for (int j = lo + 1; j < hi; ++j) {
+        const int key = w.in_edge[j];
+        int k = j - 1;
+        while (k >= lo && w.in_edge[k] > key) {
+          w.in_edge[k + 1] = w.in_edge[k];
+          --k;
+        }
+        w.in_edge[k + 1] = key;
+      }
+    }
+    __syncthreads();  // C is reused by the next event
   }
 }
 
@@ -428,9 +471,15 @@ void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t*
 }
 
 void launch_csc(const Batch& b, const Ws& w, cudaStream_t s) {
-  const int grid = num_sms() * 8;
-  k_csc_fill<<<grid, 256, 0, s>>>(w);
-  if (b.n_hits > 0) k_csc_sort<<<div_up(b.n_hits, 256), 256, 0, s>>>(b, w);
+  if (b.n_events <= 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_csc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCscSmemHits * int(sizeof(int32_t)));
+    attr_set = true;
+  }
+  k_csc_event<<<std::min(b.n_events, num_sms() * 16), kCscThreads,
+                kCscSmemHits * sizeof(int32_t), s>>>(b, w);
 }
 
 int device_sms() { return num_sms(); }
