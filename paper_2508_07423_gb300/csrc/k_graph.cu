@@ -123,10 +123,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(Batch b, Ws w, int P) {
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ float dist2(const float (&q)[D], const float* c) {
+  float cv[D];
+  if constexpr (D % 4 == 0) {  // 16-byte loads (rows are 16-byte aligned)
+#pragma unroll
+    for (int d = 0; d < D; d += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(c + d);
+      cv[d] = v.x;
+      cv[d + 1] = v.y;
+      cv[d + 2] = v.z;
+      cv[d + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < D; ++d) cv[d] = c[d];
+  }
   float s = 0.0f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    const float t = q[d] - c[d];
+    const float t = q[d] - cv[d];
     s = fmaf(t, t, s);
   }
   return s;
@@ -167,14 +181,31 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
   const bool staged = size_t(nc) * D * sizeof(float) <= size_t(kCandSmemBytes);
   const float* ce = staged ? cand_s : w.emb + size_t(c0) * D;
   if (staged) {
-    for (int k = tid; k < nc * D; k += blockDim.x) cand_s[k] = w.emb[size_t(c0) * D + k];
+    if constexpr (D % 4 == 0) {
+      const float4* g4 = reinterpret_cast<const float4*>(w.emb + size_t(c0) * D);
+      float4* s4 = reinterpret_cast<float4*>(cand_s);
+      for (int k = tid; k < nc * D / 4; k += blockDim.x) s4[k] = g4[k];
+    } else {
+      for (int k = tid; k < nc * D; k += blockDim.x) cand_s[k] = w.emb[size_t(c0) * D + k];
+    }
     __syncthreads();
   }
   const float r2 = g.radius2;
   for (int q = q0 + warp; q < q1; q += nwarps) {
     float qe[D];
+    if constexpr (D % 4 == 0) {
 #pragma unroll
-    for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+      for (int d = 0; d < D; d += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(w.emb + size_t(q) * D + d);
+        qe[d] = v.x;
+        qe[d + 1] = v.y;
+        qe[d + 2] = v.z;
+        qe[d + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+    }
     if (!FILL) {
       int cnt = 0;
       for (int base = 0; base < nc; base += 32) {
