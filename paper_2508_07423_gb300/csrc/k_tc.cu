@@ -92,8 +92,9 @@ struct Layout {
   // BF16 node-step tiles ([h, m_out, m_in], contiguous rows) are gathered by
   // coalesced cp.async copies; with PREFETCH into two alternating layer-1
   // input buffers (tile t + 1 loads while tile t computes). Edge tiles keep
-  // the per-row copies, whose h_src / h_dst loads hit L1 for edges sharing a
-  // hit (measured faster than both cp.async forms on 1000 events).
+  // the per-row copies: on the 1000-event batch they measured faster than
+  // cp.async (single or double buffered) and than conflict-free coalesced
+  // copies through registers (2.27 ms against 2.59-3.12 ms per 4 launches).
   static constexpr bool PIPE = !FP8 && MODE == M_NODE_UPD;
   static constexpr bool PREFETCH = false;
   static constexpr int A = align1k(WC + WC_BYTES);
@@ -244,6 +245,19 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, con
   }
 }
 
+// Copy slot l (0 .. H/8 - 1) of thread tid in a tile copy: warp w covers rows
+// 32w .. 32w+31; a quarter-warp (8 lanes) takes one 16-byte chunk of 8
+// consecutive rows, a contiguous 128-byte run of the canonical tile, so the
+// shared-memory stores are conflict-free, and a warp instruction reads 8 rows
+// x 4 chunks.
+template <int CH>
+__device__ __forceinline__ void copy_slot(int tid, int l, int& rr, int& c) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = l % 4, cq = l / 4;  // row group of 8, chunk quad
+  rr = warp * 32 + g * 8 + (lane & 7);
+  c = cq * 4 + (lane >> 3);
+}
+
 // Issue the cp.async copies of one BF16 tile's layer-1 input (rows row0 ..
 // row0 + 127; rows at or past `hi` are zero-filled): segment s of row r, chunk
 // c (16 bytes) lands at tile_off(r, s * H/8 + c). Consecutive threads take the
@@ -257,8 +271,9 @@ __device__ __forceinline__ void gather_async(uint8_t* dst, const TcArgs& p, int 
   const Ws& w = p.w;
   const __nv_bfloat16* msg16 = reinterpret_cast<const __nv_bfloat16*>(w.pstate);
 #pragma unroll
-  for (int L = tid; L < kRows * CH; L += kRows) {
-    const int rr = L / CH, c = L % CH;
+  for (int l = 0; l < CH; ++l) {
+    int rr, c;
+    copy_slot<CH>(tid, l, rr, c);
     const int r = row0 + rr;
     const uint32_t n = r < hi ? 16u : 0u;
     const int rs = r < hi ? r : 0;
