@@ -220,3 +220,21 @@ def test_cfg3_full_batch_sampled():
         g = tr.get_graph(e)
         a, z = int(b.offsets[e]), int(b.offsets[e + 1])
         assert np.array_equal(labels[a:z], cc_labels(z - a, g["src"], g["dst"], g["kept"]))
+
+
+def test_large_event_uses_global_scratch():
+    """One event of ~10 k hits: more than the shared-memory capacity of the
+    per-event in-edge index (8192 hits) and component labelling (6144), so
+    both take their global-memory path; parity as for small events."""
+    wl = synth.workload("cfg3_batched_bf16")
+    model = model_of(wl)
+    rng = np.random.default_rng([7007, 0])
+    ev = synth.gen_event(rng, 900, 0.05)
+    assert ev.n_hits > 8192
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=ev.n_hits, max_events=1,
+                                  edges_per_hit=32)
+    _, reps = run_and_compare(tr, ev, wl, model)
+    r = reps[0]
+    # labels equal the components of the kept edges (checked inside), scores
+    # and decisions match the oracle
+    assert r.edges > 40000 and r.scores_compared > 0.9 * r.edges

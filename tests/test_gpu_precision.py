@@ -120,6 +120,26 @@ def receptive_field(graphs, band, K, batch):
     return edges, hits
 
 
+@pytest.mark.parametrize("name,prec", [("cfg2_run3_single", "bf16"), ("cfg4_batched_fp8", "fp8")])
+def test_rescore_band_wide_models(name, prec):
+    """h = 64 (BF16) and h = 128 (FP8): band edges take the FP32 path's logits
+    bit for bit, and the re-score recomputes exactly the receptive field."""
+    wl = synth.workload(name)
+    b = synth.workload_batch(wl, 2)
+    band = 0.05
+    _, g0, _ = run(wl, b, prec, band=0.0)
+    _, g1, st = run(wl, b, prec, band=band)
+    rows = TRACKER_ROWS["rows"]
+    _, g32, _ = run(wl, b, "fp32")
+    l0, l1, l32 = cat(g0, "logit"), cat(g1, "logit"), cat(g32, "logit")
+    inband = np.abs(sigmoid(l0) - 0.5) < band
+    assert inband.any()
+    assert np.array_equal(l1[inband], l32[inband])
+    assert np.array_equal(l1[~inband], l0[~inband])
+    re, rv = receptive_field(g0, band, synth.shape_of(wl).iters, b)
+    assert rows == {"edges": re, "hits": rv}, (rows, re, rv)
+
+
 def test_bf16_rescored_agrees_with_oracle(cfg1):
     wl, b, _ = cfg1
     labels, g, _ = run(wl, b, "bf16", band=0.02)
