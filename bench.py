@@ -150,6 +150,25 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     return "hbm", N * 16, "byte"
 
 
+# DRAM bytes (read + write) per row of the dominant kernels, from one ncu
+# capture of 300 events of the same workload (profiles/dram_traffic_edge_steps_300ev.md),
+# averaged over the launches of a step; scaled to this run's rows.
+TRAFFIC_PER_ROW = {
+    ("rescore_edge_update", "bf16"): 313.9,
+    ("edge_update", "bf16"): 116.9,
+    ("edge_update", "fp32"): 257.6,
+}
+
+
+def stage_rows_per_launch(stage, launches, rows, N, E, K):
+    """Mean rows (edges or hits) one launch of `stage` processes."""
+    if stage == "rescore_edge_update":
+        return sum(rows["edges"][1:K + 1]) / max(launches, 1)
+    if stage in ("edge_update", "edge_encoder"):
+        return E
+    return N
+
+
 def stage_amount(stage, launches, rows, precision, N, E, m):
     """Algorithmic work of `stage` over one step: (bound, amount). A re-score
     stage works on the receptive field of the band edges, a different row set
@@ -290,8 +309,12 @@ def main():
         peak = pk["hbm_gbs"]
         achieved = amount / (step_stage_ms / 1e3) / 1e9
         unit = "GB/s"
+    bpr = TRAFFIC_PER_ROW.get((dname, precision))
+    traffic = (round(bpr * stage_rows_per_launch(dname, druns // a.steps, rows, N, E, m["iters"]))
+               if bpr is not None and a.workload == "cfg3_batched_bf16" else None)
     roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
-            "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_unit": "DRAM bytes per launch (ncu capture of 300 events scaled by rows)",
             "peak_src": ("derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"
                          if bound == "alu" else pk["src"]),
             "launch_ms": round(launch_ms, 4),
