@@ -357,6 +357,24 @@ gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edges, const i
  * gnntrk_create, gnntrk_serve_run or gnntrk_components_noalloc. */
 const char* gnntrk_last_error(const gnntrk_handle* h);
 
+/*
+ * FP8-E4M3 conversion of the FP8 precision path (the symmetric quantisation
+ * of the thesis's section on quantisation, with the E4M3 grid in place of
+ * INT8): each value (already divided by its scale) becomes the nearest E4M3
+ * code, ties to the even mantissa, saturating at +-448 (NaN -> 0x7F).
+ *   in, out:   n floats in, n codes out (caller-owned).
+ *   on_device: 0 -> host pointers, converted synchronously by the routine that
+ *              packs FP8 weights at gnntrk_create; 1 -> device pointers,
+ *              converted on `stream` (a cudaStream_t, 0 = default) by the
+ *              conversion the tensor-core kernels apply to activations.
+ * Errors: INVALID_ARG (n < 0, NULL pointer with n > 0), CUDA.
+ */
+gnntrk_status gnntrk_e4m3_encode(const float* in, uint8_t* out, int64_t n, int32_t on_device,
+                                 void* stream);
+
+/* Host: value of each E4M3 code (NaN for 0x7F and 0xFF). Errors: INVALID_ARG. */
+gnntrk_status gnntrk_e4m3_decode(const uint8_t* in, float* out, int64_t n);
+
 /* Release the handle's device memory, CUDA graphs and streams. NULL is a no-op.
  * The caller must make sure no work of this handle is still running. */
 void gnntrk_destroy(gnntrk_handle* h);

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
-           "gnntrk_autotune", "gnntrk_rescore_rows",
+           "gnntrk_autotune", "gnntrk_rescore_rows", "gnntrk_e4m3_encode", "gnntrk_e4m3_decode",
            "gnntrk_last_error", "gnntrk_destroy"]
 
 NOALLOC_MAX_HITS = 1 << 20
@@ -97,6 +97,10 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_stats.restype = st
     L.gnntrk_rescore_rows.argtypes = [vp, i32, vp, vp]
     L.gnntrk_rescore_rows.restype = st
+    L.gnntrk_e4m3_encode.argtypes = [vp, vp, i64, i32, vp]
+    L.gnntrk_e4m3_encode.restype = st
+    L.gnntrk_e4m3_decode.argtypes = [vp, vp, i64]
+    L.gnntrk_e4m3_decode.restype = st
     L.gnntrk_set_profiling.argtypes = [vp, i32]
     L.gnntrk_set_profiling.restype = st
     L.gnntrk_stage_times.argtypes = [vp, i32, vp, vp, vp]
@@ -348,3 +352,40 @@ def poisson_arrivals(n: int, rate_hz: float, seed: int) -> np.ndarray:
 
 def cut_logit(score_cut: float) -> float:
     return math.log(score_cut / (1.0 - score_cut))
+
+
+def _check_global(L, st):
+    if st != 0:
+        raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+
+
+def e4m3_encode(values, stream=None):
+    """FP8-E4M3 codes of `values` through the library: a numpy array is
+    converted on the host (the weight-packing routine), a CUDA tensor on the
+    device (the activation conversion of the tensor-core kernels)."""
+    L = load_library()
+    if isinstance(values, np.ndarray):
+        x = np.ascontiguousarray(values, np.float32).ravel()
+        out = np.zeros(x.size, np.uint8)
+        _check_global(L, L.gnntrk_e4m3_encode(x.ctypes.data_as(ctypes.c_void_p),
+                                               out.ctypes.data_as(ctypes.c_void_p),
+                                               x.size, 0, None))
+        return out
+    import torch
+    x = values.contiguous().view(-1)
+    out = torch.empty(x.numel(), dtype=torch.uint8, device=x.device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    _check_global(L, L.gnntrk_e4m3_encode(ctypes.c_void_p(x.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), x.numel(), 1,
+                                           ctypes.c_void_p(s)))
+    return out
+
+
+def e4m3_decode(codes) -> np.ndarray:
+    """Values of FP8-E4M3 codes (host)."""
+    L = load_library()
+    c = np.ascontiguousarray(codes, np.uint8).ravel()
+    out = np.zeros(c.size, np.float32)
+    _check_global(L, L.gnntrk_e4m3_decode(c.ctypes.data_as(ctypes.c_void_p),
+                                           out.ctypes.data_as(ctypes.c_void_p), c.size))
+    return out

@@ -1245,3 +1245,57 @@ void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s) {
 }
 
 }  // namespace gnntrk
+
+// ---------------------------------------------------------------------------
+// E4M3 conversion entry points (host packing routine, device activation
+// conversion), for checks of both against an independent codec
+// ---------------------------------------------------------------------------
+namespace gnntrk {
+namespace {
+__global__ void k_e4m3_encode(const float* in, uint8_t* out, int64_t n) {
+  const int64_t pairs = (n + 1) / 2;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < pairs;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float a = in[2 * i];
+    const float b = 2 * i + 1 < n ? in[2 * i + 1] : 0.f;
+    const uint32_t c = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    out[2 * i] = uint8_t(c & 0xff);
+    if (2 * i + 1 < n) out[2 * i + 1] = uint8_t(c >> 8);
+  }
+}
+}  // namespace
+void set_global_error(const std::string& msg);
+}  // namespace gnntrk
+
+extern "C" gnntrk_status gnntrk_e4m3_encode(const float* in, uint8_t* out, int64_t n,
+                                            int32_t on_device, void* stream) {
+  using namespace gnntrk;
+  if (n < 0 || (n > 0 && (in == nullptr || out == nullptr))) {
+    set_global_error("gnntrk_e4m3_encode: bad arguments");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  if (n == 0) return GNNTRK_OK;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i) out[i] = e4m3_from_float(in[i]);
+    return GNNTRK_OK;
+  }
+  const int64_t pairs = (n + 1) / 2;
+  const int grid = int(std::min<int64_t>(int64_t(device_sms()) * 8, (pairs + 255) / 256));
+  k_e4m3_encode<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("gnntrk_e4m3_encode: ") + cudaGetErrorString(e));
+    return GNNTRK_ERR_CUDA;
+  }
+  return GNNTRK_OK;
+}
+
+extern "C" gnntrk_status gnntrk_e4m3_decode(const uint8_t* in, float* out, int64_t n) {
+  using namespace gnntrk;
+  if (n < 0 || (n > 0 && (in == nullptr || out == nullptr))) {
+    set_global_error("gnntrk_e4m3_decode: bad arguments");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < n; ++i) out[i] = e4m3_to_float(in[i]);
+  return GNNTRK_OK;
+}

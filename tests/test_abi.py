@@ -3,6 +3,7 @@
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2508_07423_gb300 as pkg
@@ -53,3 +54,23 @@ def test_create_rejects_bad_blob_without_gpu_work(lib):
     with pytest.raises(pkg.GnntrkError) as ei:
         pkg.Tracker(b"\x00" * 64, c)
     assert ei.value.status == 7
+
+
+def test_host_e4m3_encoder_matches_the_oracle_codec():
+    """The library's host E4M3 encoder (FP8 weight packing) against the
+    oracle's brute-force codec: every code's value, the midpoints between
+    neighbouring codes (ties to even), values past 448 and seeded randoms."""
+    from oracle import quant
+    dec = np.array([quant.e4m3_decode(c) for c in range(256)])
+    fin = np.sort(np.unique(dec[~np.isnan(dec)]))
+    mids = (fin[:-1] + fin[1:]) / 2
+    rng = np.random.default_rng(17)
+    vals = np.concatenate([fin, mids, [447.9, 448.0, 460.0, 1e9, -1e9, 2.0 ** -12],
+                           rng.normal(0, 30, 4000), rng.uniform(-1e-2, 1e-2, 2000)]).astype(np.float32)
+    got = pkg.e4m3_encode(vals)
+    want = quant.e4m3_encode_array(vals.astype(np.float64))
+    assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
+    codes = np.arange(256, dtype=np.uint8)
+    back = pkg.e4m3_decode(codes)
+    ok = ~np.isnan(dec)
+    assert np.array_equal(back[ok], dec[ok].astype(np.float32)) and np.isnan(back[~ok]).all()

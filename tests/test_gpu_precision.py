@@ -257,3 +257,20 @@ def test_autotune_picks_a_count_and_keeps_results():
     # restore the resource-bound default for the other tests of this process
     lib = pkg.load_library()
     del lib
+
+
+def test_device_e4m3_conversion_matches_the_oracle_codec():
+    """The activation conversion of the FP8 kernels (device) against the
+    oracle's brute-force E4M3 codec, including ties, saturation and an odd
+    count (the last pair is half used)."""
+    from oracle import quant
+    dec = np.array([quant.e4m3_decode(c) for c in range(256)])
+    fin = np.sort(np.unique(dec[~np.isnan(dec)]))
+    mids = (fin[:-1] + fin[1:]) / 2
+    rng = np.random.default_rng(23)
+    vals = np.concatenate([fin, mids, [447.9, 448.0, 460.0, 1e9, -1e9],
+                           rng.normal(0, 30, 4001)]).astype(np.float32)
+    assert vals.size % 2 == 1
+    got = pkg.e4m3_encode(torch.from_numpy(vals).cuda()).cpu().numpy()
+    want = quant.e4m3_encode_array(vals.astype(np.float64))
+    assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]

@@ -363,3 +363,56 @@ def test_weight_blob_rejects_wrong_architecture():
         oracle.Model(blob, [3, 64, 64, 4], 32, 3)
     with pytest.raises(ValueError):
         oracle.Model(blob[:-4], [3, 64, 64, 4], 32, 4)
+
+
+# ---------------------------------------------------------------------------
+# quantisation (oracle/quant.py)
+# ---------------------------------------------------------------------------
+def test_symmetric_quantisation_worked_example():
+    """The thesis's symmetric example: inputs within [-10.8, 10.8] onto INT8
+    with the bound mapped to 127 give S = 10.8 / 127; the bound quantises to
+    +-127, values beyond are clipped, and x = S x_q inverts the grid points."""
+    from oracle import quant
+    S = quant.symmetric_scale(10.8, 127)
+    assert S == pytest.approx(10.8 / 127, rel=1e-15)
+    aq = int(round(10.8 / S))
+    assert aq == 127
+    xq = quant.quantize([10.8, -10.8, 0.0, 20.0, -50.0, S * 3.4, S * 3.6], S, aq)
+    assert list(xq) == [127, -127, 0, 127, -127, 3, 4]
+    assert quant.dequantize(xq[:2], S) == pytest.approx([10.8, -10.8], rel=1e-12)
+
+
+def test_e4m3_codes_closed_forms():
+    """Landmark codes of E4M3: 0, the smallest subnormal 2^-9, the largest
+    subnormal 7 * 2^-9, the smallest normal 2^-6, one, the largest finite 448,
+    NaN at 0x7F / 0xFF, and sign symmetry for every code."""
+    from oracle import quant
+    d = quant.e4m3_decode
+    assert d(0x00) == 0.0 and d(0x01) == 2.0 ** -9 and d(0x07) == 7 * 2.0 ** -9
+    assert d(0x08) == 2.0 ** -6 and d(0x38) == 1.0 and d(0x7E) == 448.0
+    assert math.isnan(d(0x7F)) and math.isnan(d(0xFF))
+    for c in range(0x7F):
+        assert d(c | 0x80) == -d(c)
+    finite = sorted(d(c) for c in range(0x7F))
+    assert len(set(finite)) == 127 and finite == sorted(set(finite))  # strictly increasing
+
+
+def test_e4m3_round_trip_and_rounding():
+    """encode(decode(c)) == c for all 254 finite codes (+-0 keep their sign);
+    midpoints round to the even mantissa; beyond 448 saturates; NaN -> 0x7F."""
+    from oracle import quant
+    for c in range(256):
+        v = quant.e4m3_decode(c)
+        if math.isnan(v):
+            continue
+        assert quant.e4m3_encode(v) == c, hex(c)
+    # 1.0 (m=0) and 1.125 (m=1): the midpoint goes to the even mantissa, 1.0
+    assert quant.e4m3_encode(1.0625) == 0x38
+    # 1.125 (m=1) and 1.25 (m=2): midpoint 1.1875 -> 1.25
+    assert quant.e4m3_encode(1.1875) == 0x3A
+    # largest subnormal / smallest normal midpoint -> the normal (even mantissa 0)
+    assert quant.e4m3_encode(7.5 * 2.0 ** -9) == 0x08
+    assert quant.e4m3_encode(1e6) == 0x7E and quant.e4m3_encode(-449.0) == 0xFE
+    assert quant.e4m3_encode(float("nan")) == 0x7F
+    # a planted mistake: round half away from zero would give 1.125 here
+    assert quant.e4m3_decode(quant.e4m3_encode(1.0625)) == 1.0
