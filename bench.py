@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2508_07423_gb300 import synth  # noqa: E402
+from paper_2508_07423_gb300 import replicas, synth  # noqa: E402
 
 METRIC = "events/s and hits/s on 1 GB300 (BF16/FP8 batched vs FP32 plain); p99 latency"
 DEFAULT_WORKLOAD = "cfg3_batched_bf16"
@@ -244,8 +244,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # each rank processes its own events (replicas over disjoint event ranges)
-    n_ev = a.events or wl["n_events"]
-    batch = synth.workload_batch(wl, n_ev, first_event=rank * n_ev)
+    first, n_ev = replicas.event_range(rank, world, a.events or wl["n_events"])
+    batch = synth.workload_batch(wl, n_ev, first_event=first)
     N = batch.n_hits
     dev = torch.device("cuda", local)
     xyz = torch.from_numpy(batch.xyz_soa()).to(dev)
@@ -279,14 +279,8 @@ def main():
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_events = n_ev * world
+    ms, total_events, hits_total = replicas.combine(dist, float(np.mean(step_ms)), n_ev, N, dev)
     value = total_events / (ms / 1e3)
-    hits_total = N * world
 
     # the same steps again with per-stage events (direct launches): roofline
     tr.set_profiling(True)
