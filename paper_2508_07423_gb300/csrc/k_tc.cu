@@ -218,6 +218,31 @@ __device__ __forceinline__ void add_bf16_row(float* acc, const __nv_bfloat16* sr
   }
 }
 
+// x[j] = v[j] + b[j] (BF16) or fma(v[j], sc[j], b[j]) (FP8) for 32 columns,
+// the parameters read as 16-byte broadcasts from shared memory
+template <bool FP8>
+__device__ __forceinline__ void add_params(const float (&v)[32], const float* b, const float* sc,
+                                           float (&x)[32]) {
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  const float4* s4 = reinterpret_cast<const float4*>(sc);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 bb = b4[q];
+    if constexpr (FP8) {
+      const float4 ss = s4[q];
+      x[4 * q] = fmaf(v[4 * q], ss.x, bb.x);
+      x[4 * q + 1] = fmaf(v[4 * q + 1], ss.y, bb.y);
+      x[4 * q + 2] = fmaf(v[4 * q + 2], ss.z, bb.z);
+      x[4 * q + 3] = fmaf(v[4 * q + 3], ss.w, bb.w);
+    } else {
+      x[4 * q] = v[4 * q] + bb.x;
+      x[4 * q + 1] = v[4 * q + 1] + bb.y;
+      x[4 * q + 2] = v[4 * q + 2] + bb.z;
+      x[4 * q + 3] = v[4 * q + 3] + bb.w;
+    }
+  }
+}
+
 // Issue the MMAs of one layer: A tile (kchunks 16-byte chunks per row) times
 // the weight image (H rows) over K elements. FP8 with segments: segment s
 // (H columns of K) accumulates into TMEM columns [s*H, (s+1)*H).
@@ -536,7 +561,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       //         classifier output for M_CLS) -------------------------------
       // x[n] = s_w[n] * sum_seg s_a[seg] * acc_seg[n] + b[n]  (FP8)
       //      = acc[n] + b[n]                                   (BF16)
-      auto xval = [&](int c, float (&x)[32]) {
+      auto xval_ld = [&](int c, float (&x)[32]) {
         float v[32];
         tmem_ld32(tmem_lane + uint32_t(c * 32), v);
         if constexpr (FP8) {
@@ -551,10 +576,17 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           }
         }
         tmem_wait_ld();
+        add_params<FP8>(v, pb1 + c * 32, ps1 + c * 32, x);
+      };
+      // h = 32: one chunk, read from tensor memory once and kept in registers
+      float xc[H == 32 ? 32 : 1];
+      if constexpr (H == 32) xval_ld(0, xc);
+      auto xval = [&](int c, float (&x)[32]) {
+        if constexpr (H == 32) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = c * 32 + j;
-          x[j] = FP8 ? fmaf(v[j], ps1[n], pb1[n]) : v[j] + pb1[n];
+          for (int j = 0; j < 32; ++j) x[j] = xc[j];
+        } else {
+          xval_ld(c, x);
         }
       };
       float sum = 0.f, xmax = -INFINITY;
@@ -630,11 +662,11 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       float v[32];
       tmem_ld32(tmem_lane + uint32_t(c * 32), v);
       tmem_wait_ld();
+      if constexpr (FP8) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = c * 32 + j;
-        z[j] = FP8 ? fmaf(v[j] * hid_scale, ps2[n], pb2[n]) : v[j] + pb2[n];
+        for (int j = 0; j < 32; ++j) v[j] *= hid_scale;
       }
+      add_params<FP8>(v, pb2 + c * 32, ps2 + c * 32, z);
     };
     // residual input row (BF16) for the update modes
     auto resid = [&](int c, float (&z)[32]) {
@@ -713,14 +745,24 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         aborted = true;
         break;
       }
-      auto cval = [&](int c, float (&x)[32]) {
+      auto cval_ld = [&](int c, float (&x)[32]) {
         float v[32];
         tmem_ld32(tmem_lane + uint32_t(c * 32), v);
         tmem_wait_ld();
+        if constexpr (FP8) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = c * 32 + j;
-          x[j] = FP8 ? fmaf(v[j] * es, psc[n], pbc[n]) : v[j] + pbc[n];
+          for (int j = 0; j < 32; ++j) v[j] *= es;
+        }
+        add_params<FP8>(v, pbc + c * 32, psc + c * 32, x);
+      };
+      float cc[H == 32 ? 32 : 1];
+      if constexpr (H == 32) cval_ld(0, cc);
+      auto cval = [&](int c, float (&x)[32]) {
+        if constexpr (H == 32) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) x[j] = cc[j];
+        } else {
+          cval_ld(c, x);
         }
       };
       float sum = 0.f;
