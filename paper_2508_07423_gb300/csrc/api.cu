@@ -204,6 +204,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.plane_off, int64_t(c.max_events) * (c.n_planes + 1));
   add(&w.emb, H * D);
   add(&w.deg, H);
+  add(&w.rmask, H * kMaskWords);
   add(&w.row_ptr, H + 1);
   add(&w.col, E);
   add(&w.src, E);

@@ -13,7 +13,9 @@ namespace gnntrk {
 constexpr int kMaxPlanes = 64;
 constexpr int kMaxEmbedLayers = 8;
 constexpr int kMaxIters = 16;
-constexpr int kRsMaxBlocks = 1024;  // blocks of the re-score level sort (at most)
+constexpr int kRsMaxBlocks = 1024;           // blocks of the re-score level sort (at most)
+constexpr int kMaskWords = 16;               // radius-search masks: up to 512 candidates
+constexpr int kMaskCands = 32 * kMaskWords;
 constexpr float kLnEps = 1e-5f;
 
 // Bits of the device status word (counters[C_STATUS]).
@@ -79,6 +81,7 @@ struct Ws {
   int32_t* plane_off;   // [max_events][n_planes + 1] sorted offsets (global)
   float* emb;           // [H][D]
   int32_t* deg;         // [H] candidates inside the radius (uncapped)
+  uint32_t* rmask;      // [H][kMaskWords] candidates inside the radius, one bit each
   int32_t* row_ptr;     // [H + 1]
   int32_t* col;         // [Ecap] target (sorted position)
   int32_t* src;         // [Ecap] source (sorted position)

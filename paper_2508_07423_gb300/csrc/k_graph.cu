@@ -191,6 +191,32 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
     __syncthreads();
   }
   const float r2 = g.radius2;
+  if (FILL && nc <= kMaskCands) {
+    // one thread per query: walk the set bits of its masks (ascending
+    // candidate index, the order of the warp path), recompute d^2 only there
+    const int nwords = (nc + 31) / 32;
+    for (int q = q0 + tid; q < q1; q += blockDim.x) {
+      const int cnt = w.deg[q];
+      if (cnt > g.k_max) continue;  // capped: the warp path below selects
+      float qe[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+      int64_t e = w.row_ptr[q];
+      for (int k = 0; k < nwords; ++k) {
+        unsigned m = w.rmask[size_t(q) * kMaskWords + k];
+        while (m) {
+          const int c = k * 32 + __ffs(m) - 1;
+          m &= m - 1;
+          if (e < w.e_cap) {
+            w.col[e] = c0 + c;
+            w.src[e] = q;
+            w.d2[e] = dist2<D>(qe, ce + size_t(c) * D);
+          }
+          ++e;
+        }
+      }
+    }
+  }
   for (int q = q0 + warp; q < q1; q += nwarps) {
     float qe[D];
     if constexpr (D % 4 == 0) {
@@ -212,12 +238,17 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
         const int c = base + lane;
         bool ok = false;
         if (c < nc) ok = dist2<D>(qe, ce + size_t(c) * D) < r2;
-        cnt += __popc(__ballot_sync(kFull, ok));
+        const unsigned m = __ballot_sync(kFull, ok);
+        cnt += __popc(m);
+        // the candidates inside the radius, for the fill pass
+        if (lane == 0 && nc <= kMaskCands) w.rmask[size_t(q) * kMaskWords + base / 32] = m;
       }
       if (lane == 0) w.deg[q] = cnt;
       continue;
     }
     const int cnt = w.deg[q];
+    // queries within k_max with stored masks were written lane-per-query above
+    if (nc <= kMaskCands && cnt <= g.k_max) continue;
     const int64_t out0 = w.row_ptr[q];
     // selection threshold when more than k_max candidates pass: T is the
     // k_max-th smallest key; keys < T are kept, then the first keys == T
