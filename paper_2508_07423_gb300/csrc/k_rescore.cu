@@ -32,52 +32,81 @@ __device__ __forceinline__ bool input_bad(const int32_t* counters) {
   return (*(volatile const int32_t*)&counters[C_STATUS] & ST_INPUT) != 0;
 }
 
-// E_{K-1} = band edges, V_{K-1} = their endpoints; flags the events.
+// E_{K-1} = band edges, V_{K-1} = their endpoints; flags the events. Four
+// edges per thread and iteration; the band count is summed per thread and
+// added once per warp.
+__device__ __forceinline__ int rs_init_edge(const Ws& w, int e, float l, float lo, float hi,
+                                            int8_t top) {
+  if (!(l > lo && l < hi)) return 0;
+  w.rs_elev[e] = top;
+  const int a = w.src[e], c = w.col[e];
+  w.rs_nlev[a] = top;  // every writer stores the same value
+  w.rs_nlev[c] = top;
+  w.ev_flag[w.node_event[a]] = 1;
+  return 1;
+}
+
 __global__ void k_rs_init(Ws w, float lo, float hi, int K) {
   if (input_bad(w.counters)) return;
   const int E = clamp_edges(w.counters, w.e_cap);
   const int8_t top = int8_t((K > 0 ? K - 1 : -1) + 2);
-  for (int base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
-    const int e = base + threadIdx.x;
-    bool in = false;
-    if (e < E) {
-      const float l = w.logit[e];
-      in = l > lo && l < hi;
-      if (in) {
-        w.rs_elev[e] = top;
-        const int a = w.src[e], c = w.col[e];
-        w.rs_nlev[a] = top;  // every writer stores the same value
-        w.rs_nlev[c] = top;
-        w.ev_flag[w.node_event[a]] = 1;
-      }
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&w.counters[C_BAND], __popc(m));
+  const int stride = gridDim.x * blockDim.x;
+  const int E4 = E / 4;
+  int n = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E4; i += stride) {
+    const float4 l = reinterpret_cast<const float4*>(w.logit)[i];
+    n += rs_init_edge(w, 4 * i, l.x, lo, hi, top);
+    n += rs_init_edge(w, 4 * i + 1, l.y, lo, hi, top);
+    n += rs_init_edge(w, 4 * i + 2, l.z, lo, hi, top);
+    n += rs_init_edge(w, 4 * i + 3, l.w, lo, hi, top);
+  }
+  for (int e = 4 * E4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+    n += rs_init_edge(w, e, w.logit[e], lo, hi, top);
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&w.counters[C_BAND], n);
+}
+
+__device__ __forceinline__ void rs_step_edge(const Ws& w, int8_t& L, int a, int c, int8_t la,
+                                             int8_t lc, int8_t ge_k, int8_t km1, bool& changed) {
+  if (L < km1 && (la >= ge_k || lc >= ge_k)) {
+    L = km1;
+    changed = true;
+  }
+  if (L >= km1) {
+    if (la < km1) w.rs_nlev[a] = km1;
+    if (lc < km1) w.rs_nlev[c] = km1;
   }
 }
 
-// One backward step k (K-1 .. 0), both set updates fused:
-//   E_{k-1} = E_k + edges touching V_k        (nodes at level >= k)
-//   V_{k-1} = V_k + endpoints(E_{k-1})        (stores of level k-1)
-// The stores of level k-1 only replace levels below k-1, so they never change
-// which nodes read as >= k in the same pass; concurrent writers store the same
-// value.
+// four consecutive edges per thread and iteration: their levels, sources and
+// targets in one 4-byte and two 16-byte loads, the eight hit-level gathers in
+// flight together
 __global__ void k_rs_step(Ws w, int k) {
   if (input_bad(w.counters)) return;
   const int E = clamp_edges(w.counters, w.e_cap);
   const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  const int E4 = E / 4;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E4; i += stride) {
+    char4 L4 = reinterpret_cast<const char4*>(w.rs_elev)[i];
+    const int4 a4 = reinterpret_cast<const int4*>(w.src)[i];
+    const int4 c4 = reinterpret_cast<const int4*>(w.col)[i];
+    const int8_t la0 = w.rs_nlev[a4.x], la1 = w.rs_nlev[a4.y], la2 = w.rs_nlev[a4.z], la3 = w.rs_nlev[a4.w];
+    const int8_t lc0 = w.rs_nlev[c4.x], lc1 = w.rs_nlev[c4.y], lc2 = w.rs_nlev[c4.z], lc3 = w.rs_nlev[c4.w];
+    int8_t L0 = L4.x, L1 = L4.y, L2 = L4.z, L3 = L4.w;
+    bool changed = false;
+    rs_step_edge(w, L0, a4.x, c4.x, la0, lc0, ge_k, km1, changed);
+    rs_step_edge(w, L1, a4.y, c4.y, la1, lc1, ge_k, km1, changed);
+    rs_step_edge(w, L2, a4.z, c4.z, la2, lc2, ge_k, km1, changed);
+    rs_step_edge(w, L3, a4.w, c4.w, la3, lc3, ge_k, km1, changed);
+    if (changed) reinterpret_cast<char4*>(w.rs_elev)[i] = make_char4(L0, L1, L2, L3);
+  }
+  for (int e = 4 * E4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
     int8_t L = w.rs_elev[e];
     const int a = w.src[e], c = w.col[e];
-    const int8_t la = w.rs_nlev[a], lc = w.rs_nlev[c];
-    if (L < km1 && (la >= ge_k || lc >= ge_k)) {
-      L = km1;
-      w.rs_elev[e] = L;
-    }
-    if (L >= km1) {
-      if (la < km1) w.rs_nlev[a] = km1;
-      if (lc < km1) w.rs_nlev[c] = km1;
-    }
+    bool changed = false;
+    rs_step_edge(w, L, a, c, w.rs_nlev[a], w.rs_nlev[c], ge_k, km1, changed);
+    if (changed) w.rs_elev[e] = L;
   }
 }
 
