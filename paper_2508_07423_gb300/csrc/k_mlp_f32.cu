@@ -527,10 +527,14 @@ __device__ __forceinline__ void tile_layer(const float* As, int K, const LayerF3
       const float4 q = __ldg(w4 + j / 4);
 #pragma unroll
       for (int i = 0; i < RM; ++i) {
-        acc[i][j] = fmaf(a[i], q.x, acc[i][j]);
-        acc[i][j + 1] = fmaf(a[i], q.y, acc[i][j + 1]);
-        acc[i][j + 2] = fmaf(a[i], q.z, acc[i][j + 2]);
-        acc[i][j + 3] = fmaf(a[i], q.w, acc[i][j + 3]);
+        // two columns per packed FMA (each lane rounds like fmaf)
+        const float2 a2 = make_float2(a[i], a[i]);
+        const float2 c01 = __ffma2_rn(a2, make_float2(q.x, q.y), make_float2(acc[i][j], acc[i][j + 1]));
+        const float2 c23 = __ffma2_rn(a2, make_float2(q.z, q.w), make_float2(acc[i][j + 2], acc[i][j + 3]));
+        acc[i][j] = c01.x;
+        acc[i][j + 1] = c01.y;
+        acc[i][j + 2] = c23.x;
+        acc[i][j + 3] = c23.y;
       }
     }
   }
