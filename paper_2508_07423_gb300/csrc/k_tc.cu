@@ -829,15 +829,15 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 // ---------------------------------------------------------------------------
 template <int H, bool OUT16>
 __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
-  constexpr int CPL = H / 8;                 // columns per lane
-  constexpr int NV = CPL / 8 > 0 ? CPL / 8 : 1;  // uint4 loads per lane (CPL >= 8)
+  constexpr int LPN = H / 8;    // lanes per hit: 8 columns (16 bytes) each
+  constexpr int NPW = 32 / LPN; // hits per warp
   constexpr int U = 8;
   if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
   const int E = clamp_edges(w.counters, w.e_cap);
-  const int q = threadIdx.x & 7;
-  const int groups = gridDim.x * (blockDim.x >> 3);
-  for (int row = blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3); row < b.n_hits; row += groups) {
-    float* out = w.pstate + size_t(row) * 2 * H + q * CPL;
+  const int q = threadIdx.x % LPN;
+  const int groups = gridDim.x * (blockDim.x / LPN);
+  (void)NPW;
+  for (int row = blockIdx.x * (blockDim.x / LPN) + threadIdx.x / LPN; row < b.n_hits; row += groups) {
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
       int a, n;
@@ -848,54 +848,35 @@ __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
         a = w.in_ptr[row];
         n = w.in_ptr[row + 1] - a;
       }
-      float s[CPL];
+      float2 s[4];
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) s[c] = 0.f;
+      for (int c = 0; c < 4; ++c) s[c] = make_float2(0.f, 0.f);
       for (int t0 = 0; t0 < n; t0 += U) {
-        uint32_t v[U][CPL / 2];
+        uint4 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int at = a + min(t0 + u, n - 1);
           const int e = side == 0 ? at : __ldg(w.in_edge + at);
-          const __nv_bfloat16* ep = w.estate16 + size_t(e) * H + q * CPL;
-          if constexpr (CPL == 4) {
-            const uint2 x = __ldg(reinterpret_cast<const uint2*>(ep));
-            v[u][0] = x.x;
-            v[u][1] = x.y;
-          } else {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-              const uint4 x = __ldg(reinterpret_cast<const uint4*>(ep) + k);
-              v[u][4 * k] = x.x;
-              v[u][4 * k + 1] = x.y;
-              v[u][4 * k + 2] = x.z;
-              v[u][4 * k + 3] = x.w;
-            }
-          }
+          v[u] = __ldg(reinterpret_cast<const uint4*>(w.estate16 + size_t(e) * H) + q);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (t0 + u < n) {
-#pragma unroll
-            for (int c = 0; c < CPL / 2; ++c) {
-              const float2 r = __fadd2_rn(make_float2(s[2 * c], s[2 * c + 1]),
-                                          make_float2(bf16_lo(v[u][c]), bf16_hi(v[u][c])));
-              s[2 * c] = r.x;
-              s[2 * c + 1] = r.y;
-            }
+            s[0] = __fadd2_rn(s[0], make_float2(bf16_lo(v[u].x), bf16_hi(v[u].x)));
+            s[1] = __fadd2_rn(s[1], make_float2(bf16_lo(v[u].y), bf16_hi(v[u].y)));
+            s[2] = __fadd2_rn(s[2], make_float2(bf16_lo(v[u].z), bf16_hi(v[u].z)));
+            s[3] = __fadd2_rn(s[3], make_float2(bf16_lo(v[u].w), bf16_hi(v[u].w)));
           }
       }
       if constexpr (OUT16) {
-        __nv_bfloat16* o16 = reinterpret_cast<__nv_bfloat16*>(w.pstate) + size_t(row) * 2 * H +
-                             side * H + q * CPL;
-#pragma unroll
-        for (int c = 0; c < CPL; c += 4)
-          *reinterpret_cast<uint2*>(o16 + c) =
-              make_uint2(pack_bf16(s[c], s[c + 1]), pack_bf16(s[c + 2], s[c + 3]));
+        uint4* o16 = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.pstate) +
+                                              size_t(row) * 2 * H + side * H) + q;
+        *o16 = make_uint4(pack_bf16(s[0].x, s[0].y), pack_bf16(s[1].x, s[1].y),
+                          pack_bf16(s[2].x, s[2].y), pack_bf16(s[3].x, s[3].y));
       } else {
-#pragma unroll
-        for (int c = 0; c < CPL; c += 4)
-          *reinterpret_cast<float4*>(out + side * H + c) = make_float4(s[c], s[c + 1], s[c + 2], s[c + 3]);
+        float4* o = reinterpret_cast<float4*>(w.pstate + size_t(row) * 2 * H + side * H + 8 * q);
+        o[0] = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+        o[1] = make_float4(s[2].x, s[2].y, s[3].x, s[3].y);
       }
     }
   }
@@ -1248,7 +1229,7 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
   for (int k = 0; k < K; ++k) {
     if (stage < 0 || stage == 1 + 2 * k) {
       set(m.node[k]);
-      const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 32)));
+      const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 256 / (h / 8))));
       if (h == 32)
         fp8 ? k_msg_bf16<32, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<32, true><<<grid, 256, 0, s>>>(b, w);
       else if (h == 64)
