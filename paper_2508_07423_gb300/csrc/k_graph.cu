@@ -27,6 +27,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSortThreads = 256;
 constexpr int kRadiusThreads = 256;
+constexpr int kRadiusCountThreads = 64;  // count pass: one thread per query (about 65 per plane)
 constexpr int kCandSmemBytes = 12 * 1024;  // staged candidates (about 2-6 KB needed); 8 blocks per SM
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
@@ -191,6 +192,27 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
     __syncthreads();
   }
   const float r2 = g.radius2;
+  if constexpr (!FILL) {
+    // count: one thread per query, all threads stepping through the same
+    // candidates (shared-memory broadcasts); the candidates inside the radius
+    // go to the query's mask words for the fill pass
+    for (int q = q0 + tid; q < q1; q += blockDim.x) {
+      float qe[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+      int cnt = 0;
+      for (int base = 0; base < nc; base += 32) {
+        const int m_end = min(32, nc - base);
+        unsigned m = 0;
+        for (int j = 0; j < m_end; ++j)
+          if (dist2<D>(qe, ce + size_t(base + j) * D) < r2) m |= 1u << j;
+        cnt += __popc(m);
+        if (nc <= kMaskCands) w.rmask[size_t(q) * kMaskWords + base / 32] = m;
+      }
+      w.deg[q] = cnt;
+    }
+    return;
+  }
   if (FILL && nc <= kMaskCands) {
     // one thread per query: walk the set bits of its masks (ascending
     // candidate index, the order of the warp path), recompute d^2 only there
@@ -231,20 +253,6 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphP
     } else {
 #pragma unroll
       for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
-    }
-    if (!FILL) {
-      int cnt = 0;
-      for (int base = 0; base < nc; base += 32) {
-        const int c = base + lane;
-        bool ok = false;
-        if (c < nc) ok = dist2<D>(qe, ce + size_t(c) * D) < r2;
-        const unsigned m = __ballot_sync(kFull, ok);
-        cnt += __popc(m);
-        // the candidates inside the radius, for the fill pass
-        if (lane == 0 && nc <= kMaskCands) w.rmask[size_t(q) * kMaskWords + base / 32] = m;
-      }
-      if (lane == 0) w.deg[q] = cnt;
-      continue;
     }
     const int cnt = w.deg[q];
     // queries within k_max with stored masks were written lane-per-query above
@@ -317,7 +325,7 @@ void radius_d(const Batch& b, const Ws& w, const GraphParams& g, bool fill, cuda
   if (fill)
     k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
   else
-    k_radius<D, false><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
+    k_radius<D, false><<<grid, kRadiusCountThreads, kCandSmemBytes, s>>>(b, w, g);
 }
 
 // ---------------------------------------------------------------------------
