@@ -225,7 +225,6 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.counters, C_COUNT);
   add(&w.scan_blocks, (H + 4095) / 4096 + 1);
   add(&w.ev_flag, c.max_events);
-  add(&w.rerun_list, c.max_events);
   add(&w.ev_off, int64_t(c.max_events) + 1);
   if (c.precision != GNNTRK_FP32) {
     add(&w.rs_elev, E);

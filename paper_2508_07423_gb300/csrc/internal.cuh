@@ -33,10 +33,9 @@ enum Counter : int {
   C_TICKET = 2,    // last-block ticket of the two-kernel scan
   C_KEPT = 3,      // kept edges
   C_BAND = 4,      // edges in the re-score band
-  C_RERUN = 5,     // events re-run in FP32
-  C_SCAN_TOTAL = 6,
-  C_RERUN_EDGES = 7,  // edges of the re-run events
-  C_RERUN_HITS = 8,   // hits of the re-run events
+  C_RERUN = 5,     // events holding a band edge
+  C_RERUN_EDGES = 7,  // edges the FP32 re-score recomputes (receptive field)
+  C_RERUN_HITS = 8,   // hits the FP32 re-score recomputes
   C_COUNT = 16
 };
 
@@ -100,7 +99,6 @@ struct Ws {
   int32_t* counters;    // [C_COUNT]
   int32_t* scan_blocks; // block partials of the scan
   int32_t* ev_flag;     // [max_events] events re-run in FP32
-  int32_t* rerun_list;  // [max_events] events holding a near-cut edge
   int8_t* rs_elev;      // [Ecap] re-score level of each edge + 2 (0 none)
   int8_t* rs_nlev;      // [H]    re-score level of each hit + 2 (0 none)
   int32_t* rs_elist;    // [Ecap] edges by level, descending
@@ -189,7 +187,6 @@ void launch_edge_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const
 // FP32 tile-shape variant (0 or 1) per kernel family (0 encoders, 1 node step,
 // 2 edge step + classifier), process wide; chosen by the autotuner.
 void f32_set_variant(int h, int family, int v);
-int f32_get_variant(int h, int family);
 
 // connected components
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s);

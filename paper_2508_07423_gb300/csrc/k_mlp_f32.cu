@@ -715,11 +715,6 @@ void f32_set_variant(int h, int family, int v) {
   g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family] = (v == 1) ? 1 : 0;
 }
 
-int f32_get_variant(int h, int family) {
-  if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return 0;
-  return g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family];
-}
-
 void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,
                           const Mlp2F32& node_enc, const EdgeProj& proj, int D, int h,
                           const GraphParams& g, bool do_embed, bool do_node_enc, Sel sel,

@@ -887,27 +887,20 @@ __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
 // them into counters[C_RERUN] and clear the flags
 // ---------------------------------------------------------------------------
 __global__ void k_band_list(Ws w, int n_events) {
-  __shared__ int base;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  for (int c = 0; c < n_events; c += blockDim.x) {
-    const int ev = c + threadIdx.x;
-    const bool f = ev < n_events && w.ev_flag[ev] != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, f);
-    __shared__ int wsum[32];
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    if (lane == 0) wsum[wp] = __popc(m);
-    __syncthreads();
-    int off = base;
-    for (int k = 0; k < wp; ++k) off += wsum[k];
-    if (f) w.rerun_list[off + __popc(m & ((1u << lane) - 1u))] = ev;
-    if (ev < n_events) w.ev_flag[ev] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int k = 0; k < int(blockDim.x >> 5); ++k) base += wsum[k];
-    __syncthreads();
+  __shared__ int wsum[32];
+  int n = 0;
+  for (int ev = threadIdx.x; ev < n_events; ev += blockDim.x) {
+    n += w.ev_flag[ev] != 0;
+    w.ev_flag[ev] = 0;
   }
-  if (threadIdx.x == 0) w.counters[C_RERUN] = base;
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) t += wsum[k];
+    w.counters[C_RERUN] = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
