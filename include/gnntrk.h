@@ -235,7 +235,7 @@ gnntrk_status gnntrk_rescore_rows(gnntrk_handle* h, int32_t n, int64_t* edges, i
  * max_stages; only max_stages are written), or -1 on error.
  * Stage names: sort, node_prep, radius_count, scan_out, radius_fill,
  * in_index, edge_encoder, node_update, edge_update, band_mark,
- * rescore_node_prep, rescore_edge_encoder, rescore_node_update,
+ * rescore_lists, rescore_node_prep, rescore_edge_encoder, rescore_node_update,
  * rescore_edge_update, components.
  */
 gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable);

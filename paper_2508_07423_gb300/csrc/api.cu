@@ -383,6 +383,8 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       const int32_t* cge_n = w.rs_counts + 5 * NL;  // [k + 1]: hits of step k
       auto esel = [&](int k) { return Sel{w.rs_elist, cge_e + k + 1}; };
       auto nsel = [&](int k) { return Sel{w.rs_nlist, cge_n + k + 1}; };
+      // each step's rows, compacted in index order just before the step
+      stage(h, "rescore_lists", s, 3, [&] { launch_rescore_list(b, w, -1, s); });
       stage(h, "rescore_node_prep", s, 1, [&] {
         launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
                              false, true, nsel(-1), s);
@@ -390,6 +392,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       stage(h, "rescore_edge_encoder", s, 1,
             [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, esel(-1), s); });
       for (int k = 0; k < h->K; ++k) {
+        stage(h, "rescore_lists", s, 3, [&] { launch_rescore_list(b, w, k, s); });
         stage(h, "rescore_node_update", s, 2, [&] {
           launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, nsel(k), s);
         });

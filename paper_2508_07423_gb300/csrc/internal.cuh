@@ -104,7 +104,7 @@ struct Ws {
   int32_t* rs_elist;    // [Ecap] edges by level, descending
   int32_t* rs_nlist;    // [H]    hits by level, descending
   int32_t* rs_counts;   // [6][kMaxIters + 2]: [2] and [5] rows with level >= k (edges, hits)
-  int32_t* rs_blk;      // [2][kMaxIters + 2][kRsMaxBlocks] per-block offsets of the level sort
+  int32_t* rs_blk;      // [2][kRsMaxBlocks] per-block offsets of the row compaction
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
   int64_t h_cap, e_cap;
 };
@@ -137,12 +137,15 @@ struct Sel {
 };
 
 // Levels of the FP32 re-score (exact receptive field of the edges whose logit
-// lies in (band_lo, band_hi)); afterwards rs_elist / rs_nlist prefixes of
-// rs_counts[2 * (kMaxIters + 2) + k + 1] (edges) and
-// rs_counts[5 * (kMaxIters + 2) + k + 1] (hits) are the rows of step k
-// (k = -1: the encoders). Returns the number of kernels launched.
+// lies in (band_lo, band_hi)): a row of level >= k is recomputed at step k
+// (k = -1: the encoders). Flags the events holding a band edge. Returns the
+// number of kernels launched.
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s);
+// row lists of re-score step k (k = -1: the encoders) into w.rs_elist /
+// w.rs_nlist, counts into rs_counts[2 (kMaxIters + 2) + k + 1] (edges) and
+// rs_counts[5 (kMaxIters + 2) + k + 1] (hits); returns the launch count
+int launch_rescore_list(const Batch& b, const Ws& w, int k, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (host functions), one per kernel family

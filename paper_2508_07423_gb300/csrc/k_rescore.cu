@@ -9,9 +9,8 @@
 //   edge step k-1 : E_{k-1} = edges incident to V_k       (their e^k feeds the sums)
 //   node encoder  : V_{-1} = V_0 + endpoints(E_{-1}); edge encoder: E_{-1}
 // Recomputing exactly these rows in FP32 gives the band edges the same logits
-// as an FP32 run of the whole event. A stable counting sort by level
-// (descending) turns the levels into one row list whose prefix [0, cnt_ge[k])
-// is the set of step k, rows in index order within a level.
+// as an FP32 run of the whole event. Before each step a stable compaction
+// lists that step's rows (level >= k) in index order.
 //
 // Levels are stored as int8 shifted by +2 (0 = not needed, 1 = encoders only,
 // k + 2 = up to step k), so a memset clears them.
@@ -110,20 +109,26 @@ __global__ void k_rs_step(Ws w, int k) {
   }
 }
 
-// Stable counting sort of the levels. Bucket = top - shifted level (bucket 0
-// holds the highest level); rows at level 0 (not needed) are dropped.
+// Stable compaction of the rows of one step: the rows with level >= k, in
+// index order (so a step's kernels visit rows in the batch's event order, as
+// the full FP32 path does). Each block takes one contiguous chunk of rows;
+// counts by ballots, offsets by one block, placement in the same order.
 struct SortSide {
   const int8_t* lev;
   int32_t* list;
-  int32_t* blk_cnt;      // [nb][gridDim.x] rows per bucket per block, then block offsets
+  int32_t* blk_cnt;      // [gridDim.x] rows per block, then block offsets
   const int32_t* n_ptr;  // row count on the device (edges) or null
   int n_fixed;
-  int32_t* cge;          // [K + 1]: rows with level >= k at [k + 1]
-  int counter;           // counters index receiving the total
+  int32_t* cge;          // [K + 1]: rows of step k at [k + 1]
+  int counter;           // counters index receiving the encoder step's total
 };
 
+constexpr int kRsTile = 4 * kRsThreads;  // rows per block and iteration (4 per thread)
+
+// the block's chunk of rows, a multiple of kRsTile (so every 4-row group is
+// 4-byte aligned)
 __device__ __forceinline__ void chunk_of(int n, int& lo, int& hi) {
-  const int per = (((n + gridDim.x - 1) / gridDim.x) + kRsThreads - 1) / kRsThreads * kRsThreads;
+  const int per = (((n + gridDim.x - 1) / gridDim.x) + kRsTile - 1) / kRsTile * kRsTile;
   lo = min(n, int(blockIdx.x) * per);
   hi = min(n, lo + per);
 }
@@ -132,109 +137,99 @@ __device__ __forceinline__ int side_rows(const SortSide& sd) {
   return sd.n_ptr ? min(*sd.n_ptr, sd.n_fixed) : sd.n_fixed;
 }
 
-// per block and bucket, the number of rows (ballot counts, no atomics)
-__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int K,
+// which of the 4 rows i0 .. i0+3 (< hi) have level >= thr, as bits 0..3
+__device__ __forceinline__ unsigned rows4(const int8_t* lev, int i0, int hi, int thr) {
+  unsigned bits = 0;
+  if (i0 + 3 < hi) {
+    const char4 l = *reinterpret_cast<const char4*>(lev + i0);
+    bits = (l.x >= thr ? 1u : 0u) | (l.y >= thr ? 2u : 0u) | (l.z >= thr ? 4u : 0u) |
+           (l.w >= thr ? 8u : 0u);
+  } else {
+    for (int j = 0; j < 4; ++j)
+      if (i0 + j < hi && lev[i0 + j] >= thr) bits |= 1u << j;
+  }
+  return bits;
+}
+
+// rows of this block's chunk with (shifted) level >= thr
+__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int thr,
                                                          const int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  const int nb = K + 1, top = K + 1;
-  __shared__ int cnt[kRsWarps][kMaxIters + 2];
+  __shared__ int cnt[kRsWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int mine = 0;  // lane j of each warp counts bucket j
+  int mine = 0;
   int lo, hi;
   chunk_of(side_rows(sd), lo, hi);
-  for (int base = lo; base < hi; base += kRsThreads) {
-    const int i = base + threadIdx.x;
-    const int bk = i < hi ? top - sd.lev[i] : -1;  // level 0 -> bucket K + 1 (dropped)
-    for (int j = 0; j < nb; ++j) {
-      const int c = __popc(__ballot_sync(0xffffffffu, bk == j));
-      if (lane == j) mine += c;
-    }
-  }
-  if (lane < nb) cnt[warp][lane] = mine;
+  for (int base = lo; base < hi; base += kRsTile)
+    mine += __popc(rows4(sd.lev, base + 4 * threadIdx.x, hi, thr));
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (lane == 0) cnt[warp] = mine;
   __syncthreads();
-  if (threadIdx.x < nb) {
+  if (threadIdx.x == 0) {
     int t = 0;
-    for (int q = 0; q < kRsWarps; ++q) t += cnt[q][threadIdx.x];
-    sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x] = t;
+    for (int q = 0; q < kRsWarps; ++q) t += cnt[q];
+    sd.blk_cnt[blockIdx.x] = t;
   }
 }
 
-// exclusive offsets per (bucket, block) in bucket-major order; one block per side
-__global__ void __launch_bounds__(1024) k_rs_offsets(SortSide se, SortSide sn, int K, int nblk,
-                                                     int32_t* counters) {
+// exclusive offsets per block; one warp per side; the total is the step's
+// row count (cge[k + 1]) and, for the encoders (k = -1), the re-score total
+__global__ void k_rs_offsets(SortSide se, SortSide sn, int nblk, int k, int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.x == 0 ? se : sn;
-  const int nb = K + 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int tot[kMaxIters + 2];
-  // warp j scans bucket j over the blocks
-  if (warp < nb) {
-    int32_t* row = sd.blk_cnt + warp * nblk;
-    int run = 0;
-    for (int b0 = 0; b0 < nblk; b0 += 32) {
-      const int v = b0 + lane < nblk ? row[b0 + lane] : 0;
-      int x = v;
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-      }
-      if (b0 + lane < nblk) row[b0 + lane] = run + x - v;
-      run += __shfl_sync(0xffffffffu, x, 31);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  int run = 0;
+  for (int b0 = 0; b0 < nblk; b0 += 32) {
+    const int v = b0 + lane < nblk ? sd.blk_cnt[b0 + lane] : 0;
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
     }
-    if (lane == 0) tot[warp] = run;
+    if (b0 + lane < nblk) sd.blk_cnt[b0 + lane] = run + x - v;
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
-  __syncthreads();
-  __shared__ int base[kMaxIters + 2];
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int j = 0; j < nb; ++j) {  // bucket j = level K-1-j
-      base[j] = run;
-      run += tot[j];
-      sd.cge[K - 1 - j + 1] = run;  // rows with level >= K-1-j
-    }
-    counters[sd.counter] = run;
+  if (lane == 0) {
+    sd.cge[k + 1] = run;
+    if (k < 0) counters[sd.counter] = run;
   }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j)
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) sd.blk_cnt[j * nblk + b] += base[j];
 }
 
-// scatter in the same chunk and tile order as the count: stable
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int K,
+// placement in the same chunk order as the count (stable): per tile, each
+// thread's 4 rows, ranked by a warp scan and the block's warp totals
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int thr,
                                                            const int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  const int nb = K + 1, top = K + 1;
-  __shared__ int wtot[kRsWarps][kMaxIters + 2];
-  __shared__ int run[kMaxIters + 2];
+  __shared__ int wtot[2][kRsWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  if (threadIdx.x < nb) run[threadIdx.x] = sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x];
+  int run = sd.blk_cnt[blockIdx.x];
   int lo, hi;
   chunk_of(side_rows(sd), lo, hi);
-  for (int base = lo; base < hi; base += kRsThreads) {
-    const int i = base + threadIdx.x;
-    const int bk = i < hi ? top - sd.lev[i] : -1;
-    int rank = 0;
-    for (int j = 0; j < nb; ++j) {
-      const unsigned m = __ballot_sync(0xffffffffu, bk == j);
-      if (bk == j) rank = __popc(m & lt);
-      if (lane == 0) wtot[warp][j] = __popc(m);
+  int par = 0;
+  for (int base = lo; base < hi; base += kRsTile, par ^= 1) {
+    const int i0 = base + 4 * threadIdx.x;
+    const unsigned bits = rows4(sd.lev, i0, hi, thr);
+    const int c = __popc(bits);
+    int x = c;  // inclusive scan over the warp
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
     }
-    __syncthreads();
-    if (bk >= 0 && bk < nb) {
-      int off = run[bk];
-      for (int q = 0; q < warp; ++q) off += wtot[q][bk];
-      sd.list[off + rank] = i;
+    if (lane == 31) wtot[par][warp] = x;
+    __syncthreads();  // (the other buffer of wtot is read by the next tile)
+    int off = run + x - c;
+    int tile_total = 0;
+    for (int q = 0; q < kRsWarps; ++q) {
+      const int t = wtot[par][q];
+      if (q < warp) off += t;
+      tile_total += t;
     }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      int t = 0;
-      for (int q = 0; q < kRsWarps; ++q) t += wtot[q][threadIdx.x];
-      run[threadIdx.x] += t;
-    }
-    __syncthreads();
+    for (int j = 0; j < 4; ++j)
+      if (bits & (1u << j)) sd.list[off++] = i0 + j;
+    run += tile_total;
   }
 }
 
@@ -246,21 +241,27 @@ int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_h
                         cudaStream_t s) {
   const int NL = kMaxIters + 2;
   const int grid = device_sms() * 8;
-  const int nblk = rescore_sort_blocks();
   cudaMemsetAsync(w.ev_flag, 0, sizeof(int32_t) * b.n_events, s);
   cudaMemsetAsync(w.rs_counts, 0, sizeof(int32_t) * 6 * NL, s);
   cudaMemsetAsync(w.rs_elev, 0, size_t(w.e_cap), s);
   cudaMemsetAsync(w.rs_nlev, 0, size_t(b.n_hits), s);
   k_rs_init<<<grid, kRsThreads, 0, s>>>(w, band_lo, band_hi, K);
   for (int k = K - 1; k >= 0; --k) k_rs_step<<<grid, kRsThreads, 0, s>>>(w, k);
+  return 1 + K;
+}
+
+int launch_rescore_list(const Batch& b, const Ws& w, int k, cudaStream_t s) {
+  const int NL = kMaxIters + 2;
+  const int nblk = rescore_sort_blocks();
   SortSide se{w.rs_elev, w.rs_elist, w.rs_blk, w.counters + C_EDGES, int(w.e_cap),
               w.rs_counts + 2 * NL, C_RERUN_EDGES};
-  SortSide sn{w.rs_nlev, w.rs_nlist, w.rs_blk + NL * nblk, nullptr, b.n_hits,
+  SortSide sn{w.rs_nlev, w.rs_nlist, w.rs_blk + kRsMaxBlocks, nullptr, b.n_hits,
               w.rs_counts + 5 * NL, C_RERUN_HITS};
-  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
-  k_rs_offsets<<<2, 1024, 0, s>>>(se, sn, K, nblk, w.counters);
-  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
-  return 1 + K + 3;
+  const int thr = k + 2;  // levels are stored shifted by 2
+  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, thr, w.counters);
+  k_rs_offsets<<<2, 32, 0, s>>>(se, sn, nblk, k, w.counters);
+  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, thr, w.counters);
+  return 3;
 }
 
 }  // namespace gnntrk
