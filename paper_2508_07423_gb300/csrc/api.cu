@@ -229,8 +229,8 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   if (c.precision != GNNTRK_FP32) {
     add(&w.rs_elev, E);
     add(&w.rs_nlev, H);
-    add(&w.rs_elist, E);
-    add(&w.rs_nlist, H);
+    add(&w.rs_elist, E * (c.iters + 1));
+    add(&w.rs_nlist, H * (c.iters + 1));
     add(&w.rs_counts, 6 * (kMaxIters + 2));
     add(&w.rs_blk, 2 * (kMaxIters + 2) * kRsMaxBlocks);
   }
@@ -381,10 +381,10 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       const int NL = kMaxIters + 2;
       const int32_t* cge_e = w.rs_counts + 2 * NL;  // [k + 1]: edges of step k
       const int32_t* cge_n = w.rs_counts + 5 * NL;  // [k + 1]: hits of step k
-      auto esel = [&](int k) { return Sel{w.rs_elist, cge_e + k + 1}; };
-      auto nsel = [&](int k) { return Sel{w.rs_nlist, cge_n + k + 1}; };
-      // each step's rows, compacted in index order just before the step
-      stage(h, "rescore_lists", s, 3, [&] { launch_rescore_list(b, w, -1, s); });
+      // each step's rows in index order: list k + 1 of rs_elist / rs_nlist
+      auto esel = [&](int k) { return Sel{w.rs_elist + size_t(k + 1) * w.e_cap, cge_e + k + 1}; };
+      auto nsel = [&](int k) { return Sel{w.rs_nlist + size_t(k + 1) * w.h_cap, cge_n + k + 1}; };
+      stage(h, "rescore_lists", s, 3, [&] { launch_rescore_lists(b, w, h->K, s); });
       stage(h, "rescore_node_prep", s, 1, [&] {
         launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
                              false, true, nsel(-1), s);
@@ -392,7 +392,6 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       stage(h, "rescore_edge_encoder", s, 1,
             [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, esel(-1), s); });
       for (int k = 0; k < h->K; ++k) {
-        stage(h, "rescore_lists", s, 3, [&] { launch_rescore_list(b, w, k, s); });
         stage(h, "rescore_node_update", s, 2, [&] {
           launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, nsel(k), s);
         });

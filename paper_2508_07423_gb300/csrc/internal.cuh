@@ -101,10 +101,10 @@ struct Ws {
   int32_t* ev_flag;     // [max_events] events re-run in FP32
   int8_t* rs_elev;      // [Ecap] re-score level of each edge + 2 (0 none)
   int8_t* rs_nlev;      // [H]    re-score level of each hit + 2 (0 none)
-  int32_t* rs_elist;    // [Ecap] edges by level, descending
-  int32_t* rs_nlist;    // [H]    hits by level, descending
+  int32_t* rs_elist;    // [K + 1][Ecap] rows of each re-score step, index order
+  int32_t* rs_nlist;    // [K + 1][H]    hits of each re-score step, index order
   int32_t* rs_counts;   // [6][kMaxIters + 2]: [2] and [5] rows with level >= k (edges, hits)
-  int32_t* rs_blk;      // [2][kRsMaxBlocks] per-block offsets of the row compaction
+  int32_t* rs_blk;      // [2][kMaxIters + 1][kRsMaxBlocks] per-block offsets of the lists
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
   int64_t h_cap, e_cap;
 };
@@ -142,10 +142,11 @@ struct Sel {
 // number of kernels launched.
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s);
-// row lists of re-score step k (k = -1: the encoders) into w.rs_elist /
-// w.rs_nlist, counts into rs_counts[2 (kMaxIters + 2) + k + 1] (edges) and
-// rs_counts[5 (kMaxIters + 2) + k + 1] (hits); returns the launch count
-int launch_rescore_list(const Batch& b, const Ws& w, int k, cudaStream_t s);
+// row lists of every re-score step: list k + 1 of w.rs_elist ([K + 1][e_cap])
+// and w.rs_nlist ([K + 1][h_cap]) holds the rows of step k (k = -1: the
+// encoders) in index order, their counts at rs_counts[2 (kMaxIters + 2) + k + 1]
+// (edges) and rs_counts[5 (kMaxIters + 2) + k + 1] (hits); returns the launch count
+int launch_rescore_lists(const Batch& b, const Ws& w, int K, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (host functions), one per kernel family

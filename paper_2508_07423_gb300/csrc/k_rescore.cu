@@ -109,14 +109,16 @@ __global__ void k_rs_step(Ws w, int k) {
   }
 }
 
-// Stable compaction of the rows of one step: the rows with level >= k, in
-// index order (so a step's kernels visit rows in the batch's event order, as
-// the full FP32 path does). Each block takes one contiguous chunk of rows;
-// counts by ballots, offsets by one block, placement in the same order.
+// Row lists of all steps in one sweep: list t (t = 0 .. K, step k = t - 1)
+// holds the rows with level >= k in index order (so a step's kernels visit
+// rows in the batch's event order, as the full FP32 path does). Each block
+// takes one contiguous chunk of rows; counts per list by ballots, offsets by
+// one warp per list, placement in the same order (stable).
 struct SortSide {
   const int8_t* lev;
-  int32_t* list;
-  int32_t* blk_cnt;      // [gridDim.x] rows per block, then block offsets
+  int32_t* list;         // [K + 1][stride]
+  int64_t stride;
+  int32_t* blk_cnt;      // [K + 1][gridDim.x] rows per block, then block offsets
   const int32_t* n_ptr;  // row count on the device (edges) or null
   int n_fixed;
   int32_t* cge;          // [K + 1]: rows of step k at [k + 1]
@@ -137,99 +139,126 @@ __device__ __forceinline__ int side_rows(const SortSide& sd) {
   return sd.n_ptr ? min(*sd.n_ptr, sd.n_fixed) : sd.n_fixed;
 }
 
-// which of the 4 rows i0 .. i0+3 (< hi) have level >= thr, as bits 0..3
-__device__ __forceinline__ unsigned rows4(const int8_t* lev, int i0, int hi, int thr) {
-  unsigned bits = 0;
+// shifted levels of the 4 rows i0 .. i0+3 (0 past hi)
+__device__ __forceinline__ void levels4(const int8_t* lev, int i0, int hi, int (&l)[4]) {
   if (i0 + 3 < hi) {
-    const char4 l = *reinterpret_cast<const char4*>(lev + i0);
-    bits = (l.x >= thr ? 1u : 0u) | (l.y >= thr ? 2u : 0u) | (l.z >= thr ? 4u : 0u) |
-           (l.w >= thr ? 8u : 0u);
+    const char4 v = *reinterpret_cast<const char4*>(lev + i0);
+    l[0] = v.x;
+    l[1] = v.y;
+    l[2] = v.z;
+    l[3] = v.w;
   } else {
-    for (int j = 0; j < 4; ++j)
-      if (i0 + j < hi && lev[i0 + j] >= thr) bits |= 1u << j;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) l[j] = i0 + j < hi ? lev[i0 + j] : 0;
   }
-  return bits;
 }
 
-// rows of this block's chunk with (shifted) level >= thr
-__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int thr,
+// rows of this block's chunk in each list (level >= t - 1, i.e. shifted >= t + 1)
+__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int K,
                                                          const int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  __shared__ int cnt[kRsWarps];
+  __shared__ int cnt[kRsWarps][kMaxIters + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int mine = 0;
   int lo, hi;
   chunk_of(side_rows(sd), lo, hi);
-  for (int base = lo; base < hi; base += kRsTile)
-    mine += __popc(rows4(sd.lev, base + 4 * threadIdx.x, hi, thr));
-  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-  if (lane == 0) cnt[warp] = mine;
+  int c[kMaxIters + 1];
+#pragma unroll
+  for (int t = 0; t <= kMaxIters; ++t) c[t] = 0;
+  for (int base = lo; base < hi; base += kRsTile) {
+    int l[4];
+    levels4(sd.lev, base + 4 * threadIdx.x, hi, l);
+#pragma unroll
+    for (int t = 0; t <= kMaxIters; ++t)
+      if (t <= K) c[t] += (l[0] >= t + 1) + (l[1] >= t + 1) + (l[2] >= t + 1) + (l[3] >= t + 1);
+  }
+#pragma unroll
+  for (int t = 0; t <= kMaxIters; ++t) {
+    if (t > K) break;
+    int v = c[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) cnt[warp][t] = v;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int q = 0; q < kRsWarps; ++q) t += cnt[q];
-    sd.blk_cnt[blockIdx.x] = t;
+  if (threadIdx.x <= K) {
+    int tot = 0;
+    for (int q = 0; q < kRsWarps; ++q) tot += cnt[q][threadIdx.x];
+    sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x] = tot;
   }
 }
 
-// exclusive offsets per block; one warp per side; the total is the step's
-// row count (cge[k + 1]) and, for the encoders (k = -1), the re-score total
-__global__ void k_rs_offsets(SortSide se, SortSide sn, int nblk, int k, int32_t* counters) {
+// exclusive offsets per (list, block); warp t of block `side` scans list t;
+// the totals are the steps' row counts, list 0's also the re-score total
+__global__ void k_rs_offsets(SortSide se, SortSide sn, int nblk, int K, int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.x == 0 ? se : sn;
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  if (t > K) return;
+  int32_t* row = sd.blk_cnt + t * nblk;
   int run = 0;
   for (int b0 = 0; b0 < nblk; b0 += 32) {
-    const int v = b0 + lane < nblk ? sd.blk_cnt[b0 + lane] : 0;
+    const int v = b0 + lane < nblk ? row[b0 + lane] : 0;
     int x = v;
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, d);
       if (lane >= d) x += y;
     }
-    if (b0 + lane < nblk) sd.blk_cnt[b0 + lane] = run + x - v;
+    if (b0 + lane < nblk) row[b0 + lane] = run + x - v;
     run += __shfl_sync(0xffffffffu, x, 31);
   }
   if (lane == 0) {
-    sd.cge[k + 1] = run;
-    if (k < 0) counters[sd.counter] = run;
+    sd.cge[t] = run;
+    if (t == 0) counters[sd.counter] = run;
   }
 }
 
-// placement in the same chunk order as the count (stable): per tile, each
-// thread's 4 rows, ranked by a warp scan and the block's warp totals
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int thr,
+// placement in the same chunk order as the count (stable): per tile and list,
+// each thread's rows ranked by a warp scan and the block's warp totals
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int K,
                                                            const int32_t* counters) {
   if (input_bad(counters)) return;
   const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  __shared__ int wtot[2][kRsWarps];
+  __shared__ int wtot[2][kMaxIters + 1][kRsWarps];
+  __shared__ int run[kMaxIters + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int run = sd.blk_cnt[blockIdx.x];
+  if (threadIdx.x <= K) run[threadIdx.x] = sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x];
   int lo, hi;
   chunk_of(side_rows(sd), lo, hi);
   int par = 0;
   for (int base = lo; base < hi; base += kRsTile, par ^= 1) {
     const int i0 = base + 4 * threadIdx.x;
-    const unsigned bits = rows4(sd.lev, i0, hi, thr);
-    const int c = __popc(bits);
-    int x = c;  // inclusive scan over the warp
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += y;
+    int l[4];
+    levels4(sd.lev, i0, hi, l);
+    int xs[kMaxIters + 1];
+#pragma unroll
+    for (int t = 0; t <= kMaxIters; ++t) {
+      if (t > K) break;
+      const int c = (l[0] >= t + 1) + (l[1] >= t + 1) + (l[2] >= t + 1) + (l[3] >= t + 1);
+      int x = c;  // inclusive scan over the warp
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+      }
+      if (lane == 31) wtot[par][t][warp] = x;
+      xs[t] = x - c;
     }
-    if (lane == 31) wtot[par][warp] = x;
-    __syncthreads();  // (the other buffer of wtot is read by the next tile)
-    int off = run + x - c;
-    int tile_total = 0;
-    for (int q = 0; q < kRsWarps; ++q) {
-      const int t = wtot[par][q];
-      if (q < warp) off += t;
-      tile_total += t;
+    __syncthreads();  // wtot[par] complete; run[] from the previous tile visible
+#pragma unroll
+    for (int t = 0; t <= kMaxIters; ++t) {
+      if (t > K) break;
+      int off = run[t] + xs[t];
+      for (int q = 0; q < warp; ++q) off += wtot[par][t][q];
+      int32_t* list = sd.list + t * sd.stride;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (l[j] >= t + 1) list[off++] = i0 + j;
     }
-    for (int j = 0; j < 4; ++j)
-      if (bits & (1u << j)) sd.list[off++] = i0 + j;
-    run += tile_total;
+    __syncthreads();  // every thread has read run[] of this tile
+    if (threadIdx.x <= K) {
+      int tot = 0;
+      for (int q = 0; q < kRsWarps; ++q) tot += wtot[par][threadIdx.x][q];
+      run[threadIdx.x] += tot;
+    }
   }
 }
 
@@ -250,17 +279,16 @@ int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_h
   return 1 + K;
 }
 
-int launch_rescore_list(const Batch& b, const Ws& w, int k, cudaStream_t s) {
+int launch_rescore_lists(const Batch& b, const Ws& w, int K, cudaStream_t s) {
   const int NL = kMaxIters + 2;
   const int nblk = rescore_sort_blocks();
-  SortSide se{w.rs_elev, w.rs_elist, w.rs_blk, w.counters + C_EDGES, int(w.e_cap),
+  SortSide se{w.rs_elev, w.rs_elist, w.e_cap, w.rs_blk, w.counters + C_EDGES, int(w.e_cap),
               w.rs_counts + 2 * NL, C_RERUN_EDGES};
-  SortSide sn{w.rs_nlev, w.rs_nlist, w.rs_blk + kRsMaxBlocks, nullptr, b.n_hits,
-              w.rs_counts + 5 * NL, C_RERUN_HITS};
-  const int thr = k + 2;  // levels are stored shifted by 2
-  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, thr, w.counters);
-  k_rs_offsets<<<2, 32, 0, s>>>(se, sn, nblk, k, w.counters);
-  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, thr, w.counters);
+  SortSide sn{w.rs_nlev, w.rs_nlist, w.h_cap, w.rs_blk + (kMaxIters + 1) * kRsMaxBlocks, nullptr,
+              b.n_hits, w.rs_counts + 5 * NL, C_RERUN_HITS};
+  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
+  k_rs_offsets<<<2, 32 * (K + 1), 0, s>>>(se, sn, nblk, K, w.counters);
+  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
   return 3;
 }
 
