@@ -127,6 +127,8 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     design notes; amount = figure x units of one launch.
     """
     sb = 4 if precision == "fp32" else 2   # state bytes per element
+    if stage == "rescore_node_prep":  # FP32 node encoder + projections (the embedding is reused)
+        return "alu", N * 2.0 * (3 * h + h * h + 2 * h * h), "flop"
     if stage.startswith("rescore_"):  # the FP32 re-run (same kernels as the FP32 path)
         precision, stage = "fp32", stage[len("rescore_"):]
     if stage == "edge_update":
@@ -141,8 +143,20 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
             # node network (3h x h, h x h) and the two projections (2 x h x h)
             return "alu", N * 2.0 * (3 * h * h + h * h + 2 * h * h), "flop"
         return "hbm", N * 2 * h * sb + E * 2 * h * sb + E * 8, "byte"
-    if stage == "edge_encoder" and precision == "fp32":
-        return "alu", E * 2.0 * h * h, "flop"
+    if stage == "edge_encoder":
+        if precision == "fp32":
+            return "alu", E * 2.0 * h * h, "flop"
+        # read h_src, h_dst rows; write e; indices
+        return "hbm", E * (3 * h * sb + 8), "byte"
+    if stage == "node_prep":
+        # embedding MLP (FP32 in every precision), plus the FP32 node encoder
+        # (3 x h, h x h) and its two projections (2 x h x h) on the FP32 path
+        macs = sum(a * b for a, b in zip(embed[:-1], embed[1:]))
+        if precision == "fp32":
+            macs += 3 * h + h * h + 2 * h * h
+        return "alu", N * 2.0 * macs, "flop"
+    if stage == "in_index":
+        return "hbm", E * 12 + N * 8, "byte"
     if stage in ("radius_count", "radius_fill"):
         return "hbm", N * D * 4 + N * 4 + (E * 12 if stage == "radius_fill" else 0), "byte"
     if stage == "components":
@@ -306,6 +320,19 @@ def main():
     bpr = TRAFFIC_PER_ROW.get((dname, precision))
     traffic = (round(bpr * stage_rows_per_launch(dname, druns // a.steps, rows, N, E, m["iters"]))
                if bpr is not None and a.workload == "cfg3_batched_bf16" else None)
+    # every stage with a work model: achieved rate against its roofline
+    per_stage = {}
+    for sname, (sms, sruns) in stages.items():
+        if sname in ("band_mark", "rescore_lists", "scan_out", "sort"):
+            continue
+        sb_, samt = stage_amount(sname, sruns // a.steps, rows, precision, N, E, m)
+        st_ms = sms / a.steps
+        if sb_ == "alu":
+            pk_, ach, un = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, samt / (st_ms / 1e3) / 1e12, "TFLOP/s"
+        else:
+            pk_, ach, un = pk["hbm_gbs"], samt / (st_ms / 1e3) / 1e9, "GB/s"
+        per_stage[sname] = {"ms_per_step": round(st_ms, 4), "bound": sb_, "achieved": round(ach, 2),
+                            "unit": un, "frac": round(ach / pk_, 4)}
     roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
             "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_unit": "DRAM bytes per launch (ncu capture of 300 events scaled by rows)",
@@ -314,7 +341,8 @@ def main():
             "launch_ms": round(launch_ms, 4),
             "work": "algorithmic work of the stage over one step / its time per step",
             "profiled_ms_per_step": round(float(np.mean(prof_ms)), 4),
-            "stage_ms_per_step": {k: round(v[0] / a.steps, 4) for k, v in stages.items()}}
+            "stage_ms_per_step": {k: round(v[0] / a.steps, 4) for k, v in stages.items()},
+            "stages": per_stage}
 
     e2e = None if a.no_e2e else run_e2e(a, tr, batch, stream, dev, torch)
     extra = {}
