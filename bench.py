@@ -145,7 +145,9 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
         return "hbm", N * 2 * h * sb + E * 2 * h * sb + E * 8, "byte"
     if stage == "edge_encoder":
         if precision == "fp32":
-            return "alu", E * 2.0 * h * h, "flop"
+            # 2 h^2 flop per edge against 3 rows of 4h bytes: memory-bound;
+            # read the two projection halves P[src], P[dst], write e, indices
+            return "hbm", E * (3 * h * 4 + 8), "byte"
         # read h_src, h_dst rows; write e; indices
         return "hbm", E * (3 * h * sb + 8), "byte"
     if stage == "node_prep":
