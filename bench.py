@@ -389,6 +389,7 @@ def main():
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, batch, labels.cpu().numpy(), tr, a.cpu_seconds)
         if not a.no_plain:
+            out["cfg2_report"] = cfg2_report(pkg, torch, dev, stream)
             out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
     if rank == 0:
         print(json.dumps(out))
@@ -553,6 +554,82 @@ def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
             "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4),
             "edge_decision_agreement": round(agree / max(union, 1), 6),
             "edge_decision_events": min(4, done), "max_score_error": max_err}
+
+
+def cfg2_report(pkg, torch, dev, stream, reps=3):
+    """Config 2: the run-3-like model (embed 3-128-128-128-8, IN h64 K8) on
+    100 events of 200 tracks, FP32 vs BF16: events/s with one event per call
+    and with the 100 events in one call, BF16 agreement with FP32, and both
+    against the FP64 oracle on two events."""
+    try:
+        import oracle
+        wl = synth.workload("cfg2_run3_single")
+        b = synth.workload_batch(wl)
+        res = {}
+        graphs = {}
+        for prec in ("fp32", "bf16"):
+            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events,
+                                          edges_per_hit=24, use_graph=False)
+            evs = []
+            for e in range(b.n_events):
+                ev = b.event(e)
+                evs.append((ev.n_hits, torch.from_numpy(ev.xyz_soa()).to(dev),
+                            torch.from_numpy(ev.plane).to(dev), torch.from_numpy(ev.offsets).to(dev),
+                            torch.empty(ev.n_hits, dtype=torch.int32, device=dev)))
+            xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+            plane = torch.from_numpy(b.plane).to(dev)
+            offs = torch.from_numpy(b.offsets).to(dev)
+            lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+            for n_, x_, p_, o_, l_ in evs[:5]:
+                tr.find_tracks(1, n_, x_, p_, o_, l_, stream)
+            tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+            tr.sync_status(stream)
+            s1, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                s1.record(stream)
+                for _ in range(reps):
+                    for n_, x_, p_, o_, l_ in evs:
+                        tr.find_tracks(1, n_, x_, p_, o_, l_, stream)
+                e1.record(stream)
+                s2.record(stream)
+                for _ in range(reps):
+                    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+                e2.record(stream)
+            e2.synchronize()
+            tr.sync_status(stream)
+            n = reps * b.n_events
+            res[prec] = {"one_event_per_call_events_per_s": round(n / (s1.elapsed_time(e1) / 1e3), 1),
+                         "batched_events_per_s": round(n / (s2.elapsed_time(e2) / 1e3), 1)}
+            graphs[prec] = [tr.get_graph(e) for e in range(b.n_events)]
+            tr.close()
+        g16, g32 = graphs["bf16"], graphs["fp32"]
+        sig = lambda v: 1 / (1 + np.exp(-np.asarray(v, np.float64)))
+        d = np.concatenate([np.abs(sig(a["logit"]) - sig(c["logit"])) for a, c in zip(g16, g32)])
+        agree = np.mean(np.concatenate([a["kept"] == c["kept"] for a, c in zip(g16, g32)]))
+        sh = synth.shape_of(wl)
+        m = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+        fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+        err = {"fp32": [], "bf16": []}
+        for e in range(2):
+            ev = b.event(e)
+            ref = oracle.find_tracks_event(m, ev.x, ev.y, ev.z, ev.plane, wl["radius2"], wl["k_max"],
+                                           feat_scale=fs)
+            O = {(int(u), int(v)): float(l) for u, v, l in zip(ref.src, ref.dst, ref.logit)}
+            for prec, gs in (("fp32", g32), ("bf16", g16)):
+                g = gs[e]
+                for u, v, l in zip(g["src"], g["dst"], g["logit"]):
+                    if (int(u), int(v)) in O:
+                        err[prec].append(abs(sig(l) - sig(O[(int(u), int(v))])))
+        return {"workload": f"cfg2_run3_single: {b.n_events} events, {wl['description']}",
+                "hits": int(b.n_hits), **res,
+                "bf16_vs_fp32": {"max_score_error": round(float(d.max()), 6),
+                                 "mean_score_error": round(float(d.mean()), 6),
+                                 "edge_decision_agreement": round(float(agree), 6)},
+                "vs_fp64_oracle_2_events": {p_: {"max_score_error": float(np.max(v)) if v else None}
+                                            for p_, v in err.items()}}
+    except Exception as ex:  # reported, not fatal
+        return {"error": str(ex)}
 
 
 def fp8_report(pkg, torch, dev, stream, chunk=1000):
