@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* in, 
 // event with more than kCscSmemHits hits counts in its slice of in_cnt.
 constexpr int kCscThreads = 512;
 constexpr int kCscSmemHits = 8192;
+constexpr int kCscSmemEdges = 12288;  // an event's in-edge list staged in shared memory
 
 __global__ void __launch_bounds__(kCscThreads) k_csc_event(Batch b, Ws w) {
   extern __shared__ int32_t sm_csc[];
@@ -476,25 +477,32 @@ __global__ void __launch_bounds__(kCscThreads) k_csc_event(Batch b, Ws w) {
     }
     if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
     __syncthreads();
+    // placement and per-target sort in shared memory when the event's list
+    // fits (copied out coalesced), else in its slice of in_edge
+    const bool staged = n <= kCscSmemHits && e1 - e0 <= kCscSmemEdges;
+    int32_t* L = staged ? sm_csc + kCscSmemHits : w.in_edge + e0;  // L[k]: list position e0 + k
     for (int e = e0 + tid; e < e1; e += kCscThreads) {
       const int k = atomicAdd(&C[w.col[e] - v0], 1);
-      w.in_edge[e0 + k] = e;
+      L[k] = e;
     }
     __syncthreads();
-    // C[i] is now the end of target i's list
+    // C[i] is now the end of target i's list (event-local position)
     for (int i = tid; i < n; i += kCscThreads) {
-      const int lo = w.in_ptr[v0 + i], hi = e0 + C[i];
+      const int lo = w.in_ptr[v0 + i] - e0, hi = C[i];
       for (int j = lo + 1; j < hi; ++j) {
-        const int key = w.in_edge[j];
+        const int key = L[j];
         int k = j - 1;
-        while (k >= lo && w.in_edge[k] > key) {
-          w.in_edge[k + 1] = w.in_edge[k];
+        while (k >= lo && L[k] > key) {
+          L[k + 1] = L[k];
           --k;
         }
-        w.in_edge[k + 1] = key;
+        L[k + 1] = key;
       }
     }
-    __syncthreads();  // C is reused by the next event
+    __syncthreads();
+    if (staged)
+      for (int k = tid; k < e1 - e0; k += kCscThreads) w.in_edge[e0 + k] = L[k];
+    __syncthreads();  // C and the staged list are reused by the next event
   }
 }
 
@@ -545,11 +553,11 @@ void launch_csc(const Batch& b, const Ws& w, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_csc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kCscSmemHits * int(sizeof(int32_t)));
+                         (kCscSmemHits + kCscSmemEdges) * int(sizeof(int32_t)));
     attr_set = true;
   }
   k_csc_event<<<std::min(b.n_events, num_sms() * 16), kCscThreads,
-                kCscSmemHits * sizeof(int32_t), s>>>(b, w);
+                (kCscSmemHits + kCscSmemEdges) * sizeof(int32_t), s>>>(b, w);
 }
 
 int device_sms() { return num_sms(); }
