@@ -574,7 +574,7 @@ __device__ __forceinline__ void embed_layer_tiled(const float* X, float* Y, cons
   tile_store_t<4, CW, kEmbedTM>(Y, r0, c0, acc, relu);
 }
 
-__global__ void __launch_bounds__(kThreads) k_embed_f32(Batch b, Ws w, EmbedLayers em,
+__global__ void __launch_bounds__(kThreads, 3) k_embed_f32(Batch b, Ws w, EmbedLayers em,
                                                         int n_embed, int D, GraphParams g,
                                                         int maxw) {
   extern __shared__ __align__(16) float sm[];
