@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--study", default=None, choices=["occupancy"],
+                   help="occupancy: throughput per event-size bin instead of the headline")
     return p.parse_args()
 
 
@@ -250,6 +252,15 @@ def main():
 
     import torch
     import paper_2508_07423_gb300 as pkg
+
+    if a.study == "occupancy":
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        res = occupancy_study(pkg, torch, dev, torch.cuda.Stream(device=dev))
+        if rank == 0:
+            print(json.dumps({"study": "occupancy", "metric": METRIC, "unit": "events/s",
+                              "data": "synthetic", "rows": res}))
+        return
 
     wl = synth.workload(a.workload)
     precision = a.precision or wl.get("precision", "fp32")
@@ -554,6 +565,68 @@ def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
             "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4),
             "edge_decision_agreement": round(agree / max(union, 1), 6),
             "edge_decision_events": min(4, done), "max_score_error": max_err}
+
+
+def occupancy_study(pkg, torch, dev, stream, bins=(20, 50, 100, 150, 200, 300, 400),
+                    target_hits=1_700_000):
+    """Occupancy scaling: events of a fixed track count per bin (config-3
+    model, radius and noise), about `target_hits` hits per batch. Batched BF16
+    + FP32 re-score (one call, CUDA graph) and the plain FP32 path (one event
+    per call, 100 events) per bin: events/s, hits/s and the ratio."""
+    wl = synth.workload("cfg3_batched_bf16")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    rows = []
+    for nt in bins:
+        spec = {"kind": "fixed", "n": nt}
+        probe = synth.gen_batch(20, 7700 + nt, spec, wl["noise"])
+        n_ev = max(20, int(target_hits / (probe.n_hits / probe.n_events)))
+        b = synth.gen_batch(n_ev, 7700 + nt, spec, wl["noise"])
+        band = float(wl.get("rescore_band_score", 0.0))
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+        tr = pkg.tracker_for_workload(wl, precision="bf16", rescore_band=band, max_hits=b.n_hits,
+                                      max_events=b.n_events, edges_per_hit=16, use_graph=True)
+        for _ in range(3):
+            tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+        tr.sync_status(stream)
+        ms = float(np.mean(timed_steps(torch, tr, b.n_events, b.n_hits, xyz, plane, offs, lab,
+                                       stream, flush, 5)))
+        st = tr.stats()
+        tr.close()
+        # plain FP32, one event per call
+        trp = pkg.tracker_for_workload(wl, precision="fp32", max_hits=max(b.event(e).n_hits for e in range(100)),
+                                       max_events=1, edges_per_hit=16)
+        evs = []
+        for e in range(min(100, b.n_events)):
+            ev = b.event(e)
+            evs.append((ev.n_hits, torch.from_numpy(ev.xyz_soa()).to(dev), torch.from_numpy(ev.plane).to(dev),
+                        torch.from_numpy(ev.offsets).to(dev), torch.empty(ev.n_hits, dtype=torch.int32, device=dev)))
+        for n_, x_, p_, o_, l_ in evs[:3]:
+            trp.find_tracks(1, n_, x_, p_, o_, l_, stream)
+        trp.sync_status(stream)
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s_.record(stream)
+            for n_, x_, p_, o_, l_ in evs:
+                trp.find_tracks(1, n_, x_, p_, o_, l_, stream)
+            e_.record(stream)
+        e_.synchronize()
+        trp.sync_status(stream)
+        pms = s_.elapsed_time(e_)
+        trp.close()
+        plain_rate = len(evs) / (pms / 1e3)
+        rate = b.n_events / (ms / 1e3)
+        rows.append({"tracks": nt, "hits_per_event": round(b.n_hits / b.n_events, 1),
+                     "edges_per_event": round(st["edges"] / b.n_events, 1), "events": b.n_events,
+                     "batched_bf16_rescore_events_per_s": round(rate, 1),
+                     "batched_hits_per_s": round(b.n_hits / (ms / 1e3), 1),
+                     "band_fraction": round(st["band"] / max(st["edges"], 1), 4),
+                     "rescore_edge_fraction": round(st["rescore_edges"] / max(st["edges"], 1), 4),
+                     "plain_fp32_events_per_s": round(plain_rate, 1),
+                     "batched_over_plain": round(rate / plain_rate, 2)})
+    return rows
 
 
 def cfg2_report(pkg, torch, dev, stream, reps=3):
