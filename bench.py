@@ -402,6 +402,7 @@ def main():
         if not a.no_plain:
             out["cfg2_report"] = cfg2_report(pkg, torch, dev, stream)
             out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
+            out["trained_report"] = trained_report(pkg, torch, dev, stream, flush)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -703,6 +704,66 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
                                             for p_, v in err.items()}}
     except Exception as ex:  # reported, not fatal
         return {"error": str(ex)}
+
+
+def trained_report(pkg, torch, dev, stream, flush, steps=5, sample=100):
+    """The headline's 1000 events with trained config-1 weights (the training
+    tool's hinge-loss embedding and focal-loss GNN, trained on other events):
+    events/s in BF16 with the FP32 re-score band and in FP32, graph size and
+    band size, and the track metrics of both against the FP64 oracle on the
+    first `sample` events."""
+    try:
+        import oracle
+        from oracle import metrics
+        wl = synth.workload("cfg3_trained_bf16")
+        b = synth.workload_batch(wl)
+        n_ev, N = b.n_events, b.n_hits
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        labels = torch.empty(N, dtype=torch.int32, device=dev)
+        sub = b.subset(list(range(sample)))
+        nh = int(sub.n_hits)
+        res = {}
+        for prec in ("bf16", "fp32"):
+            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=N, max_events=n_ev,
+                                          edges_per_hit=16, use_graph=True)
+            tuned = tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
+            for _ in range(3):
+                tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            tr.sync_status(stream)
+            ms = float(np.mean(timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream,
+                                           flush, steps)))
+            st = tr.stats()
+            lab = labels.cpu().numpy()[:nh]
+            c = metrics.batch_counts(lab, sub.pid, sub.offsets).summary()
+            res[prec] = {"events_per_s": round(n_ev / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+                         "edges": st["edges"], "mean_degree": round(2 * st["edges"] / N, 3),
+                         "kept_edges": st["kept"], "band_edges": st["band"],
+                         "rerun_events": st["rerun_events"], "rescore_rows": tr.rescore_rows(),
+                         "autotuned_ctas_per_sm": tuned,
+                         f"metrics_first_{sample}_events": {k: round(v, 6) if isinstance(v, float) else v
+                                                            for k, v in c.items()}}
+            tr.close()
+        sh = synth.shape_of(wl)
+        model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+        fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        lab_ref, ne_ref = oracle.find_tracks_batch(model, sub.x, sub.y, sub.z, sub.plane, sub.offsets,
+                                                   wl["radius2"], wl["k_max"], wl["cut"],
+                                                   threads=cores, feat_scale=fs)
+        t_oracle = time.perf_counter() - t0
+        co = metrics.batch_counts(lab_ref, sub.pid, sub.offsets).summary()
+        return {"workload": f"cfg3_trained_bf16: {n_ev} events, {wl['description']}",
+                "hits": int(N), **res,
+                f"oracle_first_{sample}_events": {**{k: round(v, 6) if isinstance(v, float) else v
+                                                     for k, v in co.items()},
+                                                  "edges": int(ne_ref), "seconds": round(t_oracle, 2),
+                                                  "cores": cores}}
+    except Exception as ex:  # reported, not fatal
+        import traceback
+        return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
 
 
 def fp8_report(pkg, torch, dev, stream, chunk=1000):

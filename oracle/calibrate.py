@@ -46,6 +46,8 @@ def main():
     with open(synth.WORKLOADS_PATH) as f:
         wls = json.load(f)
     for name, wl in wls.items():
+        if wl.get("weights_file"):  # trained weights: the radius comes from training
+            continue
         wl["radius2"] = calibrate(name, wl)
     with open(synth.WORKLOADS_PATH, "w") as f:
         json.dump(wls, f, indent=2)

@@ -293,7 +293,8 @@ def run_batch(tracker: Tracker, batch, device="cuda", stream=None, check=True):
 
 
 def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
-    """A Tracker for a workload of workloads.json (weights from its seed)."""
+    """A Tracker for a workload of workloads.json (seeded random weights, or
+    the trained blob the workload names)."""
     from . import synth
     prec = precision if precision is not None else wl.get("precision", "fp32")
     band = float(wl.get("rescore_band_score", 0.0)) if prec != "fp32" else 0.0

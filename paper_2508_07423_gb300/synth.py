@@ -253,4 +253,9 @@ def workload_batch(wl: dict, n_events: int | None = None, first_event: int = 0,
 
 
 def workload_weights(wl: dict) -> bytes:
+    """The workload's weight blob: a trained blob shipped with the package
+    (`weights_file`, written by the training tool) or seeded random weights."""
+    if wl.get("weights_file"):
+        with open(os.path.join(_HERE, wl["weights_file"]), "rb") as f:
+            return f.read()
     return make_weights(shape_of(wl), wl["seeds"]["weights"])

@@ -238,3 +238,41 @@ def test_large_event_uses_global_scratch():
     # labels equal the components of the kept edges (checked inside), scores
     # and decisions match the oracle
     assert r.edges > 40000 and r.scores_compared > 0.9 * r.edges
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_trained_weights(prec):
+    """Trained config-1 weights (a sparser graph and scores pushed away from the
+    cut): the FP32 path element by element against the oracle; BF16 with the
+    FP32 re-score band takes the oracle's keep decisions; both give the
+    oracle's track metrics."""
+    from oracle import metrics
+    wl = synth.workload("cfg3_trained_bf16")
+    model = model_of(wl)
+    b = synth.workload_batch(wl, 8, first_event=20)
+    tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events)
+    fs = pkg.feat_scale_of(tr.cfg)
+    if prec == "fp32":
+        labels, reps = run_and_compare(tr, b, wl, model)
+        assert sum(bool(r.labels_compared and r.labels_equal) for r in reps) >= 7
+    else:
+        labels = pkg.run_batch(tr, b)
+        agree = union = 0
+        for e in range(b.n_events):
+            ev = b.event(e)
+            ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                           wl["k_max"], wl["cut"], feat_scale=fs)
+            g = tr.get_graph(e)
+            O = {(int(s), int(t)): int(k) for s, t, k in zip(ref.src, ref.dst, ref.keep)}
+            G = {(int(s), int(t)): int(k) for s, t, k in zip(g["src"], g["dst"], g["kept"])}
+            for key in set(O) | set(G):
+                agree += O.get(key, 0) == G.get(key, 0)
+                union += 1
+        assert agree / union >= 0.999, agree / union
+    lab_ref, _ = oracle.find_tracks_batch(model, b.x, b.y, b.z, b.plane, b.offsets, wl["radius2"],
+                                          wl["k_max"], wl["cut"], feat_scale=fs)
+    g = metrics.batch_counts(labels, b.pid, b.offsets).summary()
+    o = metrics.batch_counts(lab_ref, b.pid, b.offsets).summary()
+    assert o["efficiency"] >= 0.95
+    for k in ("efficiency", "ghost_rate", "clone_rate"):
+        assert abs(g[k] - o[k]) <= 0.003, (k, g, o)
