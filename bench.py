@@ -150,6 +150,10 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
             # 2 h^2 flop per edge against 3 rows of 4h bytes: memory-bound;
             # read the two projection halves P[src], P[dst], write e, indices
             return "hbm", E * (3 * h * 4 + 8), "byte"
+        if precision == "bf16":
+            # read the FP32 encodings h_src, h_dst (split into hi + lo BF16
+            # operands on chip); write e (BF16); indices
+            return "hbm", E * (2 * h * 4 + h * sb + 8), "byte"
         # read h_src, h_dst rows; write e; indices
         return "hbm", E * (3 * h * sb + 8), "byte"
     if stage == "node_prep":

@@ -79,14 +79,22 @@ template <int H, bool FP8, int MODE>
 struct Layout {
   static constexpr int ESZ = FP8 ? 1 : 2;
   static constexpr int NSEG = n_seg(MODE);
-  static constexpr int K1 = (MODE == M_NODE_ENC) ? H : NSEG * H;
+  // BF16 encoders carry the node encoding at about 16 significant bits: an
+  // operand x enters the MMA as hi = bf16(x) and lo = bf16(x - hi) over a K
+  // twice as long, against the weight image repeated along K (node encoder
+  // layer 2: its hidden row; edge encoder layer 1: the FP32 rows h_src, h_dst).
+  // The encoders see hit coordinates, whose useful precision (a 12 um
+  // resolution over a 45 mm radius) is finer than BF16's 8-bit mantissa.
+  static constexpr bool SPLIT = !FP8 && (MODE == M_NODE_ENC || MODE == M_EDGE_ENC);
+  static constexpr int K1 = (MODE == M_NODE_ENC) ? H : (SPLIT ? 2 : 1) * NSEG * H;
+  static constexpr int K2 = (SPLIT && MODE == M_NODE_ENC) ? 2 * H : H;
   static constexpr bool HAS_W1 = MODE != M_NODE_ENC;
   static constexpr bool HAS_W2 = MODE != M_CLS;
   static constexpr bool HAS_WC = MODE == M_EDGE_UPD_CLS;
   static constexpr int W1 = 0;
   static constexpr int W1_BYTES = HAS_W1 ? H * K1 * ESZ : 0;
   static constexpr int W2 = align1k(W1 + W1_BYTES);
-  static constexpr int W2_BYTES = HAS_W2 ? H * H * ESZ : 0;
+  static constexpr int W2_BYTES = HAS_W2 ? H * K2 * ESZ : 0;
   static constexpr int WC = align1k(W2 + W2_BYTES);
   static constexpr int WC_BYTES = HAS_WC ? H * H * ESZ : 0;
   // BF16 node-step tiles ([h, m_out, m_in], contiguous rows) are gathered by
@@ -103,7 +111,7 @@ struct Layout {
   // hidden / classifier input: its own tile with two input buffers, else it
   // overwrites the layer-1 input once the layer-1 MMAs are done
   static constexpr int HA = NBUF == 2 || MODE == M_NODE_ENC ? align1k(A + NBUF * A_BYTES) : A;
-  static constexpr int HA_BYTES = NBUF == 2 || MODE == M_NODE_ENC ? kRows * H * ESZ : 0;
+  static constexpr int HA_BYTES = NBUF == 2 || MODE == M_NODE_ENC ? kRows * K2 * ESZ : 0;
   static constexpr int PAR = align1k(HA_BYTES > 0 ? HA + HA_BYTES : A + NBUF * A_BYTES);
   // fp32 parameters: b1, b2, bc1, s1, s2, sc, c2 weights, ne1 (3 x H + H)
   static constexpr int PAR_FLOATS = 7 * H + 4 * H + 8;
@@ -198,6 +206,37 @@ __device__ __forceinline__ float put_row_bf16(uint8_t* tile, int row, int kchunk
       *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 4) + c, kchunks)) = u;
     }
     return scale;
+  }
+}
+
+// Write n FP32 values (a multiple of 8) into a BF16 tile as two parts, hi =
+// bf16(v) at element k_hi and lo = bf16(v - hi) at element k_lo.
+__device__ __forceinline__ void put_row_split(uint8_t* tile, int row, int kchunks, int k_hi,
+                                              int k_lo, const float* v, int n) {
+  for (int c = 0; c < n / 8; ++c) {
+    const float* q = v + 8 * c;
+    float r[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = q[j] - __bfloat162float(__float2bfloat16_rn(q[j]));
+    *reinterpret_cast<uint4*>(tile + tile_off(row, (k_hi >> 3) + c, kchunks)) =
+        make_uint4(pack_bf16(q[0], q[1]), pack_bf16(q[2], q[3]), pack_bf16(q[4], q[5]),
+                   pack_bf16(q[6], q[7]));
+    *reinterpret_cast<uint4*>(tile + tile_off(row, (k_lo >> 3) + c, kchunks)) =
+        make_uint4(pack_bf16(r[0], r[1]), pack_bf16(r[2], r[3]), pack_bf16(r[4], r[5]),
+                   pack_bf16(r[6], r[7]));
+  }
+}
+
+// One FP32 row of H values from global memory into a BF16 tile, split as above.
+template <int H>
+__device__ __forceinline__ void put_row_f32_split(uint8_t* tile, int row, int kchunks, int k_hi,
+                                                  int k_lo, const float* src) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int c = 0; c < H / 8; ++c) {
+    const float4 a = s4[2 * c], b = s4[2 * c + 1];
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    put_row_split(tile, row, kchunks, k_hi + 8 * c, k_lo + 8 * c, v, 8);
   }
 }
 
@@ -400,6 +439,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   constexpr int K1 = L::K1;
   constexpr int KCH1 = K1 * L::ESZ / 16;  // 16-byte chunks per A row, layer 1
   constexpr int KCHH = H * L::ESZ / 16;   // 16-byte chunks per A row, K = H
+  constexpr int KCH2 = L::K2 * L::ESZ / 16;  // 16-byte chunks per A row, layer 2
 
   // wait for the MMAs committed so far; false on timeout (uniform across CTA)
   auto wait_mma = [&]() -> bool {
@@ -474,11 +514,14 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           amax = fmaxf(amax, hid[i]);
         }
         sa[0] = FP8 ? (amax > 0.f ? amax / 448.f : 1.f) : 1.f;
-        put_row_f32<FP8>(sHA, tid, KCHH, 0, hid, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
+        if constexpr (L::SPLIT)
+          put_row_split(sHA, tid, KCH2, 0, H, hid, H);
+        else
+          put_row_f32<FP8>(sHA, tid, KCHH, 0, hid, H, FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f);
       } else {
 #pragma unroll
         for (int i = 0; i < H; ++i) hid[i] = 0.f;
-        put_row_f32<FP8>(sHA, tid, KCHH, 0, hid, H, 1.f);
+        for (int k = 0; k < L::K2; k += H) put_row_f32<FP8>(sHA, tid, KCH2, k, hid, H, 1.f);
       }
     } else if constexpr (MODE == M_NODE_UPD) {
       if (valid) {
@@ -520,7 +563,11 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
                                        (H <= 64 && MODE != M_CLS) ? keep_row : nullptr);
           seg = 1;
         }
-        if constexpr (MODE != M_CLS) {
+        if constexpr (L::SPLIT) {
+          // [hi(h_src), hi(h_dst), lo(h_src), lo(h_dst)] from the FP32 encodings
+          put_row_f32_split<H>(sA, tid, KCH1, 0, 2 * H, w.hstate + size_t(w.src[r]) * H);
+          put_row_f32_split<H>(sA, tid, KCH1, H, 3 * H, w.hstate + size_t(w.col[r]) * H);
+        } else if constexpr (MODE != M_CLS) {
           sa[seg] = put_row_bf16<H, FP8>(sA, tid, KCH1, seg * H, w.hstate16 + size_t(w.src[r]) * H,
                                          nullptr);
           sa[seg + 1] = put_row_bf16<H, FP8>(sA, tid, KCH1, (seg + 1) * H,
@@ -650,7 +697,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
     // ---- 4. layer 2 ----------------------------------------------------------
     if (tid == 0) {
       tc_fence_after();
-      issue_layer<H, FP8>(tmem_base, sHA, sW2, H, 1);
+      issue_layer<H, FP8>(tmem_base, sHA, sW2, L::K2, 1);
       mma_commit(&bar[1]);
     }
     if (!wait_mma()) {
@@ -700,6 +747,12 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         zval(c, z);
         if (valid) {
           resid(c, z);
+          if constexpr (L::SPLIT && MODE == M_NODE_ENC) {
+            // the FP32 encoding, read by the edge encoder
+            float4* f4 = reinterpret_cast<float4*>(w.hstate + size_t(r) * H) + c * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) f4[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+          }
           uint4* d4 = reinterpret_cast<uint4*>(dst) + c * 4;
 #pragma unroll
           for (int q = 0; q < 4; ++q)
@@ -1097,14 +1150,17 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
               int precision, void** dmem, std::string& err) {
   const bool fp8 = precision == GNNTRK_FP8_E4M3;
   // which layers: node enc l2, edge enc l1/l2, per step node l1/l2 edge l1/l2, cls l1
+  // (BF16: the node encoder's layer 2 and the edge encoder's layer 1 take
+  // split operands, so their images repeat W along K)
   struct Item {
     int layer;
     LayerTC* dst;
+    bool repeat_k = false;
   };
   std::vector<Item> items;
   int c = n_embed;
-  items.push_back({c + 1, &m.node_enc.l2});
-  items.push_back({c + 2, &m.edge_enc.l1});
+  items.push_back({c + 1, &m.node_enc.l2, !fp8});
+  items.push_back({c + 2, &m.edge_enc.l1, !fp8});
   items.push_back({c + 3, &m.edge_enc.l2});
   c += 4;
   for (int k = 0; k < K; ++k) {
@@ -1120,7 +1176,7 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
     return GNNTRK_ERR_WEIGHTS;
   }
   // shared-memory budget of the largest kernel
-  for (int mode : {M_EDGE_UPD, M_NODE_UPD})
+  for (int mode : {M_EDGE_UPD, M_NODE_UPD, M_EDGE_ENC, M_NODE_ENC})
     if ((fp8 ? smem_total<true>(h, mode) : smem_total<false>(h, mode)) > kMaxSmem) {
       err = "tensor-core kernels do not fit shared memory at this hidden size";
       return GNNTRK_ERR_UNSUPPORTED;
@@ -1131,7 +1187,19 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   for (size_t i = 0; i < items.size(); ++i) {
     std::vector<uint8_t> img;
     std::vector<float> sc;
-    pack_layer(L[items[i].layer], fp8, img, sc);
+    if (items[i].repeat_k) {
+      const HostLayer& l = L[items[i].layer];
+      HostLayer r2;
+      r2.in = 2 * l.in;
+      r2.out = l.out;
+      r2.b = l.b;
+      r2.W.resize(size_t(r2.out) * r2.in);
+      for (int n = 0; n < l.out; ++n)
+        for (int k = 0; k < r2.in; ++k) r2.W[size_t(n) * r2.in + k] = l.W[size_t(n) * l.in + k % l.in];
+      pack_layer(r2, fp8, img, sc);
+    } else {
+      pack_layer(L[items[i].layer], fp8, img, sc);
+    }
     align(1024);
     off_img[i] = blob.size();
     blob.insert(blob.end(), img.begin(), img.end());
@@ -1161,7 +1229,8 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   for (size_t i = 0; i < items.size(); ++i) {
     const HostLayer& l = L[items[i].layer];
     *items[i].dst = LayerTC{base + off_img[i], reinterpret_cast<const float*>(base + off_b[i]),
-                            reinterpret_cast<const float*>(base + off_s[i]), l.in, l.out};
+                            reinterpret_cast<const float*>(base + off_s[i]),
+                            items[i].repeat_k ? 2 * l.in : l.in, l.out};
   }
   m.precision = precision;
   m.h = h;
