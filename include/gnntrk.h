@@ -101,6 +101,16 @@ typedef enum gnntrk_precision {
  *            graph needs more latches GNNTRK_ERR_CAPACITY (labels then invalid).
  *   use_graph: 1 = capture each call shape into a CUDA graph on first use and
  *            replay it afterwards; 0 = plain launches.
+ * Triplet stage (Secs. "Triplet Building" and "Track Building"; used by
+ * gnntrk_find_tracks_triplets):
+ *   triplets: 1 = the handle can build tracks from triplets; the weight blob
+ *            must then hold the two triplet classifiers. The last edge step
+ *            then stores the final edge encodings instead of fusing the
+ *            classifier.
+ *   triplet_cut: triplets whose classifier score is below it are removed.
+ *   triplets_per_hit: triplet workspace, per hit of max_hits, for each of
+ *            the two lists (articulations, elbows); a call that needs more
+ *            latches GNNTRK_ERR_CAPACITY.
  */
 typedef struct gnntrk_cfg {
   int32_t n_embed_layers;
@@ -118,7 +128,10 @@ typedef struct gnntrk_cfg {
   int32_t max_events;
   int32_t edges_per_hit;
   int32_t use_graph;
-  int32_t reserved[7];
+  int32_t triplets;
+  float triplet_cut;
+  int32_t triplets_per_hit;
+  int32_t reserved[4];
 } gnntrk_cfg;
 
 typedef struct gnntrk_handle gnntrk_handle;
@@ -126,7 +139,8 @@ typedef struct gnntrk_handle gnntrk_handle;
 /* Fill `cfg` with the defaults: embedding 3-64-64-4, hidden 32, 4 steps,
  * 26 planes, k_max 64, radius2 1, score cut 0.5, feature scales
  * (45, pi, 750, 45, 45, 750), FP32, no re-scoring, 1 << 20 hits, 4096 events,
- * 24 edges per hit, no CUDA graphs. */
+ * 24 edges per hit, no CUDA graphs, no triplet stage (triplet cut 0.5,
+ * 16 triplets per hit when enabled). */
 void gnntrk_default_cfg(gnntrk_cfg* cfg);
 
 /*
@@ -137,7 +151,10 @@ void gnntrk_default_cfg(gnntrk_cfg* cfg);
  *     W[fan_out][fan_in] followed by float32 b[fan_out]. Layer order:
  *     embedding layers; node encoder (3->h, h->h); edge encoder (2h->h, h->h);
  *     per step k: node network (3h->h, h->h), edge network (3h->h, h->h);
- *     classifier (h->h, h->1). The blob is copied; the caller keeps ownership.
+ *     classifier (h->h, h->1); optionally the triplet classifiers,
+ *     articulation (2h->h, h->1) then elbow (2h->h, h->1), each
+ *     Linear -> LayerNorm -> ReLU -> Linear on [e_first, e_second]. The blob
+ *     is copied; the caller keeps ownership.
  *   cfg: host; copied.
  *   out: host; receives the handle.
  * The library allocates its device weights and workspace here and keeps them
@@ -169,6 +186,71 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
 gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
                                  const float* hits_xyz, const uint8_t* plane,
                                  const int64_t* offsets, int32_t* out_labels, void* stream);
+
+/*
+ * Find tracks with the triplet stage (Secs. "Triplet Building" and "Track
+ * Building"): the whole gnntrk_find_tracks path (its labels are written too),
+ * then
+ *   1. triplets of the purified graph, pairs of kept edges sharing one hit C:
+ *      articulations (A->C, C->B), left elbows (C->A, C->B), right elbows
+ *      (A->C, B->C); an elbow's two edges are ordered by the (plane, input
+ *      index) of their far hit;
+ *   2. the articulation classifier (articulations) or the elbow classifier
+ *      (elbows) on [e^K(first edge), e^K(second edge)] in FP32 (the final edge
+ *      encodings are FP32 or, on the tensor-core paths, BF16); a triplet is
+ *      kept iff its logit >= log(c / (1 - c)) for c = cfg.triplet_cut;
+ *   3. track building: kept elbows join their two edges into one group; kept
+ *      articulations link groups; a link g1 -> g2 is shared when g1 links to
+ *      two different groups or g2 is linked from two different groups;
+ *      components of the groups over the links that are not shared; tracks
+ *      are every component touching no shared link and, for every distinct
+ *      pair of components (X, Y) joined by a shared link, X + Y (the shared
+ *      part is duplicated into each branch); a track's hits are the endpoints
+ *      of its edges, so tracks may share hits.
+ * Outputs (device):
+ *   out_event_tracks: int32 [n_events + 1]; event e's tracks are
+ *            [out_event_tracks[e], out_event_tracks[e+1]).
+ *   out_track_off: int64 [max_tracks + 1]; track t's hits are
+ *            out_track_hits[out_track_off[t] .. out_track_off[t+1]).
+ *   out_track_hits: int32 [max_track_hits]; event-local input indices, in
+ *            (plane, index) order within a track. An event's tracks: its
+ *            plain components first, then its component pairs.
+ * If the tracks or their hits exceed max_tracks / max_track_hits, or the
+ * triplets exceed the workspace, CAPACITY is latched (see
+ * gnntrk_sync_status); gnntrk_triplet_stats then gives the sizes needed.
+ * Errors: INVALID_ARG (handle without cfg.triplets, NULL or misaligned
+ * outputs, the gnntrk_find_tracks argument checks), CUDA.
+ */
+gnntrk_status gnntrk_find_tracks_triplets(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                                          const float* hits_xyz, const uint8_t* plane,
+                                          const int64_t* offsets, int32_t* out_labels,
+                                          int32_t* out_event_tracks, int64_t* out_track_off,
+                                          int32_t* out_track_hits, int64_t max_tracks,
+                                          int64_t max_track_hits, void* stream);
+
+/*
+ * Triplet-stage counts of the last call (synchronises the device).
+ *   out: host int64 [6]: [0] articulations, [1] elbows, [2] triplets kept,
+ *        [3] tracks, [4] track hits (sum of track lengths), [5] triplet
+ *        workspace per list. Zero when the last call had no triplet stage.
+ */
+gnntrk_status gnntrk_triplet_stats(gnntrk_handle* h, int64_t* out);
+
+/*
+ * Copy the triplets of one event of the last gnntrk_find_tracks_triplets
+ * call to host memory (for checks; synchronises the device). Articulations
+ * first, then elbows.
+ *   type:  host int32 [capacity]: 0 articulation, 1 left elbow, 2 right elbow.
+ *   hits3: host int32 [capacity][3]: (A, C, B) event-local input indices, C
+ *          the shared hit, A the far hit of the first edge, B of the second.
+ *   logit: host float32 [capacity]; kept: host uint8 [capacity].
+ *   n_triplets: host; receives the event's triplet count.
+ * Any of type..kept may be NULL. If capacity < *n_triplets nothing is
+ * written and CAPACITY is returned.
+ */
+gnntrk_status gnntrk_get_triplets(gnntrk_handle* h, int32_t event, int64_t capacity,
+                                  int32_t* type, int32_t* hits3, float* logit, uint8_t* kept,
+                                  int64_t* n_triplets);
 
 /*
  * Wait for `stream`, then return and clear the status latched by device-side

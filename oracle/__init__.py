@@ -63,6 +63,14 @@ def lib():
                                             vp, vp, i32]
         L.orc_candidate_d2.restype = i64
         L.orc_candidate_d2.argtypes = [i64, vp, vp, i32, i32, vp, i64]
+        L.orc_edge_states.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, vp, vp]
+        L.orc_triplets.restype = i64
+        L.orc_triplets.argtypes = [i64, vp, i64, vp, vp, vp, vp, vp, vp, i64]
+        L.orc_triplet_logits.restype = i32
+        L.orc_triplet_logits.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.orc_build_tracks.restype = i64
+        L.orc_build_tracks.argtypes = [i64, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp,
+                                       i64, vp]
         _lib = L
     return _lib
 
@@ -189,3 +197,78 @@ def candidate_d2(plane, emb, n_planes: int = 26) -> np.ndarray:
     out = np.zeros(c, np.float64)
     lib().orc_candidate_d2(n, _p(plane), _p(emb), D, n_planes, _p(out), c)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Triplet stage (Secs. "Triplet Building" and "Track Building")
+# ---------------------------------------------------------------------------
+TRIPLET_TYPES = ("articulation", "left_elbow", "right_elbow")
+
+
+def edge_states(model: Model, x, y, z, src, dst, feat_scale=DEFAULT_FEAT_SCALE) -> np.ndarray:
+    """Final edge encodings e^K [ne][h] (FP64)."""
+    x, y, z = _c(x, np.float32), _c(y, np.float32), _c(z, np.float32)
+    src, dst = _c(src, np.int32), _c(dst, np.int32)
+    out = np.zeros((src.size, model.hidden), np.float64)
+    fs = _c(feat_scale, np.float64)
+    lib().orc_edge_states(model.ptr, x.size, _p(x), _p(y), _p(z), _p(fs), src.size, _p(src),
+                          _p(dst), _p(out))
+    return out
+
+
+def triplets(plane, src, dst, keep):
+    """(type, e1, e2) of every triplet of the purified graph (kept edges)."""
+    plane, src, dst = _c(plane, np.uint8), _c(src, np.int32), _c(dst, np.int32)
+    keep = _c(keep, np.uint8)
+    n = lib().orc_triplets(plane.size, _p(plane), src.size, _p(src), _p(dst), _p(keep),
+                           None, None, None, 0)
+    ty, a, b = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
+    lib().orc_triplets(plane.size, _p(plane), src.size, _p(src), _p(dst), _p(keep),
+                       _p(ty), _p(a), _p(b), n)
+    return ty, a, b
+
+
+def triplet_logits(model: Model, ty, e1, e2, e_final) -> np.ndarray:
+    ty, e1, e2 = _c(ty, np.int32), _c(e1, np.int32), _c(e2, np.int32)
+    E = _c(e_final, np.float64)
+    out = np.zeros(ty.size, np.float64)
+    if lib().orc_triplet_logits(model.ptr, ty.size, _p(ty), _p(e1), _p(e2), _p(E), _p(out)) != 0:
+        raise ValueError("oracle: the model has no triplet classifiers")
+    return out
+
+
+def build_tracks(n_hits: int, src, dst, keep, ty, e1, e2, tkeep):
+    """Tracks (list of ascending hit-index arrays, lexicographic order)."""
+    src, dst, keep = _c(src, np.int32), _c(dst, np.int32), _c(keep, np.uint8)
+    ty, e1, e2, tk = _c(ty, np.int32), _c(e1, np.int32), _c(e2, np.int32), _c(tkeep, np.uint8)
+    th = np.zeros(1, np.int64)
+    args = lambda off, co, hits, ch: (n_hits, src.size, _p(src), _p(dst), _p(keep), ty.size,
+                                      _p(ty), _p(e1), _p(e2), _p(tk), _p(off), co, _p(hits), ch,
+                                      _p(th))
+    nk = lib().orc_build_tracks(*args(None, 0, None, 0))
+    off = np.zeros(nk + 1, np.int32)
+    hits = np.zeros(int(th[0]), np.int32)
+    lib().orc_build_tracks(*args(off, nk, hits, hits.size))
+    return [hits[off[k]:off[k + 1]].copy() for k in range(nk)]
+
+
+class TripletResult(EventResult):
+    def __init__(self, base: EventResult, ty, e1, e2, tlogit, tkeep, tracks):
+        super().__init__(base.labels, base.src, base.dst, base.d2, base.logit, base.keep)
+        self.ttype, self.te1, self.te2 = ty, e1, e2
+        self.tlogit, self.tkeep, self.tracks = tlogit, tkeep, tracks
+
+
+def find_tracks_triplets_event(model: Model, x, y, z, plane, r2: float, k_max: int,
+                               cut: float = 0.5, triplet_cut: float = 0.5, n_planes: int = 26,
+                               feat_scale=DEFAULT_FEAT_SCALE) -> TripletResult:
+    """The whole path with the triplet stage for one event: graph, edge scores
+    and cut, triplets of the kept edges scored by the triplet classifiers and
+    cut at `triplet_cut`, then track building."""
+    base = find_tracks_event(model, x, y, z, plane, r2, k_max, cut, n_planes, feat_scale)
+    E = edge_states(model, x, y, z, base.src, base.dst, feat_scale)
+    ty, e1, e2 = triplets(plane, base.src, base.dst, base.keep)
+    tl = triplet_logits(model, ty, e1, e2, E)
+    tk = (tl >= cut_logit(triplet_cut)).astype(np.uint8)
+    tracks = build_tracks(len(x), base.src, base.dst, base.keep, ty, e1, e2, tk)
+    return TripletResult(base, ty, e1, e2, tl, tk, tracks)

@@ -5,8 +5,9 @@ TEST INFRASTRUCTURE (part of the oracle package).
 
 Definitions followed here:
   * a particle is reconstructible when it left at least 3 hits;
-  * a track candidate is a component of the purified graph with at least
-    `min_len` hits (3 by default);
+  * a track candidate is a component of the purified graph (or a track of the
+    triplet track building) with at least `min_len` hits (3 by default);
+  * a hit two particles share counts as a hit of both;
   * a track is matched to the particle that contributed most of its hits when
     that particle contributed at least 70 % of them (noise hits count against
     the match); otherwise the track is a ghost (fake);
@@ -56,28 +57,35 @@ class Counts:
         }
 
 
-def event_counts(labels, pid, min_len: int = 3, match_frac: float = 0.7) -> Counts:
-    """Metrics counts of one event from per-hit component labels and particle ids.
+def track_counts(tracks, pid, pid2=None, min_len: int = 3, match_frac: float = 0.7) -> Counts:
+    """Metrics counts of one event from its track candidates.
 
-    labels: any per-hit component identifier; pid: particle id per hit, -1 for
-    noise.
+    tracks: iterable of hit-index lists (a hit may belong to several tracks);
+    pid: particle id per hit, -1 for noise; pid2: the second particle of a hit
+    two particles share (-1 otherwise) or None. A shared hit counts as a hit of
+    both particles, for their hit totals and for the match votes.
     """
-    labels = [int(v) for v in labels]
     pid = [int(v) for v in pid]
-    particle_hits = Counter(p for p in pid if p >= 0)
+    p2 = [-1] * len(pid) if pid2 is None else [int(v) for v in pid2]
+    particle_hits: Counter = Counter()
+    for a, b in zip(pid, p2):
+        if a >= 0:
+            particle_hits[a] += 1
+        if b >= 0:
+            particle_hits[b] += 1
     reconstructible = {p for p, n in particle_hits.items() if n >= 3}
-
-    members: dict[int, list[int]] = {}
-    for i, lab in enumerate(labels):
-        members.setdefault(lab, []).append(i)
 
     c = Counts(reconstructible=len(reconstructible))
     matched_count: Counter = Counter()
-    for hits in members.values():
+    for hits in tracks:
         if len(hits) < min_len:
             continue
         c.tracks += 1
-        votes = Counter(pid[i] for i in hits)
+        votes: Counter = Counter()
+        for i in hits:
+            votes[pid[i]] += 1
+            if p2[i] >= 0:
+                votes[p2[i]] += 1
         # the best real particle; noise (-1) never matches
         real = [(n, p) for p, n in votes.items() if p >= 0]
         if not real:
@@ -96,9 +104,32 @@ def event_counts(labels, pid, min_len: int = 3, match_frac: float = 0.7) -> Coun
     return c
 
 
-def batch_counts(labels, pid, offsets, min_len: int = 3) -> Counts:
+def event_counts(labels, pid, min_len: int = 3, match_frac: float = 0.7, pid2=None) -> Counts:
+    """Metrics counts of one event from per-hit component labels and particle ids.
+
+    labels: any per-hit component identifier; pid: particle id per hit, -1 for
+    noise; each component is one track candidate.
+    """
+    members: dict[int, list[int]] = {}
+    for i, lab in enumerate(labels):
+        members.setdefault(int(lab), []).append(i)
+    return track_counts(members.values(), pid, pid2, min_len, match_frac)
+
+
+def batch_counts(labels, pid, offsets, min_len: int = 3, pid2=None) -> Counts:
     tot = Counts()
     for e in range(len(offsets) - 1):
         a, b = int(offsets[e]), int(offsets[e + 1])
-        tot += event_counts(labels[a:b], pid[a:b], min_len)
+        tot += event_counts(labels[a:b], pid[a:b], min_len,
+                            pid2=None if pid2 is None else pid2[a:b])
+    return tot
+
+
+def batch_track_counts(tracks_per_event, pid, offsets, min_len: int = 3, pid2=None) -> Counts:
+    """tracks_per_event[e]: event e's track candidates (event-local hit lists)."""
+    tot = Counts()
+    for e in range(len(offsets) - 1):
+        a, b = int(offsets[e]), int(offsets[e + 1])
+        tot += track_counts(tracks_per_event[e], pid[a:b],
+                            None if pid2 is None else pid2[a:b], min_len)
     return tot

@@ -64,6 +64,10 @@ struct Model {
   Layer node_enc1, node_enc2, edge_enc1, edge_enc2;
   std::vector<Layer> node1, node2, edge1, edge2;  // per message-passing step
   Layer cls1, cls2;
+  // triplet classifiers (optional): articulation and elbow, each
+  // Linear(2h, h) -> LayerNorm -> ReLU -> Linear(h, 1) on [e_first, e_second]
+  bool has_triplets = false;
+  Layer art1, art2, elb1, elb2;
   int D = 0, h = 0, K = 0;
 };
 
@@ -166,7 +170,7 @@ std::vector<Edge> rough_graph(int64_t n, const uint8_t* plane, const double* emb
 
 void in_logits(const Model& m, const Params& P, int64_t n, const float* x, const float* y,
                const float* z, int64_t ne, const int32_t* src, const int32_t* dst,
-               double* logit) {
+               double* logit, double* e_final = nullptr) {
   const int h = m.h;
   std::vector<double> H(size_t(n) * h), E(size_t(ne) * h);
   // node encoder on normalised Cartesian coordinates
@@ -215,6 +219,7 @@ void in_logits(const Model& m, const Params& P, int64_t n, const float* x, const
       for (int c = 0; c < h; ++c) E[size_t(e) * h + c] += delta[c];
     }
   }
+  if (e_final) std::copy(E.begin(), E.end(), e_final);
   // edge classifier: one output unit; the sigmoid is monotone, so the logit is
   // what the cut compares
   for (int64_t e = 0; e < ne; ++e) {
@@ -326,6 +331,13 @@ void* orc_model_load(const void* blob, size_t nbytes, int n_embed_layers, const 
   }
   want.push_back({h, h});
   want.push_back({h, 1});
+  // optional triplet classifiers: articulation then elbow
+  const bool trip = nl == want.size() + 4;
+  if (trip)
+    for (int t = 0; t < 2; ++t) {
+      want.push_back({2 * h, h});
+      want.push_back({h, 1});
+    }
   if (nl != want.size()) return fail("layer count does not match the architecture");
   if (nbytes < 16 + 8 * size_t(nl)) return fail("blob too short for its header");
   std::vector<Layer> L(nl);
@@ -366,6 +378,13 @@ void* orc_model_load(const void* blob, size_t nbytes, int n_embed_layers, const 
   }
   m->cls1 = L[c++];
   m->cls2 = L[c++];
+  if (trip) {
+    m->has_triplets = true;
+    m->art1 = L[c++];
+    m->art2 = L[c++];
+    m->elb1 = L[c++];
+    m->elb2 = L[c++];
+  }
   m->D = embed_dims[n_embed_layers];
   m->h = hidden;
   m->K = iters;
@@ -462,6 +481,193 @@ int64_t orc_find_tracks_batch(const void* mp, int n_planes, int k_max, double r2
   int64_t tot = 0;
   for (int64_t e : edges) tot += e;
   return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Triplet stage (Secs. "Triplet Building" and "Track Building")
+// ---------------------------------------------------------------------------
+
+// Final edge encodings e^K [ne][h] of the interaction network (the input of
+// the edge and triplet classifiers).
+int orc_edge_states(const void* mp, int64_t n, const float* x, const float* y, const float* z,
+                    const double* feat_scale, int64_t ne, const int32_t* src, const int32_t* dst,
+                    double* e_final) {
+  const Model& m = *static_cast<const Model*>(mp);
+  Params P = make_params(0, 0, 0.0, 0.0, feat_scale);
+  std::vector<double> logit(ne);
+  in_logits(m, P, n, x, y, z, ne, src, dst, logit.data(), e_final);
+  return 0;
+}
+
+// Triplets of the purified graph: pairs of kept edges sharing one hit C.
+//   type 0, articulation: A -> C and C -> B     (e1 = A->C, e2 = C->B)
+//   type 1, left elbow:   C -> A and C -> B     (e1 = C->A, e2 = C->B)
+//   type 2, right elbow:  A -> C and B -> C     (e1 = A->C, e2 = B->C)
+// An elbow's two edges are ordered by the (plane, index) of their far hit,
+// A before B. Triplets are listed by C ascending, then type, then the far
+// hits' keys. Returns the count; writes only when it fits `cap`.
+int64_t orc_triplets(int64_t n, const uint8_t* plane, int64_t ne, const int32_t* src,
+                     const int32_t* dst, const uint8_t* keep, int32_t* type, int32_t* e1,
+                     int32_t* e2, int64_t cap) {
+  std::vector<std::vector<int32_t>> in(n), out(n);
+  for (int64_t e = 0; e < ne; ++e) {
+    if (!keep[e]) continue;
+    out[src[e]].push_back(int32_t(e));
+    in[dst[e]].push_back(int32_t(e));
+  }
+  // far-hit key of an edge seen from C
+  auto key = [&](int32_t far) { return std::make_pair(int(plane[far]), far); };
+  auto by_dst = [&](int32_t a, int32_t b) { return key(dst[a]) < key(dst[b]); };
+  auto by_src = [&](int32_t a, int32_t b) { return key(src[a]) < key(src[b]); };
+  int64_t t = 0;
+  auto put = [&](int ty, int32_t a, int32_t b) {
+    if (t < cap) {
+      type[t] = ty;
+      e1[t] = a;
+      e2[t] = b;
+    }
+    ++t;
+  };
+  for (int64_t c = 0; c < n; ++c) {
+    std::vector<int32_t> I = in[c], O = out[c];
+    std::sort(I.begin(), I.end(), by_src);
+    std::sort(O.begin(), O.end(), by_dst);
+    for (int32_t a : I)
+      for (int32_t b : O) put(0, a, b);
+    for (size_t i = 0; i < O.size(); ++i)
+      for (size_t j = i + 1; j < O.size(); ++j) put(1, O[i], O[j]);
+    for (size_t i = 0; i < I.size(); ++i)
+      for (size_t j = i + 1; j < I.size(); ++j) put(2, I[i], I[j]);
+  }
+  return t;
+}
+
+// Triplet logits: the articulation classifier for type 0, the elbow
+// classifier for types 1 and 2, on [e^K(e1), e^K(e2)].
+int orc_triplet_logits(const void* mp, int64_t nt, const int32_t* type, const int32_t* e1,
+                       const int32_t* e2, const double* e_final, double* logit) {
+  const Model& m = *static_cast<const Model*>(mp);
+  if (!m.has_triplets) return -1;
+  const int h = m.h;
+  std::vector<double> cat(2 * h);
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int c = 0; c < h; ++c) {
+      cat[c] = e_final[size_t(e1[t]) * h + c];
+      cat[h + c] = e_final[size_t(e2[t]) * h + c];
+    }
+    const bool art = type[t] == 0;
+    mlp2(art ? m.art1 : m.elb1, art ? m.art2 : m.elb2, cat.data(), &logit[t]);
+  }
+  return 0;
+}
+
+namespace {
+struct Dsu {
+  std::vector<int64_t> p;
+  explicit Dsu(int64_t n) : p(n) {
+    for (int64_t i = 0; i < n; ++i) p[i] = i;
+  }
+  int64_t find(int64_t a) {
+    while (p[a] != a) a = p[a] = p[p[a]];
+    return a;
+  }
+  void unite(int64_t a, int64_t b) {
+    a = find(a);
+    b = find(b);
+    if (a != b) p[std::max(a, b)] = std::min(a, b);
+  }
+};
+}  // namespace
+
+// Track building from the purified edge graph, in the thesis's four steps:
+//  1. kept elbows join their two edges into one group (the two edges are the
+//     same track segment; the second one is the duplicate);
+//  2. kept articulations link groups, once per ordered group pair; a link
+//     g1 -> g2 is shared when g1 links onwards to more than one group or g2
+//     is reached from more than one group; weakly connected components of the
+//     groups over the links that are not shared;
+//  3. every component touching no shared link is a track; every distinct pair
+//     of components (X, Y) joined by a shared link X -> Y is a track X + Y
+//     (the shared component is duplicated into each branch);
+//  4. a track's hits are the endpoints of its edges.
+// Tracks are written with their hits ascending, in lexicographic order of
+// the hit lists. Returns the track count and sets *total_hits; writes only
+// when both fit (track_off[tracks + 1], track_hits[total_hits]).
+int64_t orc_build_tracks(int64_t n, int64_t ne, const int32_t* src, const int32_t* dst,
+                         const uint8_t* keep, int64_t nt, const int32_t* type, const int32_t* e1,
+                         const int32_t* e2, const uint8_t* tkeep, int32_t* track_off,
+                         int64_t cap_tracks, int32_t* track_hits, int64_t cap_hits,
+                         int64_t* total_hits) {
+  (void)n;
+  Dsu grp(ne);
+  for (int64_t t = 0; t < nt; ++t)
+    if (tkeep[t] && type[t] != 0) grp.unite(e1[t], e2[t]);
+  std::vector<std::pair<int64_t, int64_t>> links;
+  for (int64_t t = 0; t < nt; ++t)
+    if (tkeep[t] && type[t] == 0) {
+      const int64_t a = grp.find(e1[t]), b = grp.find(e2[t]);
+      if (a != b) links.push_back({a, b});
+    }
+  std::sort(links.begin(), links.end());
+  links.erase(std::unique(links.begin(), links.end()), links.end());
+  std::vector<int> n_out(ne, 0), n_in(ne, 0);
+  for (auto& l : links) {
+    ++n_out[l.first];
+    ++n_in[l.second];
+  }
+  Dsu comp(ne);
+  std::vector<std::pair<int64_t, int64_t>> shared;
+  for (auto& l : links) {
+    if (n_out[l.first] > 1 || n_in[l.second] > 1)
+      shared.push_back(l);
+    else
+      comp.unite(l.first, l.second);
+  }
+  // hits of every component of kept edges
+  std::vector<std::vector<int32_t>> hits(ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    if (!keep[e]) continue;
+    const int64_t c = comp.find(grp.find(e));
+    hits[c].push_back(src[e]);
+    hits[c].push_back(dst[e]);
+  }
+  std::vector<std::pair<int64_t, int64_t>> pairs;
+  std::vector<char> in_shared(ne, 0);
+  for (auto& l : shared) {
+    const int64_t a = comp.find(l.first), b = comp.find(l.second);
+    if (a == b) continue;
+    pairs.push_back({a, b});
+    in_shared[a] = in_shared[b] = 1;
+  }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  std::vector<std::vector<int32_t>> tracks;
+  auto uniq = [](std::vector<int32_t> v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    return v;
+  };
+  for (int64_t c = 0; c < ne; ++c)
+    if (!hits[c].empty() && !in_shared[c]) tracks.push_back(uniq(hits[c]));
+  for (auto& pr : pairs) {
+    std::vector<int32_t> v = hits[pr.first];
+    v.insert(v.end(), hits[pr.second].begin(), hits[pr.second].end());
+    tracks.push_back(uniq(v));
+  }
+  std::sort(tracks.begin(), tracks.end());
+  int64_t th = 0;
+  for (auto& t : tracks) th += int64_t(t.size());
+  *total_hits = th;
+  const int64_t nk = int64_t(tracks.size());
+  if (nk <= cap_tracks && th <= cap_hits) {
+    int64_t o = 0;
+    track_off[0] = 0;
+    for (int64_t k = 0; k < nk; ++k) {
+      for (int32_t v : tracks[k]) track_hits[o++] = v;
+      track_off[k + 1] = int32_t(o);
+    }
+  }
+  return nk;
 }
 
 // All candidate pairs (plane p to p+1 or p+2) with their squared distance, no

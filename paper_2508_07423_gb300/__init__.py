@@ -27,6 +27,7 @@ EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
            "gnntrk_autotune", "gnntrk_rescore_rows", "gnntrk_e4m3_encode", "gnntrk_e4m3_decode",
+           "gnntrk_find_tracks_triplets", "gnntrk_triplet_stats", "gnntrk_get_triplets",
            "gnntrk_last_error", "gnntrk_destroy"]
 
 NOALLOC_MAX_HITS = 1 << 20
@@ -67,7 +68,10 @@ class Cfg(ctypes.Structure):
         ("max_events", ctypes.c_int32),
         ("edges_per_hit", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("triplets", ctypes.c_int32),
+        ("triplet_cut", ctypes.c_float),
+        ("triplets_per_hit", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -114,6 +118,13 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_serve_run.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(Cfg),
                                    ctypes.POINTER(ServeCfg), i32, vp, vp, vp, vp, vp, vp, vp]
     L.gnntrk_serve_run.restype = st
+    L.gnntrk_find_tracks_triplets.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, i64, i64,
+                                              vp]
+    L.gnntrk_find_tracks_triplets.restype = st
+    L.gnntrk_triplet_stats.argtypes = [vp, vp]
+    L.gnntrk_triplet_stats.restype = st
+    L.gnntrk_get_triplets.argtypes = [vp, i32, i64, vp, vp, vp, vp, ctypes.POINTER(i64)]
+    L.gnntrk_get_triplets.restype = st
     L.gnntrk_last_error.argtypes = [vp]
     L.gnntrk_last_error.restype = ctypes.c_char_p
     L.gnntrk_destroy.argtypes = [vp]
@@ -131,7 +142,8 @@ def default_cfg() -> Cfg:
 def make_cfg(model: dict, radius2: float, k_max: int = 64, score_cut: float = 0.5,
              precision="fp32", rescore_band: float = 0.0, max_hits: int = 1 << 20,
              max_events: int = 4096, edges_per_hit: int = 24, use_graph: bool = False,
-             n_planes: int = 26, feat_scale=None) -> Cfg:
+             n_planes: int = 26, feat_scale=None, triplets: bool = False,
+             triplet_cut: float = 0.5, triplets_per_hit: int = 16) -> Cfg:
     """Build a cfg from a model description {"embed": [...], "hidden", "iters"}."""
     c = default_cfg()
     emb = list(model["embed"])
@@ -153,6 +165,9 @@ def make_cfg(model: dict, radius2: float, k_max: int = 64, score_cut: float = 0.
     c.max_events = max_events
     c.edges_per_hit = edges_per_hit
     c.use_graph = int(bool(use_graph))
+    c.triplets = int(bool(triplets))
+    c.triplet_cut = triplet_cut
+    c.triplets_per_hit = triplets_per_hit
     return c
 
 
@@ -205,6 +220,43 @@ class Tracker:
         self._check(self._L.gnntrk_find_tracks(self._h, n_events, n_hits, _ptr(hits_xyz),
                                                _ptr(plane), _ptr(offsets), _ptr(out_labels),
                                                ctypes.c_void_p(s)))
+
+    def find_tracks_triplets(self, n_events: int, n_hits: int, hits_xyz, plane, offsets,
+                             out_labels, out_event_tracks, out_track_off, out_track_hits,
+                             stream=None):
+        """The hot path plus the triplet stage (handle created with
+        cfg.triplets). out_event_tracks: int32 [n_events + 1];
+        out_track_off: int64 [max_tracks + 1]; out_track_hits: int32
+        [max_track_hits] (CUDA tensors; capacities from their sizes)."""
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._check(self._L.gnntrk_find_tracks_triplets(
+            self._h, n_events, n_hits, _ptr(hits_xyz), _ptr(plane), _ptr(offsets),
+            _ptr(out_labels), _ptr(out_event_tracks), _ptr(out_track_off), _ptr(out_track_hits),
+            out_track_off.numel() - 1, out_track_hits.numel(), ctypes.c_void_p(s)))
+
+    def triplet_stats(self) -> dict:
+        out = np.zeros(6, np.int64)
+        self._check(self._L.gnntrk_triplet_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return {"articulations": int(out[0]), "elbows": int(out[1]), "kept": int(out[2]),
+                "tracks": int(out[3]), "track_hits": int(out[4]), "capacity": int(out[5])}
+
+    def get_triplets(self, event: int) -> dict:
+        """Triplets of one event of the last triplet call: 'type' (0 articulation,
+        1 left elbow, 2 right elbow), 'hits' [n, 3] = (A, C, B), 'logit', 'kept'."""
+        n = ctypes.c_int64(0)
+        st = self._L.gnntrk_get_triplets(self._h, event, 0, None, None, None, None,
+                                         ctypes.byref(n))
+        if st not in (0, 4):
+            self._check(st)
+        nt = n.value
+        ty = np.zeros(nt, np.int32)
+        h3 = np.zeros((nt, 3), np.int32)
+        lg = np.zeros(nt, np.float32)
+        kp = np.zeros(nt, np.uint8)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._L.gnntrk_get_triplets(self._h, event, nt, p(ty), p(h3), p(lg), p(kp),
+                                                ctypes.byref(n)))
+        return {"type": ty, "hits": h3, "logit": lg, "kept": kp}
 
     def sync_status(self, stream=None):
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
@@ -292,6 +344,28 @@ def run_batch(tracker: Tracker, batch, device="cuda", stream=None, check=True):
     return labels.cpu().numpy()
 
 
+def run_batch_triplets(tracker: Tracker, batch, device="cuda", stream=None, tracks_per_hit=2,
+                       hits_per_hit=8):
+    """As run_batch, with the triplet stage: returns (labels, tracks) where
+    tracks[e] is the list of event e's tracks (numpy arrays of event-local
+    input indices)."""
+    import torch
+    xyz = torch.from_numpy(batch.xyz_soa()).to(device)
+    plane = torch.from_numpy(batch.plane).to(device)
+    offs = torch.from_numpy(batch.offsets).to(device)
+    labels = torch.full((batch.n_hits,), -7, dtype=torch.int32, device=device)
+    ev_t = torch.zeros(batch.n_events + 1, dtype=torch.int32, device=device)
+    t_off = torch.zeros(tracks_per_hit * batch.n_hits + 2, dtype=torch.int64, device=device)
+    t_hits = torch.zeros(hits_per_hit * batch.n_hits + 16, dtype=torch.int32, device=device)
+    tracker.find_tracks_triplets(batch.n_events, batch.n_hits, xyz, plane, offs, labels, ev_t,
+                                 t_off, t_hits, stream)
+    tracker.sync_status(stream)
+    ev_t, t_off, t_hits = ev_t.cpu().numpy(), t_off.cpu().numpy(), t_hits.cpu().numpy()
+    tracks = [[t_hits[t_off[t]:t_off[t + 1]] for t in range(ev_t[e], ev_t[e + 1])]
+              for e in range(batch.n_events)]
+    return labels.cpu().numpy(), tracks
+
+
 def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
     """A Tracker for a workload of workloads.json (seeded random weights, or
     the trained blob the workload names)."""
@@ -299,6 +373,8 @@ def tracker_for_workload(wl: dict, precision=None, **kw) -> Tracker:
     prec = precision if precision is not None else wl.get("precision", "fp32")
     band = float(wl.get("rescore_band_score", 0.0)) if prec != "fp32" else 0.0
     args = dict(k_max=wl["k_max"], score_cut=wl["cut"], precision=prec, rescore_band=band)
+    if wl.get("triplets"):
+        args.update(triplets=True, triplet_cut=float(wl.get("triplet_cut", 0.5)))
     args.update(kw)
     cfg = make_cfg(wl["model"], wl["radius2"], **args)
     return Tracker(synth.workload_weights(wl), cfg)

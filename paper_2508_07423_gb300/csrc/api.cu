@@ -24,6 +24,10 @@ struct gnntrk_handle {
   float* d_wf32 = nullptr;
   LayerF32 embed[kMaxEmbedLayers]{};
   Mlp2F32 node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
+  TripletHeads trip{};   // triplet classifiers (blob with triplet layers)
+  bool has_trip = false;
+  TrackOut track_out{};  // outputs of the current triplet call
+  bool want_tracks = false;
   EdgeProj enc_proj{}, step_proj[kMaxIters]{};  // h_src / h_dst column blocks
   // tensor-core weights (BF16 / FP8 packed operands)
   TcModel tc{};
@@ -55,6 +59,8 @@ struct gnntrk_handle {
     int32_t n_events;
     int64_t n_hits;
     const void *xyz, *plane, *offsets, *labels;
+    const void *ev_tracks, *track_off, *track_hits;
+    int64_t max_tracks, max_track_hits;
     cudaGraphExec_t exec;
     int launches;
   };
@@ -102,6 +108,12 @@ bool parse_weights(const void* blob, size_t n, const gnntrk_cfg& c, std::vector<
   }
   want.push_back({h, h});
   want.push_back({h, 1});
+  // optional triplet classifiers (articulation, elbow): 2h -> h -> 1 each
+  if (nl == want.size() + 4)
+    for (int t = 0; t < 2; ++t) {
+      want.push_back({2 * h, h});
+      want.push_back({h, 1});
+    }
   if (nl != want.size()) return why = "weight blob: layer count does not match cfg", false;
   if (n < 16 + 8 * size_t(nl)) return why = "weight blob: truncated header", false;
   size_t need = 16 + 8 * size_t(nl);
@@ -180,6 +192,11 @@ gnntrk_status upload_f32(gnntrk_handle* h, const std::vector<HostLayer>& L) {
     c += 4;
   }
   h->cls = {lay(c), lay(c + 1)};
+  if (L.size() == c + 6) {
+    h->trip.art = {lay(c + 2), lay(c + 3)};
+    h->trip.elb = {lay(c + 4), lay(c + 5)};
+    h->has_trip = true;
+  }
   // projection views: rows [k0, k0 + h) of a transposed first layer
   const float* zero = h->d_wf32 + zofs;
   auto view = [&](const LayerF32& l1, int k0) {
@@ -234,8 +251,39 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
     add(&w.rs_counts, 6 * (kMaxIters + 2));
     add(&w.rs_blk, 2 * (kMaxIters + 2) * kRsMaxBlocks);
   }
+  const int64_t T = c.triplets ? H * c.triplets_per_hit : 0;
+  if (c.triplets) {
+    add(&w.trip_cnt_a, H);
+    add(&w.trip_cnt_e, H);
+    add(&w.trip_off_a, H + 1);
+    add(&w.trip_off_e, H + 1);
+    add(&w.trip_a1, T);
+    add(&w.trip_a2, T);
+    add(&w.trip_alogit, T);
+    add(&w.trip_akeep, T);
+    add(&w.trip_e1, T);
+    add(&w.trip_e2, T);
+    add(&w.trip_et, T);
+    add(&w.trip_elogit, T);
+    add(&w.trip_ekeep, T);
+    add(&w.tb_par, E);
+    add(&w.tb_par2, E);
+    add(&w.tb_out, E);
+    add(&w.tb_in, E);
+    add(&w.tb_flag, E);
+    add(&w.tb_cnt, E);
+    add(&w.tb_off, E);
+    add(&w.tb_cur, E);
+    add(&w.tb_hits, 2 * E);
+    add(&w.tb_pairs, T);
+    add(&w.tb_ev_tracks, c.max_events);
+    add(&w.tb_ev_hits, c.max_events);
+    add(&w.tb_ev_pairs, c.max_events);
+    add(&w.tb_ev_hit_off, int64_t(c.max_events) + 1);
+  }
   w.h_cap = H;
   w.e_cap = E;
+  w.t_cap = T;
   return v;
 }
 
@@ -344,10 +392,21 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     for (int k = 0; k < h->K; ++k) {
       stage(h, "node_update", s, 2,
             [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, all, s); });
-      stage(h, "edge_update", s, 1, [&] {
-        launch_edge_update_f32(b, w, h->edge[k], k + 1 == h->K ? &h->cls : nullptr, h->h,
-                               g.cut_logit, false, 0.f, 0.f, all, s);
-      });
+      const bool last = k + 1 == h->K;
+      if (last && c.triplets) {
+        // e^K stays in memory for the triplet classifiers: step, then classifier
+        stage(h, "edge_update", s, 2, [&] {
+          launch_edge_update_f32(b, w, h->edge[k], nullptr, h->h, g.cut_logit, false, 0.f, 0.f,
+                                 all, s);
+          launch_edge_update_f32(b, w, Mlp2F32{}, &h->cls, h->h, g.cut_logit, false, 0.f, 0.f,
+                                 all, s);
+        });
+      } else {
+        stage(h, "edge_update", s, 1, [&] {
+          launch_edge_update_f32(b, w, h->edge[k], last ? &h->cls : nullptr, h->h, g.cut_logit,
+                                 false, 0.f, 0.f, all, s);
+        });
+      }
     }
     if (h->K == 0)  // no message passing: the classifier reads the edge encodings
       stage(h, "edge_update", s, 1, [&] {
@@ -355,14 +414,14 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
                                all, s);
       });
   } else {
-    const bool fused = tc_cls_fused(h->h, c.precision);
+    const bool fused = tc_cls_fused(h->h, c.precision) && !c.triplets;
     stage(h, "edge_encoder", s, 1,
           [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
     for (int k = 0; k < h->K; ++k) {
       stage(h, "node_update", s, 2,
             [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
       stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
-            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k); });
+            [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k, c.triplets != 0); });
     }
     if (h->K == 0)
       stage(h, "edge_update", s, 1, [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1); });
@@ -408,6 +467,14 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     }
   }
   stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });
+  if (h->want_tracks) {
+    const float tcut = float(std::log(double(c.triplet_cut) / (1.0 - double(c.triplet_cut))));
+    stage(h, "triplets", s, 6, [&] { launch_triplets(b, w, h->h, s); });
+    stage(h, "triplet_scores", s, 3, [&] {
+      launch_triplet_scores(b, w, h->trip, h->h, c.precision != GNNTRK_FP32, tcut, s);
+    });
+    stage(h, "track_build", s, 6, [&] { launch_track_build(b, w, h->track_out, s); });
+  }
 }
 
 namespace gnntrk {
@@ -439,6 +506,9 @@ void gnntrk_default_cfg(gnntrk_cfg* c) {
   c->max_events = 4096;
   c->edges_per_hit = 24;
   c->use_graph = 0;
+  c->triplets = 0;
+  c->triplet_cut = 0.5f;
+  c->triplets_per_hit = 16;
 }
 
 gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnntrk_cfg* cfg,
@@ -478,6 +548,13 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
     return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "max_events must be 1..65535");
   if (c.edges_per_hit < 1 || int64_t(c.max_hits) * c.edges_per_hit >= (int64_t(1) << 31))
     return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "edge workspace must hold < 2^31 edges");
+  if (c.triplets != 0 && c.triplets != 1)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "triplets must be 0 or 1");
+  if (c.triplets && !(c.triplet_cut > 0.f && c.triplet_cut < 1.f))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "triplet_cut must be in (0, 1)");
+  if (c.triplets && (c.triplets_per_hit < 1 ||
+                     int64_t(c.max_hits) * c.triplets_per_hit >= (int64_t(1) << 31)))
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "triplet workspace must hold < 2^31 triplets");
 
   std::vector<HostLayer> L;
   std::string why;
@@ -492,7 +569,10 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
   h->h = c.hidden;
   h->K = c.iters;
   gnntrk_status st = upload_f32(h, L);
-  if (!st && c.precision != GNNTRK_FP32) st = (gnntrk_status)tc_upload(h->tc, L.data(), int(L.size()), h->n_embed,
+  const int n_gnn_layers = int(L.size()) - (h->has_trip ? 4 : 0);
+  if (!st && c.triplets && !h->has_trip)
+    st = fail(h, GNNTRK_ERR_WEIGHTS, "cfg.triplets needs a blob with the triplet classifiers");
+  if (!st && c.precision != GNNTRK_FP32) st = (gnntrk_status)tc_upload(h->tc, L.data(), n_gnn_layers, h->n_embed,
                                                        h->h, h->K, c.precision, &h->d_wtc, h->err);
   if (!st) st = alloc_workspace(h);
   if (st) {
@@ -511,11 +591,18 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
   return GNNTRK_OK;
 }
 
-gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
-                                 const float* hits_xyz, const uint8_t* plane,
-                                 const int64_t* offsets, int32_t* out_labels, void* stream) {
+}  // extern "C"
+
+namespace {
+// One call of the path; `tracks` (when not null) adds the triplet stage.
+gnntrk_status run_call(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                       const float* hits_xyz, const uint8_t* plane, const int64_t* offsets,
+                       int32_t* out_labels, const TrackOut* tracks, void* stream) {
   if (!h) return GNNTRK_ERR_INVALID_ARG;
   const gnntrk_cfg& c = h->cfg;
+  h->want_tracks = tracks != nullptr;
+  if (tracks) h->track_out = *tracks;
+  const TrackOut tk = tracks ? *tracks : TrackOut{};
   if (n_events < 1 || n_events > c.max_events)
     return fail(h, GNNTRK_ERR_INVALID_ARG, "n_events out of range");
   if (n_hits < 0 || n_hits > c.max_hits) return fail(h, GNNTRK_ERR_INVALID_ARG, "n_hits out of range");
@@ -544,7 +631,10 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
   if (c.use_graph && !h->profiling && s != nullptr) {
     for (auto& ge : h->graphs)
       if (ge.n_events == n_events && ge.n_hits == n_hits && ge.xyz == hits_xyz &&
-          ge.plane == plane && ge.offsets == offsets && ge.labels == out_labels) {
+          ge.plane == plane && ge.offsets == offsets && ge.labels == out_labels &&
+          ge.ev_tracks == tk.ev_tracks && ge.track_off == tk.track_off &&
+          ge.track_hits == tk.track_hits && ge.max_tracks == tk.max_tracks &&
+          ge.max_track_hits == tk.max_hits) {
         h->last_launches = ge.launches;
         cudaError_t e = cudaGraphLaunch(ge.exec, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
@@ -564,7 +654,8 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
       cudaGraphExecDestroy(h->graphs.front().exec);
       h->graphs.erase(h->graphs.begin());
     }
-    h->graphs.push_back({n_events, n_hits, hits_xyz, plane, offsets, out_labels, exec,
+    h->graphs.push_back({n_events, n_hits, hits_xyz, plane, offsets, out_labels, tk.ev_tracks,
+                         tk.track_off, tk.track_hits, tk.max_tracks, tk.max_hits, exec,
                          h->last_launches});
     e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
@@ -573,6 +664,141 @@ gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_h
   enqueue_pipeline(h, b, offsets, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+  return GNNTRK_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gnntrk_status gnntrk_find_tracks(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                                 const float* hits_xyz, const uint8_t* plane,
+                                 const int64_t* offsets, int32_t* out_labels, void* stream) {
+  return run_call(h, n_events, n_hits, hits_xyz, plane, offsets, out_labels, nullptr, stream);
+}
+
+gnntrk_status gnntrk_find_tracks_triplets(gnntrk_handle* h, int32_t n_events, int64_t n_hits,
+                                          const float* hits_xyz, const uint8_t* plane,
+                                          const int64_t* offsets, int32_t* out_labels,
+                                          int32_t* out_event_tracks, int64_t* out_track_off,
+                                          int32_t* out_track_hits, int64_t max_tracks,
+                                          int64_t max_track_hits, void* stream) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  if (!h->cfg.triplets)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "the handle was created without cfg.triplets");
+  if (!out_event_tracks || !out_track_off || (max_track_hits > 0 && !out_track_hits) ||
+      max_tracks < 0 || max_track_hits < 0)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "NULL or negative track output");
+  if ((reinterpret_cast<uintptr_t>(out_event_tracks) & 3) ||
+      (reinterpret_cast<uintptr_t>(out_track_off) & 7) ||
+      (reinterpret_cast<uintptr_t>(out_track_hits) & 3))
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "misaligned pointer");
+  const TrackOut t{out_event_tracks, out_track_off, out_track_hits, max_tracks, max_track_hits};
+  return run_call(h, n_events, n_hits, hits_xyz, plane, offsets, out_labels, &t, stream);
+}
+
+gnntrk_status gnntrk_triplet_stats(gnntrk_handle* h, int64_t* out) {
+  if (!h || !out) return GNNTRK_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  int32_t cnt[C_COUNT];
+  e = cudaMemcpy(cnt, h->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stats read");
+  const bool ran = h->want_tracks;
+  out[0] = ran ? cnt[C_TRIP_A] : 0;
+  out[1] = ran ? cnt[C_TRIP_E] : 0;
+  out[2] = ran ? cnt[C_TRIP_KEPT] : 0;
+  out[3] = ran ? cnt[C_TRACKS] : 0;
+  out[4] = ran ? cnt[C_TRACK_HITS] : 0;
+  out[5] = h->ws.t_cap;
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_get_triplets(gnntrk_handle* h, int32_t event, int64_t capacity,
+                                  int32_t* type, int32_t* hits3, float* logit, uint8_t* kept,
+                                  int64_t* n_triplets) {
+  if (!h || !n_triplets) return GNNTRK_ERR_INVALID_ARG;
+  if (!h->want_tracks) return fail(h, GNNTRK_ERR_INVALID_ARG, "the last call built no triplets");
+  if (event < 0 || event >= h->last_events) return fail(h, GNNTRK_ERR_INVALID_ARG, "event out of range");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  const Ws& w = h->ws;
+  int64_t off[2];
+  int32_t cnt[C_COUNT];
+  e = cudaMemcpy(off, w.ev_off + event, sizeof(off), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "triplet read");
+  if (cnt[C_STATUS] & (ST_INPUT | ST_CAPACITY))
+    return fail(h, GNNTRK_ERR_CAPACITY, "the last call failed; no triplets");
+  int32_t ra[2], re[2], rp[2];
+  e = cudaMemcpy(&ra[0], w.trip_off_a + off[0], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&ra[1], w.trip_off_a + off[1], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&re[0], w.trip_off_e + off[0], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&re[1], w.trip_off_e + off[1], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&rp[0], w.row_ptr + off[0], 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&rp[1], w.row_ptr + off[1], 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "triplet read");
+  const int64_t na = ra[1] - ra[0], nl = re[1] - re[0], nt = na + nl;
+  *n_triplets = nt;
+  if (capacity < nt) return fail(h, GNNTRK_ERR_CAPACITY, "capacity below the event's triplet count");
+  const int64_t nh = off[1] - off[0], ne = rp[1] - rp[0];
+  std::vector<int32_t> perm(nh), s(ne), d(ne), a1(na), a2(na), l1(nl), l2(nl);
+  std::vector<uint8_t> lt(nl);
+  std::vector<float> la(na), le(nl);
+  std::vector<uint8_t> ka(na), kl(nl);
+  auto rd = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+  };
+  rd(perm.data(), w.perm + off[0], 4 * nh);
+  rd(s.data(), w.src + rp[0], 4 * ne);
+  rd(d.data(), w.col + rp[0], 4 * ne);
+  rd(a1.data(), w.trip_a1 + ra[0], 4 * na);
+  rd(a2.data(), w.trip_a2 + ra[0], 4 * na);
+  rd(la.data(), w.trip_alogit + ra[0], 4 * na);
+  rd(ka.data(), w.trip_akeep + ra[0], na);
+  rd(l1.data(), w.trip_e1 + re[0], 4 * nl);
+  rd(l2.data(), w.trip_e2 + re[0], 4 * nl);
+  rd(lt.data(), w.trip_et + re[0], nl);
+  rd(le.data(), w.trip_elogit + re[0], 4 * nl);
+  rd(kl.data(), w.trip_ekeep + re[0], nl);
+  if (e != cudaSuccess) return cuda_fail(h, e, "triplet read");
+  auto loc = [&](int32_t pos) { return perm[pos - off[0]] - int32_t(off[0]); };
+  auto far_src = [&](int32_t edge) { return loc(s[edge - rp[0]]); };
+  auto far_dst = [&](int32_t edge) { return loc(d[edge - rp[0]]); };
+  for (int64_t t = 0; t < nt; ++t) {
+    int ty, A, C, B;
+    float lg;
+    uint8_t k;
+    if (t < na) {
+      ty = 0;
+      A = far_src(a1[t]);
+      C = far_dst(a1[t]);
+      B = far_dst(a2[t]);
+      lg = la[t];
+      k = ka[t];
+    } else {
+      const int64_t u = t - na;
+      ty = lt[u];
+      if (ty == 1) {
+        C = far_src(l1[u]);
+        A = far_dst(l1[u]);
+        B = far_dst(l2[u]);
+      } else {
+        C = far_dst(l1[u]);
+        A = far_src(l1[u]);
+        B = far_src(l2[u]);
+      }
+      lg = le[u];
+      k = kl[u];
+    }
+    if (type) type[t] = ty;
+    if (hits3) {
+      hits3[3 * t] = A;
+      hits3[3 * t + 1] = C;
+      hits3[3 * t + 2] = B;
+    }
+    if (logit) logit[t] = lg;
+    if (kept) kept[t] = k;
+  }
   return GNNTRK_OK;
 }
 
@@ -699,6 +925,14 @@ gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream) {
   if (st & ST_INPUT)
     return fail(h, GNNTRK_ERR_INVALID_ARG,
                 "input out of range (offsets not 0..n_hits non-decreasing, or plane >= n_planes)");
+  if ((st & ST_CAPACITY) && cnt[C_EDGES] <= h->ws.e_cap && h->want_tracks)
+    return fail(h, GNNTRK_ERR_CAPACITY,
+                "triplet stage: " + std::to_string(cnt[C_TRIP_A]) + " articulations and " +
+                    std::to_string(cnt[C_TRIP_E]) + " elbows (workspace " +
+                    std::to_string(h->ws.t_cap) + " each), " + std::to_string(cnt[C_TRACKS]) +
+                    " tracks with " + std::to_string(cnt[C_TRACK_HITS]) + " hits (outputs " +
+                    std::to_string(h->track_out.max_tracks) + ", " +
+                    std::to_string(h->track_out.max_hits) + ")");
   if (st & ST_CAPACITY)
     return fail(h, GNNTRK_ERR_CAPACITY,
                 "graph needs " + std::to_string(cnt[C_EDGES]) + " edges; workspace holds " +

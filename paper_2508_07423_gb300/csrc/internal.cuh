@@ -36,6 +36,11 @@ enum Counter : int {
   C_RERUN = 5,     // events holding a band edge
   C_RERUN_EDGES = 7,  // edges the FP32 re-score recomputes (receptive field)
   C_RERUN_HITS = 8,   // hits the FP32 re-score recomputes
+  C_TRIP_A = 9,       // articulations of the last call
+  C_TRIP_E = 10,      // elbows of the last call
+  C_TRACKS = 11,      // tracks built from triplets
+  C_TRACK_HITS = 12,  // hits over all those tracks
+  C_TRIP_KEPT = 13,   // triplets above the triplet cut
   C_COUNT = 16
 };
 
@@ -106,7 +111,35 @@ struct Ws {
   int32_t* rs_counts;   // [6][kMaxIters + 2]: [2] and [5] rows with level >= k (edges, hits)
   int32_t* rs_blk;      // [2][kMaxIters + 1][kRsMaxBlocks] per-block offsets of the lists
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
-  int64_t h_cap, e_cap;
+  // triplet stage (allocated when the handle builds tracks from triplets)
+  int32_t* trip_cnt_a;  // [H] articulations per hit
+  int32_t* trip_cnt_e;  // [H] elbows per hit
+  int32_t* trip_off_a;  // [H + 1]
+  int32_t* trip_off_e;  // [H + 1]
+  int32_t* trip_a1;     // [Tcap] articulation: edge A -> C
+  int32_t* trip_a2;     // [Tcap]               edge C -> B
+  float* trip_alogit;   // [Tcap]
+  uint8_t* trip_akeep;  // [Tcap]
+  int32_t* trip_e1;     // [Tcap] elbow: edge to / from the nearer far hit
+  int32_t* trip_e2;     // [Tcap]        the other edge
+  uint8_t* trip_et;     // [Tcap] 1 left elbow, 2 right elbow
+  float* trip_elogit;   // [Tcap]
+  uint8_t* trip_ekeep;  // [Tcap]
+  int32_t* tb_par;      // [Ecap] edge groups (union-find)
+  int32_t* tb_par2;     // [Ecap] components of groups (union-find)
+  int32_t* tb_out;      // [Ecap] first group linked onwards
+  int32_t* tb_in;       // [Ecap] first group linked from
+  int32_t* tb_flag;     // [Ecap] 1 several onwards, 2 several from, 4 in a shared pair
+  int32_t* tb_cnt;      // [Ecap] hits of a component
+  int32_t* tb_off;      // [Ecap] its hit list in tb_hits
+  int32_t* tb_cur;      // [Ecap] placement cursor
+  int32_t* tb_hits;     // [2 Ecap] component hit lists (sorted positions)
+  unsigned long long* tb_pairs;  // [Tcap] component pairs of shared links
+  int32_t* tb_ev_tracks;   // [max_events]
+  int32_t* tb_ev_hits;     // [max_events]
+  int32_t* tb_ev_pairs;    // [max_events]
+  int32_t* tb_ev_hit_off;  // [max_events + 1]
+  int64_t h_cap, e_cap, t_cap;
 };
 
 // The current call.
@@ -194,6 +227,24 @@ void f32_set_variant(int h, int family, int v);
 
 // connected components
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s);
+
+// triplet stage
+struct TripletHeads {
+  Mlp2F32 art, elb;  // articulation and elbow classifiers (2h -> h -> 1)
+};
+struct TrackOut {
+  int32_t* ev_tracks;   // [n_events + 1] tracks of event e: [ev_tracks[e], ev_tracks[e+1])
+  int64_t* track_off;   // [max_tracks + 1] hits of track t: [track_off[t], track_off[t+1])
+  int32_t* track_hits;  // [max_hits] event-local input indices
+  int64_t max_tracks, max_hits;
+};
+// triplet lists of the kept edges
+void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s);
+// triplet classifiers (FP32; the final edge encodings in FP32 or BF16)
+void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h, bool bf16,
+                           float cut_logit, cudaStream_t s);
+// track building into `out`
+void launch_track_build(const Batch& b, const Ws& w, const TrackOut& out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // device helpers

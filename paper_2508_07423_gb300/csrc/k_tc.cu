@@ -1266,14 +1266,15 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
 }
 
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
-            const LayerF32& cls2_f32, cudaStream_t s, int stage) {
+            const LayerF32& cls2_f32, cudaStream_t s, int stage, bool store_final) {
   const bool fp8 = m.precision == GNNTRK_FP8_E4M3;
   TcArgs a = base_args(b, w, g);
   a.c2 = cls2_f32;
   a.Wc = static_cast<const uint8_t*>(m.cls.l1.B);
   a.bc1 = m.cls.l1.b;
   a.sc = m.cls.l1.scale;
-  const bool fuse = (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
+  const bool fuse = !store_final &&
+                    (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
   auto set = [&](const Mlp2TC& mm) {
     a.W1 = static_cast<const uint8_t*>(mm.l1.B);
     a.b1 = mm.l1.b;

@@ -30,8 +30,10 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
 // writes w.logit and w.keep. stage < 0 runs everything; otherwise only
 // stage 0 (edge encoder), 1 + 2k (node step k) or 2 + 2k (edge step k, with
 // the classifier at the last step; stage 1 is the classifier when K = 0).
+// With store_final the last edge step stores e^K (BF16) and the classifier
+// runs as its own kernel (the triplet classifiers read e^K).
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
-            const LayerF32& cls2_f32, cudaStream_t s, int stage);
+            const LayerF32& cls2_f32, cudaStream_t s, int stage, bool store_final = false);
 
 // Autotuner hooks: resident CTAs per SM for a tensor-core kernel family
 // (0 node encoder, 1 edge encoder, 2 node step, 3 edge step + classifier) at a

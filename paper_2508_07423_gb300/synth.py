@@ -67,7 +67,9 @@ class Batch:
     """Events concatenated in structure-of-arrays form.
 
     x, y, z: float32 [n_hits]; plane: uint8 [n_hits]; pid: int32 [n_hits]
-    (-1 for noise); offsets: int64 [n_events + 1].
+    (-1 for noise); offsets: int64 [n_events + 1]; pid2: int32 [n_hits], the
+    second particle of a hit that two particles share (-1 otherwise), or None
+    when no hit is shared.
     """
     x: np.ndarray
     y: np.ndarray
@@ -75,6 +77,7 @@ class Batch:
     plane: np.ndarray
     pid: np.ndarray
     offsets: np.ndarray
+    pid2: np.ndarray | None = None
 
     @property
     def n_events(self) -> int:
@@ -87,7 +90,8 @@ class Batch:
     def event(self, e: int) -> "Batch":
         a, b = int(self.offsets[e]), int(self.offsets[e + 1])
         return Batch(self.x[a:b], self.y[a:b], self.z[a:b], self.plane[a:b],
-                     self.pid[a:b], np.array([0, b - a], dtype=np.int64))
+                     self.pid[a:b], np.array([0, b - a], dtype=np.int64),
+                     None if self.pid2 is None else self.pid2[a:b])
 
     def xyz_soa(self) -> np.ndarray:
         """float32 [3][n_hits]: the layout the library takes."""
@@ -104,12 +108,28 @@ def concat(parts) -> Batch:
     offs[1:] = np.cumsum(sizes)
     cat = lambda k, dt: (np.concatenate([getattr(p, k) for p in parts]).astype(dt)
                          if parts else np.zeros(0, dt))
+    pid2 = None
+    if any(p.pid2 is not None for p in parts):
+        pid2 = np.concatenate([p.pid2 if p.pid2 is not None else np.full(p.n_hits, -1)
+                               for p in parts]).astype(np.int32)
     return Batch(cat("x", np.float32), cat("y", np.float32), cat("z", np.float32),
-                 cat("plane", np.uint8), cat("pid", np.int32), offs)
+                 cat("plane", np.uint8), cat("pid", np.int32), offs, pid2)
 
 
-def gen_event(rng: np.random.Generator, n_tracks: int, noise_frac: float) -> Batch:
-    """One event of `n_tracks` straight tracks plus uniform noise hits."""
+def gen_event(rng: np.random.Generator, n_tracks: int, noise_frac: float,
+              pair_frac: float = 0.0) -> Batch:
+    """One event of `n_tracks` straight tracks plus uniform noise hits.
+
+    pair_frac > 0 adds round(pair_frac * n_tracks) close pairs standing in for
+    the electron-positron conversions of the thesis's triplet motivation: each
+    pair is a new track from the vertex of a randomly chosen track, its slopes
+    off by N(0, PAIR_OPENING) in x and y; where the two true positions on a
+    plane lie within PAIR_MERGE_MM they leave one shared hit (at their mean,
+    smeared; pid = the first track, pid2 = the partner). With pair_frac = 0
+    the draws are exactly those of the plain generator.
+    """
+    if pair_frac > 0.0:
+        return _gen_event_pairs(rng, n_tracks, noise_frac, pair_frac)
     vx = rng.normal(0.0, 0.05, n_tracks)
     vy = rng.normal(0.0, 0.05, n_tracks)
     vz = rng.normal(0.0, 50.0, n_tracks)
@@ -146,6 +166,71 @@ def gen_event(rng: np.random.Generator, n_tracks: int, noise_frac: float) -> Bat
                  np.array([0, x.size], dtype=np.int64))
 
 
+PAIR_OPENING = 4e-4      # rad, per slope component
+PAIR_MERGE_MM = 0.1      # two crossings closer than this make one hit
+
+
+def _gen_event_pairs(rng, n_tracks, noise_frac, pair_frac):
+    n_pairs = int(round(pair_frac * n_tracks))
+    vx = rng.normal(0.0, 0.05, n_tracks)
+    vy = rng.normal(0.0, 0.05, n_tracks)
+    vz = rng.normal(0.0, 50.0, n_tracks)
+    eta = rng.uniform(2.0, 5.0, n_tracks)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n_tracks)
+    theta = 2.0 * np.arctan(np.exp(-eta))
+    tx = np.tan(theta) * np.cos(phi)
+    ty = np.tan(theta) * np.sin(phi)
+    mother = rng.choice(n_tracks, n_pairs, replace=False) if n_pairs else np.zeros(0, np.int64)
+    ptx = tx[mother] + rng.normal(0.0, PAIR_OPENING, n_pairs)
+    pty = ty[mother] + rng.normal(0.0, PAIR_OPENING, n_pairs)
+    T = n_tracks + n_pairs
+    VX = np.concatenate([vx, vx[mother]])
+    VY = np.concatenate([vy, vy[mother]])
+    VZ = np.concatenate([vz, vz[mother]])
+    TX = np.concatenate([tx, ptx])
+    TY = np.concatenate([ty, pty])
+    dz = PLANE_Z[None, :] - VZ[:, None]
+    xs = VX[:, None] + TX[:, None] * dz
+    ys = VY[:, None] + TY[:, None] * dz
+    r = np.hypot(xs, ys)
+    eff = rng.uniform(0.0, 1.0, dz.shape) < HIT_EFF
+    hit = (dz > 0) & (r >= R_MIN) & (r <= R_MAX) & eff
+    # a partner crossing within the merge distance of its mother's crossing on
+    # the same plane (both detected) is absorbed into one shared hit
+    shared = np.zeros((T, N_PLANES), bool)
+    for k, mo in enumerate(mother):
+        pk = n_tracks + k
+        close = np.hypot(xs[pk] - xs[mo], ys[pk] - ys[mo]) < PAIR_MERGE_MM
+        both = hit[pk] & hit[mo] & close
+        shared[mo] = both
+        hit[pk] &= ~both
+        xs[mo, both] = 0.5 * (xs[mo, both] + xs[pk, both])
+        ys[mo, both] = 0.5 * (ys[mo, both] + ys[pk, both])
+    partner = np.full(T, -1)
+    partner[mother] = n_tracks + np.arange(n_pairs)
+    ti, pi = np.nonzero(hit)
+    sx = xs[ti, pi] + rng.normal(0.0, SMEAR_MM, ti.size)
+    sy = ys[ti, pi] + rng.normal(0.0, SMEAR_MM, ti.size)
+    sz = PLANE_Z[pi]
+    p2 = np.where(shared[ti, pi], partner[ti], -1)
+
+    n_noise = int(round(noise_frac * ti.size))
+    npl = rng.integers(0, N_PLANES, n_noise)
+    nr = np.sqrt(rng.uniform(R_MIN ** 2, R_MAX ** 2, n_noise))
+    nphi = rng.uniform(0.0, 2.0 * np.pi, n_noise)
+
+    x = np.concatenate([sx, nr * np.cos(nphi)])
+    y = np.concatenate([sy, nr * np.sin(nphi)])
+    z = np.concatenate([sz, PLANE_Z[npl]])
+    plane = np.concatenate([pi, npl]).astype(np.uint8)
+    pid = np.concatenate([ti, np.full(n_noise, -1)]).astype(np.int32)
+    pid2 = np.concatenate([p2, np.full(n_noise, -1)]).astype(np.int32)
+    order = rng.permutation(x.size)
+    return Batch(x[order].astype(np.float32), y[order].astype(np.float32),
+                 z[order].astype(np.float32), plane[order], pid[order],
+                 np.array([0, x.size], dtype=np.int64), pid2[order])
+
+
 def track_count(rng: np.random.Generator, spec: dict) -> int:
     if spec["kind"] == "fixed":
         return int(spec["n"])
@@ -155,7 +240,7 @@ def track_count(rng: np.random.Generator, spec: dict) -> int:
 
 
 def gen_batch(n_events: int, seed: int, tracks: dict, noise_frac: float,
-              first_event: int = 0) -> Batch:
+              first_event: int = 0, pair_frac: float = 0.0) -> Batch:
     """Events first_event .. first_event + n_events - 1 of the stream `seed`.
 
     Event e draws from its own PCG64 stream seeded with (seed, e), so any
@@ -164,7 +249,7 @@ def gen_batch(n_events: int, seed: int, tracks: dict, noise_frac: float,
     parts = []
     for e in range(first_event, first_event + n_events):
         rng = np.random.default_rng([seed, e])
-        parts.append(gen_event(rng, track_count(rng, tracks), noise_frac))
+        parts.append(gen_event(rng, track_count(rng, tracks), noise_frac, pair_frac))
     return concat(parts)
 
 
@@ -249,7 +334,8 @@ def shape_of(wl: dict) -> ModelShape:
 def workload_batch(wl: dict, n_events: int | None = None, first_event: int = 0,
                    seed_key: str = "events") -> Batch:
     n = wl["n_events"] if n_events is None else n_events
-    return gen_batch(n, wl["seeds"][seed_key], wl["tracks"], wl["noise"], first_event)
+    return gen_batch(n, wl["seeds"][seed_key], wl["tracks"], wl["noise"], first_event,
+                     wl.get("pair_frac", 0.0))
 
 
 def workload_weights(wl: dict) -> bytes:

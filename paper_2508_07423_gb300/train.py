@@ -49,7 +49,7 @@ def _torch():
 # ----------------------------------------------------------------------------
 # model (same layer order as synth.ModelShape)
 # ----------------------------------------------------------------------------
-def build(shape: synth.ModelShape, seed: int, device):
+def build(shape: synth.ModelShape, seed: int, device, triplets: bool = False):
     torch = _torch()
     nn = torch.nn
     gen = torch.Generator().manual_seed(seed)
@@ -72,6 +72,9 @@ def build(shape: synth.ModelShape, seed: int, device):
         "edge": nn.ModuleList([nn.ModuleList([lin(3 * h, h), lin(h, h)]) for _ in range(K)]),
         "cls": nn.ModuleList([lin(h, h), lin(h, 1)]),
     }
+    if triplets:  # articulation and elbow classifiers on [e_first, e_second]
+        mods["art"] = nn.ModuleList([lin(2 * h, h), lin(h, 1)])
+        mods["elb"] = nn.ModuleList([lin(2 * h, h), lin(h, 1)])
     return nn.ModuleDict(mods).to(device)
 
 
@@ -92,8 +95,9 @@ def _sub(pair, x):
     return pair[1](torch.relu(y))
 
 
-def gnn_forward(m, nf, src, dst):
-    """Logits of the edges src -> dst for node features nf [N, 3]."""
+def gnn_forward(m, nf, src, dst, with_states: bool = False):
+    """Logits of the edges src -> dst for node features nf [N, 3] (and the
+    final edge encodings e^K with `with_states`)."""
     torch = _torch()
     h = _sub(m["node_enc"], nf)
     e = _sub(m["edge_enc"], torch.cat([h[src], h[dst]], 1))
@@ -103,7 +107,8 @@ def gnn_forward(m, nf, src, dst):
         mi = e.new_zeros(n, e.shape[1]).index_add(0, dst, e)
         h = h + _sub(m["node"][k], torch.cat([h, mo, mi], 1))
         e = e + _sub(m["edge"][k], torch.cat([e, h[src], h[dst]], 1))
-    return _sub(m["cls"], e).squeeze(1)
+    logit = _sub(m["cls"], e).squeeze(1)
+    return (logit, e) if with_states else logit
 
 
 def to_blob(m) -> bytes:
@@ -115,8 +120,10 @@ def to_blob(m) -> bytes:
         for group in ("node", "edge"):
             for l in m[group][k]:
                 arrays.append((l.weight.detach().cpu().numpy(), l.bias.detach().cpu().numpy()))
-    for l in m["cls"]:
-        arrays.append((l.weight.detach().cpu().numpy(), l.bias.detach().cpu().numpy()))
+    for g in ("cls", "art", "elb"):
+        if g in m:
+            for l in m[g]:
+                arrays.append((l.weight.detach().cpu().numpy(), l.bias.detach().cpu().numpy()))
     return synth.pack_weights(arrays)
 
 
@@ -156,6 +163,53 @@ def _signal_only(ev):
     return idx
 
 
+def _same_particle(ev, i, j):
+    """Hits i and j (arrays) share a particle (a shared hit belongs to both
+    of its particles); noise shares none."""
+    p1, p2 = ev.pid, ev.pid2 if ev.pid2 is not None else np.full(len(ev.pid), -1)
+    a1, a2, b1, b2 = p1[i], p2[i], p1[j], p2[j]
+    return (((a1 == b1) & (a1 >= 0)) | ((a1 == b2) & (a1 >= 0)) |
+            ((a2 == b1) & (a2 >= 0)) | ((a2 == b2) & (a2 >= 0)))
+
+
+def triplets_of(plane, src, dst, kept):
+    """Triplets of the kept edges (indices `kept`): (type, e1, e2) with type 0
+    articulation (A->C, C->B), 1 left elbow (C->A, C->B), 2 right elbow
+    (A->C, B->C); elbow edges ordered by the (plane, index) of the far hit."""
+    n = len(plane)
+    ins = [[] for _ in range(n)]
+    outs = [[] for _ in range(n)]
+    for e in kept:
+        outs[src[e]].append(e)
+        ins[dst[e]].append(e)
+    key = lambda v: (int(plane[v]), int(v))
+    T = []
+    for c in range(n):
+        I = sorted(ins[c], key=lambda e: key(src[e]))
+        O = sorted(outs[c], key=lambda e: key(dst[e]))
+        T += [(0, a, b) for a in I for b in O]
+        T += [(1, O[i], O[j]) for i in range(len(O)) for j in range(i + 1, len(O))]
+        T += [(2, I[i], I[j]) for i in range(len(I)) for j in range(i + 1, len(I))]
+    return np.array(T, np.int64).reshape(-1, 3)
+
+
+def triplet_labels(ev, src, dst, T):
+    """A triplet is genuine when one particle left all three of its hits."""
+    ty, a, b = T[:, 0], T[:, 1], T[:, 2]
+    hits = np.where(ty[:, None] == 0, np.stack([src[a], dst[a], dst[b]], 1),
+                    np.where(ty[:, None] == 1, np.stack([src[a], dst[a], dst[b]], 1),
+                             np.stack([dst[a], src[a], src[b]], 1)))
+    p1 = ev.pid
+    p2 = ev.pid2 if ev.pid2 is not None else np.full(len(p1), -1)
+    lab = np.zeros(len(T), bool)
+    for cand in (p1[hits[:, 0]], p2[hits[:, 0]]):  # the first hit's particles
+        ok = cand >= 0
+        for k in (1, 2):
+            ok &= (p1[hits[:, k]] == cand) | (p2[hits[:, k]] == cand)
+        lab |= ok
+    return lab
+
+
 # ----------------------------------------------------------------------------
 # training
 # ----------------------------------------------------------------------------
@@ -171,7 +225,7 @@ def train_embedding(m, events, fs, device, epochs=6, lr=2e-3, w_genuine=3.0, mar
         emb_in, _ = _features(ev, fs)
         q, a = _candidate_pairs(ev.plane[idx])
         q, a = idx[q], idx[a]
-        genuine = ev.pid[q] == ev.pid[a]
+        genuine = _same_particle(ev, q, a)
         data.append((torch.from_numpy(emb_in).to(device), q, a, genuine))
     for ep in range(epochs):
         tot = 0.0
@@ -227,7 +281,7 @@ def embedding_radius(m, events, fs, device, keep=0.995):
             emb_in, _ = _features(ev, fs)
             q, a = _candidate_pairs(ev.plane[idx])
             q, a = idx[q], idx[a]
-            g = ev.pid[q] == ev.pid[a]
+            g = _same_particle(ev, q, a)
             z = embed_forward(m, torch.from_numpy(emb_in).to(device))
             d2 = ((z[torch.from_numpy(q[g]).to(device)] - z[torch.from_numpy(a[g]).to(device)]) ** 2).sum(1)
             ds.append(d2.cpu().numpy())
@@ -270,7 +324,7 @@ def train_gnn(m, events, fs, r2, k_max, device, epochs=8, lr=2e-3, seed=0):
     data = []
     for ev in events:
         src, dst, node_in = graph(m, ev, fs, r2, k_max, device)
-        y = ((ev.pid[src] == ev.pid[dst]) & (ev.pid[src] >= 0)).astype(np.float32)
+        y = _same_particle(ev, src, dst).astype(np.float32)
         data.append((torch.from_numpy(node_in).to(device), torch.from_numpy(src).to(device),
                      torch.from_numpy(dst).to(device), torch.from_numpy(y).to(device)))
     for ep in range(epochs):
@@ -288,18 +342,60 @@ def train_gnn(m, events, fs, r2, k_max, device, epochs=8, lr=2e-3, seed=0):
               flush=True)
 
 
+def train_triplets(m, events, fs, r2, k_max, device, epochs=10, lr=2e-3, seed=0):
+    """The two triplet classifiers on the final edge encodings of the trained
+    (frozen) GNN, over the triplets of the edges it keeps (score >= 0.5)."""
+    torch = _torch()
+    rng = np.random.default_rng(seed)
+    opt = torch.optim.Adam([p for g in ("art", "elb") for p in m[g].parameters()], lr=lr)
+    data = []
+    for ev in events:
+        src, dst, node_in = graph(m, ev, fs, r2, k_max, device)
+        if len(src) == 0:
+            continue
+        with torch.no_grad():
+            logit, e = gnn_forward(m, torch.from_numpy(node_in).to(device),
+                                   torch.from_numpy(src).to(device),
+                                   torch.from_numpy(dst).to(device), with_states=True)
+        kept = np.flatnonzero(logit.cpu().numpy() >= 0.0)
+        T = triplets_of(ev.plane, src, dst, kept)
+        if len(T) == 0:
+            continue
+        y = triplet_labels(ev, src, dst, T).astype(np.float32)
+        data.append((e, torch.from_numpy(T).to(device), torch.from_numpy(y).to(device)))
+    for ep in range(epochs):
+        tot = 0.0
+        for ei in rng.permutation(len(data)):
+            e, T, y = data[ei]
+            x = torch.cat([e[T[:, 1]], e[T[:, 2]]], 1)
+            art = T[:, 0] == 0
+            lg = torch.where(art, _sub(m["art"], x).squeeze(1), _sub(m["elb"], x).squeeze(1))
+            loss = focal_loss(lg, y)
+            opt.zero_grad()
+            loss.backward()
+            opt.step()
+            tot += float(loss.detach())
+        print(json.dumps({"stage": "triplets", "epoch": ep,
+                          "loss": round(tot / max(len(data), 1), 6)}), flush=True)
+
+
 def train(shape: synth.ModelShape, tracks: dict, noise: float, n_events: int, seed: int,
-          k_max: int = 64, device=None, emb_epochs=6, gnn_epochs=8):
-    """Train a model of `shape`; returns (blob, r2)."""
+          k_max: int = 64, device=None, emb_epochs=6, gnn_epochs=8, pair_frac: float = 0.0,
+          triplet_epochs: int = 0):
+    """Train a model of `shape` (with triplet classifiers when
+    `triplet_epochs` > 0); returns (blob, r2)."""
     torch = _torch()
     device = device or ("cuda" if torch.cuda.is_available() else "cpu")
     torch.manual_seed(seed)
     fs = (45.0, math.pi, 750.0, 45.0, 45.0, 750.0)
-    events = [synth.gen_batch(1, seed, tracks, noise, first_event=e) for e in range(n_events)]
-    m = build(shape, seed, device)
+    events = [synth.gen_batch(1, seed, tracks, noise, first_event=e, pair_frac=pair_frac)
+              for e in range(n_events)]
+    m = build(shape, seed, device, triplets=triplet_epochs > 0)
     train_embedding(m, events, fs, device, epochs=emb_epochs, seed=seed)
     r2 = embedding_radius(m, events, fs, device)
     train_gnn(m, events, fs, r2, k_max, device, epochs=gnn_epochs, seed=seed)
+    if triplet_epochs > 0:
+        train_triplets(m, events, fs, r2, k_max, device, epochs=triplet_epochs, seed=seed)
     return to_blob(m), r2
 
 
@@ -317,17 +413,23 @@ def main():
     p.add_argument("--emb-epochs", type=int, default=8)
     p.add_argument("--gnn-epochs", type=int, default=15)
     p.add_argument("--device", default="cpu")
+    p.add_argument("--pair-frac", type=float, default=0.0,
+                   help="close track pairs with shared hits per track (generator option)")
+    p.add_argument("--triplet-epochs", type=int, default=0,
+                   help="> 0: also train the articulation and elbow classifiers")
     a = p.parse_args()
     _torch().use_deterministic_algorithms(True)
     shape = synth.ModelShape([int(v) for v in a.embed.split(",")], a.hidden, a.iters)
     tracks = json.loads(a.tracks)
     blob, r2 = train(shape, tracks, a.noise, a.events, a.seed, device=a.device,
-                     emb_epochs=a.emb_epochs, gnn_epochs=a.gnn_epochs)
+                     emb_epochs=a.emb_epochs, gnn_epochs=a.gnn_epochs, pair_frac=a.pair_frac,
+                     triplet_epochs=a.triplet_epochs)
     with open(a.out, "wb") as f:
         f.write(blob)
     meta = {"radius2": r2, "embed": shape.embed, "hidden": a.hidden, "iters": a.iters,
             "train_events": a.events, "train_seed": a.seed, "tracks": tracks, "noise": a.noise,
             "emb_epochs": a.emb_epochs, "gnn_epochs": a.gnn_epochs, "device": a.device,
+            "pair_frac": a.pair_frac, "triplet_epochs": a.triplet_epochs,
             "radius_quantile_of_genuine_pairs": 0.995}
     with open(a.out.rsplit(".", 1)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=2)
