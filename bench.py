@@ -211,15 +211,19 @@ def stage_amount(stage, launches, rows, precision, N, E, m):
     return bound, total
 
 
-def timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, steps):
-    """Per-step CUDA-event times on `stream`, L2 flushed between steps."""
+def timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, steps, tracks=None):
+    """Per-step CUDA-event times on `stream`, L2 flushed between steps;
+    `tracks` = (event_tracks, track_off, track_hits) runs the triplet stage."""
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     with torch.cuda.stream(stream):
         for i in range(steps):
             flush.fill_(i)
             ev_s[i].record(stream)
-            tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            if tracks is None:
+                tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            else:
+                tr.find_tracks_triplets(n_ev, N, xyz, plane, offs, labels, *tracks, stream)
             ev_e[i].record(stream)
     torch.cuda.synchronize()
     tr.sync_status(stream)
@@ -407,6 +411,7 @@ def main():
             out["cfg2_report"] = cfg2_report(pkg, torch, dev, stream)
             out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
             out["trained_report"] = trained_report(pkg, torch, dev, stream, flush)
+            out["triplet_report"] = triplet_report(pkg, torch, dev, stream, flush)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -765,6 +770,134 @@ def trained_report(pkg, torch, dev, stream, flush, steps=5, sample=100):
                                                      for k, v in co.items()},
                                                   "edges": int(ne_ref), "seconds": round(t_oracle, 2),
                                                   "cores": cores}}
+    except Exception as ex:  # reported, not fatal
+        import traceback
+        return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
+
+
+def pair_particle_efficiency(tracks_per_event, b):
+    """Efficiency over the particles that share a hit with another one (the
+    close pairs), with the same matching rule as the track metrics."""
+    from collections import Counter
+    rec = tot = 0
+    for e, trk in enumerate(tracks_per_event):
+        a0, a1 = int(b.offsets[e]), int(b.offsets[e + 1])
+        pid, pid2 = b.pid[a0:a1], b.pid2[a0:a1]
+        nh = Counter(pid[pid >= 0].tolist()) + Counter(pid2[pid2 >= 0].tolist())
+        shared = set(pid[pid2 >= 0].tolist()) | set(pid2[pid2 >= 0].tolist())
+        matched = set()
+        for t in trk:
+            if len(t) < 3:
+                continue
+            v = Counter()
+            for i in t:
+                v[int(pid[i])] += 1
+                if pid2[i] >= 0:
+                    v[int(pid2[i])] += 1
+            real = [(n, -p) for p, n in v.items() if p >= 0]
+            if real:
+                n_, p_ = max(real)
+                if n_ >= 0.7 * len(t):
+                    matched.add(-p_)
+        for p in shared:
+            if nh[p] >= 3:
+                tot += 1
+                rec += p in matched
+    return round(rec / max(tot, 1), 6), tot
+
+
+def triplet_report(pkg, torch, dev, stream, flush, steps=5, sample=50):
+    """The triplet stage on 1000 events with close track pairs (trained
+    config-1 model with triplet classifiers): events/s with and without the
+    triplet stage (BF16 + re-score and FP32), the triplet-stage kernels' share
+    of a step, and track metrics of triplet tracks against plain components,
+    GPU against the FP64 oracle on the first `sample` events."""
+    try:
+        import oracle
+        from oracle import metrics
+        wl = synth.workload("cfg6_triplets")
+        b = synth.workload_batch(wl)
+        n_ev, N = b.n_events, b.n_hits
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        labels = torch.empty(N, dtype=torch.int32, device=dev)
+        ev_t = torch.zeros(n_ev + 1, dtype=torch.int32, device=dev)
+        t_off = torch.zeros(2 * N + 1, dtype=torch.int64, device=dev)
+        t_hits = torch.zeros(8 * N, dtype=torch.int32, device=dev)
+        outs = (ev_t, t_off, t_hits)
+        sub = b.subset(list(range(sample)))
+        nh = int(sub.n_hits)
+        res = {}
+        for prec in ("bf16", "fp32"):
+            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=N, max_events=n_ev,
+                                          edges_per_hit=16, use_graph=True)
+            tuned = tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
+            for _ in range(3):
+                tr.find_tracks_triplets(n_ev, N, xyz, plane, offs, labels, *outs, stream)
+            tr.sync_status(stream)
+            ms = float(np.mean(timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream,
+                                           flush, steps, tracks=outs)))
+            st, ts = tr.stats(), tr.triplet_stats()
+            tr.set_profiling(True)
+            timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, steps,
+                        tracks=outs)
+            stages = tr.stage_times()
+            tr.set_profiling(False)
+            lab = labels.cpu().numpy()
+            et, to, th = ev_t.cpu().numpy(), t_off.cpu().numpy(), t_hits.cpu().numpy()
+            tracks = [[th[to[t]:to[t + 1]] for t in range(et[e], et[e + 1])] for e in range(sample)]
+            ct = metrics.batch_track_counts(tracks, sub.pid, sub.offsets, pid2=sub.pid2).summary()
+            cw = metrics.batch_counts(lab[:nh], sub.pid, sub.offsets, pid2=sub.pid2).summary()
+            wcc_tracks = []
+            for e in range(sample):
+                a0, a1 = int(sub.offsets[e]), int(sub.offsets[e + 1])
+                mem = {}
+                for i, l in enumerate(lab[a0:a1]):
+                    mem.setdefault(int(l), []).append(i)
+                wcc_tracks.append(list(mem.values()))
+            tr.close()
+            base = pkg.tracker_for_workload(wl, precision=prec, max_hits=N, max_events=n_ev,
+                                            edges_per_hit=16, use_graph=True, triplets=False)
+            base.autotune(n_ev, N, xyz, plane, offs, labels, stream)
+            for _ in range(3):
+                base.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            base.sync_status(stream)
+            ms0 = float(np.mean(timed_steps(torch, base, n_ev, N, xyz, plane, offs, labels,
+                                            stream, flush, steps)))
+            base.close()
+            rnd = lambda d: {k: round(v, 6) if isinstance(v, float) else v for k, v in d.items()}
+            res[prec] = {
+                "events_per_s_with_triplets": round(n_ev / (ms / 1e3), 1),
+                "events_per_s_without": round(n_ev / (ms0 / 1e3), 1),
+                "ms_per_step": round(ms, 4), "ms_per_step_without": round(ms0, 4),
+                "stage_ms_per_step": {k: round(stages[k][0] / steps, 4)
+                                      for k in ("triplets", "triplet_scores", "track_build")
+                                      if k in stages},
+                "edges": st["edges"], "kept_edges": st["kept"], **{f"triplet_{k}": v for k, v in ts.items()},
+                "autotuned_ctas_per_sm": tuned,
+                f"triplet_tracks_first_{sample}_events": rnd(ct),
+                f"plain_components_first_{sample}_events": rnd(cw),
+                "pair_particle_efficiency_triplets": pair_particle_efficiency(tracks, sub),
+                "pair_particle_efficiency_components": pair_particle_efficiency(wcc_tracks, sub)}
+        sh = synth.shape_of(wl)
+        model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+        fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+        t0 = time.perf_counter()
+        ref = []
+        for e in range(sample):
+            ev = sub.event(e)
+            ref.append(oracle.find_tracks_triplets_event(
+                model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"], wl["k_max"], wl["cut"],
+                wl["triplet_cut"], feat_scale=fs).tracks)
+        t_or = time.perf_counter() - t0
+        co = metrics.batch_track_counts(ref, sub.pid, sub.offsets, pid2=sub.pid2).summary()
+        return {"workload": f"cfg6_triplets: {n_ev} events, {wl['description']}", "hits": int(N),
+                **res,
+                f"oracle_triplet_tracks_first_{sample}_events": {
+                    **{k: round(v, 6) if isinstance(v, float) else v for k, v in co.items()},
+                    "pair_particle_efficiency": pair_particle_efficiency(ref, sub),
+                    "seconds_one_core": round(t_or, 2)}}
     except Exception as ex:  # reported, not fatal
         import traceback
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}

@@ -32,6 +32,7 @@ struct gnntrk_handle {
   // tensor-core weights (BF16 / FP8 packed operands)
   TcModel tc{};
   void* d_wtc = nullptr;
+  void* d_wtrip = nullptr;  // triplet-classifier images (tensor-core paths)
   // workspace
   Ws ws{};
   std::vector<void*> allocs;
@@ -471,7 +472,14 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     const float tcut = float(std::log(double(c.triplet_cut) / (1.0 - double(c.triplet_cut))));
     stage(h, "triplets", s, 6, [&] { launch_triplets(b, w, h->h, s); });
     stage(h, "triplet_scores", s, 3, [&] {
-      launch_triplet_scores(b, w, h->trip, h->h, c.precision != GNNTRK_FP32, tcut, s);
+      if (h->tc.has_trip) {
+        // tensor cores: BF16 final edge encodings times BF16 first layers
+        tc_triplet_scores(b, w, h->tc, h->h, h->trip.art.l2, h->trip.elb.l2, h->trip.art.l1.b,
+                          h->trip.elb.l1.b, tcut, s);
+        launch_triplet_kept(w, s);
+      } else {
+        launch_triplet_scores(b, w, h->trip, h->h, false, tcut, s);
+      }
     });
     stage(h, "track_build", s, 6, [&] { launch_track_build(b, w, h->track_out, s); });
   }
@@ -574,6 +582,9 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
     st = fail(h, GNNTRK_ERR_WEIGHTS, "cfg.triplets needs a blob with the triplet classifiers");
   if (!st && c.precision != GNNTRK_FP32) st = (gnntrk_status)tc_upload(h->tc, L.data(), n_gnn_layers, h->n_embed,
                                                        h->h, h->K, c.precision, &h->d_wtc, h->err);
+  if (!st && c.precision != GNNTRK_FP32 && c.triplets)
+    st = (gnntrk_status)tc_upload_triplets(h->tc, L[n_gnn_layers], L[n_gnn_layers + 2],
+                                           &h->d_wtrip, h->err);
   if (!st) st = alloc_workspace(h);
   if (st) {
     g_create_error = h->err;
@@ -1053,6 +1064,7 @@ void gnntrk_destroy(gnntrk_handle* h) {
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->d_wtc) cudaFree(h->d_wtc);
+  if (h->d_wtrip) cudaFree(h->d_wtrip);
   delete h;
 }
 

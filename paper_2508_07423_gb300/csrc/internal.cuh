@@ -243,6 +243,8 @@ void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s);
 // triplet classifiers (FP32; the final edge encodings in FP32 or BF16)
 void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h, bool bf16,
                            float cut_logit, cudaStream_t s);
+// count of the triplets above the cut (after either classifier path)
+void launch_triplet_kept(const Ws& w, cudaStream_t s);
 // track building into `out`
 void launch_track_build(const Batch& b, const Ws& w, const TrackOut& out, cudaStream_t s);
 

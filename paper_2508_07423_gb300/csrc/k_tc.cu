@@ -46,7 +46,7 @@ constexpr int kRows = 128;       // rows per tile = threads per CTA = TMEM lanes
 constexpr long long kWaitCycles = 4000000000LL;  // bounded waits: about 2 s
 
 enum Mode : int { M_NODE_ENC = 0, M_EDGE_ENC = 1, M_NODE_UPD = 2, M_EDGE_UPD = 3,
-                  M_EDGE_UPD_CLS = 4, M_CLS = 5 };
+                  M_EDGE_UPD_CLS = 4, M_CLS = 5, M_TRIP = 6 };
 
 struct TcArgs {
   Batch b;
@@ -62,12 +62,20 @@ struct TcArgs {
   const float* sc;
   LayerF32 ne1;       // node encoder layer 1 (FP32, M_NODE_ENC)
   LayerF32 c2;        // classifier layer 2 (FP32, h -> 1)
+  // M_TRIP: one triplet list (edge pairs, count on the device) and its outputs
+  const int32_t* t1;
+  const int32_t* t2;
+  const int32_t* tn;
+  float* tlogit;
+  uint8_t* tkeep;
   float fs[6];
   float cut;
 };
 
 __host__ __device__ constexpr int n_seg(int mode) {
-  return mode == M_EDGE_ENC ? 2 : ((mode == M_NODE_UPD || mode == M_EDGE_UPD || mode == M_EDGE_UPD_CLS) ? 3 : 1);
+  return (mode == M_EDGE_ENC || mode == M_TRIP)
+             ? 2
+             : ((mode == M_NODE_UPD || mode == M_EDGE_UPD || mode == M_EDGE_UPD_CLS) ? 3 : 1);
 }
 __host__ __device__ constexpr int align1k(int x) { return (x + 1023) & ~1023; }
 __host__ __device__ constexpr int pow2_cols(int x) {
@@ -89,7 +97,7 @@ struct Layout {
   static constexpr int K1 = (MODE == M_NODE_ENC) ? H : (SPLIT ? 2 : 1) * NSEG * H;
   static constexpr int K2 = (SPLIT && MODE == M_NODE_ENC) ? 2 * H : H;
   static constexpr bool HAS_W1 = MODE != M_NODE_ENC;
-  static constexpr bool HAS_W2 = MODE != M_CLS;
+  static constexpr bool HAS_W2 = MODE != M_CLS && MODE != M_TRIP;
   static constexpr bool HAS_WC = MODE == M_EDGE_UPD_CLS;
   static constexpr int W1 = 0;
   static constexpr int W1_BYTES = HAS_W1 ? H * K1 * ESZ : 0;
@@ -382,7 +390,9 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const Ws& w = p.w;
-  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+  // (the triplet lists are only valid when the triplet workspace held them)
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & (MODE == M_TRIP ? (ST_INPUT | ST_CAPACITY) : ST_INPUT))
+    return;
 
   // ---- set-up: barriers, TMEM, weights --------------------------------------
   if (tid == 0) {
@@ -396,20 +406,20 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   }
   for (int i = tid; i < H; i += kRows) {
     pb1[i] = MODE == M_NODE_ENC ? p.ne1.b[i] : (MODE == M_CLS ? p.bc1[i] : p.b1[i]);
-    pb2[i] = MODE == M_CLS ? 0.f : p.b2[i];
+    pb2[i] = (MODE == M_CLS || MODE == M_TRIP) ? 0.f : p.b2[i];
     pbc[i] = (MODE == M_EDGE_UPD_CLS) ? p.bc1[i] : 0.f;
     if constexpr (FP8) {
       ps1[i] = MODE == M_NODE_ENC ? 1.f : (MODE == M_CLS ? p.sc[i] : p.s1[i]);
-      ps2[i] = MODE == M_CLS ? 1.f : p.s2[i];
+      ps2[i] = (MODE == M_CLS || MODE == M_TRIP) ? 1.f : p.s2[i];
       psc[i] = (MODE == M_EDGE_UPD_CLS) ? p.sc[i] : 1.f;
     }
-    if (MODE == M_EDGE_UPD_CLS || MODE == M_CLS) pc2[i] = p.c2.WT[i * p.c2.ldo];
+    if (MODE == M_EDGE_UPD_CLS || MODE == M_CLS || MODE == M_TRIP) pc2[i] = p.c2.WT[i * p.c2.ldo];
     if (MODE == M_NODE_ENC) {
       for (int j = 0; j < 3; ++j) pne[j * H + i] = p.ne1.WT[j * p.ne1.ldo + i];
       pne[3 * H + i] = p.ne1.b[i];
     }
   }
-  if (tid == 0 && (MODE == M_EDGE_UPD_CLS || MODE == M_CLS)) pc2[H] = p.c2.b[0];
+  if (tid == 0 && (MODE == M_EDGE_UPD_CLS || MODE == M_CLS || MODE == M_TRIP)) pc2[H] = p.c2.b[0];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -434,6 +444,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   {
     const Batch& b = p.b;
     hi = edge_rows ? clamp_edges(w.counters, w.e_cap) : b.n_hits;
+    if constexpr (MODE == M_TRIP) hi = min(*p.tn, int(w.t_cap));
   }
   const int n_tiles = (hi - lo + kRows - 1) / kRows;
   constexpr int K1 = L::K1;
@@ -558,7 +569,12 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       // edge rows: [e], [h_src, h_dst], [e, h_src, h_dst]
       if (valid) {
         int seg = 0;
-        if constexpr (MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS || MODE == M_CLS) {
+        if constexpr (MODE == M_TRIP) {
+          // [e^K(first edge), e^K(second edge)]
+          sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.estate16 + size_t(p.t1[r]) * H, nullptr);
+          sa[1] = put_row_bf16<H, FP8>(sA, tid, KCH1, H, w.estate16 + size_t(p.t2[r]) * H, nullptr);
+          seg = 2;
+        } else if constexpr (MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS || MODE == M_CLS) {
           sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.estate16 + size_t(r) * H,
                                        (H <= 64 && MODE != M_CLS) ? keep_row : nullptr);
           seg = 1;
@@ -567,7 +583,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           // [hi(h_src), hi(h_dst), lo(h_src), lo(h_dst)] from the FP32 encodings
           put_row_f32_split<H>(sA, tid, KCH1, 0, 2 * H, w.hstate + size_t(w.src[r]) * H);
           put_row_f32_split<H>(sA, tid, KCH1, H, 3 * H, w.hstate + size_t(w.col[r]) * H);
-        } else if constexpr (MODE != M_CLS) {
+        } else if constexpr (MODE != M_CLS && MODE != M_TRIP) {
           sa[seg] = put_row_bf16<H, FP8>(sA, tid, KCH1, seg * H, w.hstate16 + size_t(w.src[r]) * H,
                                          nullptr);
           sa[seg + 1] = put_row_bf16<H, FP8>(sA, tid, KCH1, (seg + 1) * H,
@@ -660,7 +676,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         }
       }
       const float inv = 1.0f / sqrtf(var / float(H) + kLnEps);
-      if constexpr (MODE == M_CLS) {
+      if constexpr (MODE == M_CLS || MODE == M_TRIP) {
         float logit = pc2[H];
 #pragma unroll
         for (int c = 0; c < H / 32; ++c) {
@@ -670,8 +686,13 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           for (int j = 0; j < 32; ++j) logit = fmaf(fmaxf((x[j] - mean) * inv, 0.f), pc2[c * 32 + j], logit);
         }
         if (valid) {
-          w.logit[r] = logit;
-          w.keep[r] = logit >= p.cut ? 1 : 0;
+          if constexpr (MODE == M_TRIP) {
+            p.tlogit[r] = logit;
+            p.tkeep[r] = logit >= p.cut ? 1 : 0;
+          } else {
+            w.logit[r] = logit;
+            w.keep[r] = logit >= p.cut ? 1 : 0;
+          }
         }
         tc_fence_before();
         continue;
@@ -1008,6 +1029,7 @@ int g_tuned[2][3][4] = {};
 constexpr int family_of(int mode) {
   return mode == M_NODE_ENC ? 0 : mode == M_EDGE_ENC ? 1 : mode == M_NODE_UPD ? 2 : 3;
 }
+static_assert(family_of(M_TRIP) == 3, "triplet classifier tunes with the edge family");
 constexpr int hidx(int h) { return h == 32 ? 0 : (h == 64 ? 1 : 2); }
 
 template <int H, bool FP8, int MODE>
@@ -1030,6 +1052,9 @@ void launch_h(int mode, const TcArgs& a, cudaStream_t s, int rows_hint) {
     case M_EDGE_UPD: launch_mode<H, FP8, M_EDGE_UPD>(a, s, rows_hint); break;
     case M_EDGE_UPD_CLS: launch_mode<H, FP8, M_EDGE_UPD_CLS>(a, s, rows_hint); break;
     case M_CLS: launch_mode<H, FP8, M_CLS>(a, s, rows_hint); break;
+    case M_TRIP:
+      if constexpr (!FP8) launch_mode<H, false, M_TRIP>(a, s, rows_hint);
+      break;
   }
 }
 
@@ -1041,6 +1066,7 @@ constexpr int smem_total(int H, int mode) {
    : mode == M_NODE_UPD ? Layout<HH, FP8, M_NODE_UPD>::TOTAL                          \
    : mode == M_EDGE_UPD ? Layout<HH, FP8, M_EDGE_UPD>::TOTAL                          \
    : mode == M_EDGE_UPD_CLS ? Layout<HH, FP8, M_EDGE_UPD_CLS>::TOTAL                  \
+   : mode == M_TRIP ? Layout<HH, FP8, M_TRIP>::TOTAL                                  \
                             : Layout<HH, FP8, M_CLS>::TOTAL)
   return H == 32 ? GNNTRK_LT(32) : (H == 64 ? GNNTRK_LT(64) : GNNTRK_LT(128));
 #undef GNNTRK_LT
@@ -1239,6 +1265,35 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   return GNNTRK_OK;
 }
 
+int tc_upload_triplets(TcModel& m, const HostLayer& art1, const HostLayer& elb1, void** dmem,
+                       std::string& err) {
+  std::vector<uint8_t> ia, ie;
+  std::vector<float> sa, se;
+  pack_layer(art1, false, ia, sa);
+  pack_layer(elb1, false, ie, se);
+  const size_t off_e = (ia.size() + 1023) / 1024 * 1024;
+  std::vector<uint8_t> blob(off_e + ie.size());
+  std::memcpy(blob.data(), ia.data(), ia.size());
+  std::memcpy(blob.data() + off_e, ie.data(), ie.size());
+  void* d = nullptr;
+  if (cudaMalloc(&d, blob.size()) != cudaSuccess) {
+    cudaGetLastError();
+    err = "cudaMalloc of the triplet-classifier weights failed";
+    return GNNTRK_ERR_OOM;
+  }
+  if (cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    err = "triplet-classifier weight upload failed";
+    return GNNTRK_ERR_CUDA;
+  }
+  *dmem = d;
+  const uint8_t* base = static_cast<const uint8_t*>(d);
+  m.art1 = LayerTC{base, nullptr, nullptr, art1.in, art1.out};
+  m.elb1 = LayerTC{base + off_e, nullptr, nullptr, elb1.in, elb1.out};
+  m.has_trip = true;
+  return GNNTRK_OK;
+}
+
 namespace {
 TcArgs base_args(const Batch& b, const Ws& w, const GraphParams& g) {
   TcArgs a{};
@@ -1319,6 +1374,34 @@ void tc_set_ctas(int precision, int h, int family, int n) {
 int tc_get_ctas(int precision, int h, int family) {
   if (family < 0 || family > 3 || (h != 32 && h != 64 && h != 128)) return 0;
   return g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family];
+}
+
+void tc_triplet_scores(const Batch& b, const Ws& w, const TcModel& m, int h, const LayerF32& art2,
+                       const LayerF32& elb2, const float* art_b1, const float* elb_b1,
+                       float cut_logit, cudaStream_t s) {
+  GraphParams g{};
+  g.cut_logit = cut_logit;
+  TcArgs a = base_args(b, w, g);
+  // articulations
+  a.W1 = static_cast<const uint8_t*>(m.art1.B);
+  a.b1 = art_b1;
+  a.c2 = art2;
+  a.t1 = w.trip_a1;
+  a.t2 = w.trip_a2;
+  a.tn = w.counters + C_TRIP_A;
+  a.tlogit = w.trip_alogit;
+  a.tkeep = w.trip_akeep;
+  launch_any(h, false, M_TRIP, a, s, -1);
+  // elbows
+  a.W1 = static_cast<const uint8_t*>(m.elb1.B);
+  a.b1 = elb_b1;
+  a.c2 = elb2;
+  a.t1 = w.trip_e1;
+  a.t2 = w.trip_e2;
+  a.tn = w.counters + C_TRIP_E;
+  a.tlogit = w.trip_elogit;
+  a.tkeep = w.trip_ekeep;
+  launch_any(h, false, M_TRIP, a, s, -1);
 }
 
 bool tc_cls_fused(int h, int precision) {

@@ -632,6 +632,10 @@ void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, i
   if (h == 32) score_h<32>(w, t, bf16, cut_logit, s);
   else if (h == 64) score_h<64>(w, t, bf16, cut_logit, s);
   else score_h<128>(w, t, bf16, cut_logit, s);
+  launch_triplet_kept(w, s);
+}
+
+void launch_triplet_kept(const Ws& w, cudaStream_t s) {
   k_trip_kept<<<device_sms() * 4, 256, 0, s>>>(w.trip_akeep, w.counters + C_TRIP_A, w.trip_ekeep,
                                                w.counters + C_TRIP_E, w.counters);
 }

@@ -12,12 +12,28 @@ struct TcModel {
   int h = 0, K = 0, n_embed = 0;
   LayerTC embed[kMaxEmbedLayers]{};
   Mlp2TC node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
+  // first layers of the triplet classifiers (BF16 images in every precision)
+  LayerTC art1{}, elb1{};
+  bool has_trip = false;
 };
 
 // Pack the layers (blob order) for the tensor cores and upload them to one
 // device allocation (*dmem, freed by the caller). Returns a gnntrk_status.
 int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, int K,
               int precision, void** dmem, std::string& err);
+
+// Pack the first layers of the triplet classifiers (BF16) into their own
+// device allocation (*dmem, freed by the caller). Returns a gnntrk_status.
+int tc_upload_triplets(TcModel& m, const HostLayer& art1, const HostLayer& elb1, void** dmem,
+                       std::string& err);
+
+// Triplet classifiers on the tensor cores: [e^K(e1), e^K(e2)] (BF16) times
+// the first layer, LayerNorm and ReLU in the epilogue, the 1-unit second
+// layer (FP32) as a dot product; writes the logits and keep flags of both
+// triplet lists.
+void tc_triplet_scores(const Batch& b, const Ws& w, const TcModel& m, int h, const LayerF32& art2,
+                       const LayerF32& elb2, const float* art_b1, const float* elb_b1,
+                       float cut_logit, cudaStream_t s);
 
 // FP32 embedding (its output feeds the radius test) and the node encoder
 // (FP32 K = 3 first layer, tensor-core second layer); writes w.emb and
