@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kTbThreads = 256;
 constexpr int kUnionRetries = 1 << 20;
-constexpr int kPairSort = 4096;  // pairs sorted in shared memory (else in place, O(n^2))
+constexpr int kPairSort = 1024;  // pairs sorted in shared memory (else in place, O(n^2))
 
 __device__ __forceinline__ int tb_find(volatile int32_t* P, int x) {
   int cur = P[x];
@@ -67,6 +67,31 @@ __device__ __forceinline__ void tb_union(volatile int32_t* P, int a, int b, int3
     ra = tb_find(P, ra);
   }
   set_status(counters, ST_TIMEOUT);
+}
+
+// Inclusive scan of one int per thread over a kTbThreads block (warp shuffles,
+// then the warp totals); `sw` holds kTbThreads / 32 ints of shared scratch.
+// Returns the thread's inclusive sum, the block total in `total`. Every thread
+// must call it (two barriers inside).
+__device__ __forceinline__ int block_scan(int v, int* sw, int& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  if (lane == 31) sw[wid] = v;
+  __syncthreads();
+  int off = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < kTbThreads / 32; ++k) {
+    const int t = sw[k];
+    off += k < wid ? t : 0;
+    tot += t;
+  }
+  __syncthreads();
+  total = tot;
+  return v + off;
 }
 
 // ---- 1. triplet counts per hit ----------------------------------------------
@@ -215,7 +240,7 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
   __shared__ int s_np, s_nuniq, s_tracks, s_hits;
   __shared__ unsigned long long s_last;
   __shared__ unsigned long long s_pairs[kPairSort];
-  __shared__ int s_scan[kTbThreads];
+  __shared__ int s_w[kTbThreads / 32];
   if (*(volatile int32_t*)&w.counters[C_STATUS] & (ST_INPUT | ST_CAPACITY)) return;
   const int tid = threadIdx.x;
   for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
@@ -340,20 +365,12 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
         const unsigned long long prev =
             tid > 0 ? (i < np ? pairs[i - 1] : 0ull) : (base > 0 ? s_last : ~v);
         const bool f = i < np && (i == 0 || v != prev);
-        s_scan[tid] = f;
-        __syncthreads();
+        int tot;
+        const int inc = block_scan(f ? 1 : 0, s_w, tot);
         if (tid == kTbThreads - 1 || i == np - 1) s_last = v;
-        for (int d = 1; d < kTbThreads; d <<= 1) {
-          const int add = tid >= d ? s_scan[tid - d] : 0;
-          __syncthreads();
-          s_scan[tid] += add;
-          __syncthreads();
-        }
-        const int tot = s_scan[kTbThreads - 1];
-        // writes go to slots < base + tid + 1 <= i, never past unread entries
-        // of this chunk: every thread read its value above
-        __syncthreads();
-        if (f) pairs[nu + s_scan[tid] - 1] = v;
+        // every thread read its entries before the scan's barriers; a write
+        // goes to slot nu + inc - 1 <= i
+        if (f) pairs[nu + inc - 1] = v;
         nu += tot;
         __syncthreads();
       }
@@ -386,24 +403,17 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
       for (int base = E0; base < E1; base += kTbThreads) {
         const int e = base + tid;
         const int c = (e < E1 && w.keep[e] && P[e] == e && P2[e] == e) ? w.tb_cnt[e] : 0;
-        s_scan[tid] = c;
-        __syncthreads();
-        for (int d = 1; d < kTbThreads; d <<= 1) {
-          const int add = tid >= d ? s_scan[tid - d] : 0;
-          __syncthreads();
-          s_scan[tid] += add;
-          __syncthreads();
-        }
+        int tot;
+        const int inc = block_scan(c, s_w, tot);
         if (c > 0) {
-          w.tb_off[e] = 2 * E0 + run + s_scan[tid] - c;
+          w.tb_off[e] = 2 * E0 + run + inc - c;
           w.tb_cur[e] = 0;
           if (!(w.tb_flag[e] & 4)) {
             atomicAdd(&s_tracks, 1);
             atomicAdd(&s_hits, c);
           }
         }
-        run += s_scan[kTbThreads - 1];
-        __syncthreads();
+        run += tot;
       }
     }
     __syncthreads();
@@ -469,7 +479,7 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
 __global__ void __launch_bounds__(kTbThreads) k_tb_write(Batch b, Ws w, const int32_t* ev_tracks,
                                                           int64_t* track_off, int32_t* track_hits,
                                                           int64_t max_tracks, int64_t max_hits) {
-  __shared__ int s_scan[kTbThreads], s_scan2[kTbThreads];
+  __shared__ int s_w[kTbThreads / 32];
   __shared__ int s_t, s_h;
   if (*(volatile int32_t*)&w.counters[C_STATUS] & (ST_INPUT | ST_CAPACITY)) return;
   const int tid = threadIdx.x;
@@ -498,25 +508,16 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_write(Batch b, Ws w, const in
       const int e = base + tid;
       const bool f = e < E1 && w.keep[e] && P[e] == e && P2[e] == e && !(w.tb_flag[e] & 4);
       const int c = f ? w.tb_cnt[e] : 0;
-      s_scan[tid] = f ? 1 : 0;
-      s_scan2[tid] = c;
-      __syncthreads();
-      for (int d = 1; d < kTbThreads; d <<= 1) {
-        const int add = tid >= d ? s_scan[tid - d] : 0;
-        const int add2 = tid >= d ? s_scan2[tid - d] : 0;
-        __syncthreads();
-        s_scan[tid] += add;
-        s_scan2[tid] += add2;
-        __syncthreads();
-      }
+      int last, last2;
+      const int inc = block_scan(f ? 1 : 0, s_w, last);
+      const int inc2 = block_scan(c, s_w, last2);
       if (f) {
-        const int t = s_t + s_scan[tid] - 1;
-        const int64_t o = s_h + s_scan2[tid] - c;
+        const int t = s_t + inc - 1;
+        const int64_t o = s_h + inc2 - c;
         track_off[t] = o;
         const int32_t* L = w.tb_hits + w.tb_off[e];
         for (int i = 0; i < c; ++i) track_hits[o + i] = w.perm[L[i]] - base_ev;
       }
-      const int last = s_scan[kTbThreads - 1], last2 = s_scan2[kTbThreads - 1];
       __syncthreads();
       if (tid == 0) {
         s_t += last;
@@ -542,17 +543,11 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_write(Batch b, Ws w, const in
           ++u;
         }
       }
-      s_scan[tid] = u;
-      __syncthreads();
-      for (int d = 1; d < kTbThreads; d <<= 1) {
-        const int add = tid >= d ? s_scan[tid - d] : 0;
-        __syncthreads();
-        s_scan[tid] += add;
-        __syncthreads();
-      }
+      int last;
+      const int inc = block_scan(u, s_w, last);
       if (k < nu) {
         const int t = s_t + k - base;
-        const int64_t o = s_h + s_scan[tid] - u;
+        const int64_t o = s_h + inc - u;
         track_off[t] = o;
         const int32_t *a = w.tb_hits + w.tb_off[X], *c = w.tb_hits + w.tb_off[Y];
         const int na = w.tb_cnt[X], nc = w.tb_cnt[Y];
@@ -565,7 +560,6 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_write(Batch b, Ws w, const in
           track_hits[o + m++] = w.perm[v] - base_ev;
         }
       }
-      const int last = s_scan[kTbThreads - 1];
       __syncthreads();
       if (tid == 0) {
         s_t += min(kTbThreads, nu - base);
