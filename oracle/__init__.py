@@ -10,7 +10,10 @@ holds the track-finding metrics of the thesis (efficiency, ghost rate, clone
 rate, hit purity, hit efficiency).
 
 Parity status: every step is pinned by tests against closed forms, hand-worked
-examples and brute force (see tests/test_oracle_pins.py). The composition of
+examples and brute force (see tests/test_oracle_pins.py; the triplet stage in
+tests/test_oracle_triplets.py: triplets against a brute-force pair
+enumeration, the classifiers' operand order and routing tied to the edge
+classifier, track building on hand-worked graphs including a shared-hit pair). The composition of
 the steps into the whole pipeline has no external pin of its own (parity
 unpinned beyond the per-step pins).
 """
