@@ -233,6 +233,36 @@ __global__ void __launch_bounds__(128) k_trip_score(Ws w, LayerF32 l1, LayerF32 
   }
 }
 
+// Call f(X) once for every distinct component X among the kept edges of hit v
+// (CE[e] = component of edge e, -1 if the edge is not kept). The components
+// of up to 16 incident kept edges are kept in registers; beyond that the
+// earlier edges are re-read.
+template <class F>
+__device__ __forceinline__ void for_hit_components(const Ws& w, const int32_t* CE, int v, F&& f) {
+  constexpr int kReg = 16;
+  const int o0 = w.row_ptr[v], o1 = w.row_ptr[v + 1];
+  const int i0 = w.in_ptr[v], i1 = w.in_ptr[v + 1];
+  const int dout = o1 - o0, deg = dout + (i1 - i0);
+  auto edge = [&](int q) { return q < dout ? o0 + q : w.in_edge[i0 + q - dout]; };
+  int cs[kReg];
+  int nc = 0;
+  for (int q = 0; q < deg; ++q) {
+    const int X = CE[edge(q)];
+    if (X < 0) continue;
+    bool seen = false;
+    if (q <= kReg) {
+      // every earlier distinct component is in cs (fewer than kReg edges before q)
+#pragma unroll
+      for (int r = 0; r < kReg; ++r) seen |= r < nc && cs[r] == X;
+    } else {
+      for (int r = 0; r < q && !seen; ++r) seen = CE[edge(r)] == X;
+    }
+    if (seen) continue;
+    if (nc < kReg) cs[nc++] = X;
+    f(X);
+  }
+}
+
 // ---- 4. track building, per event ------------------------------------------------
 // Phase 1: groups, links, components, component hit lists, pair list; counts
 // of tracks and track hits per event.
@@ -378,23 +408,14 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
     }
     __syncthreads();
     // 4. hits per component: every hit with a kept edge counts once per
-    //    distinct component among its kept edges
-    for (int v = h0 + tid; v < h1; v += kTbThreads) {
-      const int o0 = w.row_ptr[v], o1 = w.row_ptr[v + 1];
-      const int i0 = w.in_ptr[v], i1 = w.in_ptr[v + 1];
-      const int deg = (o1 - o0) + (i1 - i0);
-      for (int q = 0; q < deg; ++q) {
-        const int e = q < o1 - o0 ? o0 + q : w.in_edge[i0 + q - (o1 - o0)];
-        if (!w.keep[e]) continue;
-        const int X = P2[P[e]];
-        bool seen = false;
-        for (int r = 0; r < q && !seen; ++r) {
-          const int f = r < o1 - o0 ? o0 + r : w.in_edge[i0 + r - (o1 - o0)];
-          seen = w.keep[f] && P2[P[f]] == X;
-        }
-        if (!seen) atomicAdd(&w.tb_cnt[X], 1);
-      }
-    }
+    //    distinct component among its kept edges. The component of every
+    //    edge first (-1 if not kept; tb_in is free again), so a hit reads
+    //    one value per incident edge.
+    int32_t* CE = w.tb_in;
+    for (int e = E0 + tid; e < E1; e += kTbThreads) CE[e] = w.keep[e] ? P2[P[e]] : -1;
+    __syncthreads();
+    for (int v = h0 + tid; v < h1; v += kTbThreads)
+      for_hit_components(w, CE, v, [&](int X) { atomicAdd(&w.tb_cnt[X], 1); });
     __syncthreads();
     // offsets of the component hit lists (block scan over the event's edges),
     // and counts of the plain tracks
@@ -418,22 +439,10 @@ __global__ void __launch_bounds__(kTbThreads) k_tb_event(Batch b, Ws w) {
     }
     __syncthreads();
     // place the hits (sorted positions), then sort each list
-    for (int v = h0 + tid; v < h1; v += kTbThreads) {
-      const int o0 = w.row_ptr[v], o1 = w.row_ptr[v + 1];
-      const int i0 = w.in_ptr[v], i1 = w.in_ptr[v + 1];
-      const int deg = (o1 - o0) + (i1 - i0);
-      for (int q = 0; q < deg; ++q) {
-        const int e = q < o1 - o0 ? o0 + q : w.in_edge[i0 + q - (o1 - o0)];
-        if (!w.keep[e]) continue;
-        const int X = P2[P[e]];
-        bool seen = false;
-        for (int r = 0; r < q && !seen; ++r) {
-          const int f = r < o1 - o0 ? o0 + r : w.in_edge[i0 + r - (o1 - o0)];
-          seen = w.keep[f] && P2[P[f]] == X;
-        }
-        if (!seen) w.tb_hits[w.tb_off[X] + atomicAdd(&w.tb_cur[X], 1)] = v;
-      }
-    }
+    for (int v = h0 + tid; v < h1; v += kTbThreads)
+      for_hit_components(w, CE, v, [&](int X) {
+        w.tb_hits[w.tb_off[X] + atomicAdd(&w.tb_cur[X], 1)] = v;
+      });
     __syncthreads();
     for (int e = E0 + tid; e < E1; e += kTbThreads) {
       if (!(w.keep[e] && P[e] == e && P2[e] == e)) continue;
