@@ -412,6 +412,7 @@ def main():
             out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
             out["trained_report"] = trained_report(pkg, torch, dev, stream, flush)
             out["triplet_report"] = triplet_report(pkg, torch, dev, stream, flush)
+            out["int8_report"] = int8_report(pkg, torch, dev, stream, flush)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -898,6 +899,71 @@ def triplet_report(pkg, torch, dev, stream, flush, steps=5, sample=50):
                     **{k: round(v, 6) if isinstance(v, float) else v for k, v in co.items()},
                     "pair_particle_efficiency": pair_particle_efficiency(ref, sub),
                     "seconds_one_core": round(t_or, 2)}}
+    except Exception as ex:  # reported, not fatal
+        import traceback
+        return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
+
+
+def int8_report(pkg, torch, dev, stream, flush, steps=5, calib_events=5000, sample=100):
+    """INT8 embedding (post-training quantisation, the thesis's Sec. on MLP
+    quantisation) on the trained config-1 model and the headline's 1000
+    events: graph size and track metrics with the FP32 embedding, the INT8
+    one uncalibrated (alpha = 1) and the INT8 one after max calibration on
+    `calib_events` other events; BF16 + re-score GNN in all three."""
+    try:
+        from oracle import metrics
+        wl = synth.workload("cfg3_trained_bf16")
+        b = synth.workload_batch(wl)
+        n_ev, N = b.n_events, b.n_hits
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        labels = torch.empty(N, dtype=torch.int32, device=dev)
+        sub = b.subset(list(range(sample)))
+        nh = int(sub.n_hits)
+        t0 = time.perf_counter()
+        cal = synth.workload_batch(wl, calib_events, first_event=n_ev)
+        t_gen = time.perf_counter() - t0
+        cal_xyz = torch.from_numpy(cal.xyz_soa()).to(dev)
+        res = {}
+        alpha = None
+        for name in ("fp32_embedding", "int8_uncalibrated", "int8_calibrated"):
+            tr = pkg.tracker_for_workload(wl, max_hits=N, max_events=n_ev,
+                                          edges_per_hit=40 if name == "int8_uncalibrated" else 16,
+                                          use_graph=True, embed_int8=name != "fp32_embedding")
+            if name == "int8_calibrated":
+                t1 = time.perf_counter()
+                alpha = tr.embed_amax(cal_xyz, stream)
+                t_cal = time.perf_counter() - t1
+                tr.set_embed_scales(alpha)
+            tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
+            for _ in range(3):
+                tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
+            tr.sync_status(stream)
+            ms = float(np.mean(timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream,
+                                           flush, steps)))
+            st = tr.stats()
+            tr.set_profiling(True)
+            timed_steps(torch, tr, n_ev, N, xyz, plane, offs, labels, stream, flush, steps)
+            stages = tr.stage_times()
+            tr.set_profiling(False)
+            lab = labels.cpu().numpy()[:nh]
+            c = metrics.batch_counts(lab, sub.pid, sub.offsets).summary()
+            res[name] = {"events_per_s": round(n_ev / (ms / 1e3), 1), "edges": st["edges"],
+                         "node_prep_ms_per_step": round(stages["node_prep"][0] / steps, 4),
+                         f"metrics_first_{sample}_events": {
+                             k: round(v, 6) if isinstance(v, float) else v for k, v in c.items()}}
+            tr.close()
+        e32 = res["fp32_embedding"]["edges"]
+        for k in ("int8_uncalibrated", "int8_calibrated"):
+            res[k]["edges_vs_fp32"] = round(res[k]["edges"] / e32 - 1.0, 4)
+        return {"workload": f"cfg3_trained_bf16: {n_ev} events, {wl['description']}",
+                "calibration": {"events": calib_events, "hits": int(cal.n_hits),
+                                "method": "max |layer input| over the calibration events (GPU, FP32 embedding)",
+                                "alpha": [round(float(a), 6) for a in alpha],
+                                "seconds_on_gpu": round(t_cal, 3),
+                                "seconds_generating_events": round(t_gen, 2)},
+                "uncalibrated_alpha": 1.0, **res}
     except Exception as ex:  # reported, not fatal
         import traceback
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}

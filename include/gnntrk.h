@@ -111,6 +111,13 @@ typedef enum gnntrk_precision {
  *   triplets_per_hit: triplet workspace, per hit of max_hits, for each of
  *            the two lists (articulations, elbows); a call that needs more
  *            latches GNNTRK_ERR_CAPACITY.
+ * INT8 embedding (the thesis's post-training quantisation of the embedding):
+ *   embed_int8: 1 = the embedding MLP runs in INT8 in every precision: each
+ *            layer's input quantised with a static scale alpha / 127
+ *            (gnntrk_set_embed_scales; alpha = 1 until set, "uncalibrated"),
+ *            weights per output channel (max |W_row| / 127), codes
+ *            clip(round(v / S), -127, 127), INT32 dot products, then
+ *            y = S_a S_w acc + b in FP32, ReLU between layers.
  */
 typedef struct gnntrk_cfg {
   int32_t n_embed_layers;
@@ -131,7 +138,8 @@ typedef struct gnntrk_cfg {
   int32_t triplets;
   float triplet_cut;
   int32_t triplets_per_hit;
-  int32_t reserved[4];
+  int32_t embed_int8;
+  int32_t reserved[3];
 } gnntrk_cfg;
 
 typedef struct gnntrk_handle gnntrk_handle;
@@ -251,6 +259,25 @@ gnntrk_status gnntrk_triplet_stats(gnntrk_handle* h, int64_t* out);
 gnntrk_status gnntrk_get_triplets(gnntrk_handle* h, int32_t event, int64_t capacity,
                                   int32_t* type, int32_t* hits3, float* logit, uint8_t* kept,
                                   int64_t* n_triplets);
+
+/*
+ * Max calibration of the INT8 embedding: run the FP32 embedding over n_hits
+ * hits and return, per embedding layer, the largest |input| (the first
+ * layer's input is the feature vector (r/s0, phi/s1, z/s2)).
+ *   hits_xyz: device float32 [3][n_hits] as for gnntrk_find_tracks.
+ *   out_amax: host float [cfg.n_embed_layers].
+ * Synchronises `stream`. Errors: INVALID_ARG, CUDA.
+ */
+gnntrk_status gnntrk_embed_amax(gnntrk_handle* h, int64_t n_hits, const float* hits_xyz,
+                                float* out_amax, void* stream);
+
+/*
+ * Set the ranges alpha of the INT8 embedding's layer inputs (scale
+ * alpha / 127); host float [n], n = cfg.n_embed_layers, each > 0 and
+ * finite. Takes effect for the next call (also in captured CUDA graphs).
+ * Errors: INVALID_ARG (no cfg.embed_int8, wrong n or value), CUDA.
+ */
+gnntrk_status gnntrk_set_embed_scales(gnntrk_handle* h, const float* alpha, int32_t n);
 
 /*
  * Wait for `stream`, then return and clear the status latched by device-side

@@ -28,6 +28,7 @@ EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
            "gnntrk_autotune", "gnntrk_rescore_rows", "gnntrk_e4m3_encode", "gnntrk_e4m3_decode",
            "gnntrk_find_tracks_triplets", "gnntrk_triplet_stats", "gnntrk_get_triplets",
+           "gnntrk_embed_amax", "gnntrk_set_embed_scales",
            "gnntrk_last_error", "gnntrk_destroy"]
 
 NOALLOC_MAX_HITS = 1 << 20
@@ -71,7 +72,8 @@ class Cfg(ctypes.Structure):
         ("triplets", ctypes.c_int32),
         ("triplet_cut", ctypes.c_float),
         ("triplets_per_hit", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("embed_int8", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -125,6 +127,10 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_triplet_stats.restype = st
     L.gnntrk_get_triplets.argtypes = [vp, i32, i64, vp, vp, vp, vp, ctypes.POINTER(i64)]
     L.gnntrk_get_triplets.restype = st
+    L.gnntrk_embed_amax.argtypes = [vp, i64, vp, vp, vp]
+    L.gnntrk_embed_amax.restype = st
+    L.gnntrk_set_embed_scales.argtypes = [vp, vp, i32]
+    L.gnntrk_set_embed_scales.restype = st
     L.gnntrk_last_error.argtypes = [vp]
     L.gnntrk_last_error.restype = ctypes.c_char_p
     L.gnntrk_destroy.argtypes = [vp]
@@ -143,7 +149,8 @@ def make_cfg(model: dict, radius2: float, k_max: int = 64, score_cut: float = 0.
              precision="fp32", rescore_band: float = 0.0, max_hits: int = 1 << 20,
              max_events: int = 4096, edges_per_hit: int = 24, use_graph: bool = False,
              n_planes: int = 26, feat_scale=None, triplets: bool = False,
-             triplet_cut: float = 0.5, triplets_per_hit: int = 16) -> Cfg:
+             triplet_cut: float = 0.5, triplets_per_hit: int = 16,
+             embed_int8: bool = False) -> Cfg:
     """Build a cfg from a model description {"embed": [...], "hidden", "iters"}."""
     c = default_cfg()
     emb = list(model["embed"])
@@ -168,6 +175,7 @@ def make_cfg(model: dict, radius2: float, k_max: int = 64, score_cut: float = 0.
     c.triplets = int(bool(triplets))
     c.triplet_cut = triplet_cut
     c.triplets_per_hit = triplets_per_hit
+    c.embed_int8 = int(bool(embed_int8))
     return c
 
 
@@ -233,6 +241,22 @@ class Tracker:
             self._h, n_events, n_hits, _ptr(hits_xyz), _ptr(plane), _ptr(offsets),
             _ptr(out_labels), _ptr(out_event_tracks), _ptr(out_track_off), _ptr(out_track_hits),
             out_track_off.numel() - 1, out_track_hits.numel(), ctypes.c_void_p(s)))
+
+    def embed_amax(self, hits_xyz, stream=None) -> np.ndarray:
+        """Max calibration: the largest |input| of every embedding layer over
+        the hits of hits_xyz (float32 CUDA tensor [3, n_hits])."""
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        out = np.zeros(self.cfg.n_embed_layers, np.float32)
+        self._check(self._L.gnntrk_embed_amax(self._h, hits_xyz.shape[1], _ptr(hits_xyz),
+                                              out.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.c_void_p(s)))
+        return out
+
+    def set_embed_scales(self, alpha):
+        """Ranges alpha of the INT8 embedding's layer inputs (scale alpha / 127)."""
+        a = np.ascontiguousarray(alpha, np.float32)
+        self._check(self._L.gnntrk_set_embed_scales(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                    a.size))
 
     def triplet_stats(self) -> dict:
         out = np.zeros(6, np.int64)

@@ -24,6 +24,13 @@ struct gnntrk_handle {
   float* d_wf32 = nullptr;
   LayerF32 embed[kMaxEmbedLayers]{};
   Mlp2F32 node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
+  // INT8 embedding: packed weights, scales, the ranges set by the caller
+  Int8Embed i8{};
+  void* d_i8 = nullptr;
+  std::vector<std::vector<float>> i8_sw;  // per layer: weight scales S_w
+  std::vector<float> i8_alpha;            // per layer: input range
+  EmbedAmax amax_layers{};
+  int32_t* d_amax = nullptr;
   TripletHeads trip{};   // triplet classifiers (blob with triplet layers)
   bool has_trip = false;
   TrackOut track_out{};  // outputs of the current triplet call
@@ -374,12 +381,14 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   stage(h, "sort", s, 1, [&] { launch_sort(b, w, c.n_planes, s); });
   const Sel all{nullptr, nullptr};
   const bool tc = c.precision != GNNTRK_FP32;
-  stage(h, "node_prep", s, tc ? 2 : 1, [&] {
+  const bool i8 = c.embed_int8 != 0;
+  stage(h, "node_prep", s, (tc ? 2 : 1) + (i8 ? 1 : 0) - (tc && i8 ? 1 : 0), [&] {
+    if (i8) launch_embed_int8(b, w, h->i8, h->D, g, s);
     if (!tc)
       launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
-                           true, true, all, s);
+                           !i8, true, all, s);
     else
-      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s);
+      tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s, !i8);
   });
   stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
   stage(h, "scan_out", s, 2, [&] {
@@ -485,6 +494,83 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   }
 }
 
+namespace {
+// Upload the dequantisation scales (alpha / 127) S_w and 127 / alpha of the
+// INT8 embedding for the current ranges.
+gnntrk_status upload_i8_scales(gnntrk_handle* h) {
+  const int n = h->n_embed;
+  std::vector<float> buf;
+  for (int l = 0; l < n; ++l) {
+    const float sa = h->i8_alpha[l] / 127.0f;
+    for (float sw : h->i8_sw[l]) buf.push_back(sa * sw);
+  }
+  for (int l = 0; l < n; ++l) buf.push_back(127.0f / h->i8_alpha[l]);
+  float* d = const_cast<float*>(h->i8.l[0].s);
+  cudaError_t e = cudaMemcpy(d, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? GNNTRK_OK : cuda_fail(h, e, "INT8 scale upload");
+}
+
+// Quantise the embedding weights per output channel and lay out the INT8
+// kernel's operands: codes (4 per word along K, rows padded to whole 16-byte
+// chunks), biases, then the scales.
+gnntrk_status setup_int8(gnntrk_handle* h, const std::vector<HostLayer>& L) {
+  const int n = h->n_embed;
+  std::vector<uint32_t> words;
+  std::vector<size_t> w_off(n);
+  std::vector<int> in4(n), in16(n);
+  h->i8_sw.assign(n, {});
+  h->i8_alpha.assign(n, 1.0f);
+  int max_in4 = 1;
+  for (int l = 0; l < n; ++l) {
+    const HostLayer& y = L[l];
+    int q4 = (y.in + 3) / 4, p4 = 1;
+    while (p4 < q4) p4 *= 2;
+    in4[l] = p4;
+    in16[l] = (p4 + 3) / 4;
+    if (l > 0) max_in4 = std::max(max_in4, p4);
+    w_off[l] = words.size();
+    words.resize(words.size() + size_t(y.out) * in16[l] * 4, 0u);
+    for (int o = 0; o < y.out; ++o) {
+      float amax = 0.f;
+      for (int k = 0; k < y.in; ++k) amax = std::max(amax, std::fabs(y.W[size_t(o) * y.in + k]));
+      const float sw = amax > 0.f ? amax / 127.0f : 1.0f;
+      h->i8_sw[l].push_back(sw);
+      for (int k = 0; k < y.in; ++k) {
+        float q = std::nearbyint(y.W[size_t(o) * y.in + k] / sw);
+        q = std::min(127.f, std::max(-127.f, q));
+        const uint32_t byte = uint32_t(int(q)) & 0xffu;
+        words[w_off[l] + size_t(o) * in16[l] * 4 + k / 4] |= byte << (8 * (k % 4));
+      }
+    }
+  }
+  // device image: [scales of all layers | 127/alpha] [biases] [codes]
+  size_t n_s = 0, n_b = 0;
+  for (int l = 0; l < n; ++l) n_s += L[l].out, n_b += L[l].out;
+  const size_t bytes = 4 * (n_s + n + n_b) + 16 + 4 * words.size();
+  gnntrk_status st = alloc(h, &h->d_i8, bytes);
+  if (st) return st;
+  uint8_t* base = static_cast<uint8_t*>(h->d_i8);
+  float* ds = reinterpret_cast<float*>(base);
+  float* dinv = ds + n_s;
+  float* db = dinv + n;
+  uint32_t* dw = reinterpret_cast<uint32_t*>(base + ((4 * (n_s + n + n_b) + 15) / 16) * 16);
+  std::vector<float> bias;
+  for (int l = 0; l < n; ++l) bias.insert(bias.end(), L[l].b.begin(), L[l].b.end());
+  cudaError_t e = cudaMemcpy(db, bias.data(), 4 * bias.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dw, words.data(), 4 * words.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "INT8 weight upload");
+  size_t so = 0;
+  for (int l = 0; l < n; ++l) {
+    h->i8.l[l] = Int8Layer{dw + w_off[l], ds + so, db + so, in4[l], in16[l], L[l].out};
+    so += L[l].out;
+  }
+  h->i8.inv = dinv;
+  h->i8.n = n;
+  h->i8.max_in4 = max_in4;
+  return upload_i8_scales(h);
+}
+}  // namespace
+
 namespace gnntrk {
 // failure text of handle-less calls, returned by gnntrk_last_error(NULL)
 void set_global_error(const std::string& msg) { g_create_error = msg; }
@@ -558,6 +644,8 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
     return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "edge workspace must hold < 2^31 edges");
   if (c.triplets != 0 && c.triplets != 1)
     return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "triplets must be 0 or 1");
+  if (c.embed_int8 != 0 && c.embed_int8 != 1)
+    return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "embed_int8 must be 0 or 1");
   if (c.triplets && !(c.triplet_cut > 0.f && c.triplet_cut < 1.f))
     return fail(nullptr, GNNTRK_ERR_INVALID_ARG, "triplet_cut must be in (0, 1)");
   if (c.triplets && (c.triplets_per_hit < 1 ||
@@ -582,6 +670,10 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
     st = fail(h, GNNTRK_ERR_WEIGHTS, "cfg.triplets needs a blob with the triplet classifiers");
   if (!st && c.precision != GNNTRK_FP32) st = (gnntrk_status)tc_upload(h->tc, L.data(), n_gnn_layers, h->n_embed,
                                                        h->h, h->K, c.precision, &h->d_wtc, h->err);
+  if (!st && c.embed_int8) st = setup_int8(h, L);
+  if (!st) st = alloc_n(h, &h->d_amax, kMaxEmbedLayers);
+  for (int l = 0; l < h->n_embed; ++l) h->amax_layers.l[l] = h->embed[l];
+  h->amax_layers.n = h->n_embed;
   if (!st && c.precision != GNNTRK_FP32 && c.triplets)
     st = (gnntrk_status)tc_upload_triplets(h->tc, L[n_gnn_layers], L[n_gnn_layers + 2],
                                            &h->d_wtrip, h->err);
@@ -705,6 +797,35 @@ gnntrk_status gnntrk_find_tracks_triplets(gnntrk_handle* h, int32_t n_events, in
     return fail(h, GNNTRK_ERR_INVALID_ARG, "misaligned pointer");
   const TrackOut t{out_event_tracks, out_track_off, out_track_hits, max_tracks, max_track_hits};
   return run_call(h, n_events, n_hits, hits_xyz, plane, offsets, out_labels, &t, stream);
+}
+
+gnntrk_status gnntrk_embed_amax(gnntrk_handle* h, int64_t n_hits, const float* hits_xyz,
+                                float* out_amax, void* stream) {
+  if (!h || !out_amax) return GNNTRK_ERR_INVALID_ARG;
+  if (n_hits < 0 || n_hits >= (int64_t(1) << 31) || (n_hits > 0 && !hits_xyz))
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "n_hits out of range or NULL hits");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  launch_embed_amax(hits_xyz, int(n_hits), h->amax_layers, graph_params(h), h->d_amax, s);
+  int32_t bits[kMaxEmbedLayers];
+  cudaError_t e = cudaMemcpyAsync(bits, h->d_amax, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "embedding calibration");
+  for (int l = 0; l < h->n_embed; ++l) std::memcpy(&out_amax[l], &bits[l], 4);
+  return GNNTRK_OK;
+}
+
+gnntrk_status gnntrk_set_embed_scales(gnntrk_handle* h, const float* alpha, int32_t n) {
+  if (!h || !alpha) return GNNTRK_ERR_INVALID_ARG;
+  if (!h->cfg.embed_int8) return fail(h, GNNTRK_ERR_INVALID_ARG, "the handle has no INT8 embedding");
+  if (n != h->n_embed) return fail(h, GNNTRK_ERR_INVALID_ARG, "n must equal cfg.n_embed_layers");
+  for (int l = 0; l < n; ++l)
+    if (!(alpha[l] > 0.f) || !std::isfinite(alpha[l]))
+      return fail(h, GNNTRK_ERR_INVALID_ARG, "alpha must be positive and finite");
+  // the scales are read by the next launch: wait for work in flight
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+  h->i8_alpha.assign(alpha, alpha + n);
+  return upload_i8_scales(h);
 }
 
 gnntrk_status gnntrk_triplet_stats(gnntrk_handle* h, int64_t* out) {

@@ -228,6 +228,29 @@ void f32_set_variant(int h, int family, int v);
 // connected components
 void launch_cc(const Batch& b, const Ws& w, cudaStream_t s);
 
+// INT8 embedding (post-training quantisation)
+struct Int8Layer {
+  const uint32_t* Wq;  // [out][in16 * 4] weight codes, 4 per word along K, zero padded
+  const float* s;      // [out] dequantisation scale (alpha / 127) S_w
+  const float* b;      // [out] bias
+  int in4, in16, out;  // input words (padded to 1, 2, 4, ..., 64), int4 per row, outputs
+};
+struct Int8Embed {
+  Int8Layer l[kMaxEmbedLayers];
+  const float* inv;  // [n] 127 / alpha of every layer's input
+  int n, max_in4;
+};
+struct EmbedAmax {
+  LayerF32 l[kMaxEmbedLayers];
+  int n;
+};
+void launch_embed_int8(const Batch& b, const Ws& w, const Int8Embed& m, int D,
+                       const GraphParams& g, cudaStream_t s);
+// max calibration over n_hits input hits (device xyz [3][n_hits]); the largest
+// |input| of each embedding layer as float bits in amax_bits[layer]
+void launch_embed_amax(const float* xyz, int n_hits, const EmbedAmax& m, const GraphParams& g,
+                       int32_t* amax_bits, cudaStream_t s);
+
 // triplet stage
 struct TripletHeads {
   Mlp2F32 art, elb;  // articulation and elbow classifiers (2h -> h -> 1)

@@ -1307,11 +1307,12 @@ TcArgs base_args(const Batch& b, const Ws& w, const GraphParams& g) {
 
 void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32* embed_f32,
                   int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool do_embed) {
   // embedding in FP32: its output feeds the threshold d^2 < r^2
   const Sel all{nullptr, nullptr};
-  launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, EdgeProj{}, D, h, g, true, false, all,
-                       s);
+  if (do_embed)
+    launch_node_prep_f32(b, w, embed_f32, n_embed, Mlp2F32{}, EdgeProj{}, D, h, g, true, false,
+                         all, s);
   TcArgs a = base_args(b, w, g);
   a.ne1 = ne1_f32;
   a.W2 = static_cast<const uint8_t*>(m.node_enc.l2.B);

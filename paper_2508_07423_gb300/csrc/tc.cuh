@@ -40,7 +40,7 @@ void tc_triplet_scores(const Batch& b, const Ws& w, const TcModel& m, int h, con
 // w.hstate16.
 void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32* embed_f32,
                   int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
-                  cudaStream_t s);
+                  cudaStream_t s, bool do_embed = true);
 
 // Edge encoder, K message-passing steps and the classifier with the cut;
 // writes w.logit and w.keep. stage < 0 runs everything; otherwise only

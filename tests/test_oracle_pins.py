@@ -416,3 +416,58 @@ def test_e4m3_round_trip_and_rounding():
     assert quant.e4m3_encode(float("nan")) == 0x7F
     # a planted mistake: round half away from zero would give 1.125 here
     assert quant.e4m3_decode(quant.e4m3_encode(1.0625)) == 1.0
+
+
+# ---------------------------------------------------------------------------
+# INT8 embedding (the thesis's post-training quantisation)
+# ---------------------------------------------------------------------------
+def test_int8_layer_exact_on_representable_values():
+    """Inputs that are multiples of S_a and weights that are multiples of their
+    row's S_w quantise without error, so the INT8 layer equals the float
+    product: a dropped or swapped scale, or a transposed weight, fails."""
+    from oracle import quant
+    rng = np.random.default_rng(3)
+    alpha = 2.54
+    sa = np.float32(alpha) / np.float32(127)
+    xq = rng.integers(-127, 128, (20, 12))
+    W = np.zeros((5, 12), np.float32)
+    sw = np.float32([0.01, 0.02, 0.05, 0.1, 0.5]) / np.float32(127)
+    Wq = rng.integers(-126, 127, (5, 12))
+    Wq[:, 0] = 127  # the row maximum fixes S_w exactly
+    W[:] = (Wq * sw[:, None]).astype(np.float32)
+    b = rng.normal(size=5).astype(np.float32)
+    x = (xq * np.float64(sa)).astype(np.float32)
+    codes = quant.int8_codes(x, np.float32(127) / np.float32(alpha))
+    assert np.array_equal(codes, xq)
+    y = quant.int8_layer(codes, alpha, W, b)
+    want = x.astype(np.float64) @ W.T.astype(np.float64) + b
+    assert np.allclose(y, want, rtol=1e-6, atol=1e-6)
+    # saturation: inputs beyond alpha clip to +-127
+    assert list(quant.int8_codes([10.0, -10.0], np.float32(127) / np.float32(alpha))) == [127, -127]
+
+
+def test_int8_embedding_converges_to_float_with_range():
+    """With a calibrated range the INT8 embedding stays within a few code steps
+    of the float64 one; with a range 100x too wide it is far coarser (the
+    thesis's uncalibrated case)."""
+    from oracle import quant
+    wl = synth.workload("cfg3_trained_bf16")
+    arrs = synth.weight_arrays(synth.workload_weights(wl))
+    n_emb = len(wl["model"]["embed"]) - 1
+    layers = arrs[:n_emb]
+    ev = synth.workload_batch(wl, 1)
+    r = np.hypot(ev.x.astype(np.float64), ev.y)
+    feats = np.stack([r / 45.0, np.arctan2(ev.y.astype(np.float64), ev.x) / np.pi, ev.z / 750.0],
+                     1).astype(np.float32)
+    ref = feats.astype(np.float64)
+    for l, (W, b) in enumerate(layers):
+        ref = ref @ W.T.astype(np.float64) + b
+        if l + 1 < n_emb:
+            ref = np.maximum(ref, 0)
+    amax = quant.embed_amax(layers, feats)
+    cal = quant.int8_embed(layers, amax, feats)
+    wide = quant.int8_embed(layers, [100 * a for a in amax], feats)
+    e_cal = np.abs(cal - ref).max()
+    e_wide = np.abs(wide - ref).max()
+    assert e_cal < 0.05 * np.abs(ref).max(), e_cal
+    assert e_wide > 5 * e_cal, (e_wide, e_cal)
