@@ -659,7 +659,7 @@ int64_t orc_build_tracks(int64_t n, int64_t ne, const int32_t* src, const int32_
   for (auto& t : tracks) th += int64_t(t.size());
   *total_hits = th;
   const int64_t nk = int64_t(tracks.size());
-  if (nk <= cap_tracks && th <= cap_hits) {
+  if (track_off && nk <= cap_tracks && th <= cap_hits) {
     int64_t o = 0;
     track_off[0] = 0;
     for (int64_t k = 0; k < nk; ++k) {

@@ -263,8 +263,8 @@ struct TrackOut {
 };
 // triplet lists of the kept edges
 void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s);
-// triplet classifiers (FP32; the final edge encodings in FP32 or BF16)
-void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h, bool bf16,
+// triplet classifiers on the FP32 path (FP32 final edge encodings)
+void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h,
                            float cut_logit, cudaStream_t s);
 // count of the triplets above the cut (after either classifier path)
 void launch_triplet_kept(const Ws& w, cudaStream_t s);

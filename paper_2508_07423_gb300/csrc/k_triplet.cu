@@ -152,10 +152,12 @@ __global__ void k_trip_fill(Batch b, Ws w) {
   }
 }
 
-// ---- 3. triplet classifier ------------------------------------------------------
-// logit = W2 relu(LN(W1 [e1, e2] + b1)) + b2, one thread per triplet, the
-// weights staged in shared memory: W1 transposed [2H][H], b1 [H], W2 [H], b2.
-template <int H, bool BF16IN>
+// ---- 3. triplet classifier (FP32 path) ------------------------------------------
+// logit = W2 relu(LN(W1 [e1, e2] + b1)) + b2 on the FP32 final edge encodings,
+// one thread per triplet, the weights staged in shared memory: W1 transposed
+// [2H][H], b1 [H], W2 [H], b2. (The tensor-core paths score triplets with the
+// k_tc kernels.)
+template <int H>
 __global__ void __launch_bounds__(128) k_trip_score(Ws w, LayerF32 l1, LayerF32 l2,
                                                      const int32_t* e1, const int32_t* e2,
                                                      const int32_t* n_rows, float cut,
@@ -186,20 +188,10 @@ __global__ void __launch_bounds__(128) k_trip_score(Ws w, LayerF32 l1, LayerF32 
 #pragma unroll 1
       for (int k0 = 0; k0 < H; k0 += 8) {
         float x[8];
-        if constexpr (BF16IN) {
-          const uint4 u = *reinterpret_cast<const uint4*>(w.estate16 + size_t(e) * H + k0);
-          const uint32_t q[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            x[2 * j] = __uint_as_float(q[j] << 16);
-            x[2 * j + 1] = __uint_as_float(q[j] & 0xffff0000u);
-          }
-        } else {
-          const float4 a = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0);
-          const float4 c = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0 + 4);
-          x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
-          x[4] = c.x, x[5] = c.y, x[6] = c.z, x[7] = c.w;
-        }
+        const float4 a = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0);
+        const float4 c = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0 + 4);
+        x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
+        x[4] = c.x, x[5] = c.y, x[6] = c.z, x[7] = c.w;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4* wr = reinterpret_cast<const float4*>(sW + size_t(side * H + k0 + j) * H);
@@ -592,28 +584,18 @@ __global__ void k_trip_kept(const uint8_t* ka, const int32_t* na, const uint8_t*
 }
 
 template <int H>
-void score_h(const Ws& w, const TripletHeads& t, bool bf16, float cut, cudaStream_t s) {
+void score_h(const Ws& w, const TripletHeads& t, float cut, cudaStream_t s) {
   const int smem = (2 * H * H + 2 * H + 4) * 4;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_trip_score<H, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_trip_score<H, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_trip_score<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
   const int grid = device_sms() * 4;
-  const int32_t* na = w.counters + C_TRIP_A;
-  const int32_t* ne = w.counters + C_TRIP_E;
-  if (bf16) {
-    k_trip_score<H, true><<<grid, 128, smem, s>>>(w, t.art.l1, t.art.l2, w.trip_a1, w.trip_a2, na,
-                                                  cut, w.trip_alogit, w.trip_akeep);
-    k_trip_score<H, true><<<grid, 128, smem, s>>>(w, t.elb.l1, t.elb.l2, w.trip_e1, w.trip_e2, ne,
-                                                  cut, w.trip_elogit, w.trip_ekeep);
-  } else {
-    k_trip_score<H, false><<<grid, 128, smem, s>>>(w, t.art.l1, t.art.l2, w.trip_a1, w.trip_a2,
-                                                   na, cut, w.trip_alogit, w.trip_akeep);
-    k_trip_score<H, false><<<grid, 128, smem, s>>>(w, t.elb.l1, t.elb.l2, w.trip_e1, w.trip_e2,
-                                                   ne, cut, w.trip_elogit, w.trip_ekeep);
-  }
+  k_trip_score<H><<<grid, 128, smem, s>>>(w, t.art.l1, t.art.l2, w.trip_a1, w.trip_a2,
+                                          w.counters + C_TRIP_A, cut, w.trip_alogit, w.trip_akeep);
+  k_trip_score<H><<<grid, 128, smem, s>>>(w, t.elb.l1, t.elb.l2, w.trip_e1, w.trip_e2,
+                                          w.counters + C_TRIP_E, cut, w.trip_elogit, w.trip_ekeep);
 }
 
 }  // namespace
@@ -629,12 +611,12 @@ void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s) {
   (void)h;
 }
 
-void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h, bool bf16,
+void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h,
                            float cut_logit, cudaStream_t s) {
   (void)b;
-  if (h == 32) score_h<32>(w, t, bf16, cut_logit, s);
-  else if (h == 64) score_h<64>(w, t, bf16, cut_logit, s);
-  else score_h<128>(w, t, bf16, cut_logit, s);
+  if (h == 32) score_h<32>(w, t, cut_logit, s);
+  else if (h == 64) score_h<64>(w, t, cut_logit, s);
+  else score_h<128>(w, t, cut_logit, s);
   launch_triplet_kept(w, s);
 }
 

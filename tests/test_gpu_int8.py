@@ -101,3 +101,34 @@ def test_embed_scales_validation(trained):
     plain = pkg.tracker_for_workload(wl, max_hits=1024, max_events=1)
     with pytest.raises(pkg.GnntrkError):
         plain.set_embed_scales([1.0, 1.0, 1.0])
+
+
+def test_int8_wide_embedding_graph():
+    """The run-3 model's embedding 3-128-128-128-8 (32-word inputs, 8-wide
+    output) in INT8 against the oracle emulation."""
+    wl = synth.workload("cfg2_run3_single")
+    arrs = synth.weight_arrays(synth.workload_weights(wl))
+    layers = arrs[:len(wl["model"]["embed"]) - 1]
+    b = synth.workload_batch(wl, 2)
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=b.n_hits, max_events=b.n_events,
+                                  embed_int8=True, edges_per_hit=32)
+    fs = pkg.feat_scale_of(tr.cfg)
+    alpha = tr.embed_amax(torch.from_numpy(b.xyz_soa()).cuda())
+    assert np.allclose(alpha, quant.embed_amax(layers, feats_of(b, fs)), rtol=2e-5)
+    tr.set_embed_scales(alpha)
+    pkg.run_batch(tr, b)
+    n_edges = n_diff = n_same = 0
+    for e in range(b.n_events):
+        ev = b.event(e)
+        emb = quant.int8_embed(layers, alpha, feats_of(ev, fs))
+        src, dst, d2 = oracle.radius_graph(ev.plane, emb, wl["radius2"], wl["k_max"])
+        g = tr.get_graph(e)
+        O = {(int(a), int(c)): float(d) for a, c, d in zip(src, dst, d2)}
+        G = {(int(a), int(c)): float(d) for a, c, d in zip(g["src"], g["dst"], g["d2"])}
+        n_edges += len(O)
+        n_diff += len(set(O) ^ set(G))
+        for k in set(O) & set(G):
+            n_same += abs(O[k] - G[k]) <= 1e-5 * max(O[k], 0.05)
+    assert n_edges > 1000
+    assert n_diff <= 0.01 * n_edges, (n_diff, n_edges)
+    assert n_same >= 0.99 * (n_edges - n_diff), (n_same, n_edges - n_diff)

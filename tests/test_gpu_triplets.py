@@ -201,3 +201,38 @@ def test_triplets_need_heads_and_flag():
     with pytest.raises(pkg.GnntrkError) as ei:
         pkg.run_batch_triplets(tr, b)
     assert ei.value.status == 1
+
+
+def test_triplets_ragged_and_degenerate_events(cfg6):
+    """Empty, single-hit, one-plane and last-plane-only events, a dense event
+    and a small one in one batch: per event, triplets and tracks against the
+    oracle; events without kept edges have no tracks."""
+    from test_gpu_parity import special_events
+    wl, model = cfg6
+    evs = special_events()
+    b = synth.concat(evs)
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=b.n_hits, max_events=b.n_events)
+    labels, tracks = pkg.run_batch_triplets(tr, b)
+    fs = pkg.feat_scale_of(tr.cfg)
+    assert tracks[0] == [] and tracks[1] == [] and tracks[2] == [] and tracks[3] == []
+    checked = 0
+    for e in range(b.n_events):
+        ev = b.event(e)
+        a = int(b.offsets[e])
+        _, nt, nk = compare_triplet_event(tr, e, ev, tr.get_graph(e), labels[a:a + ev.n_hits],
+                                          tracks[e], model, wl, fs)
+        checked += nk is not None
+    assert checked >= 5
+
+
+def test_triplet_workspace_capacity_latches_and_recovers(cfg6):
+    wl, _ = cfg6
+    b = synth.workload_batch(wl, 2)
+    tr = pkg.tracker_for_workload(wl, precision="fp32", max_hits=b.n_hits, max_events=b.n_events,
+                                  triplets_per_hit=1)
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.run_batch_triplets(tr, b)
+    assert ei.value.status == 4 and "articulations" in str(ei.value)
+    # a call that fits works afterwards
+    small = synth.gen_batch(1, 5, {"kind": "fixed", "n": 3}, 0.0)
+    pkg.run_batch_triplets(tr, small)

@@ -193,3 +193,17 @@ def test_track_building_all_kept_no_forks_equals_components():
     for i, l in enumerate(lab):
         comps.setdefault(int(l), []).append(i)
     assert got == sorted(v for v in comps.values() if len(v) > 1)
+
+
+def test_empty_inputs():
+    """No hits, no edges, no kept edges: no triplets and no tracks."""
+    e = np.zeros(0, np.int32)
+    ty, e1, e2 = oracle.triplets(np.zeros(0, np.uint8), e, e, np.zeros(0, np.uint8))
+    assert len(ty) == 0
+    assert oracle.build_tracks(0, e, e, np.zeros(0, np.uint8), ty, e1, e2,
+                               np.zeros(0, np.uint8)) == []
+    src, dst = np.array([0], np.int32), np.array([1], np.int32)
+    ty, e1, e2 = oracle.triplets(np.array([0, 1], np.uint8), src, dst, np.zeros(1, np.uint8))
+    assert len(ty) == 0
+    assert oracle.build_tracks(2, src, dst, np.zeros(1, np.uint8), ty, e1, e2,
+                               np.zeros(0, np.uint8)) == []
