@@ -719,9 +719,9 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
 def trained_report(pkg, torch, dev, stream, flush, steps=5, sample=100):
     """The headline's 1000 events with trained config-1 weights (the training
     tool's hinge-loss embedding and focal-loss GNN, trained on other events):
-    events/s in BF16 with the FP32 re-score band and in FP32, graph size and
-    band size, and the track metrics of both against the FP64 oracle on the
-    first `sample` events."""
+    events/s in BF16 and FP8 with the FP32 re-score band and in FP32, graph
+    size and band size, and the track metrics of each against the FP64 oracle
+    on the first `sample` events."""
     try:
         import oracle
         from oracle import metrics
@@ -735,9 +735,10 @@ def trained_report(pkg, torch, dev, stream, flush, steps=5, sample=100):
         sub = b.subset(list(range(sample)))
         nh = int(sub.n_hits)
         res = {}
-        for prec in ("bf16", "fp32"):
+        for prec in ("bf16", "fp32", "fp8"):
             tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=N, max_events=n_ev,
-                                          edges_per_hit=16, use_graph=True)
+                                          edges_per_hit=16, use_graph=True,
+                                          **({"rescore_band": 0.02} if prec == "fp8" else {}))
             tuned = tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
             for _ in range(3):
                 tr.find_tracks(n_ev, N, xyz, plane, offs, labels, stream)
@@ -830,9 +831,10 @@ def triplet_report(pkg, torch, dev, stream, flush, steps=5, sample=50):
         sub = b.subset(list(range(sample)))
         nh = int(sub.n_hits)
         res = {}
-        for prec in ("bf16", "fp32"):
+        for prec in ("bf16", "fp32", "fp8"):
             tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=N, max_events=n_ev,
-                                          edges_per_hit=16, use_graph=True)
+                                          edges_per_hit=16, use_graph=True,
+                                          **({"rescore_band": 0.02} if prec == "fp8" else {}))
             tuned = tr.autotune(n_ev, N, xyz, plane, offs, labels, stream)
             for _ in range(3):
                 tr.find_tracks_triplets(n_ev, N, xyz, plane, offs, labels, *outs, stream)

@@ -1178,16 +1178,26 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   // which layers: node enc l2, edge enc l1/l2, per step node l1/l2 edge l1/l2, cls l1
   // (BF16: the node encoder's layer 2 and the edge encoder's layer 1 take
   // split operands, so their images repeat W along K)
+  // (FP8 up to hidden 64: the encoders run as the BF16 split-operand kernels,
+  // whose images are packed in BF16 as well; E4M3 cannot carry the node
+  // encoding the encoders consume)
   struct Item {
     int layer;
     LayerTC* dst;
     bool repeat_k = false;
+    bool bf16 = false;  // a BF16 image on an FP8 handle
   };
   std::vector<Item> items;
   int c = n_embed;
   items.push_back({c + 1, &m.node_enc.l2, !fp8});
   items.push_back({c + 2, &m.edge_enc.l1, !fp8});
   items.push_back({c + 3, &m.edge_enc.l2});
+  m.enc16 = fp8 && h <= 64;
+  if (m.enc16) {
+    items.push_back({c + 1, &m.node_enc16.l2, true, true});
+    items.push_back({c + 2, &m.edge_enc16.l1, true, true});
+    items.push_back({c + 3, &m.edge_enc16.l2, false, true});
+  }
   c += 4;
   for (int k = 0; k < K; ++k) {
     items.push_back({c, &m.node[k].l1});
@@ -1222,9 +1232,9 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
       r2.W.resize(size_t(r2.out) * r2.in);
       for (int n = 0; n < l.out; ++n)
         for (int k = 0; k < r2.in; ++k) r2.W[size_t(n) * r2.in + k] = l.W[size_t(n) * l.in + k % l.in];
-      pack_layer(r2, fp8, img, sc);
+      pack_layer(r2, fp8 && !items[i].bf16, img, sc);
     } else {
-      pack_layer(L[items[i].layer], fp8, img, sc);
+      pack_layer(L[items[i].layer], fp8 && !items[i].bf16, img, sc);
     }
     align(1024);
     off_img[i] = blob.size();
@@ -1315,10 +1325,11 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
                          all, s);
   TcArgs a = base_args(b, w, g);
   a.ne1 = ne1_f32;
-  a.W2 = static_cast<const uint8_t*>(m.node_enc.l2.B);
-  a.b2 = m.node_enc.l2.b;
-  a.s2 = m.node_enc.l2.scale;
-  launch_any(h, m.precision == GNNTRK_FP8_E4M3, M_NODE_ENC, a, s, b.n_hits);
+  const Mlp2TC& ne = m.enc16 ? m.node_enc16 : m.node_enc;
+  a.W2 = static_cast<const uint8_t*>(ne.l2.B);
+  a.b2 = ne.l2.b;
+  a.s2 = ne.l2.scale;
+  launch_any(h, m.precision == GNNTRK_FP8_E4M3 && !m.enc16, M_NODE_ENC, a, s, b.n_hits);
 }
 
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
@@ -1342,8 +1353,13 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
   // stage < 0: everything; otherwise 0 = edge encoder, 1 + 2k = node step k,
   // 2 + 2k = edge step k (with the classifier at the last step)
   if (stage < 0 || stage == 0) {
-    set(m.edge_enc);
-    launch_any(h, fp8, M_EDGE_ENC, a, s, -1);
+    if (m.enc16) {
+      set(m.edge_enc16);
+      launch_any(h, false, M_EDGE_ENC, a, s, -1);
+    } else {
+      set(m.edge_enc);
+      launch_any(h, fp8, M_EDGE_ENC, a, s, -1);
+    }
   }
   for (int k = 0; k < K; ++k) {
     if (stage < 0 || stage == 1 + 2 * k) {

@@ -276,3 +276,33 @@ def test_trained_weights(prec):
     assert o["efficiency"] >= 0.95
     for k in ("efficiency", "ghost_rate", "clone_rate"):
         assert abs(g[k] - o[k]) <= 0.003, (k, g, o)
+
+
+def test_trained_weights_fp8():
+    """FP8-E4M3 steps on trained weights (the encoders run as the BF16
+    split-operand kernels up to hidden 64): keep decisions and track
+    efficiency close to the oracle's."""
+    from oracle import metrics
+    wl = synth.workload("cfg3_trained_bf16")
+    model = model_of(wl)
+    b = synth.workload_batch(wl, 8, first_event=40)
+    tr = pkg.tracker_for_workload(wl, precision="fp8", max_hits=b.n_hits, max_events=b.n_events)
+    fs = pkg.feat_scale_of(tr.cfg)
+    labels = pkg.run_batch(tr, b)
+    agree = union = 0
+    for e in range(b.n_events):
+        ev = b.event(e)
+        ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                       wl["k_max"], wl["cut"], feat_scale=fs)
+        g = tr.get_graph(e)
+        O = {(int(s), int(t)): int(k) for s, t, k in zip(ref.src, ref.dst, ref.keep)}
+        G = {(int(s), int(t)): int(k) for s, t, k in zip(g["src"], g["dst"], g["kept"])}
+        for key in set(O) | set(G):
+            agree += O.get(key, 0) == G.get(key, 0)
+            union += 1
+    assert agree / union >= 0.995, agree / union
+    lab_ref, _ = oracle.find_tracks_batch(model, b.x, b.y, b.z, b.plane, b.offsets, wl["radius2"],
+                                          wl["k_max"], wl["cut"], feat_scale=fs)
+    g = metrics.batch_counts(labels, b.pid, b.offsets).summary()
+    o = metrics.batch_counts(lab_ref, b.pid, b.offsets).summary()
+    assert abs(g["efficiency"] - o["efficiency"]) <= 0.01, (g, o)
