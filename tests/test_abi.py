@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(lib):
     assert declared, "no declarations found"
     missing = [n for n in sorted(declared) if not hasattr(lib, n)]
     assert not missing, missing
-    assert set(pkg.EXPORTS) <= declared
+    assert set(pkg.EXPORTS) == declared, sorted(declared ^ set(pkg.EXPORTS))
 
 
 def test_default_cfg_layout(lib):
@@ -42,6 +42,8 @@ def test_default_cfg_layout(lib):
     assert c.hidden == 32 and c.iters == 4 and c.n_planes == 26 and c.k_max == 64
     assert abs(c.feat_scale[1] - 3.14159265) < 1e-6
     assert c.max_hits == 1 << 20 and c.max_events == 4096 and c.edges_per_hit == 24
+    assert c.triplets == 0 and abs(c.triplet_cut - 0.5) < 1e-7 and c.triplets_per_hit == 16
+    assert c.embed_int8 == 0
 
 
 def test_create_rejects_bad_blob_without_gpu_work(lib):
@@ -74,3 +76,18 @@ def test_host_e4m3_encoder_matches_the_oracle_codec():
     back = pkg.e4m3_decode(codes)
     ok = ~np.isnan(dec)
     assert np.array_equal(back[ok], dec[ok].astype(np.float32)) and np.isnan(back[~ok]).all()
+
+
+def test_triplet_and_int8_arguments_rejected_without_gpu_work(lib):
+    """cfg checks of the triplet stage and the INT8 embedding run before any
+    device call."""
+    from paper_2508_07423_gb300 import synth
+    wl = synth.workload("cfg6_triplets")
+    blob = synth.workload_weights(wl)
+    for field, value in (("triplets", 2), ("triplet_cut", 1.5), ("triplets_per_hit", 0),
+                         ("embed_int8", 3)):
+        c = pkg.make_cfg(wl["model"], wl["radius2"], triplets=True)
+        setattr(c, field, value)
+        with pytest.raises(pkg.GnntrkError) as ei:
+            pkg.Tracker(blob, c)
+        assert ei.value.status == 1, field
