@@ -487,7 +487,8 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
                           h->trip.elb.l1.b, tcut, s);
         launch_triplet_kept(w, s);
       } else {
-        launch_triplet_scores(b, w, h->trip, h->h, tcut, s);
+        launch_triplet_scores_f32(b, w, h->trip, h->h, tcut, s);
+        launch_triplet_kept(w, s);
       }
     });
     stage(h, "track_build", s, 6, [&] { launch_track_build(b, w, h->track_out, s); });

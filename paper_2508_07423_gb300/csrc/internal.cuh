@@ -263,9 +263,10 @@ struct TrackOut {
 };
 // triplet lists of the kept edges
 void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s);
-// triplet classifiers on the FP32 path (FP32 final edge encodings)
-void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h,
-                           float cut_logit, cudaStream_t s);
+// triplet classifiers on the FP32 path (FP32 final edge encodings; the
+// warp-tile FP32 kernels in triplet mode)
+void launch_triplet_scores_f32(const Batch& b, const Ws& w, const TripletHeads& t, int h,
+                               float cut_logit, cudaStream_t s);
 // count of the triplets above the cut (after either classifier path)
 void launch_triplet_kept(const Ws& w, cudaStream_t s);
 // track building into `out`

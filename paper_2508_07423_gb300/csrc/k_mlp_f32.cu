@@ -61,7 +61,7 @@ struct Warps {
 int g_f32_variant[3][3] = {};
 
 enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
-                   G_EDGE_UPD_CLS = 4, G_CLS = 5 };
+                   G_EDGE_UPD_CLS = 4, G_CLS = 5, G_TRIP = 6 };
 
 __device__ __forceinline__ bool input_bad(const Ws& w) {
   return (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) != 0;
@@ -253,6 +253,12 @@ struct GnnArgs {
   int rescore_only;
   float band_lo, band_hi;
   Sel sel;
+  // G_TRIP: one triplet list (its two edges, count on the device) and outputs
+  const int32_t* t1;
+  const int32_t* t2;
+  const int32_t* tn;
+  float* tlogit;
+  uint8_t* tkeep;
 };
 
 template <int H, int MODE>
@@ -293,7 +299,14 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
   const Ws& w = p.w;
   if (input_bad(w)) return;
   int lo, hi;
-  if (!sel_rows(p.b, w, p.sel, EDGE_ROWS, lo, hi)) return;
+  if constexpr (MODE == G_TRIP) {
+    if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_CAPACITY) return;
+    lo = 0;
+    hi = min(*p.tn, int(w.t_cap));
+    if (hi <= 0) return;
+  } else {
+    if (!sel_rows(p.b, w, p.sel, EDGE_ROWS, lo, hi)) return;
+  }
   const int rg = lane >> 3, cg = lane & 7;
   const int E = clamp_edges(w.counters, w.e_cap);
 
@@ -303,8 +316,11 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
       const int pos = base + lane;
       int row = -1, a = 0, c = 0;
       if (pos < hi) {
-        row = sel_row(p.sel, pos);
-        if (EDGE_ROWS) {
+        row = MODE == G_TRIP ? pos : sel_row(p.sel, pos);
+        if (MODE == G_TRIP) {
+          a = p.t1[row];
+          c = p.t2[row];
+        } else if (EDGE_ROWS) {
           a = w.src[row];
           c = w.col[row];
         }
@@ -367,6 +383,32 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
       acc_bias<H>(p.proj.dst.b, cg, acc);
       warp_layer<H, H, H, T::LDH>(Hs, p.proj.dst, 0, rg, cg, acc);
       acc_store_rows<H>(w.pstate, 2 * H, H, rows, rg, cg, acc);
+    } else if constexpr (MODE == G_TRIP) {
+      // ---- triplet classifier: [e^K(first), e^K(second)] -> Linear ->
+      //      LayerNorm -> ReLU -> dot, then the triplet cut -----------------
+      stage_rows<H, false>(As, srcs, w.estate, H, 0, nullptr, nullptr, 0, 0, lane);
+      stage_rows<H, false>(Hs, dsts, w.estate, H, 0, nullptr, nullptr, 0, 0, lane);
+      __syncwarp();
+      acc_bias<H>(p.m.l1.b, cg, acc);
+      warp_layer<H, H, H, LDA>(As, p.m.l1, 0, rg, cg, acc);
+      warp_layer<H, H, H, T::LDH>(Hs, p.m.l1, H, rg, cg, acc);
+      acc_ln_relu<H>(acc);
+      const LayerF32& l2 = p.m.l2;
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        float part = 0.f;
+#pragma unroll
+        for (int j = 0; j < T::NJ; ++j)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            part = fmaf(acc[i][4 * j + u], __ldg(l2.WT + size_t(32 * j + 4 * cg + u) * l2.ldo), part);
+        const float lg = l2.b[0] + row_sum(part);
+        const int row = rows[rg + 4 * i];
+        if (cg == 0 && row >= 0) {
+          p.tlogit[row] = lg;
+          p.tkeep[row] = lg >= p.cut ? 1 : 0;
+        }
+      }
     } else {
       if constexpr (MODE != G_CLS) {
         // ---- layer 1: b + W_e e + (W_src h_src + W_dst h_dst, projected) ----
@@ -689,6 +731,7 @@ void launch_gnn_any(int h, int mode, const GnnArgs& a, int64_t rows_hint, cudaSt
     case G_EDGE_UPD: launch_gnn<HH, G_EDGE_UPD>(a, rows_hint, s); break;            \
     case G_EDGE_UPD_CLS: launch_gnn<HH, G_EDGE_UPD_CLS>(a, rows_hint, s); break;    \
     case G_CLS: launch_gnn<HH, G_CLS>(a, rows_hint, s); break;                      \
+    case G_TRIP: launch_gnn<HH, G_TRIP>(a, rows_hint, s); break;                    \
   }
   if (h == 32) {
     GNNTRK_M(32)
@@ -709,6 +752,29 @@ GnnArgs gnn_args(const Batch& b, const Ws& w, Sel sel) {
 }
 
 }  // namespace
+
+void launch_triplet_scores_f32(const Batch& b, const Ws& w, const TripletHeads& t, int h,
+                               float cut_logit, cudaStream_t s) {
+  GnnArgs a{};
+  a.b = b;
+  a.w = w;
+  a.cut = cut_logit;
+  a.sel = Sel{nullptr, nullptr};
+  a.m = t.art;
+  a.t1 = w.trip_a1;
+  a.t2 = w.trip_a2;
+  a.tn = w.counters + C_TRIP_A;
+  a.tlogit = w.trip_alogit;
+  a.tkeep = w.trip_akeep;
+  launch_gnn_any(h, G_TRIP, a, -1, s);
+  a.m = t.elb;
+  a.t1 = w.trip_e1;
+  a.t2 = w.trip_e2;
+  a.tn = w.counters + C_TRIP_E;
+  a.tlogit = w.trip_elogit;
+  a.tkeep = w.trip_ekeep;
+  launch_gnn_any(h, G_TRIP, a, -1, s);
+}
 
 void f32_set_variant(int h, int family, int v) {
   if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return;

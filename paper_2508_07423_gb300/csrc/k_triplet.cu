@@ -9,6 +9,9 @@
 // to two lists (they take different classifiers); within a list the triplets
 // of hit C are contiguous and C ascends, so each event owns one range of each.
 //
+// The triplet classifiers run on the tensor cores (k_tc, triplet mode) or, on
+// the FP32 path, on the warp-tile FP32 kernels (k_gnn_f32, triplet mode).
+//
 // Track building, per event (one block):
 //   1. kept elbows join their edges into groups (union-find over edge ids);
 //   2. kept articulations link groups; a link g1 -> g2 is shared when g1 links
@@ -149,79 +152,6 @@ __global__ void k_trip_fill(Batch b, Ws w) {
         ++te;
       }
     }
-  }
-}
-
-// ---- 3. triplet classifier (FP32 path) ------------------------------------------
-// logit = W2 relu(LN(W1 [e1, e2] + b1)) + b2 on the FP32 final edge encodings,
-// one thread per triplet, the weights staged in shared memory: W1 transposed
-// [2H][H], b1 [H], W2 [H], b2. (The tensor-core paths score triplets with the
-// k_tc kernels.)
-template <int H>
-__global__ void __launch_bounds__(128) k_trip_score(Ws w, LayerF32 l1, LayerF32 l2,
-                                                     const int32_t* e1, const int32_t* e2,
-                                                     const int32_t* n_rows, float cut,
-                                                     float* logit, uint8_t* keep) {
-  extern __shared__ float4 smem4[];
-  float* sW = reinterpret_cast<float*>(smem4);  // [2H][H]
-  float* sb1 = sW + 2 * H * H;
-  float* sW2 = sb1 + H;
-  if (*(volatile int32_t*)&w.counters[C_STATUS] & (ST_INPUT | ST_CAPACITY)) return;
-  for (int i = threadIdx.x; i < 2 * H * H; i += blockDim.x) {
-    const int k = i / H, o = i % H;
-    sW[i] = l1.WT[size_t(k) * l1.ldo + o];
-  }
-  for (int i = threadIdx.x; i < H; i += blockDim.x) {
-    sb1[i] = l1.b[i];
-    sW2[i] = l2.WT[size_t(i) * l2.ldo];
-  }
-  if (threadIdx.x == 0) sW2[H] = l2.b[0];
-  __syncthreads();
-  const int n = *n_rows;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    float y[H];
-#pragma unroll
-    for (int o = 0; o < H; ++o) y[o] = sb1[o];
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-      const int e = side == 0 ? e1[t] : e2[t];
-#pragma unroll 1
-      for (int k0 = 0; k0 < H; k0 += 8) {
-        float x[8];
-        const float4 a = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0);
-        const float4 c = *reinterpret_cast<const float4*>(w.estate + size_t(e) * H + k0 + 4);
-        x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
-        x[4] = c.x, x[5] = c.y, x[6] = c.z, x[7] = c.w;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4* wr = reinterpret_cast<const float4*>(sW + size_t(side * H + k0 + j) * H);
-#pragma unroll
-          for (int q = 0; q < H / 4; ++q) {
-            const float4 v = wr[q];
-            y[4 * q] = fmaf(x[j], v.x, y[4 * q]);
-            y[4 * q + 1] = fmaf(x[j], v.y, y[4 * q + 1]);
-            y[4 * q + 2] = fmaf(x[j], v.z, y[4 * q + 2]);
-            y[4 * q + 3] = fmaf(x[j], v.w, y[4 * q + 3]);
-          }
-        }
-      }
-    }
-    float s = 0.f;
-#pragma unroll
-    for (int o = 0; o < H; ++o) s += y[o];
-    const float mean = s / float(H);
-    float v = 0.f;
-#pragma unroll
-    for (int o = 0; o < H; ++o) {
-      const float d = y[o] - mean;
-      v = fmaf(d, d, v);
-    }
-    const float inv = 1.0f / sqrtf(v / float(H) + kLnEps);
-    float lg = sW2[H];
-#pragma unroll
-    for (int o = 0; o < H; ++o) lg = fmaf(fmaxf((y[o] - mean) * inv, 0.f), sW2[o], lg);
-    logit[t] = lg;
-    keep[t] = lg >= cut ? 1 : 0;
   }
 }
 
@@ -583,21 +513,6 @@ __global__ void k_trip_kept(const uint8_t* ka, const int32_t* na, const uint8_t*
   if ((threadIdx.x & 31) == 0 && k) atomicAdd(&counters[C_TRIP_KEPT], k);
 }
 
-template <int H>
-void score_h(const Ws& w, const TripletHeads& t, float cut, cudaStream_t s) {
-  const int smem = (2 * H * H + 2 * H + 4) * 4;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_trip_score<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
-  const int grid = device_sms() * 4;
-  k_trip_score<H><<<grid, 128, smem, s>>>(w, t.art.l1, t.art.l2, w.trip_a1, w.trip_a2,
-                                          w.counters + C_TRIP_A, cut, w.trip_alogit, w.trip_akeep);
-  k_trip_score<H><<<grid, 128, smem, s>>>(w, t.elb.l1, t.elb.l2, w.trip_e1, w.trip_e2,
-                                          w.counters + C_TRIP_E, cut, w.trip_elogit, w.trip_ekeep);
-}
-
 }  // namespace
 
 void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s) {
@@ -609,15 +524,6 @@ void launch_triplets(const Batch& b, const Ws& w, int h, cudaStream_t s) {
               w.scan_blocks, s);
   k_trip_fill<<<grid, 256, 0, s>>>(b, w);
   (void)h;
-}
-
-void launch_triplet_scores(const Batch& b, const Ws& w, const TripletHeads& t, int h,
-                           float cut_logit, cudaStream_t s) {
-  (void)b;
-  if (h == 32) score_h<32>(w, t, cut_logit, s);
-  else if (h == 64) score_h<64>(w, t, cut_logit, s);
-  else score_h<128>(w, t, cut_logit, s);
-  launch_triplet_kept(w, s);
 }
 
 void launch_triplet_kept(const Ws& w, cudaStream_t s) {
