@@ -1010,6 +1010,35 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000):
                     res[prec + "_labels0"] = lab.cpu().numpy()
             res[prec] = {"events_per_s": round(n / (ms / 1e3), 1), "ms_per_1000_events": round(ms / len(chunks), 3)}
             tr.close()
+        # FP8 with the FP32 re-score band on the first chunk: events/s and
+        # decisions against FP32 (a wider band trades throughput for agreement)
+        b0 = chunks[0]
+        xyz0 = torch.from_numpy(b0.xyz_soa()).to(dev)
+        plane0 = torch.from_numpy(b0.plane).to(dev)
+        offs0 = torch.from_numpy(b0.offsets).to(dev)
+        lab0 = torch.empty(b0.n_hits, dtype=torch.int32, device=dev)
+        kept32 = np.concatenate([g["kept"] for g in graphs["fp32"]])
+        banded = {}
+        for band in (0.05, 0.1):
+            tr = pkg.tracker_for_workload(wl, precision="fp8", rescore_band=band, max_hits=maxh,
+                                          max_events=chunk, edges_per_hit=16, use_graph=True)
+            tr.find_tracks(b0.n_events, b0.n_hits, xyz0, plane0, offs0, lab0, stream)
+            tr.sync_status(stream)
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                s_.record(stream)
+                tr.find_tracks(b0.n_events, b0.n_hits, xyz0, plane0, offs0, lab0, stream)
+                e_.record(stream)
+            e_.synchronize()
+            tr.sync_status(stream)
+            kb = np.concatenate([tr.get_graph(e)["kept"] for e in range(b0.n_events)])
+            st = tr.stats()
+            banded[f"band_{band}"] = {
+                "events_per_s": round(b0.n_events / (s_.elapsed_time(e_) / 1e3), 1),
+                "edge_decision_agreement_vs_fp32": round(float(np.mean(kb == kept32)), 6),
+                "band_edges": st["band"], "rescore_edges": st["rescore_edges"]}
+            tr.close()
+        res["fp8_with_rescore_first_1000_events"] = banded
         # FP8 vs FP32 on the first chunk (same graph: the embedding is FP32 in both)
         g8, g32 = graphs["fp8"], graphs["fp32"]
         d = np.concatenate([np.abs(1 / (1 + np.exp(-a["logit"].astype(np.float64))) -
@@ -1054,6 +1083,7 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000):
         co = metrics.batch_counts(lab_ref, sub.pid, sub.offsets).summary()
         return {"workload": f"cfg4_batched_fp8: {n} events, {wl['description']}",
                 "fp8": res["fp8"], "fp32": res["fp32"],
+                "fp8_with_rescore_first_1000_events": res["fp8_with_rescore_first_1000_events"],
                 "vs_fp32_first_1000_events": {"max_score_error": round(float(d.max()), 5),
                                               "mean_score_error": round(float(d.mean()), 6),
                                               "edge_decision_agreement": round(float(agree32), 6)},
