@@ -379,9 +379,50 @@ def train_triplets(m, events, fs, r2, k_max, device, epochs=10, lr=2e-3, seed=0)
                           "loss": round(tot / max(len(data), 1), 6)}), flush=True)
 
 
+def train_joint(m, events, fs, r2, k_max, device, epochs=5, lr=5e-4, seed=0):
+    """The GNN and both triplet classifiers together on L = L_edges +
+    L_triplets (the thesis's joint objective), each step taking the triplets
+    of the edges the current model keeps."""
+    torch = _torch()
+    rng = np.random.default_rng(seed)
+    params = [p for g in ("node_enc", "edge_enc", "node", "edge", "cls", "art", "elb")
+              for p in m[g].parameters()]
+    opt = torch.optim.Adam(params, lr=lr)
+    data = []
+    for ev in events:
+        src, dst, node_in = graph(m, ev, fs, r2, k_max, device)
+        if len(src) == 0:
+            continue
+        y = _same_particle(ev, src, dst).astype(np.float32)
+        data.append((ev, src, dst, torch.from_numpy(node_in).to(device),
+                     torch.from_numpy(src).to(device), torch.from_numpy(dst).to(device),
+                     torch.from_numpy(y).to(device)))
+    for ep in range(epochs):
+        tot = 0.0
+        for ei in rng.permutation(len(data)):
+            ev, src, dst, nf, s_, d_, y = data[ei]
+            logit, e = gnn_forward(m, nf, s_, d_, with_states=True)
+            loss = focal_loss(logit, y)
+            kept = np.flatnonzero(logit.detach().cpu().numpy() >= 0.0)
+            T = triplets_of(ev.plane, src, dst, kept)
+            if len(T):
+                ty = torch.from_numpy(triplet_labels(ev, src, dst, T).astype(np.float32)).to(device)
+                Tt = torch.from_numpy(T).to(device)
+                x = torch.cat([e[Tt[:, 1]], e[Tt[:, 2]]], 1)
+                art = Tt[:, 0] == 0
+                lg = torch.where(art, _sub(m["art"], x).squeeze(1), _sub(m["elb"], x).squeeze(1))
+                loss = loss + focal_loss(lg, ty)
+            opt.zero_grad()
+            loss.backward()
+            opt.step()
+            tot += float(loss.detach())
+        print(json.dumps({"stage": "joint", "epoch": ep, "loss": round(tot / max(len(data), 1), 6)}),
+              flush=True)
+
+
 def train(shape: synth.ModelShape, tracks: dict, noise: float, n_events: int, seed: int,
           k_max: int = 64, device=None, emb_epochs=6, gnn_epochs=8, pair_frac: float = 0.0,
-          triplet_epochs: int = 0):
+          triplet_epochs: int = 0, joint_epochs: int = 0):
     """Train a model of `shape` (with triplet classifiers when
     `triplet_epochs` > 0); returns (blob, r2)."""
     torch = _torch()
@@ -396,6 +437,8 @@ def train(shape: synth.ModelShape, tracks: dict, noise: float, n_events: int, se
     train_gnn(m, events, fs, r2, k_max, device, epochs=gnn_epochs, seed=seed)
     if triplet_epochs > 0:
         train_triplets(m, events, fs, r2, k_max, device, epochs=triplet_epochs, seed=seed)
+        if joint_epochs > 0:
+            train_joint(m, events, fs, r2, k_max, device, epochs=joint_epochs, seed=seed)
     return to_blob(m), r2
 
 
@@ -417,19 +460,22 @@ def main():
                    help="close track pairs with shared hits per track (generator option)")
     p.add_argument("--triplet-epochs", type=int, default=0,
                    help="> 0: also train the articulation and elbow classifiers")
+    p.add_argument("--joint-epochs", type=int, default=0,
+                   help="then fine-tune the GNN and the triplet classifiers together")
     a = p.parse_args()
     _torch().use_deterministic_algorithms(True)
     shape = synth.ModelShape([int(v) for v in a.embed.split(",")], a.hidden, a.iters)
     tracks = json.loads(a.tracks)
     blob, r2 = train(shape, tracks, a.noise, a.events, a.seed, device=a.device,
                      emb_epochs=a.emb_epochs, gnn_epochs=a.gnn_epochs, pair_frac=a.pair_frac,
-                     triplet_epochs=a.triplet_epochs)
+                     triplet_epochs=a.triplet_epochs, joint_epochs=a.joint_epochs)
     with open(a.out, "wb") as f:
         f.write(blob)
     meta = {"radius2": r2, "embed": shape.embed, "hidden": a.hidden, "iters": a.iters,
             "train_events": a.events, "train_seed": a.seed, "tracks": tracks, "noise": a.noise,
             "emb_epochs": a.emb_epochs, "gnn_epochs": a.gnn_epochs, "device": a.device,
             "pair_frac": a.pair_frac, "triplet_epochs": a.triplet_epochs,
+            "joint_epochs": a.joint_epochs,
             "radius_quantile_of_genuine_pairs": 0.995}
     with open(a.out.rsplit(".", 1)[0] + ".json", "w") as f:
         json.dump(meta, f, indent=2)
