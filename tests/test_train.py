@@ -94,3 +94,18 @@ def test_shipped_trained_model():
     b = synth.workload_batch(wl, 3)
     s = efficiency(blob, sh, wl["radius2"], b)
     assert s["efficiency"] >= 0.95 and s["ghost_rate"] <= 0.03, s
+
+
+def test_triplet_heads_and_joint_training_produce_a_loadable_blob():
+    """Triplet-head training and the joint edge + triplet fine-tuning run on a
+    few events with close pairs, and the blob carries both classifiers the
+    oracle's triplet stage reads."""
+    shape = synth.ModelShape([3, 16, 4], 16, 1)
+    tracks = {"kind": "fixed", "n": 20}
+    blob, r2 = train.train(shape, tracks, 0.05, 6, 31, device="cpu", emb_epochs=2, gnn_epochs=2,
+                           pair_frac=0.2, triplet_epochs=1, joint_epochs=1)
+    assert len(synth.weight_arrays(blob)) == len(shape.layers) + 4
+    m = oracle.Model(blob, shape.embed, shape.hidden, shape.iters)
+    ev = synth.gen_batch(1, 32, tracks, 0.05, pair_frac=0.2)
+    r = oracle.find_tracks_triplets_event(m, ev.x, ev.y, ev.z, ev.plane, r2, 64)
+    assert len(r.tlogit) == len(r.ttype) and np.all(np.isfinite(r.tlogit))
