@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--profile-case", default=None,
+                   choices=["headline_300ev_bf16", "headline_300ev_fp32", "triplets_int8_100ev"],
+                   help="run one small case for a profiler capture (no timing, no JSON line)")
     p.add_argument("--study", default=None, choices=["occupancy"],
                    help="occupancy: throughput per event-size bin instead of the headline")
     return p.parse_args()
@@ -260,6 +263,9 @@ def main():
 
     import torch
     import paper_2508_07423_gb300 as pkg
+
+    if a.profile_case:
+        return profile_case(a.profile_case, pkg, torch)
 
     if a.study == "occupancy":
         torch.cuda.set_device(local)
@@ -1098,6 +1104,44 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000):
     except Exception as ex:  # reported, not fatal
         import traceback
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
+
+
+def profile_case(name, pkg, torch):
+    """Small fixed cases for kernel captures (ncu): the first 300 events of the
+    headline batch (three calls, BF16 + FP32 re-score band 0.02, or FP32), or
+    one triplet-stage call on 100 events of the triplet workload followed by
+    the INT8 embedding (calibrated on the same 100 events) of the trained
+    workload."""
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if name.startswith("headline_300ev"):
+        prec = name.rsplit("_", 1)[1]
+        wl = synth.workload("cfg3_batched_bf16")
+        b = synth.workload_batch(wl, 300)
+        tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events,
+                                      edges_per_hit=16,
+                                      **({"rescore_band": 0.02} if prec != "fp32" else {}))
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        lab = torch.zeros(b.n_hits, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab)
+        tr.sync_status()
+        print(name, tr.stats(), tr.rescore_rows())
+        return
+    wl = synth.workload("cfg6_triplets")
+    b = synth.workload_batch(wl, 100)
+    tr = pkg.tracker_for_workload(wl, max_hits=b.n_hits, max_events=b.n_events)
+    pkg.run_batch_triplets(tr, b)
+    print(name, "triplets", tr.triplet_stats())
+    tr.close()
+    wl3 = synth.workload("cfg3_trained_bf16")
+    b3 = synth.workload_batch(wl3, 100)
+    t3 = pkg.tracker_for_workload(wl3, max_hits=b3.n_hits, max_events=b3.n_events, embed_int8=True)
+    t3.set_embed_scales(t3.embed_amax(torch.from_numpy(b3.xyz_soa()).to(dev)))
+    pkg.run_batch(t3, b3)
+    print(name, "int8 edges", t3.stats()["edges"])
 
 
 def run_reference(a, rank, world):
