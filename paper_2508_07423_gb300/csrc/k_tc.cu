@@ -94,7 +94,11 @@ struct Layout {
   // The encoders see hit coordinates, whose useful precision (a 12 um
   // resolution over a 45 mm radius) is finer than BF16's 8-bit mantissa.
   static constexpr bool SPLIT = !FP8 && (MODE == M_NODE_ENC || MODE == M_EDGE_ENC);
-  static constexpr int K1 = (MODE == M_NODE_ENC) ? H : (SPLIT ? 2 : 1) * NSEG * H;
+  // at hidden 128 the split edge encoder runs layer 1 in two passes over one
+  // [h_src, h_dst] tile (hi parts, then lo parts accumulated into the same
+  // tensor memory) against the plain weight image, so it fits shared memory
+  static constexpr bool SPLIT2 = SPLIT && MODE == M_EDGE_ENC && H > 64;
+  static constexpr int K1 = (MODE == M_NODE_ENC) ? H : (SPLIT && !SPLIT2 ? 2 : 1) * NSEG * H;
   static constexpr int K2 = (SPLIT && MODE == M_NODE_ENC) ? 2 * H : H;
   static constexpr bool HAS_W1 = MODE != M_NODE_ENC;
   static constexpr bool HAS_W2 = MODE != M_CLS && MODE != M_TRIP;
@@ -248,6 +252,26 @@ __device__ __forceinline__ void put_row_f32_split(uint8_t* tile, int row, int kc
   }
 }
 
+// One FP32 row of H values into a BF16 tile at element k0: its hi parts
+// bf16(v) (lo = false) or its lo parts bf16(v - bf16(v)) (lo = true).
+template <int H>
+__device__ __forceinline__ void put_row_f32_part(uint8_t* tile, int row, int kchunks, int k0,
+                                                 const float* src, bool lo) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int c = 0; c < H / 8; ++c) {
+    const float4 a = s4[2 * c], b = s4[2 * c + 1];
+    float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    if (lo) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] -= __bfloat162float(__float2bfloat16_rn(v[j]));
+    }
+    *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 3) + c, kchunks)) =
+        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                   pack_bf16(v[6], v[7]));
+  }
+}
+
 template <int H>
 __device__ __forceinline__ void add_bf16_row(float* acc, const __nv_bfloat16* src) {
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
@@ -295,7 +319,7 @@ __device__ __forceinline__ void add_params(const float (&v)[32], const float* b,
 // (H columns of K) accumulates into TMEM columns [s*H, (s+1)*H).
 template <int H, bool FP8>
 __device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, const uint8_t* W,
-                                            int K, int nseg_sep) {
+                                            int K, int nseg_sep, bool accumulate = false) {
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int KSTEP = FP8 ? 32 : 16;
   constexpr uint32_t IDESC = FP8 ? idesc_e4m3(kRows, H) : idesc_bf16(kRows, H);
@@ -309,7 +333,7 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, con
     const uint64_t ad = smem_desc(a0 + byte_k, 128, sbo);
     const uint64_t bd = smem_desc(w0 + byte_k, 128, sbo);
     const uint32_t d = tmem + uint32_t(nseg_sep > 1 ? seg * H : 0);
-    const uint32_t acc = (k % seg_len) != 0;
+    const uint32_t acc = accumulate || (k % seg_len) != 0;
     if constexpr (FP8)
       mma_e4m3(d, ad, bd, IDESC, acc);
     else
@@ -579,7 +603,11 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
                                        (H <= 64 && MODE != M_CLS) ? keep_row : nullptr);
           seg = 1;
         }
-        if constexpr (L::SPLIT) {
+        if constexpr (L::SPLIT2) {
+          // pass 1: [hi(h_src), hi(h_dst)] (the lo parts follow after the MMA)
+          put_row_f32_part<H>(sA, tid, KCH1, 0, w.hstate + size_t(w.src[r]) * H, false);
+          put_row_f32_part<H>(sA, tid, KCH1, H, w.hstate + size_t(w.col[r]) * H, false);
+        } else if constexpr (L::SPLIT) {
           // [hi(h_src), hi(h_dst), lo(h_src), lo(h_dst)] from the FP32 encodings
           put_row_f32_split<H>(sA, tid, KCH1, 0, 2 * H, w.hstate + size_t(w.src[r]) * H);
           put_row_f32_split<H>(sA, tid, KCH1, H, 3 * H, w.hstate + size_t(w.col[r]) * H);
@@ -609,6 +637,25 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       if (!wait_mma()) {
         aborted = true;
         break;
+      }
+      if constexpr (L::SPLIT2) {
+        // pass 2: [lo(h_src), lo(h_dst)] into the same tile, accumulated
+        if (valid) {
+          put_row_f32_part<H>(sA, tid, KCH1, 0, w.hstate + size_t(w.src[r]) * H, true);
+          put_row_f32_part<H>(sA, tid, KCH1, H, w.hstate + size_t(w.col[r]) * H, true);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          issue_layer<H, FP8>(tmem_base, sA, sW1, K1, 1, true);
+          mma_commit(&bar[1]);
+        }
+        if (!wait_mma()) {
+          aborted = true;
+          break;
+        }
       }
       if constexpr (L::PIPE && L::HA == L::A) {
         // the hidden tile overwrites the layer-1 input: keep this row's
@@ -1178,9 +1225,9 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   // which layers: node enc l2, edge enc l1/l2, per step node l1/l2 edge l1/l2, cls l1
   // (BF16: the node encoder's layer 2 and the edge encoder's layer 1 take
   // split operands, so their images repeat W along K)
-  // (FP8 up to hidden 64: the encoders run as the BF16 split-operand kernels,
-  // whose images are packed in BF16 as well; E4M3 cannot carry the node
-  // encoding the encoders consume)
+  // (FP8: the encoders run as the BF16 split-operand kernels, whose images
+  // are packed in BF16 as well; E4M3 cannot carry the node encoding the
+  // encoders consume)
   struct Item {
     int layer;
     LayerTC* dst;
@@ -1192,10 +1239,10 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
   items.push_back({c + 1, &m.node_enc.l2, !fp8});
   items.push_back({c + 2, &m.edge_enc.l1, !fp8});
   items.push_back({c + 3, &m.edge_enc.l2});
-  m.enc16 = fp8 && h <= 64;
+  m.enc16 = fp8;
   if (m.enc16) {
     items.push_back({c + 1, &m.node_enc16.l2, true, true});
-    items.push_back({c + 2, &m.edge_enc16.l1, true, true});
+    items.push_back({c + 2, &m.edge_enc16.l1, h <= 64, true});  // h 128: two passes, plain image
     items.push_back({c + 3, &m.edge_enc16.l2, false, true});
   }
   c += 4;
@@ -1211,12 +1258,15 @@ int tc_upload(TcModel& m, const HostLayer* L, int n_layers, int n_embed, int h, 
     err = "tensor-core packing: unexpected layer count";
     return GNNTRK_ERR_WEIGHTS;
   }
-  // shared-memory budget of the largest kernel
-  for (int mode : {M_EDGE_UPD, M_NODE_UPD, M_EDGE_ENC, M_NODE_ENC})
-    if ((fp8 ? smem_total<true>(h, mode) : smem_total<false>(h, mode)) > kMaxSmem) {
+  // shared-memory budget of the largest kernel (FP8: its encoders are BF16)
+  for (int mode : {M_EDGE_UPD, M_NODE_UPD, M_EDGE_ENC, M_NODE_ENC}) {
+    const bool enc = mode == M_EDGE_ENC || mode == M_NODE_ENC;
+    const bool as_fp8 = fp8 && !(enc && m.enc16);
+    if ((as_fp8 ? smem_total<true>(h, mode) : smem_total<false>(h, mode)) > kMaxSmem) {
       err = "tensor-core kernels do not fit shared memory at this hidden size";
       return GNNTRK_ERR_UNSUPPORTED;
     }
+  }
   std::vector<uint8_t> blob;
   std::vector<size_t> off_img(items.size()), off_b(items.size()), off_s(items.size());
   auto align = [&](size_t a) { blob.resize((blob.size() + a - 1) / a * a, 0); };

@@ -12,8 +12,9 @@ struct TcModel {
   int h = 0, K = 0, n_embed = 0;
   LayerTC embed[kMaxEmbedLayers]{};
   Mlp2TC node_enc{}, edge_enc{}, cls{}, node[kMaxIters]{}, edge[kMaxIters]{};
-  // FP8 up to hidden 64: BF16 split-operand encoders (node_enc16.l2,
-  // edge_enc16.l1 and .l2 hold BF16 images)
+  // FP8: BF16 split-operand encoders (node_enc16.l2, edge_enc16.l1 and .l2
+  // hold BF16 images; edge_enc16.l1 repeated along K up to hidden 64, plain at
+  // 128 where the edge encoder runs its layer 1 in two passes)
   Mlp2TC node_enc16{}, edge_enc16{};
   bool enc16 = false;
   // first layers of the triplet classifiers (BF16 images in every precision)
