@@ -876,7 +876,24 @@ def triplet_report(pkg, torch, dev, stream, flush, steps=5, sample=50):
                                             stream, flush, steps)))
             base.close()
             rnd = lambda d: {k: round(v, 6) if isinstance(v, float) else v for k, v in d.items()}
+            # roofline of the triplet classifiers: tensor cores gather two BF16
+            # e^K rows per triplet (HBM-bound); FP32 warp tiles do 2(2h^2 + h)
+            # flop per triplet (ALU-bound)
+            h = wl["model"]["hidden"]
+            n_t = ts["articulations"] + ts["elbows"]
+            t_ms = stages["triplet_scores"][0] / steps if "triplet_scores" in stages else 0.0
+            pk = peaks()
+            if prec == "fp32":
+                ach = n_t * 2.0 * (2 * h * h + h) / (t_ms / 1e3) / 1e12 if t_ms else 0.0
+                peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+                roof = {"bound": "alu", "achieved": round(ach, 2), "unit": "TFLOP/s",
+                        "peak": round(peak, 2), "frac": round(ach / peak, 4)}
+            else:
+                ach = n_t * (2 * h * 2 + 8 + 5) / (t_ms / 1e3) / 1e9 if t_ms else 0.0
+                roof = {"bound": "hbm", "achieved": round(ach, 1), "unit": "GB/s",
+                        "peak": pk["hbm_gbs"], "frac": round(ach / pk["hbm_gbs"], 4)}
             res[prec] = {
+                "triplet_classifier_roofline": roof,
                 "events_per_s_with_triplets": round(n_ev / (ms / 1e3), 1),
                 "events_per_s_without": round(n_ev / (ms0 / 1e3), 1),
                 "ms_per_step": round(ms, 4), "ms_per_step_without": round(ms0, 4),

@@ -14,8 +14,10 @@ examples and brute force (see tests/test_oracle_pins.py; the triplet stage in
 tests/test_oracle_triplets.py: triplets against a brute-force pair
 enumeration, the classifiers' operand order and routing tied to the edge
 classifier, track building on hand-worked graphs including a shared-hit pair). The composition of
-the steps into the whole pipeline has no external pin of its own (parity
-unpinned beyond the per-step pins).
+the steps into the whole pipeline is pinned by a hand-built event
+(tests/golden/pipeline_hand.json: identity embedding, straight lines with
+gaps of one and two planes, a constant classifier on either side of the cut)
+whose edge set and candidates are worked out by hand.
 """
 from __future__ import annotations
 

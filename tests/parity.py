@@ -9,7 +9,7 @@ from scipy.sparse.csgraph import connected_components
 
 import oracle
 
-# spec tolerances: scores within 1e-4 absolute; edge sets identical except
+# parity tolerances: scores within 1e-4 absolute; edge sets identical except
 # pairs whose embedding distance lies within 1e-5 relative of the radius (or of
 # the k_max-th distance of a capped row)
 SCORE_TOL = 1e-4
@@ -124,3 +124,56 @@ def compare_event(ev, g, labels, model, r2, k_max, iters, cut=0.5, feat_scale=No
         rep.labels_equal = bool(np.array_equal(labels, ref.labels))
         assert rep.labels_equal, "labels differ from the oracle for the same kept edges"
     return rep
+
+
+# ----------------------------------------------------------------------------
+# the hand-built whole-pipeline event (tests/golden/pipeline_hand.json)
+# ----------------------------------------------------------------------------
+def hand_pipeline():
+    """(fixture, x, y, z, plane, index of each hit name) of the hand-built event."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pipeline_hand.json")) as f:
+        g = json.load(f)
+    z0, dz = g["z_of_plane_mm"]
+    phi = np.array([h[1] for h in g["hits"]])
+    r = np.array([h[2] for h in g["hits"]])
+    plane = np.array([h[3] for h in g["hits"]], np.uint8)
+    x = (r * np.cos(phi)).astype(np.float32)
+    y = (r * np.sin(phi)).astype(np.float32)
+    z = (z0 + dz * plane.astype(np.float64)).astype(np.float32)
+    idx = {h[0]: i for i, h in enumerate(g["hits"])}
+    return g, x, y, z, plane, idx
+
+
+def hand_pipeline_blob(h: int, K: int, bias: float, seed: int = 0) -> bytes:
+    """Weights of the hand-built event: identity embedding 3 -> 4 -> 4 (the
+    features and a zero coordinate), a random interaction network of width h
+    and K steps, and a classifier whose last layer is zero with bias `bias`."""
+    from paper_2508_07423_gb300 import synth
+    rng = np.random.default_rng(seed)
+
+    def rnd(o, i):
+        b = math.sqrt(6.0 / i)
+        return (rng.uniform(-b, b, (o, i)).astype(np.float32),
+                rng.uniform(-0.3, 0.3, o).astype(np.float32))
+    W1 = np.zeros((4, 3), np.float32)
+    W1[:3, :3] = np.eye(3)
+    layers = [(W1, np.zeros(4, np.float32)), (np.eye(4, dtype=np.float32), np.zeros(4, np.float32))]
+    layers += [rnd(h, 3), rnd(h, h), rnd(h, 2 * h), rnd(h, h)]
+    for _ in range(K):
+        layers += [rnd(h, 3 * h), rnd(h, h), rnd(h, 3 * h), rnd(h, h)]
+    layers += [rnd(h, h), (np.zeros((1, h), np.float32), np.array([bias], np.float32))]
+    return synth.pack_weights(layers)
+
+
+def hand_pipeline_labels(g, idx, keep_all: bool) -> np.ndarray:
+    """Expected canonical labels: the smallest input index of each hand-listed
+    candidate (every hit alone when no edge is kept)."""
+    n = len(idx)
+    lab = np.arange(n, dtype=np.int32)
+    if keep_all:
+        for group in g["candidates_keep_all"]:
+            ids = [idx[nm] for nm in group]
+            lab[ids] = min(ids)
+    return lab

@@ -306,3 +306,33 @@ def test_trained_weights_fp8():
     g = metrics.batch_counts(labels, b.pid, b.offsets).summary()
     o = metrics.batch_counts(lab_ref, b.pid, b.offsets).summary()
     assert abs(g["efficiency"] - o["efficiency"]) <= 0.01, (g, o)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_hand_built_event(prec):
+    """The hand-built event of tests/golden/pipeline_hand.json, three copies in
+    one batch: the edge set, the constant logit and the candidates the fixture
+    works out by hand, for a score cut that keeps every edge and one that keeps
+    none."""
+    from parity import hand_pipeline, hand_pipeline_blob, hand_pipeline_labels
+    g, x, y, z, plane, idx = hand_pipeline()
+    n = len(x)
+    reps = 3
+    b = synth.Batch(np.tile(x, reps), np.tile(y, reps), np.tile(z, reps), np.tile(plane, reps),
+                    np.zeros(n * reps, np.int32), np.arange(reps + 1, dtype=np.int64) * n)
+    blob = hand_pipeline_blob(32, 2, g["classifier_bias"])
+    want_edges = {(idx[a], idx[c]) for a, c in g["edges"]}
+    for cut, keep_all in ((g["cut_keep_all"], True), (g["cut_keep_none"], False)):
+        cfg = pkg.make_cfg({"embed": [3, 4, 4], "hidden": 32, "iters": 2}, g["r2"],
+                           k_max=g["k_max"], score_cut=cut, precision=prec,
+                           max_hits=4096, max_events=8)
+        tr = pkg.Tracker(blob, cfg)
+        labels = pkg.run_batch(tr, b)
+        want = hand_pipeline_labels(g, idx, keep_all)
+        for e in range(reps):
+            assert np.array_equal(labels[e * n:(e + 1) * n], want)
+            gr = tr.get_graph(e)
+            assert {(int(s), int(d)) for s, d in zip(gr["src"], gr["dst"])} == want_edges
+            assert np.all(gr["logit"] == np.float32(g["classifier_bias"]))
+            assert np.all(gr["kept"] == (1 if keep_all else 0))
+        tr.close()

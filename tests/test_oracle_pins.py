@@ -323,6 +323,23 @@ def test_pipeline_is_composition_of_steps():
     assert 6 < deg < 24
 
 
+def test_pipeline_hand_built_event():
+    """The whole pipeline on the hand-built event of
+    tests/golden/pipeline_hand.json: identity embedding, rough graph over
+    planes p+1 and p+2, constant logit 0.5, the score cut, components. Edge
+    set, logits, decisions and candidates are those worked out by hand."""
+    from parity import hand_pipeline, hand_pipeline_blob, hand_pipeline_labels
+    g, x, y, z, plane, idx = hand_pipeline()
+    m = oracle.Model(hand_pipeline_blob(8, 2, g["classifier_bias"]), [3, 4, 4], 8, 2)
+    want_edges = {(idx[a], idx[b]) for a, b in g["edges"]}
+    for cut, keep_all in ((g["cut_keep_all"], True), (g["cut_keep_none"], False)):
+        r = oracle.find_tracks_event(m, x, y, z, plane, g["r2"], g["k_max"], cut=cut)
+        assert edge_set(r.src, r.dst) == want_edges
+        assert np.all(r.logit == g["classifier_bias"])
+        assert np.all(r.keep == (1 if keep_all else 0))
+        assert np.array_equal(r.labels, hand_pipeline_labels(g, idx, keep_all))
+
+
 def test_batch_matches_events_and_threads():
     wl = synth.workload("cfg1_plain_fp32")
     sh = synth.shape_of(wl)
