@@ -364,6 +364,19 @@ def test_metrics_hand_worked():
         assert got[k] == pytest.approx(v), k
 
 
+def test_metrics_shared_hits_and_overlapping_tracks():
+    g = gold("metrics_shared_hand.json")
+    got = metrics.track_counts(g["tracks"], g["pid"], g["pid2"]).summary()
+    for k, v in g["expected"].items():
+        assert got[k] == pytest.approx(v, abs=1e-12), k
+    # the per-event wrapper over a batch of two copies gives the same ratios
+    n = len(g["pid"])
+    tot = metrics.batch_track_counts([g["tracks"], g["tracks"]], g["pid"] * 2, [0, n, 2 * n],
+                                     pid2=g["pid2"] * 2).summary()
+    for k in ("efficiency", "ghost_rate", "clone_rate", "hit_purity", "hit_efficiency"):
+        assert tot[k] == pytest.approx(g["expected"][k], abs=1e-12), k
+
+
 def test_metrics_perfect_tracks():
     # labels equal to the truth: efficiency 1, no ghosts, no clones
     pid = [0, 0, 0, 1, 1, 1, 1, 2, 2, -1]
