@@ -358,8 +358,8 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
  *     by the shared memory, registers and tensor-memory columns each CTA needs;
  *     choice[0..3] = node encoder, edge encoder, node step, edge step;
  *   - FP32 SIMT kernels (FP32 handles, and the FP32 re-score of BF16/FP8 handles
- *     with a re-score band): tile-shape variant 0 or 1 (rows per tile, threads,
- *     columns per thread); choice[4..6] = encoders, node step, edge step.
+ *     with a re-score band): tile-shape variant 0 (4 warps per block) or 1
+ *     (8 warps per block); choice[4..6] = encoders, node step, edge step.
  * The fastest setting of each family is kept and applies to every handle of
  * the process with the same precision and hidden width. choice: host int32 [8]
  * or NULL (entry 7 is 0). Synchronous. Errors: as gnntrk_find_tracks and
@@ -369,6 +369,21 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
                               const float* hits_xyz, const uint8_t* plane,
                               const int64_t* offsets, int32_t* out_labels, void* stream,
                               int32_t* choice);
+
+/*
+ * Applies a launch configuration without timing anything, e.g. the choice a
+ * previous gnntrk_autotune returned (saved by the caller): choice[0..3] =
+ * resident CTAs per SM of the tensor-core families (0 = the resource bound;
+ * ignored by FP32 handles; capped by the resources each CTA needs),
+ * choice[4..6] = FP32 tile variant 0 or 1 of the encoders, node step and edge
+ * step; entry 7 is ignored. Like the autotuner's result it applies to every
+ * handle of the process with the same precision and hidden width, and drops
+ * the handle's captured CUDA graphs. Results do not depend on the choice: a
+ * row's arithmetic is the same in every variant. choice: host int32 [8].
+ * Errors: GNNTRK_ERR_INVALID_ARG (NULL handle or choice, an entry out of
+ * range; nothing is changed then). No GPU work.
+ */
+gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice);
 
 /*
  * Device memory a handle created with `cfg` allocates (weights and workspace),

@@ -26,7 +26,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
-           "gnntrk_autotune", "gnntrk_rescore_rows", "gnntrk_e4m3_encode", "gnntrk_e4m3_decode",
+           "gnntrk_autotune", "gnntrk_set_tuning", "gnntrk_rescore_rows", "gnntrk_e4m3_encode",
+           "gnntrk_e4m3_decode",
            "gnntrk_find_tracks_triplets", "gnntrk_triplet_stats", "gnntrk_get_triplets",
            "gnntrk_embed_amax", "gnntrk_set_embed_scales",
            "gnntrk_last_error", "gnntrk_destroy"]
@@ -115,6 +116,8 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_components_noalloc.restype = st
     L.gnntrk_autotune.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, vp]
     L.gnntrk_autotune.restype = st
+    L.gnntrk_set_tuning.argtypes = [vp, vp]
+    L.gnntrk_set_tuning.restype = st
     L.gnntrk_workspace_bytes.argtypes = [ctypes.POINTER(Cfg)]
     L.gnntrk_workspace_bytes.restype = i64
     L.gnntrk_serve_run.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(Cfg),
@@ -318,6 +321,15 @@ class Tracker:
                 "tc_node_update": int(ch[2]), "tc_edge_update": int(ch[3]),
                 "f32_encoders": int(ch[4]), "f32_node_update": int(ch[5]),
                 "f32_edge_update": int(ch[6])}
+
+    def set_tuning(self, choice: dict):
+        """Apply a launch configuration (the dict autotune returns) without timing."""
+        keys = ("tc_node_prep", "tc_edge_encoder", "tc_node_update", "tc_edge_update",
+                "f32_encoders", "f32_node_update", "f32_edge_update")
+        ch = np.zeros(8, np.int32)
+        for i, k in enumerate(keys):
+            ch[i] = int(choice.get(k, 0))
+        self._check(self._L.gnntrk_set_tuning(self._h, ch.ctypes.data_as(ctypes.c_void_p)))
 
     def set_profiling(self, enable: bool):
         self._check(self._L.gnntrk_set_profiling(self._h, int(bool(enable))))

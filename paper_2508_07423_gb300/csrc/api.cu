@@ -1043,6 +1043,25 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
   return st;
 }
 
+gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  if (!choice) return fail(h, GNNTRK_ERR_INVALID_ARG, "choice is NULL");
+  for (int f = 0; f < 4; ++f)
+    if (choice[f] < 0 || choice[f] > 8)
+      return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[0..3] must be 0..8 CTAs per SM");
+  for (int f = 4; f < 7; ++f)
+    if (choice[f] < 0 || choice[f] > 1)
+      return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[4..6] must be an FP32 variant 0 or 1");
+  const int prec = h->cfg.precision, hd = h->h;
+  if (prec != GNNTRK_FP32)
+    for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, choice[f]);
+  for (int f = 0; f < 3; ++f) f32_set_variant(hd, f, choice[4 + f]);
+  // captured graphs hold the old launch configuration
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
+  return GNNTRK_OK;
+}
+
 gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream) {
   if (!h) return GNNTRK_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));

@@ -91,3 +91,10 @@ def test_triplet_and_int8_arguments_rejected_without_gpu_work(lib):
         with pytest.raises(pkg.GnntrkError) as ei:
             pkg.Tracker(blob, c)
         assert ei.value.status == 1, field
+
+
+def test_set_tuning_null_arguments_rejected_without_gpu_work(lib):
+    import ctypes
+    ch = (ctypes.c_int32 * 8)()
+    assert lib.gnntrk_set_tuning(None, ch) == 1
+    assert lib.gnntrk_set_tuning(None, None) == 1

@@ -253,10 +253,57 @@ def test_autotune_picks_a_count_and_keeps_results():
     g = tr.get_graph(5)
     for k in g:
         assert np.array_equal(g[k], g0[5][k]), k
+    # the choice re-applied without timing gives the same results again
+    tr.set_tuning(choice)
+    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, labels)
+    tr.sync_status()
+    assert np.array_equal(labels.cpu().numpy(), lab0)
+    # restore the default launch configuration for the other tests of this process
+    tr.set_tuning({})
     tr.close()
-    # restore the resource-bound default for the other tests of this process
-    lib = pkg.load_library()
-    del lib
+
+
+@pytest.mark.parametrize("name,prec", [("cfg1_plain_fp32", "fp32"), ("cfg2_run3_single", "fp32"),
+                                       ("cfg4_batched_fp8", "fp32"), ("cfg3_batched_bf16", "bf16"),
+                                       ("cfg4_batched_fp8", "fp8")])
+def test_fp32_tile_variants_give_identical_results(name, prec):
+    """Every FP32 tile variant (warps per block) computes each
+    row with the same arithmetic: labels, graphs and logits are bit-identical
+    across variants, for the FP32 path and for the FP32 re-score of the
+    tensor-core paths, at hidden 32, 64 and 128."""
+    wl = synth.workload(name)
+    b = synth.workload_batch(wl, 3)
+    band = 0.02 if prec != "fp32" else 0.0
+    tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=band, max_hits=b.n_hits,
+                                  max_events=b.n_events, edges_per_hit=32)
+    ref = None
+    try:
+        for v in (0, 1):
+            tr.set_tuning({"f32_encoders": v, "f32_node_update": v, "f32_edge_update": v})
+            labels = pkg.run_batch(tr, b)
+            graphs = [tr.get_graph(e) for e in range(b.n_events)]
+            if ref is None:
+                ref = (labels, graphs)
+                if prec != "fp32":
+                    assert tr.stats()["band"] > 0
+                continue
+            assert np.array_equal(labels, ref[0]), v
+            for e in range(b.n_events):
+                for k in graphs[e]:
+                    assert np.array_equal(graphs[e][k], ref[1][e][k]), (v, e, k)
+    finally:
+        tr.set_tuning({})
+        tr.close()
+
+
+def test_set_tuning_rejects_out_of_range_choices():
+    wl = synth.workload("cfg1_plain_fp32")
+    tr = pkg.tracker_for_workload(wl, max_hits=1024, max_events=2)
+    for bad in ({"f32_edge_update": 2}, {"tc_edge_update": 9}, {"f32_encoders": -1}):
+        with pytest.raises(pkg.GnntrkError):
+            tr.set_tuning(bad)
+    tr.set_tuning({})
+    tr.close()
 
 
 def test_device_e4m3_conversion_matches_the_oracle_codec():
