@@ -378,7 +378,8 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
  * choice[4..6] = FP32 tile variant 0 or 1 of the encoders, node step and edge
  * step; entry 7 is ignored. Like the autotuner's result it applies to every
  * handle of the process with the same precision and hidden width, and drops
- * the handle's captured CUDA graphs. Results do not depend on the choice: a
+ * this handle's captured CUDA graphs (another handle's graphs keep the launch
+ * shapes they were captured with). Results do not depend on the choice: a
  * row's arithmetic is the same in every variant. choice: host int32 [8].
  * Errors: GNNTRK_ERR_INVALID_ARG (NULL handle or choice, an entry out of
  * range; nothing is changed then). No GPU work.
