@@ -179,7 +179,7 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
 # capture of 300 events of the same workload (profiles/dram_traffic_edge_steps_300ev.md),
 # averaged over the launches of a step; scaled to this run's rows.
 TRAFFIC_PER_ROW = {
-    ("rescore_edge_update", "bf16"): 313.9,
+    ("rescore_edge_update", "bf16"): 279.7,
     ("edge_update", "bf16"): 116.9,
     ("edge_update", "fp32"): 257.6,
 }
