@@ -36,7 +36,9 @@
  *   - gnntrk_last_error() returns a human-readable description of the last
  *     error of a handle (valid until the next call on that handle).
  *   - A handle is not thread safe: one host thread at a time, and calls on one
- *     handle are stream-ordered on the stream they are given.
+ *     handle are stream-ordered on the stream they are given. Distinct
+ *     handles may be used from distinct host threads at the same time (the
+ *     library's process-wide caches and tuning choices are synchronised).
  */
 #ifndef GNNTRK_H
 #define GNNTRK_H
@@ -478,8 +480,9 @@ gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edges, const i
                                         int32_t* out_labels, void* stream);
 
 /* Description of the last error on this handle ("" if none). The string is
- * owned by the handle. NULL handle: description of the last failure of
- * gnntrk_create, gnntrk_serve_run or gnntrk_components_noalloc. */
+ * owned by the handle. NULL handle: description of the calling host thread's
+ * last failure of gnntrk_create, gnntrk_serve_run or
+ * gnntrk_components_noalloc (valid until that thread's next such failure). */
 const char* gnntrk_last_error(const gnntrk_handle* h);
 
 /*

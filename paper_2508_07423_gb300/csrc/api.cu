@@ -77,7 +77,7 @@ struct gnntrk_handle {
 
 namespace {
 
-std::string g_create_error;
+thread_local std::string g_create_error;  // per host thread, like errno
 
 gnntrk_status fail(gnntrk_handle* h, gnntrk_status st, const std::string& msg) {
   if (h) h->err = msg;

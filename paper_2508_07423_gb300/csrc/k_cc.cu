@@ -194,12 +194,13 @@ void launch_cc(const Batch& b, const Ws& w, cudaStream_t s) {
     k_cc_union<<<device_sms() * 8, 256, 0, s>>>(w);
     return;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
+  // set once per process (thread-safe initialisation of a local static)
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(k_cc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * kCcSmemHits * int(sizeof(int32_t)));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   k_cc_event<<<std::min(b.n_events, device_sms() * 16), kCcThreads,
                2 * kCcSmemHits * sizeof(int32_t), s>>>(b, w);
 }

@@ -14,6 +14,7 @@
 // keeps the largest |input| of every layer.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "../../include/gnntrk.h"
 #include "internal.cuh"
@@ -200,10 +201,15 @@ size_t embed_int8_smem(const Int8Embed& m) {
 void launch_embed_int8(const Batch& b, const Ws& w, const Int8Embed& m, int D,
                        const GraphParams& g, cudaStream_t s) {
   const size_t smem = embed_int8_smem(m);
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_embed_int8, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr = smem;
+  {
+    // the attribute only grows; handles may launch from several host threads
+    static size_t attr = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > attr) {
+      cudaFuncSetAttribute(k_embed_int8, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      attr = smem;
+    }
   }
   const int grid = std::max(1, std::min(div_up(b.n_hits, kI8Threads), device_sms() * 8));
   k_embed_int8<<<grid, kI8Threads, smem, s>>>(b, w, m, D, g);

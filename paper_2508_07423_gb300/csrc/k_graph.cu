@@ -314,14 +314,15 @@ template <int D>
 void radius_d(const Batch& b, const Ws& w, const GraphParams& g, bool fill, cudaStream_t s) {
   const int grid = b.n_events * (g.n_planes - 1);
   if (grid <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  // set once per instantiation (thread-safe initialisation of a local static)
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_radius<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kCandSmemBytes);
     cudaFuncSetAttribute(k_radius<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kCandSmemBytes);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   if (fill)
     k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
   else
@@ -506,16 +507,15 @@ __global__ void __launch_bounds__(kCscThreads) k_csc_event(Batch b, Ws w) {
   }
 }
 
-int g_num_sms = 0;
-
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
+  // queried once per process (thread-safe initialisation of a local static)
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
 }
 
 }  // namespace
@@ -550,12 +550,12 @@ void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t*
 
 void launch_csc(const Batch& b, const Ws& w, cudaStream_t s) {
   if (b.n_events <= 0) return;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(k_csc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (kCscSmemHits + kCscSmemEdges) * int(sizeof(int32_t)));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   k_csc_event<<<std::min(b.n_events, num_sms() * 16), kCscThreads,
                 (kCscSmemHits + kCscSmemEdges) * sizeof(int32_t), s>>>(b, w);
 }

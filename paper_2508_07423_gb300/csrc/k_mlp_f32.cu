@@ -20,6 +20,8 @@
 //                  Network and Classifiers"). Sub-networks are
 //                  Linear -> LayerNorm -> ReLU -> Linear.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -58,7 +60,7 @@ struct Warps {
 
 // Variant chosen per (hidden index, kernel family: 0 encoders, 1 node step,
 // 2 edge step and classifier); set by the autotuner, process wide.
-int g_f32_variant[3][3] = {};
+std::atomic<int> g_f32_variant[3][3] = {};
 
 enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
                    G_EDGE_UPD_CLS = 4, G_CLS = 5, G_TRIP = 6 };
@@ -683,6 +685,8 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   };
   static Entry cache[64];
   static int used = 0;
+  static std::mutex mu;  // handles may launch from several host threads
+  std::lock_guard<std::mutex> lock(mu);
   for (int i = 0; i < used; ++i)
     if (cache[i].fn == fn && cache[i].threads == threads && cache[i].smem == smem) return cache[i].n;
   int n = 0;
@@ -715,7 +719,8 @@ constexpr int f32_family(int mode) {
 
 template <int H, int MODE>
 void launch_gnn(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
-  const int v = g_f32_variant[H == 32 ? 0 : (H == 64 ? 1 : 2)][f32_family(MODE)];
+  const int v =
+      g_f32_variant[H == 32 ? 0 : (H == 64 ? 1 : 2)][f32_family(MODE)].load(std::memory_order_relaxed);
   if (v == 1)
     launch_gnn_v<H, MODE, 1>(a, rows_hint, s);
   else
@@ -778,7 +783,8 @@ void launch_triplet_scores_f32(const Batch& b, const Ws& w, const TripletHeads& 
 
 void f32_set_variant(int h, int family, int v) {
   if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return;
-  g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family] = (v == 1) ? 1 : 0;
+  g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family].store((v == 1) ? 1 : 0,
+                                                                std::memory_order_relaxed);
 }
 
 void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, int n_embed,

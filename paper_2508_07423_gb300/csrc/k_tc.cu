@@ -25,6 +25,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1032,8 +1033,8 @@ __global__ void k_band_list(Ws w, int n_events) {
 template <int H, bool FP8, int MODE>
 int tc_blocks_per_sm() {
   using L = Layout<H, FP8, MODE>;
-  static int per_sm = 0;
-  if (per_sm == 0) {
+  // computed once per instantiation (thread-safe initialisation of a local static)
+  static const int per_sm = [] {
     cudaError_t e = cudaFuncSetAttribute(k_tc<H, FP8, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
     if (e == cudaSuccess)
@@ -1063,15 +1064,15 @@ int tc_blocks_per_sm() {
     if (getenv("GNNTRK_VERBOSE"))
       fprintf(stderr, "gnntrk: k_tc<%d,%d,%d> smem %d B, %d CTAs/SM\n", H, int(FP8), MODE,
               L::TOTAL, n);
-    per_sm = n;
-  }
+    return n;
+  }();
   return per_sm;
 }
 
 // Resident CTAs per SM chosen by the autotuner, per (FP8, hidden, kernel
 // family); 0 = the resource bound. Families: 0 node encoder, 1 edge encoder,
 // 2 node step, 3 edge step and classifier.
-int g_tuned[2][3][4] = {};
+std::atomic<int> g_tuned[2][3][4] = {};
 
 constexpr int family_of(int mode) {
   return mode == M_NODE_ENC ? 0 : mode == M_EDGE_ENC ? 1 : mode == M_NODE_UPD ? 2 : 3;
@@ -1083,7 +1084,7 @@ template <int H, bool FP8, int MODE>
 void launch_mode(const TcArgs& a, cudaStream_t s, int rows_hint) {
   using L = Layout<H, FP8, MODE>;
   int per_sm = tc_blocks_per_sm<H, FP8, MODE>();
-  const int tuned = g_tuned[FP8 ? 1 : 0][hidx(H)][family_of(MODE)];
+  const int tuned = g_tuned[FP8 ? 1 : 0][hidx(H)][family_of(MODE)].load(std::memory_order_relaxed);
   if (tuned > 0 && tuned < per_sm) per_sm = tuned;
   int grid = device_sms() * per_sm;
   if (rows_hint >= 0) grid = rows_hint == 0 ? 1 : min(grid, div_up(rows_hint, kRows));
@@ -1435,12 +1436,14 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
 
 void tc_set_ctas(int precision, int h, int family, int n) {
   if (family < 0 || family > 3 || (h != 32 && h != 64 && h != 128)) return;
-  g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family] = n < 0 ? 0 : n;
+  g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family].store(n < 0 ? 0 : n,
+                                                                       std::memory_order_relaxed);
 }
 
 int tc_get_ctas(int precision, int h, int family) {
   if (family < 0 || family > 3 || (h != 32 && h != 64 && h != 128)) return 0;
-  return g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family];
+  return g_tuned[precision == GNNTRK_FP8_E4M3 ? 1 : 0][hidx(h)][family].load(
+      std::memory_order_relaxed);
 }
 
 void tc_triplet_scores(const Batch& b, const Ws& w, const TcModel& m, int h, const LayerF32& art2,

@@ -98,3 +98,35 @@ def test_set_tuning_null_arguments_rejected_without_gpu_work(lib):
     ch = (ctypes.c_int32 * 8)()
     assert lib.gnntrk_set_tuning(None, ch) == 1
     assert lib.gnntrk_set_tuning(None, None) == 1
+
+
+def test_handle_less_errors_are_per_thread(lib):
+    """gnntrk_last_error(NULL) reports the calling thread's own failure while
+    other threads fail differently at the same time (no GPU work: the blob and
+    cfg checks come first)."""
+    import ctypes
+    import threading
+    bad_blob = pkg.default_cfg()
+    bad_width = pkg.default_cfg()
+    bad_width.hidden = 48
+    cases = [(b"\x00" * 8, bad_blob, 6), (b"\x00" * 64, bad_width, 7)]
+    errors = []
+
+    def worker(blob, cfg, want):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        h = ctypes.c_void_p()
+        first = None
+        for _ in range(25):
+            st = lib.gnntrk_create(buf, len(blob), ctypes.byref(cfg), ctypes.byref(h))
+            msg = lib.gnntrk_last_error(None).decode()
+            first = first or msg
+            if st != want or msg != first:
+                errors.append((want, st, msg, first))
+                return
+
+    threads = [threading.Thread(target=worker, args=c) for c in cases for _ in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors[:3]
