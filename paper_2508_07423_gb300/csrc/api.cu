@@ -1064,15 +1064,19 @@ gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
 
 gnntrk_status gnntrk_sync_status(gnntrk_handle* h, void* stream) {
   if (!h) return GNNTRK_ERR_INVALID_ARG;
-  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  // every copy is ordered on the caller's stream (never the legacy default
+  // stream, which would join the streams other threads may be capturing)
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t cnt[C_COUNT];
-  e = cudaMemcpy(cnt, h->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(cnt, h->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "status read");
   const int st = cnt[C_STATUS];
   if (st) {
     const int32_t zero = 0;
-    cudaMemcpy(h->ws.counters + C_STATUS, &zero, 4, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(h->ws.counters + C_STATUS, &zero, 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
   }
   if (st & ST_INPUT)
     return fail(h, GNNTRK_ERR_INVALID_ARG,

@@ -43,3 +43,46 @@ def test_serving_budget_too_small_is_rejected():
     with pytest.raises(pkg.GnntrkError) as ei:
         pkg.serve_run(synth.workload_weights(wl), cfg, b, np.zeros(2), memory_budget_bytes=1000)
     assert ei.value.status == 3
+
+
+def test_two_handles_from_two_host_threads():
+    """Two handles (FP32 and BF16 + re-score, CUDA graphs on) driven at the same
+    time from two host threads on their own streams: every call's labels equal
+    the handle's own result computed alone beforehand."""
+    import threading
+    jobs = []
+    for name, prec, n in (("cfg1_plain_fp32", "fp32", 6), ("cfg3_batched_bf16", "bf16", 8)):
+        wl = synth.workload(name)
+        b = synth.workload_batch(wl, n)
+        tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits,
+                                      max_events=b.n_events, edges_per_hit=32, use_graph=True)
+        want = pkg.run_batch(tr, b)
+        xyz = torch.from_numpy(b.xyz_soa()).cuda()
+        plane = torch.from_numpy(b.plane).cuda()
+        offs = torch.from_numpy(b.offsets).cuda()
+        labels = torch.full((b.n_hits,), -7, dtype=torch.int32, device="cuda")
+        jobs.append((tr, b, want, xyz, plane, offs, labels))
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(tr, b, want, xyz, plane, offs, labels):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for it in range(6):
+                    labels.fill_(-7)
+                    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, labels, s)
+                    tr.sync_status(s)
+                    if not np.array_equal(labels.cpu().numpy(), want):
+                        errors.append((tr.cfg.precision, it))
+        except Exception as e:  # reported below, after both threads end
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=j) for j in jobs]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for j in jobs:
+        j[0].close()
+    assert not errors, errors
