@@ -13,7 +13,9 @@ Parity status: every step is pinned by tests against closed forms, hand-worked
 examples and brute force (see tests/test_oracle_pins.py; the triplet stage in
 tests/test_oracle_triplets.py: triplets against a brute-force pair
 enumeration, the classifiers' operand order and routing tied to the edge
-classifier, track building on hand-worked graphs including a shared-hit pair). The composition of
+classifier, track building on hand-worked graphs including a shared-hit pair,
+and the whole path with the triplet stage on a hand-built event for every
+on/off setting of the two heads). The composition of
 the steps into the whole pipeline is pinned by a hand-built event
 (tests/golden/pipeline_hand.json: identity embedding, straight lines with
 gaps of one and two planes, a constant classifier on either side of the cut)

@@ -146,10 +146,13 @@ def hand_pipeline():
     return g, x, y, z, plane, idx
 
 
-def hand_pipeline_blob(h: int, K: int, bias: float, seed: int = 0) -> bytes:
+def hand_pipeline_blob(h: int, K: int, bias: float, seed: int = 0,
+                       triplet_bias=None) -> bytes:
     """Weights of the hand-built event: identity embedding 3 -> 4 -> 4 (the
     features and a zero coordinate), a random interaction network of width h
-    and K steps, and a classifier whose last layer is zero with bias `bias`."""
+    and K steps, and a classifier whose last layer is zero with bias `bias`.
+    triplet_bias = (articulation, elbow): the two triplet classifiers appended,
+    random first layers and zero last layers with these biases."""
     from paper_2508_07423_gb300 import synth
     rng = np.random.default_rng(seed)
 
@@ -164,6 +167,9 @@ def hand_pipeline_blob(h: int, K: int, bias: float, seed: int = 0) -> bytes:
     for _ in range(K):
         layers += [rnd(h, 3 * h), rnd(h, h), rnd(h, 3 * h), rnd(h, h)]
     layers += [rnd(h, h), (np.zeros((1, h), np.float32), np.array([bias], np.float32))]
+    if triplet_bias is not None:
+        for tb in triplet_bias:
+            layers += [rnd(h, 2 * h), (np.zeros((1, h), np.float32), np.array([tb], np.float32))]
     return synth.pack_weights(layers)
 
 

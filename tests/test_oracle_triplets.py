@@ -207,3 +207,30 @@ def test_empty_inputs():
     assert len(ty) == 0
     assert oracle.build_tracks(2, src, dst, np.zeros(1, np.uint8), ty, e1, e2,
                                np.zeros(0, np.uint8)) == []
+
+
+def test_whole_path_with_triplets_on_hand_built_event():
+    """The hand-built event through the whole path and the triplet stage, for
+    the four on/off settings of the two triplet heads; the triplet counts and
+    the tracks are those worked out by hand in
+    tests/golden/triplet_pipeline_hand.json."""
+    import json
+    import os
+    from parity import hand_pipeline, hand_pipeline_blob
+    gold = os.path.join(os.path.dirname(__file__), "golden", "triplet_pipeline_hand.json")
+    with open(gold) as f:
+        t = json.load(f)
+    g, x, y, z, plane, idx = hand_pipeline()
+    for case in t["cases"]:
+        blob = hand_pipeline_blob(8, 2, g["classifier_bias"],
+                                  triplet_bias=(case["articulation_bias"], case["elbow_bias"]))
+        m = oracle.Model(blob, [3, 4, 4], 8, 2)
+        r = oracle.find_tracks_triplets_event(m, x, y, z, plane, g["r2"], g["k_max"],
+                                              cut=g["cut_keep_all"])
+        assert np.all(r.keep == 1)
+        counts = np.bincount(r.ttype, minlength=3)
+        assert list(counts) == [t["triplets"]["articulation"], t["triplets"]["left_elbow"],
+                                t["triplets"]["right_elbow"]]
+        want = sorted(sorted(idx[n] for n in tr) for tr in case["tracks"])
+        got = sorted(sorted(int(i) for i in tr) for tr in r.tracks)
+        assert got == want, case
