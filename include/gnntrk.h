@@ -389,6 +389,19 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
 gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice);
 
 /*
+ * Self-test of failure detection (test hook; no pipeline work). Enqueues on
+ * `stream` one thread that waits on a fresh mbarrier nothing ever arrives on,
+ * through the bounded wait the tensor-core kernels use, for at most
+ * max_cycles SM cycles (1..4e9; about 0.5 ms per 1e6 at 2 GHz), and then
+ * latches the timeout bit of the handle's device status word exactly as a
+ * tensor-core kernel whose wait ran out does. The next gnntrk_sync_status on
+ * that stream returns GNNTRK_ERR_TIMEOUT and clears the word; the handle stays
+ * usable. Errors: GNNTRK_ERR_INVALID_ARG (NULL handle, max_cycles out of
+ * range), GNNTRK_ERR_CUDA (launch).
+ */
+gnntrk_status gnntrk_selftest_wait(gnntrk_handle* h, int64_t max_cycles, void* stream);
+
+/*
  * Device memory a handle created with `cfg` allocates (weights and workspace),
  * in bytes; 0 if cfg is invalid. For admission planning.
  */

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIM
 EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_sync_status",
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
-           "gnntrk_autotune", "gnntrk_set_tuning", "gnntrk_rescore_rows", "gnntrk_e4m3_encode",
+           "gnntrk_autotune", "gnntrk_set_tuning", "gnntrk_selftest_wait", "gnntrk_rescore_rows", "gnntrk_e4m3_encode",
            "gnntrk_e4m3_decode",
            "gnntrk_find_tracks_triplets", "gnntrk_triplet_stats", "gnntrk_get_triplets",
            "gnntrk_embed_amax", "gnntrk_set_embed_scales",
@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_autotune.restype = st
     L.gnntrk_set_tuning.argtypes = [vp, vp]
     L.gnntrk_set_tuning.restype = st
+    L.gnntrk_selftest_wait.argtypes = [vp, i64, vp]
+    L.gnntrk_selftest_wait.restype = st
     L.gnntrk_workspace_bytes.argtypes = [ctypes.POINTER(Cfg)]
     L.gnntrk_workspace_bytes.restype = i64
     L.gnntrk_serve_run.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(Cfg),
@@ -330,6 +332,11 @@ class Tracker:
         for i, k in enumerate(keys):
             ch[i] = int(choice.get(k, 0))
         self._check(self._L.gnntrk_set_tuning(self._h, ch.ctypes.data_as(ctypes.c_void_p)))
+
+    def selftest_wait(self, max_cycles: int, stream=None):
+        """Test hook: a bounded device wait that runs out and latches a timeout."""
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._check(self._L.gnntrk_selftest_wait(self._h, int(max_cycles), ctypes.c_void_p(s)))
 
     def set_profiling(self, enable: bool):
         self._check(self._L.gnntrk_set_profiling(self._h, int(bool(enable))))

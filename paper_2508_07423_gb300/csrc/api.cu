@@ -1043,6 +1043,16 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
   return st;
 }
 
+gnntrk_status gnntrk_selftest_wait(gnntrk_handle* h, int64_t max_cycles, void* stream) {
+  if (!h) return GNNTRK_ERR_INVALID_ARG;
+  if (max_cycles < 1 || max_cycles > 4000000000LL)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "max_cycles must be 1..4e9");
+  tc_wait_selftest(h->ws.counters, max_cycles, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+  return GNNTRK_OK;
+}
+
 gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
   if (!h) return GNNTRK_ERR_INVALID_ARG;
   if (!choice) return fail(h, GNNTRK_ERR_INVALID_ARG, "choice is NULL");

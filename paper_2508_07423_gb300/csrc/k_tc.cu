@@ -1483,6 +1483,23 @@ void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s) {
   k_band_list<<<1, 1024, 0, s>>>(w, b.n_events);
 }
 
+namespace {
+// Self-test of the bounded waits: one thread waits on an mbarrier that no
+// thread ever arrives on, through the same bounded wait the tensor-core
+// kernels use, and latches ST_TIMEOUT when it runs out, as they do.
+__global__ void k_wait_selftest(int32_t* counters, long long max_cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0, max_cycles)) set_status(counters, ST_TIMEOUT);
+}
+}  // namespace
+
+void tc_wait_selftest(int32_t* counters, long long max_cycles, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(counters, max_cycles);
+}
+
 }  // namespace gnntrk
 
 // ---------------------------------------------------------------------------

@@ -74,4 +74,8 @@ float e4m3_to_float(uint8_t c);
 // counters[C_RERUN] and clear the flags.
 void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s);
 
+// Launch the bounded-wait self-test: a wait on an mbarrier nothing arrives on,
+// for at most max_cycles SM cycles, then ST_TIMEOUT in counters.
+void tc_wait_selftest(int32_t* counters, long long max_cycles, cudaStream_t s);
+
 }  // namespace gnntrk

@@ -130,3 +130,7 @@ def test_handle_less_errors_are_per_thread(lib):
     for t in threads:
         t.join()
     assert not errors, errors[:3]
+
+
+def test_selftest_wait_null_handle_rejected_without_gpu_work(lib):
+    assert lib.gnntrk_selftest_wait(None, 1000, None) == 1

@@ -336,3 +336,27 @@ def test_hand_built_event(prec):
             assert np.all(gr["logit"] == np.float32(g["classifier_bias"]))
             assert np.all(gr["kept"] == (1 if keep_all else 0))
         tr.close()
+
+
+def test_bounded_wait_runs_out_and_the_handle_recovers(cfg1):
+    """Failure detection without a fault: a bounded device wait on an mbarrier
+    nothing arrives on runs out after about 1 ms, the timeout surfaces from
+    gnntrk_sync_status, the status word is cleared, and the handle keeps
+    giving the same results."""
+    import time
+    wl, _ = cfg1
+    tr = pkg.tracker_for_workload(wl, max_hits=8192, max_events=8)
+    b = synth.workload_batch(wl, 2)
+    want = pkg.run_batch(tr, b)
+    s = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    tr.selftest_wait(2_000_000, s)
+    with pytest.raises(pkg.GnntrkError) as ei:
+        tr.sync_status(s)
+    assert ei.value.status == 5
+    assert time.perf_counter() - t0 < 5.0
+    tr.sync_status(s)
+    assert np.array_equal(pkg.run_batch(tr, b), want)
+    with pytest.raises(pkg.GnntrkError):
+        tr.selftest_wait(0, s)
+    tr.close()
