@@ -10,8 +10,12 @@ JSON line (rank 0).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp32|bf16|fp8] [--workload NAME]
 
---impl reference times the FP64 CPU oracle on the same workload instead (the
-only other place this file runs the oracle is the cpu_baseline leg).
+--impl reference times the FP64 CPU oracle on the same workload instead. The
+only other place this file runs the oracle is the cpu_baseline leg (rank 0,
+N = 1, after every timed region; --no-cpu-baseline turns it off): it times the
+oracle on the host cores and checks GPU results against it, the headline's
+and those of the extra reports (score error, decision agreement, track
+metrics). No GPU number comes from the oracle.
 """
 from __future__ import annotations
 
