@@ -109,3 +109,13 @@ def test_triplet_heads_and_joint_training_produce_a_loadable_blob():
     ev = synth.gen_batch(1, 32, tracks, 0.05, pair_frac=0.2)
     r = oracle.find_tracks_triplets_event(m, ev.x, ev.y, ev.z, ev.plane, r2, 64)
     assert len(r.tlogit) == len(r.ttype) and np.all(np.isfinite(r.tlogit))
+
+
+def test_training_is_deterministic():
+    """Same seed and settings: byte-identical weights and the same radius."""
+    shape = synth.ModelShape([3, 16, 16, 4], 8, 1)
+    tracks = {"kind": "fixed", "n": 20}
+    runs = [train.train(shape, tracks, 0.05, 6, 41, device="cpu", emb_epochs=2, gnn_epochs=2)
+            for _ in range(2)]
+    assert runs[0][0] == runs[1][0]
+    assert runs[0][1] == runs[1][1]
