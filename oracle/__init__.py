@@ -33,6 +33,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# a prebuilt variant of the library to load instead (the planted-mistake tests
+# compile copies of oracle.cpp with one mistake each and point here)
+_LIB_VARIANT = os.environ.get("GNNTRK_ORACLE_LIB")
 _lib = None
 
 DEFAULT_FEAT_SCALE = (45.0, math.pi, 750.0, 45.0, 45.0, 750.0)
@@ -40,6 +43,8 @@ DEFAULT_FEAT_SCALE = (45.0, math.pi, 750.0, 45.0, 45.0, 750.0)
 
 def build(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so (plain g++, no GPU code)."""
+    if _LIB_VARIANT:
+        return _LIB_VARIANT
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
@@ -51,8 +56,7 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(build())
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.orc_model_load.restype = vp
         L.orc_model_load.argtypes = [vp, ctypes.c_size_t, i32, vp, i32, i32, ctypes.c_char_p, i32]
