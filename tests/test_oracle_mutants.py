@@ -5,6 +5,7 @@ must fail. A control build of the unmodified source must pass them all, so a
 failure means the pins caught the mistake, not that the harness broke.
 CPU only; the shipped oracle is never modified."""
 import os
+import shutil
 import subprocess
 import sys
 
@@ -81,3 +82,66 @@ def test_planted_mistake_fails_a_pin(name, edits, tmp_path):
     r = _run_pins(_build(tmp_path, edits))
     tail = r.stdout[-3000:]
     assert r.returncode == 1 and " failed" in tail, f"{name}: no pin failed\n{tail}"
+
+
+# Planted mistakes in the oracle's Python parts (quantisers, track metrics):
+# a copy of the oracle package with one edited file goes first on the path of
+# the child process (the C++ library is the unmodified one).
+PY_MUTANTS = [
+    ("e4m3_ties_to_odd", "quant.py", [("if (pos[b] & 1) == 0]", "if (pos[b] & 1) == 1]")]),
+    ("e4m3_subnormal_step", "quant.py", [("return sign * m * 2.0 ** -9",
+                                          "return sign * m * 2.0 ** -10")]),
+    ("int8_per_tensor_weight_scale", "quant.py", [("a = np.abs(W).max(axis=1)",
+                                                   "a = np.full(W.shape[0], np.abs(W).max())")]),
+    ("int8_round_half_up", "quant.py", [("q = np.rint(np.asarray(v, np.float32) * np.float32(inv_scale))",
+                                         "q = np.floor(np.asarray(v, np.float32) * np.float32(inv_scale) + 0.5)")]),
+    ("match_needs_more_than_70_percent", "metrics.py", [("if n_best < match_frac * len(hits):",
+                                                         "if n_best <= match_frac * len(hits):")]),
+    ("reconstructible_from_2_hits", "metrics.py", [("if n >= 3}", "if n >= 2}")]),
+    ("shared_hit_votes_once", "metrics.py", [("            if p2[i] >= 0:\n                votes[p2[i]] += 1\n", "")]),
+    ("clones_include_the_first", "metrics.py", [("c.clones = sum(n - 1 for n in matched_count.values())",
+                                                 "c.clones = sum(n for n in matched_count.values())")]),
+]
+
+
+@pytest.mark.parametrize("name,fname,edits", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_python_mistake_fails_a_pin(name, fname, edits, tmp_path):
+    import oracle
+    lib = oracle.build()
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so"))
+    path = pkg / fname
+    src = path.read_text()
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation site not found once: {old!r}"
+        src = src.replace(old, new)
+    path.write_text(src)
+    env = dict(os.environ, GNNTRK_ORACLE_LIB=lib,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        *[os.path.join(ROOT, p) for p in PINS]], cwd=str(tmp_path), env=env,
+                       capture_output=True, text=True, timeout=900)
+    tail = r.stdout[-3000:]
+    assert r.returncode == 1 and " failed" in tail, f"{name}: no pin failed\n{tail}"
+
+
+def test_python_variant_harness_loads_the_copy(tmp_path):
+    """Control of the harness: an unmodified copy passes, and a copy whose
+    module raises on import is the one the child imports."""
+    import oracle
+    lib = oracle.build()
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so"))
+    env = dict(os.environ, GNNTRK_ORACLE_LIB=lib,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT]))
+    args = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+            *[os.path.join(ROOT, p) for p in PINS]]
+    r = subprocess.run(args, cwd=str(tmp_path), env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:]
+    (pkg / "metrics.py").write_text("raise ImportError('variant copy imported')\n")
+    r = subprocess.run(args, cwd=str(tmp_path), env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode != 0 and "variant copy imported" in r.stdout + r.stderr

@@ -474,6 +474,10 @@ def test_int8_layer_exact_on_representable_values():
     assert np.allclose(y, want, rtol=1e-6, atol=1e-6)
     # saturation: inputs beyond alpha clip to +-127
     assert list(quant.int8_codes([10.0, -10.0], np.float32(127) / np.float32(alpha))) == [127, -127]
+    # ties round half to even (reading Q1, the rounding of the device's
+    # float-to-int conversion): 0.5, 1.5, 2.5, 3.5 -> 0, 2, 2, 4 and the negatives
+    ties = [0.5, 1.5, 2.5, 3.5, -0.5, -1.5, -2.5, -3.5]
+    assert list(quant.int8_codes(ties, 1.0)) == [0, 2, 2, 4, 0, -2, -2, -4]
 
 
 def test_int8_embedding_converges_to_float_with_range():
