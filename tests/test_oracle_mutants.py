@@ -49,6 +49,12 @@ MUTANTS = [
                                        "if (n_out[l.first] > 1 && n_in[l.second] > 1)")]),
     ("articulations_join_groups", [("if (tkeep[t] && type[t] != 0) grp.unite(e1[t], e2[t]);",
                                     "if (tkeep[t]) grp.unite(e1[t], e2[t]);")]),
+    ("elbow_order_ignores_plane", [("return std::make_pair(int(plane[far]), far);",
+                                    "return std::make_pair(0, far);")]),
+    ("triplets_from_cut_edges", [("    if (!keep[e]) continue;\n    out[src[e]].push_back",
+                                  "    out[src[e]].push_back")]),
+    ("elbows_counted_both_ways", [("for (size_t j = i + 1; j < O.size(); ++j) put(1, O[i], O[j]);",
+                                   "for (size_t j = 0; j < O.size(); ++j) if (j != i) put(1, O[i], O[j]);")]),
 ]
 
 
