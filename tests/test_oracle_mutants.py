@@ -49,6 +49,12 @@ MUTANTS = [
                                        "if (n_out[l.first] > 1 && n_in[l.second] > 1)")]),
     ("articulations_join_groups", [("if (tkeep[t] && type[t] != 0) grp.unite(e1[t], e2[t]);",
                                     "if (tkeep[t]) grp.unite(e1[t], e2[t]);")]),
+    ("embedding_relu_on_output", [("    if (l + 1 < m.embed.size())\n      for (double& v : o)",
+                                   "    for (double& v : o)")]),
+    ("kmax_keeps_farthest", [("    std::sort(cand.begin(), cand.end());\n    size_t keep",
+                              "    std::sort(cand.rbegin(), cand.rend());\n    size_t keep")]),
+    ("radius_feature_from_x_only", [("std::sqrt(xd * xd + yd * yd) / P.feat_scale[0]",
+                                     "std::sqrt(xd * xd) / P.feat_scale[0]")]),
     ("elbow_order_ignores_plane", [("return std::make_pair(int(plane[far]), far);",
                                     "return std::make_pair(0, far);")]),
     ("triplets_from_cut_edges", [("    if (!keep[e]) continue;\n    out[src[e]].push_back",
