@@ -505,3 +505,14 @@ def test_int8_embedding_converges_to_float_with_range():
     e_wide = np.abs(wide - ref).max()
     assert e_cal < 0.05 * np.abs(ref).max(), e_cal
     assert e_wide > 5 * e_cal, (e_wide, e_cal)
+
+
+@pytest.mark.parametrize("name", ["cfg1_plain_fp32", "cfg2_run3_single", "cfg3_batched_bf16",
+                                  "cfg4_batched_fp8", "cfg5_serving"])
+def test_stored_radii_come_from_the_calibration(name):
+    """Every stored squared radius of a seeded-weight workload is what
+    oracle/calibrate.py computes from the workload's calibration events (its
+    own seed): exactly E = round(degree x N / 2) candidate pairs pass."""
+    from oracle import calibrate
+    wl = synth.workload(name)
+    assert calibrate.calibrate(name, wl) == wl["radius2"]
