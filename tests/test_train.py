@@ -119,3 +119,31 @@ def test_training_is_deterministic():
             for _ in range(2)]
     assert runs[0][0] == runs[1][0]
     assert runs[0][1] == runs[1][1]
+
+
+def test_shipped_radius_is_the_genuine_pair_quantile():
+    """The trained blob's stored squared radius is the 99.5 % quantile of the
+    squared embedding distances of genuine pairs (same particle, next two
+    planes, particles of at least 3 hits) over its training events (reading
+    R19), recomputed here with the FP64 oracle embedding."""
+    wl = synth.workload("cfg3_trained_bf16")
+    meta_path = os.path.join(os.path.dirname(synth.__file__), wl["weights_file"][:-4] + ".json")
+    with open(meta_path) as f:
+        meta = json.load(f)
+    sh = synth.shape_of(wl)
+    m = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+    b = synth.gen_batch(meta["train_events"], meta["train_seed"], meta["tracks"], meta["noise"])
+    ds = []
+    for e in range(b.n_events):
+        ev = b.event(e)
+        keep = ev.pid >= 0
+        keep &= np.bincount(ev.pid[keep])[np.maximum(ev.pid, 0)] >= 3
+        idx = np.flatnonzero(keep)
+        emb = oracle.embed(m, ev.x[idx], ev.y[idx], ev.z[idx])
+        pl, pid = ev.plane[idx].astype(int), ev.pid[idx]
+        dp = pl[None, :] - pl[:, None]
+        q, a = np.nonzero(((dp == 1) | (dp == 2)) & (pid[:, None] == pid[None, :]))
+        ds.append(((emb[q] - emb[a]) ** 2).sum(1))
+    r2 = np.quantile(np.concatenate(ds), meta["radius_quantile_of_genuine_pairs"])
+    assert r2 == pytest.approx(meta["radius2"], rel=1e-4)
+    assert meta["radius2"] == wl["radius2"]
