@@ -134,3 +134,25 @@ def test_handle_less_errors_are_per_thread(lib):
 
 def test_selftest_wait_null_handle_rejected_without_gpu_work(lib):
     assert lib.gnntrk_selftest_wait(None, 1000, None) == 1
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/gnntrk.h compiles as pedantic C99, and a C program linked
+    against the library gets the documented defaults (no GPU work)."""
+    import subprocess
+    from paper_2508_07423_gb300 import LIB_PATH
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "gnntrk.h"\n'
+                   "int main(void) {\n"
+                   "  gnntrk_cfg c;\n"
+                   "  gnntrk_default_cfg(&c);\n"
+                   "  if (c.hidden != 32 || c.iters != 4 || c.embed_dims[3] != 4) return 1;\n"
+                   "  return gnntrk_set_tuning(0, 0) == GNNTRK_ERR_INVALID_ARG ? 0 : 2;\n"
+                   "}\n")
+    libdir = os.path.dirname(LIB_PATH)
+    exe = tmp_path / "use"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(root, "include"), str(src), "-L", libdir,
+                           "-lgnntrk", f"-Wl,-rpath,{libdir}", "-o", str(exe)])
+    assert subprocess.run([str(exe)]).returncode == 0
