@@ -64,6 +64,15 @@ def parse():
     return p.parse_args()
 
 
+def fp32_peak(torch, dev, pk):
+    """FP32 SIMT peak (TFLOP/s) of this device: SMs (read from the device) x 128
+    FP32 FMA per clock x 2 flop x the maximum SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return (sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12,
+            f"derived: {sms} SMs (device query) x 128 FP32 FMA/clk x 2 x max SM clock "
+            f"{pk['sm_max_mhz']:.0f} MHz ({pk['src']})")
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -132,8 +141,8 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     """Algorithmic work of ONE launch of `stage`: (bound, amount, unit-of-amount).
 
     FP32 SIMT stages are ALU bound (flops); tensor-core and gather stages are
-    HBM bound (bytes). Per-unit figures (per edge / per hit) are the ones in the
-    design notes; amount = figure x units of one launch.
+    HBM bound (bytes). The per-unit figure (per edge / per hit) is written
+    beside each stage below; amount = figure x units of one launch.
     """
     sb = 4 if precision == "fp32" else 2   # state bytes per element
     if stage == "rescore_node_prep":  # FP32 node encoder + projections (the embedding is reused)
@@ -340,8 +349,9 @@ def main():
     bound, amount = stage_amount(dname, druns // a.steps, rows, precision, N, E, m)
     launch_ms = dms / max(druns, 1)
     step_stage_ms = dms / a.steps
+    f32_peak, f32_src = fp32_peak(torch, dev, pk)
     if bound == "alu":
-        peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        peak = f32_peak
         achieved = amount / (step_stage_ms / 1e3) / 1e12
         unit = "TFLOP/s"
     else:
@@ -359,7 +369,7 @@ def main():
         sb_, samt = stage_amount(sname, sruns // a.steps, rows, precision, N, E, m)
         st_ms = sms / a.steps
         if sb_ == "alu":
-            pk_, ach, un = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, samt / (st_ms / 1e3) / 1e12, "TFLOP/s"
+            pk_, ach, un = f32_peak, samt / (st_ms / 1e3) / 1e12, "TFLOP/s"
         else:
             pk_, ach, un = pk["hbm_gbs"], samt / (st_ms / 1e3) / 1e9, "GB/s"
         per_stage[sname] = {"ms_per_step": round(st_ms, 4), "bound": sb_, "achieved": round(ach, 2),
@@ -367,8 +377,7 @@ def main():
     roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
             "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_unit": "DRAM bytes per launch (ncu capture of 300 events scaled by rows)",
-            "peak_src": ("derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"
-                         if bound == "alu" else pk["src"]),
+            "peak_src": f32_src if bound == "alu" else pk["src"],
             "launch_ms": round(launch_ms, 4),
             "work": "algorithmic work of the stage over one step / its time per step",
             "profiled_ms_per_step": round(float(np.mean(prof_ms)), 4),
@@ -384,7 +393,7 @@ def main():
                                              precision=precision, rescore_band=0.0)
         extra["fp32_batched"] = quick_rate(pkg, torch, wl, batch, dev, stream, flush,
                                            precision="fp32")
-        extra["serving"] = run_serving(pkg, precision)
+        extra["serving"] = run_serving(pkg, precision, tuned)
     plain = extra.get("plain_fp32_one_event_per_launch")
 
     out = {
@@ -415,6 +424,12 @@ def main():
         "wall_s_timed": round(wall, 3),
     }
     out.update(extra)
+    if rank == 0 and world == 1 and not a.no_plain:
+        out["occupancy_study"] = {
+            "what": "config-3 model, radius and noise at a fixed tracks per event, about 1.7 M "
+                    "hits per batch: batched BF16 + FP32 re-score (one call, CUDA graph) against "
+                    "the plain FP32 path (one event per call, 100 events)",
+            "rows": occupancy_study(pkg, torch, dev, stream)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, batch, labels.cpu().numpy(), tr, a.cpu_seconds)
         if not a.no_plain:
@@ -429,9 +444,12 @@ def main():
         dist.destroy_process_group()
 
 
-def run_serving(pkg, precision):
+def run_serving(pkg, precision, tuning=None):
     """Config 5: Poisson arrivals at 50 k events/s, continuous batching within a
-    40 GB budget; p50/p99 latency and sustained events/s."""
+    40 GB budget; p50/p99 latency and sustained events/s. Each slot's workspace
+    holds a batch of up to 256 k hits (about 150 events of this workload, over
+    twice the largest batch the arrival rate forms), so 8 slots fit the budget;
+    the slots apply the headline's autotuned launch configuration."""
     try:
         wl = synth.workload("cfg5_serving")
         n = wl["n_events"]
@@ -443,14 +461,16 @@ def run_serving(pkg, precision):
         res = {}
         for name, bnd in (("rescore", band), ("no_rescore", 0.0)):
             cfg.rescore_band = bnd
-            _, done, st = pkg.serve_run(synth.workload_weights(wl), cfg, b, arr, n_slots=4,
-                                        max_events_per_batch=2048, max_hits_per_batch=4 << 20,
-                                        memory_budget_bytes=wl["memory_budget_bytes"])
+            _, done, st = pkg.serve_run(synth.workload_weights(wl), cfg, b, arr, n_slots=8,
+                                        max_events_per_batch=512, max_hits_per_batch=1 << 18,
+                                        memory_budget_bytes=wl["memory_budget_bytes"],
+                                        tuning=tuning)
             lat = (done - arr) * 1e3
             res[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
                          "p99_ms": round(float(np.percentile(lat, 99)), 3),
                          "sustained_events_per_s": round(n / (done.max() - arr[0]), 1),
                          "batches": st["batches"], "slots": st["slots"],
+                         "slot_bytes": st["slot_bytes"],
                          "max_in_flight": st["max_in_flight"],
                          "largest_batch": st["largest_batch"]}
             if precision == "fp32":
@@ -526,9 +546,68 @@ def run_plain(pkg, torch, dev, stream):
         return {"events_per_s": None, "error": str(ex)}
 
 
-def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
-    """The FP64 oracle on the host cores over a bounded sample of the same events,
-    plus agreement of the GPU result on that sample."""
+def compare_edges(g, ref, n_hits):
+    """One event's GPU graph (`get_graph` dict) against the oracle's
+    (`oracle.EventResult`) over the union of both edge sets, an edge absent on
+    one side counting as not kept there: (agreeing keep decisions, size of the
+    union, |score difference| on the edges both sides hold)."""
+    kg = g["src"].astype(np.int64) * n_hits + g["dst"].astype(np.int64)
+    ko = ref.src.astype(np.int64) * n_hits + ref.dst.astype(np.int64)
+    allk = np.union1d(kg, ko)
+    keep_g = np.zeros(allk.size, bool)
+    keep_g[np.searchsorted(allk, kg)] = np.asarray(g["kept"]) != 0
+    keep_o = np.zeros(allk.size, bool)
+    keep_o[np.searchsorted(allk, ko)] = np.asarray(ref.keep) != 0
+    _, ig, io = np.intersect1d(kg, ko, assume_unique=True, return_indices=True)
+    sig = lambda v: 1.0 / (1.0 + np.exp(-np.asarray(v, np.float64)))
+    err = np.abs(sig(np.asarray(g["logit"])[ig]) - sig(ref.logit[io]))
+    return int(np.count_nonzero(keep_g == keep_o)), int(allk.size), err
+
+
+class Agreement:
+    """Edge-decision agreement and score error summed over events."""
+
+    def __init__(self):
+        self.agree = self.union = self.events = self.n_err = 0
+        self.sum_err = self.max_err = 0.0
+
+    def add(self, g, ref, n_hits):
+        a, u, err = compare_edges(g, ref, n_hits)
+        self.agree += a
+        self.union += u
+        self.events += 1
+        if err.size:
+            self.max_err = max(self.max_err, float(err.max()))
+            self.sum_err += float(err.sum())
+            self.n_err += err.size
+
+    def summary(self):
+        return {"events": self.events, "edges_compared": self.union,
+                "edge_decision_agreement": round(self.agree / max(self.union, 1), 6),
+                "decisions_differing": self.union - self.agree,
+                "max_score_error": round(self.max_err, 7),
+                "mean_score_error": round(self.sum_err / max(self.n_err, 1), 8)}
+
+
+def oracle_events(model, batch, idx, wl, fs, threads):
+    """The FP64 oracle on events `idx` of `batch`, one event per thread (the
+    oracle call releases the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    def one(e):
+        ev = batch.event(e)
+        return oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                        wl["k_max"], wl["cut"], feat_scale=fs)
+    with cf.ThreadPoolExecutor(max(1, threads)) as ex:
+        return list(ex.map(one, idx))
+
+
+def cpu_baseline(wl, batch, gpu_labels, tr, seconds, seconds_one_core=4.0):
+    """The FP64 oracle on the host cores over a bounded sample of the same events
+    (all cores, one event per thread; and one core alone on the first events),
+    plus the GPU result's agreement with it on every sampled event."""
     import oracle
     from oracle import metrics
     sh = synth.shape_of(wl)
@@ -536,56 +615,49 @@ def cpu_baseline(wl, batch, gpu_labels, tr, seconds):
     import paper_2508_07423_gb300 as pkg
     fs = pkg.feat_scale_of(tr.cfg)
     cores = os.cpu_count() or 1
+    # one core
+    n1, h1, t1 = 0, 0, 0.0
+    while t1 < seconds_one_core and n1 < batch.n_events:
+        t0 = time.perf_counter()
+        oracle_events(model, batch, [n1], wl, fs, 1)
+        t1 += time.perf_counter() - t0
+        h1 += int(batch.offsets[n1 + 1] - batch.offsets[n1])
+        n1 += 1
+    # all cores, `cores` events at a time until the time budget is spent
     done, hits, t_used = 0, 0, 0.0
-    lab_ref = []
+    refs = []
     while t_used < seconds and done < batch.n_events:
         idx = list(range(done, min(done + cores, batch.n_events)))
-        sub = batch.subset(idx)
         t0 = time.perf_counter()
-        lab, _ = oracle.find_tracks_batch(model, sub.x, sub.y, sub.z, sub.plane, sub.offsets,
-                                          wl["radius2"], wl["k_max"], wl["cut"], threads=cores,
-                                          feat_scale=fs)
+        refs += oracle_events(model, batch, idx, wl, fs, cores)
         t_used += time.perf_counter() - t0
-        lab_ref.append(lab)
         done += len(idx)
-        hits += sub.n_hits
-    lab_ref = np.concatenate(lab_ref)
+        hits += int(batch.offsets[done] - batch.offsets[idx[0]])
+    lab_ref = np.concatenate([r.labels for r in refs])
     n_s = int(batch.offsets[done])
     same = sum(np.array_equal(gpu_labels[batch.offsets[e]:batch.offsets[e + 1]],
                               lab_ref[batch.offsets[e]:batch.offsets[e + 1]]) for e in range(done))
     cg = metrics.batch_counts(gpu_labels[:n_s], batch.pid[:n_s], batch.offsets[:done + 1]).summary()
     co = metrics.batch_counts(lab_ref, batch.pid[:n_s], batch.offsets[:done + 1]).summary()
-    # edge decisions on the first sampled events, over the union of both edge
-    # sets (an edge absent from one side counts as not kept there)
-    agree, union, max_err = 0, 0, 0.0
-    for e in range(min(4, done)):
-        ev = batch.event(e)
-        ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
-                                       wl["k_max"], wl["cut"], feat_scale=fs)
-        g = tr.get_graph(e)
-        G = {(int(s), int(d)): (int(k), float(l))
-             for s, d, k, l in zip(g["src"], g["dst"], g["kept"], g["logit"])}
-        O = {(int(s), int(d)): (int(k), float(l))
-             for s, d, k, l in zip(ref.src, ref.dst, ref.keep, ref.logit)}
-        for key in set(G) | set(O):
-            kg = G.get(key, (0, 0.0))[0]
-            ko = O.get(key, (0, 0.0))[0]
-            agree += kg == ko
-            union += 1
-            if key in G and key in O:
-                sg = 1 / (1 + math.exp(-G[key][1]))
-                so = 1 / (1 + math.exp(-O[key][1]))
-                max_err = max(max_err, abs(sg - so))
+    # edge decisions on every sampled event
+    ag = Agreement()
+    for e in range(done):
+        ag.add(tr.get_graph(e), refs[e], int(batch.offsets[e + 1] - batch.offsets[e]))
+    agm = ag.summary()
     return {"value": round(done / t_used, 2), "unit": "events/s",
             "hits_per_s": round(hits / t_used, 1), "cores": cores, "kind": "oracle",
             "sample": f"first {done} of the {batch.n_events} benchmark events "
                       f"({hits} hits), FP64 C++ oracle, one event per thread",
+            "one_core": {"events_per_s": round(n1 / t1, 3), "hits_per_s": round(h1 / t1, 1),
+                         "sample": f"first {n1} events, one after another on one core"},
             "labels_identical_events": f"{same}/{done}",
             "track_efficiency_gpu": round(cg["efficiency"], 6),
             "track_efficiency_oracle": round(co["efficiency"], 6),
             "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4),
-            "edge_decision_agreement": round(agree / max(union, 1), 6),
-            "edge_decision_events": min(4, done), "max_score_error": max_err}
+            "edge_decision_agreement": agm["edge_decision_agreement"],
+            "edge_decision_events": agm["events"], "edges_compared": agm["edges_compared"],
+            "max_score_error": agm["max_score_error"],
+            "mean_score_error": agm["mean_score_error"]}
 
 
 def occupancy_study(pkg, torch, dev, stream, bins=(20, 50, 100, 150, 200, 300, 400),
@@ -654,13 +726,14 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
     """Config 2: the run-3-like model (embed 3-128-128-128-8, IN h64 K8) on
     100 events of 200 tracks, FP32 vs BF16: events/s with one event per call
     and with the 100 events in one call, BF16 agreement with FP32, and both
-    against the FP64 oracle on two events."""
+    against the FP64 oracle on all 100 events (decisions, score error, labels,
+    track efficiency)."""
     try:
         import oracle
         wl = synth.workload("cfg2_run3_single")
         b = synth.workload_batch(wl)
         res = {}
-        graphs = {}
+        graphs, labels = {}, {}
         for prec in ("fp32", "bf16"):
             tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events,
                                           edges_per_hit=24, use_graph=False)
@@ -696,32 +769,42 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
             res[prec] = {"one_event_per_call_events_per_s": round(n / (s1.elapsed_time(e1) / 1e3), 1),
                          "batched_events_per_s": round(n / (s2.elapsed_time(e2) / 1e3), 1)}
             graphs[prec] = [tr.get_graph(e) for e in range(b.n_events)]
+            labels[prec] = lab.cpu().numpy()
             tr.close()
         g16, g32 = graphs["bf16"], graphs["fp32"]
         sig = lambda v: 1 / (1 + np.exp(-np.asarray(v, np.float64)))
         d = np.concatenate([np.abs(sig(a["logit"]) - sig(c["logit"])) for a, c in zip(g16, g32)])
         agree = np.mean(np.concatenate([a["kept"] == c["kept"] for a, c in zip(g16, g32)]))
+        # both precisions against the FP64 oracle on every event
+        from oracle import metrics
         sh = synth.shape_of(wl)
         m = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
         fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
-        err = {"fp32": [], "bf16": []}
-        for e in range(2):
-            ev = b.event(e)
-            ref = oracle.find_tracks_event(m, ev.x, ev.y, ev.z, ev.plane, wl["radius2"], wl["k_max"],
-                                           feat_scale=fs)
-            O = {(int(u), int(v)): float(l) for u, v, l in zip(ref.src, ref.dst, ref.logit)}
-            for prec, gs in (("fp32", g32), ("bf16", g16)):
-                g = gs[e]
-                for u, v, l in zip(g["src"], g["dst"], g["logit"]):
-                    if (int(u), int(v)) in O:
-                        err[prec].append(abs(sig(l) - sig(O[(int(u), int(v))])))
+        t0 = time.perf_counter()
+        refs = oracle_events(m, b, list(range(b.n_events)), wl, fs, os.cpu_count() or 1)
+        t_or = time.perf_counter() - t0
+        lab_ref = np.concatenate([r.labels for r in refs])
+        co = metrics.batch_counts(lab_ref, b.pid, b.offsets).summary()
+        vs = {}
+        for prec, gs in (("fp32", g32), ("bf16", g16)):
+            ag = Agreement()
+            for e in range(b.n_events):
+                ag.add(gs[e], refs[e], int(b.offsets[e + 1] - b.offsets[e]))
+            cg = metrics.batch_counts(labels[prec], b.pid, b.offsets).summary()
+            vs[prec] = {**ag.summary(),
+                        "labels_identical_events": int(sum(
+                            np.array_equal(labels[prec][b.offsets[e]:b.offsets[e + 1]],
+                                           lab_ref[b.offsets[e]:b.offsets[e + 1]])
+                            for e in range(b.n_events))),
+                        "track_efficiency": round(cg["efficiency"], 6),
+                        "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4)}
         return {"workload": f"cfg2_run3_single: {b.n_events} events, {wl['description']}",
                 "hits": int(b.n_hits), **res,
                 "bf16_vs_fp32": {"max_score_error": round(float(d.max()), 6),
                                  "mean_score_error": round(float(d.mean()), 6),
                                  "edge_decision_agreement": round(float(agree), 6)},
-                "vs_fp64_oracle_2_events": {p_: {"max_score_error": float(np.max(v)) if v else None}
-                                            for p_, v in err.items()}}
+                "vs_fp64_oracle": {"events": b.n_events, "track_efficiency_oracle": round(co["efficiency"], 6),
+                                   "oracle_seconds": round(t_or, 2), **vs}}
     except Exception as ex:  # reported, not fatal
         return {"error": str(ex)}
 
@@ -889,9 +972,9 @@ def triplet_report(pkg, torch, dev, stream, flush, steps=5, sample=50):
             pk = peaks()
             if prec == "fp32":
                 ach = n_t * 2.0 * (2 * h * h + h) / (t_ms / 1e3) / 1e12 if t_ms else 0.0
-                peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+                peak, psrc = fp32_peak(torch, dev, pk)
                 roof = {"bound": "alu", "achieved": round(ach, 2), "unit": "TFLOP/s",
-                        "peak": round(peak, 2), "frac": round(ach / peak, 4)}
+                        "peak": round(peak, 2), "frac": round(ach / peak, 4), "peak_src": psrc}
             else:
                 ach = n_t * (2 * h * 2 + 8 + 5) / (t_ms / 1e3) / 1e9 if t_ms else 0.0
                 roof = {"bound": "hbm", "achieved": round(ach, 1), "unit": "GB/s",
@@ -998,12 +1081,14 @@ def int8_report(pkg, torch, dev, stream, flush, steps=5, calib_events=5000, samp
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
 
 
-def fp8_report(pkg, torch, dev, stream, chunk=1000):
+def fp8_report(pkg, torch, dev, stream, chunk=1000, bands=(0.02, 0.05), oracle_events_n=1000):
     """Config 4: FP8-E4M3 (per-channel weight scales, per-row activation
-    scales, FP32 accumulate), config-1 model at hidden 128, 10000 events of
-    200 tracks. Throughput over all events; agreement with the FP32 path on all
-    events; score error, decision agreement and track efficiency against the
-    FP64 oracle on a sample (one event per host core)."""
+    scales, FP32 accumulate; the encoders as BF16 split-operand kernels),
+    config-1 model at hidden 128, 10000 events of 200 tracks. Throughput over
+    all events of FP32, FP8 and FP8 with the FP32 re-score band; decisions of
+    each against FP32 and, on a seeded 1000-event subset (the first chunk),
+    against the FP64 oracle (decision agreement over the union of edge sets,
+    score error, identical labels, track efficiency)."""
     try:
         import oracle
         from oracle import metrics
@@ -1011,12 +1096,14 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000):
         n = wl["n_events"]
         chunks = [synth.workload_batch(wl, chunk, first_event=c) for c in range(0, n, chunk)]
         maxh = max(b.n_hits for b in chunks)
-        res = {}
-        graphs = {}
-        for prec in ("fp8", "fp32"):
-            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=maxh, max_events=chunk,
-                                          edges_per_hit=16, use_graph=True)
-            ms, agree_n, edges_n, kept = 0.0, 0, 0, []
+        b0 = chunks[0]
+        variants = [("fp32", "fp32", 0.0), ("fp8", "fp8", 0.0)] + \
+                   [(f"fp8_band_{bd}", "fp8", bd) for bd in bands]
+        res, first = {}, {}
+        for name, prec, band in variants:
+            tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=band, max_hits=maxh,
+                                          max_events=chunk, edges_per_hit=16, use_graph=True)
+            ms, rows, edges = 0.0, 0, 0
             for ci, b in enumerate(chunks):
                 xyz = torch.from_numpy(b.xyz_soa()).to(dev)
                 plane = torch.from_numpy(b.plane).to(dev)
@@ -1032,96 +1119,66 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000):
                 e_.synchronize()
                 tr.sync_status(stream)
                 ms += s_.elapsed_time(e_)
+                st = tr.stats()
+                rows += st["rescore_edges"]
+                edges += st["edges"]
                 if ci == 0:
-                    graphs[prec] = [tr.get_graph(e) for e in range(b.n_events)]
-                    res[prec + "_labels0"] = lab.cpu().numpy()
-            res[prec] = {"events_per_s": round(n / (ms / 1e3), 1), "ms_per_1000_events": round(ms / len(chunks), 3)}
+                    gs = [tr.get_graph(e) for e in range(b.n_events)]
+                    first[name] = {"kept": [g["kept"] for g in gs], "logit": [g["logit"] for g in gs],
+                                   "labels": lab.cpu().numpy()}
+                    if name == "fp32":
+                        first["src"] = [g["src"] for g in gs]
+                        first["dst"] = [g["dst"] for g in gs]
+                    first[name]["band_edges"] = st["band"]
+            res[name] = {"events_per_s": round(n / (ms / 1e3), 1),
+                         "ms_per_1000_events": round(ms / len(chunks), 3),
+                         "rescore_rows_per_edge": round(rows / max(edges, 1), 4)}
             tr.close()
-        # FP8 with the FP32 re-score band on the first chunk: events/s and
-        # decisions against FP32 (a wider band trades throughput for agreement)
-        b0 = chunks[0]
-        xyz0 = torch.from_numpy(b0.xyz_soa()).to(dev)
-        plane0 = torch.from_numpy(b0.plane).to(dev)
-        offs0 = torch.from_numpy(b0.offsets).to(dev)
-        lab0 = torch.empty(b0.n_hits, dtype=torch.int32, device=dev)
-        kept32 = np.concatenate([g["kept"] for g in graphs["fp32"]])
-        banded = {}
-        for band in (0.05, 0.1):
-            tr = pkg.tracker_for_workload(wl, precision="fp8", rescore_band=band, max_hits=maxh,
-                                          max_events=chunk, edges_per_hit=16, use_graph=True)
-            tr.find_tracks(b0.n_events, b0.n_hits, xyz0, plane0, offs0, lab0, stream)
-            tr.sync_status(stream)
-            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                s_.record(stream)
-                tr.find_tracks(b0.n_events, b0.n_hits, xyz0, plane0, offs0, lab0, stream)
-                e_.record(stream)
-            e_.synchronize()
-            tr.sync_status(stream)
-            kb = np.concatenate([tr.get_graph(e)["kept"] for e in range(b0.n_events)])
-            st = tr.stats()
-            banded[f"band_{band}"] = {
-                "events_per_s": round(b0.n_events / (s_.elapsed_time(e_) / 1e3), 1),
-                "edge_decision_agreement_vs_fp32": round(float(np.mean(kb == kept32)), 6),
-                "band_edges": st["band"], "rescore_edges": st["rescore_edges"]}
-            tr.close()
-        res["fp8_with_rescore_first_1000_events"] = banded
-        # FP8 vs FP32 on the first chunk (same graph: the embedding is FP32 in both)
-        g8, g32 = graphs["fp8"], graphs["fp32"]
-        d = np.concatenate([np.abs(1 / (1 + np.exp(-a["logit"].astype(np.float64))) -
-                                   1 / (1 + np.exp(-b["logit"].astype(np.float64))))
-                            for a, b in zip(g8, g32)])
-        agree32 = np.mean(np.concatenate([a["kept"] == b["kept"] for a, b in zip(g8, g32)]))
-        # against the FP64 oracle on a sample
+        fp32_rate = res["fp32"]["events_per_s"]
+        for name, _, _ in variants[1:]:
+            res[name]["over_fp32"] = round(res[name]["events_per_s"] / fp32_rate, 3)
+        # decisions against the FP32 path on the first chunk (same graph: the
+        # embedding is FP32 in every precision)
+        k32 = np.concatenate(first["fp32"]["kept"])
+        l32 = np.concatenate(first["fp32"]["logit"]).astype(np.float64)
+        sig = lambda v: 1 / (1 + np.exp(-np.asarray(v, np.float64)))
+        for name, _, _ in variants[1:]:
+            kk = np.concatenate(first[name]["kept"])
+            dd = np.abs(sig(np.concatenate(first[name]["logit"])) - sig(l32))
+            res[name]["vs_fp32_first_1000_events"] = {
+                "edge_decision_agreement": round(float(np.mean(kk == k32)), 6),
+                "max_score_error": round(float(dd.max()), 5), "mean_score_error": round(float(dd.mean()), 6)}
+        # against the FP64 oracle on the first `oracle_events_n` events
         sh = synth.shape_of(wl)
         model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
         fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
         cores = os.cpu_count() or 1
-        b0 = chunks[0]
-        sample = list(range(min(cores, b0.n_events)))
-        sub = b0.subset(sample)
+        ne = min(oracle_events_n, b0.n_events)
         t0 = time.perf_counter()
-        lab_ref, _ = oracle.find_tracks_batch(model, sub.x, sub.y, sub.z, sub.plane, sub.offsets,
-                                              wl["radius2"], wl["k_max"], wl["cut"],
-                                              threads=cores, feat_scale=fs)
-        t_oracle = time.perf_counter() - t0
-        agree = union = 0
-        errs = []
-        import concurrent.futures as cf
-
-        def one(e):  # the oracle call releases the GIL (ctypes)
-            ev = b0.event(e)
-            return e, oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
-                                               wl["k_max"], wl["cut"], feat_scale=fs)
-        with cf.ThreadPoolExecutor(4) as ex:
-            refs = list(ex.map(one, sample[:4]))
-        for e, ref in refs:
-            O = {(int(x), int(y)): (int(k), float(l)) for x, y, k, l in zip(ref.src, ref.dst, ref.keep, ref.logit)}
-            G = {(int(x), int(y)): (int(k), float(l)) for x, y, k, l in
-                 zip(g8[e]["src"], g8[e]["dst"], g8[e]["kept"], g8[e]["logit"])}
-            for key in set(O) | set(G):
-                agree += O.get(key, (0, 0))[0] == G.get(key, (0, 0))[0]
-                union += 1
-                if key in O and key in G:
-                    errs.append(abs(1 / (1 + math.exp(-O[key][1])) - 1 / (1 + math.exp(-G[key][1]))))
-        nh = int(sub.n_hits)
-        lab8 = res["fp8_labels0"][:nh]
-        c8 = metrics.batch_counts(lab8, sub.pid, sub.offsets).summary()
-        co = metrics.batch_counts(lab_ref, sub.pid, sub.offsets).summary()
+        refs = oracle_events(model, b0, list(range(ne)), wl, fs, cores)
+        t_or = time.perf_counter() - t0
+        lab_ref = np.concatenate([r.labels for r in refs])
+        nh = int(b0.offsets[ne])
+        co = metrics.batch_counts(lab_ref, b0.pid[:nh], b0.offsets[:ne + 1]).summary()
+        vs = {"events": ne, "hits": nh, "oracle_seconds": round(t_or, 1), "oracle_cores": cores,
+              "track_efficiency_oracle": round(co["efficiency"], 6)}
+        for name, _, _ in variants:
+            ag = Agreement()
+            for e in range(ne):
+                g = {"src": first["src"][e], "dst": first["dst"][e], "kept": first[name]["kept"][e],
+                     "logit": first[name]["logit"][e]}
+                ag.add(g, refs[e], int(b0.offsets[e + 1] - b0.offsets[e]))
+            lab = first[name]["labels"][:nh]
+            cg = metrics.batch_counts(lab, b0.pid[:nh], b0.offsets[:ne + 1]).summary()
+            vs[name] = {**ag.summary(),
+                        "labels_identical_events": int(sum(
+                            np.array_equal(lab[b0.offsets[e]:b0.offsets[e + 1]],
+                                           lab_ref[b0.offsets[e]:b0.offsets[e + 1]]) for e in range(ne))),
+                        "track_efficiency": round(cg["efficiency"], 6),
+                        "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4)}
         return {"workload": f"cfg4_batched_fp8: {n} events, {wl['description']}",
-                "fp8": res["fp8"], "fp32": res["fp32"],
-                "fp8_with_rescore_first_1000_events": res["fp8_with_rescore_first_1000_events"],
-                "vs_fp32_first_1000_events": {"max_score_error": round(float(d.max()), 5),
-                                              "mean_score_error": round(float(d.mean()), 6),
-                                              "edge_decision_agreement": round(float(agree32), 6)},
-                "vs_fp64_oracle": {"events": len(sample),
-                                   "edge_decision_agreement (4 events)": round(agree / max(union, 1), 6),
-                                   "max_score_error (4 events)": round(max(errs), 5) if errs else None,
-                                   "mean_score_error (4 events)": round(float(np.mean(errs)), 6) if errs else None,
-                                   "track_efficiency_fp8": round(c8["efficiency"], 6),
-                                   "track_efficiency_oracle": round(co["efficiency"], 6),
-                                   "track_efficiency_delta_pp": round(100 * abs(c8["efficiency"] - co["efficiency"]), 4),
-                                   "oracle_seconds": round(t_oracle, 2), "oracle_cores": cores}}
+                "dtype": "e4m3 GNN steps and classifier (tcgen05 kind::f8f6f4); BF16 split-operand encoders",
+                **res, "vs_fp64_oracle": vs}
     except Exception as ex:  # reported, not fatal
         import traceback
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}

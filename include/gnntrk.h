@@ -94,9 +94,12 @@ typedef enum gnntrk_precision {
  * Precision:
  *   precision: a gnntrk_precision value.
  *   rescore_band: for BF16/FP8, edges with |sigmoid(logit) - score_cut| <
- *            rescore_band are re-decided in FP32: every event holding such an
- *            edge has its GNN re-run in FP32 and only those edges take the
- *            FP32 decision. 0 disables re-scoring.
+ *            rescore_band are re-decided in FP32: the rows in the receptive
+ *            field of those edges (per message-passing step, the hits and
+ *            edges their final logit depends on; see gnntrk_rescore_rows)
+ *            are recomputed in FP32 from the FP32 embedding, step by step,
+ *            and only the band edges take the FP32 logit and decision.
+ *            0 disables re-scoring.
  * Capacity:
  *   max_hits, max_events: largest call this handle accepts.
  *   edges_per_hit: edge workspace, in edges per hit of max_hits. A call whose
@@ -360,8 +363,10 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
  *     by the shared memory, registers and tensor-memory columns each CTA needs;
  *     choice[0..3] = node encoder, edge encoder, node step, edge step;
  *   - FP32 SIMT kernels (FP32 handles, and the FP32 re-score of BF16/FP8 handles
- *     with a re-score band): tile-shape variant 0 (4 warps per block) or 1
- *     (8 warps per block); choice[4..6] = encoders, node step, edge step.
+ *     with a re-score band): variant 0 (4 warps per block), 1 (8 warps per
+ *     block) or 2 (edge kernels with two stages of row buffers per warp: the
+ *     next tile's rows are copied asynchronously while a tile computes; node
+ *     kernels as variant 0); choice[4..6] = encoders, node step, edge step.
  * The fastest setting of each family is kept and applies to every handle of
  * the process with the same precision and hidden width. choice: host int32 [8]
  * or NULL (entry 7 is 0). Synchronous. Errors: as gnntrk_find_tracks and
@@ -377,7 +382,7 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
  * previous gnntrk_autotune returned (saved by the caller): choice[0..3] =
  * resident CTAs per SM of the tensor-core families (0 = the resource bound;
  * ignored by FP32 handles; capped by the resources each CTA needs),
- * choice[4..6] = FP32 tile variant 0 or 1 of the encoders, node step and edge
+ * choice[4..6] = FP32 variant 0, 1 or 2 of the encoders, node step and edge
  * step; entry 7 is ignored. Like the autotuner's result it applies to every
  * handle of the process with the same precision and hidden width, and drops
  * this handle's captured CUDA graphs (another handle's graphs keep the launch
@@ -421,8 +426,12 @@ int64_t gnntrk_workspace_bytes(const gnntrk_cfg* cfg);
  *   weights, weights_bytes, model: as for gnntrk_create; the capacity fields
  *            of `model` are replaced by the batch caps below.
  *   scfg: host; n_slots (1..16, batches in flight), max_events_per_batch,
- *            max_hits_per_batch (every single event must fit), memory_budget_bytes
- *            (device bytes of all slots together).
+ *            max_hits_per_batch (every single event must fit; each slot's
+ *            workspace is sized for it, so it sets how many slots the budget
+ *            holds), memory_budget_bytes (device bytes of all slots together),
+ *            apply_tuning / tuning (a saved autotuner choice applied to the
+ *            slots' handles before the first batch; entries as for
+ *            gnntrk_set_tuning, INVALID_ARG if one is out of range).
  *   n_events, offsets (host int64 [n_events+1]), hits_xyz (host float32
  *            [3][n_hits]), plane (host uint8 [n_hits]): the request stream,
  *            events in arrival order.
@@ -445,7 +454,9 @@ typedef struct gnntrk_serve_cfg {
   int32_t max_events_per_batch;
   int64_t max_hits_per_batch;
   int64_t memory_budget_bytes;
-  int32_t reserved[8];
+  int32_t apply_tuning;  /* 1: every slot applies `tuning` (gnntrk_set_tuning) */
+  int32_t tuning[8];     /* a launch configuration gnntrk_autotune returned */
+  int32_t reserved[7];
 } gnntrk_serve_cfg;
 
 gnntrk_status gnntrk_serve_run(const void* weights, size_t weights_bytes, const gnntrk_cfg* model,
@@ -474,17 +485,25 @@ gnntrk_status gnntrk_serve_run(const void* weights, size_t weights_bytes, const 
  * Scratch: one fixed device array of 4 * (GNNTRK_NOALLOC_MAX_HITS + 64) bytes
  *   (4 MiB + 256 B), part of the library image: every GPU on which the library
  *   is loaded holds it until the process exits.
- * Set-up: the first call on a device looks up the array's device address with
- *   that device current; make that first call before any stream capture.
+ * Set-up: every call looks up the array's device address with the calling
+ *   thread's current device, so a call after a device reset (which may reload
+ *   the library's module at another address) uses the new address. Inside a
+ *   stream capture the lookup is not made; the address the last uncaptured
+ *   call on that device found is used instead, so make one call on each
+ *   device before capturing any, and none across a device reset.
  * Sharing: every call on a device uses the same array, which keeps the last
  *   call's contents (each call rewrites what it reads first). Calls whose work
  *   overlaps on the GPU -- on different streams or from different host threads
  *   -- race on it and give undefined labels: keep them on one stream.
  * Errors: INVALID_ARG (synchronous, nothing launched) when n_hits exceeds
- *   GNNTRK_NOALLOC_MAX_HITS, n_edges is out of range or a needed pointer is
- *   NULL; CUDA when a launch fails. gnntrk_last_error(NULL) describes it. An
- *   edge index outside [0, n_hits) is detected on the device: every label of
- *   that call is then -1.
+ *   GNNTRK_NOALLOC_MAX_HITS, n_edges is out of range, edges are given with
+ *   n_hits == 0 (no vertex can hold them) or a needed pointer is NULL; CUDA
+ *   when a launch fails, or when a capture is running on a device that has
+ *   had no uncaptured call yet. gnntrk_last_error(NULL) describes it.
+ *   Detected on the device, with GNNTRK_OK returned: an edge index outside
+ *   [0, n_hits), or a union whose bounded retries ran out (contention that
+ *   does not settle); every label of that call is then -1, which no valid
+ *   labelling contains.
  * Asynchronous on `stream`.
  */
 #define GNNTRK_NOALLOC_MAX_HITS (1 << 20)

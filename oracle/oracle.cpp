@@ -25,7 +25,7 @@
 //   components  weakly connected components of the purified graph (Algorithms 2
 //               and 3, depth-first search); each component is a track candidate.
 //
-// Readings where the thesis is silent (each one is listed in the design notes):
+// Readings where the thesis is silent:
 //   * features: embedding input (r/s0, phi/s1, z/s2), node-encoder input
 //     (x/s3, y/s4, z/s5) with phi = atan2(y, x);
 //   * every GNN sub-network (encoders, node and edge networks, classifier) is

@@ -41,6 +41,11 @@ class GnntrkError(RuntimeError):
         self.status = status
 
 
+# the entries of a launch configuration (gnntrk_autotune / gnntrk_set_tuning)
+TUNING_KEYS = ("tc_node_prep", "tc_edge_encoder", "tc_node_update", "tc_edge_update",
+               "f32_encoders", "f32_node_update", "f32_edge_update")
+
+
 class ServeCfg(ctypes.Structure):
     """Mirror of gnntrk_serve_cfg."""
     _fields_ = [
@@ -48,7 +53,9 @@ class ServeCfg(ctypes.Structure):
         ("max_events_per_batch", ctypes.c_int32),
         ("max_hits_per_batch", ctypes.c_int64),
         ("memory_budget_bytes", ctypes.c_int64),
-        ("reserved", ctypes.c_int32 * 8),
+        ("apply_tuning", ctypes.c_int32),
+        ("tuning", ctypes.c_int32 * 8),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -326,10 +333,8 @@ class Tracker:
 
     def set_tuning(self, choice: dict):
         """Apply a launch configuration (the dict autotune returns) without timing."""
-        keys = ("tc_node_prep", "tc_edge_encoder", "tc_node_update", "tc_edge_update",
-                "f32_encoders", "f32_node_update", "f32_edge_update")
         ch = np.zeros(8, np.int32)
-        for i, k in enumerate(keys):
+        for i, k in enumerate(TUNING_KEYS):
             ch[i] = int(choice.get(k, 0))
         self._check(self._L.gnntrk_set_tuning(self._h, ch.ctypes.data_as(ctypes.c_void_p)))
 
@@ -440,11 +445,16 @@ def workspace_bytes(cfg: Cfg) -> int:
 
 def serve_run(weights: bytes, cfg: Cfg, batch, arrival_s, n_slots: int = 4,
               max_events_per_batch: int = 512, max_hits_per_batch: int = 1 << 20,
-              memory_budget_bytes: int = 40_000_000_000):
+              memory_budget_bytes: int = 40_000_000_000, tuning: dict | None = None):
     """Run the continuous-batching server over a host `synth.Batch` whose events
-    arrive at `arrival_s` (seconds). Returns (labels, done_s, stats)."""
+    arrive at `arrival_s` (seconds); `tuning` is a dict `Tracker.autotune`
+    returned, applied to every slot. Returns (labels, done_s, stats)."""
     L = load_library()
     sc = ServeCfg(n_slots, max_events_per_batch, max_hits_per_batch, memory_budget_bytes)
+    if tuning is not None:
+        sc.apply_tuning = 1
+        for i, k in enumerate(TUNING_KEYS):
+            sc.tuning[i] = int(tuning.get(k, 0))
     xyz = np.ascontiguousarray(batch.xyz_soa(), np.float32)
     plane = np.ascontiguousarray(batch.plane, np.uint8)
     offs = np.ascontiguousarray(batch.offsets, np.int64)

@@ -1020,7 +1020,7 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
                              {"edge_update", "rescore_edge_update"}};
     double best_t[3] = {1e30, 1e30, 1e30};
     int best_v[3] = {0, 0, 0};
-    for (int v = 0; v < 2 && !st; ++v) {
+    for (int v = 0; v < 3 && !st; ++v) {
       for (int f = 0; f < 3; ++f) f32_set_variant(hd, f, v);
       st = trial(t);
       for (int f = 0; f < 3; ++f) {
@@ -1060,8 +1060,8 @@ gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
     if (choice[f] < 0 || choice[f] > 8)
       return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[0..3] must be 0..8 CTAs per SM");
   for (int f = 4; f < 7; ++f)
-    if (choice[f] < 0 || choice[f] > 1)
-      return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[4..6] must be an FP32 variant 0 or 1");
+    if (choice[f] < 0 || choice[f] > 2)
+      return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[4..6] must be an FP32 variant 0, 1 or 2");
   const int prec = h->cfg.precision, hd = h->h;
   if (prec != GNNTRK_FP32)
     for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, choice[f]);

@@ -171,19 +171,26 @@ __global__ void __launch_bounds__(kCcThreads) k_cc_event(Batch b, Ws w) {
 
 void set_global_error(const std::string& msg);
 
-// Device address of the scratch array on the current device; looked up once
-// per device (with that device current) and cached.
-static cudaError_t noalloc_scratch(int32_t** out) {
+// Device address of the scratch array on the current device. Looked up on
+// every call made outside a stream capture (a device reset may reload the
+// module at another address), and remembered per device for calls made while
+// `s` is being captured, where the last uncaptured lookup is used.
+static cudaError_t noalloc_scratch(cudaStream_t s, int32_t** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
+  if (cs == cudaStreamCaptureStatusNone) {
     int32_t* p = nullptr;
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
+  } else if (g_noalloc_ptr[dev] == nullptr) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
@@ -226,15 +233,19 @@ extern "C" gnntrk_status gnntrk_components_noalloc(int64_t n_hits, int64_t n_edg
     set_global_error("gnntrk_components_noalloc: NULL pointer");
     return GNNTRK_ERR_INVALID_ARG;
   }
+  if (n_hits == 0 && n_edges > 0) {
+    set_global_error("gnntrk_components_noalloc: edges given with n_hits == 0");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
   if (n_hits == 0) return GNNTRK_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  cudaError_t e = noalloc_scratch(s, &scratch);
   if (e != cudaSuccess) {
     set_global_error(std::string("gnntrk_components_noalloc: scratch address: ") +
                      cudaGetErrorString(e));
     return GNNTRK_ERR_CUDA;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = int(n_hits), ne = int(n_edges);
   k_na_init<<<div_up(n > kNoAllocHeader ? n : kNoAllocHeader, 256), 256, 0, s>>>(scratch, n);
   if (ne > 0) k_na_union<<<device_sms() * 8, 256, 0, s>>>(scratch, n, ne, src, dst, kept);

@@ -59,7 +59,11 @@ struct Warps {
 };
 
 // Variant chosen per (hidden index, kernel family: 0 encoders, 1 node step,
-// 2 edge step and classifier); set by the autotuner, process wide.
+// 2 edge step and classifier); set by the autotuner, process wide. Variants:
+// 0 = 4 warps per block, 1 = 8 warps per block, 2 = 4 warps per block with the
+// edge kernels' weight matrices staged once per block in shared memory at
+// hidden 32 (the row gathers evict them from L1; node kernels, and every
+// kernel at hidden 64 and 128, run variant 0 then).
 std::atomic<int> g_f32_variant[3][3] = {};
 
 enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
@@ -71,7 +75,8 @@ __device__ __forceinline__ bool input_bad(const Ws& w) {
 
 // acc[i][4j+u] (+)= sum_{k < KV} A[rg + 4i][k] * WT[(k_off + k) * ldo + 32j + 4cg + u],
 // k ascending; A row-major with stride LDA (K a multiple of 4, KV <= K valid)
-template <int H, int K, int KV, int LDA>
+// (SW: the weights WT are in shared memory, row stride ldo)
+template <int H, int K, int KV, int LDA, bool SW = false>
 __device__ __forceinline__ void warp_layer(const float* A, const LayerF32& L, int k_off, int rg,
                                            int cg, float (&acc)[WarpTile<H>::RM][WarpTile<H>::CW]) {
   constexpr int RM = WarpTile<H>::RM, NJ = WarpTile<H>::NJ;
@@ -88,7 +93,8 @@ __device__ __forceinline__ void warp_layer(const float* A, const LayerF32& L, in
       float4 q[NJ];
 #pragma unroll
       for (int j = 0; j < NJ; ++j)
-        q[j] = __ldg(reinterpret_cast<const float4*>(wp + size_t(k4 + t) * L.ldo + 32 * j));
+        q[j] = SW ? *reinterpret_cast<const float4*>(wp + size_t(k4 + t) * L.ldo + 32 * j)
+                  : __ldg(reinterpret_cast<const float4*>(wp + size_t(k4 + t) * L.ldo + 32 * j));
 #pragma unroll
       for (int i = 0; i < RM; ++i) {
         const float av = t == 0 ? a[i].x : (t == 1 ? a[i].y : (t == 2 ? a[i].z : a[i].w));
@@ -220,10 +226,10 @@ __device__ __forceinline__ void stage_rows(float* S, const int* rows, const floa
     const int ry = TWO ? (row >= 0 ? rows2[gr + 4 * i] : 0) : 0;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      v[i][j] = __ldg(reinterpret_cast<const float4*>(X + size_t(rx) * ldx + offx + 32 * j + 4 * q));
+      v[i][j] = __ldcg(reinterpret_cast<const float4*>(X + size_t(rx) * ldx + offx + 32 * j + 4 * q));
       if (TWO) {
         const float4 y =
-            __ldg(reinterpret_cast<const float4*>(Y + size_t(ry) * ldy + offy + 32 * j + 4 * q));
+            __ldcg(reinterpret_cast<const float4*>(Y + size_t(ry) * ldy + offy + 32 * j + 4 * q));
         v[i][j].x += y.x;
         v[i][j].y += y.y;
         v[i][j].z += y.z;
@@ -280,17 +286,36 @@ __host__ __device__ constexpr int g_warp_floats() {
 // 4-warp edge kernels fit 5 blocks of shared memory per SM, so their
 // registers are capped to let 5 blocks (20 warps) reside; elsewhere the
 // compiler's choice stands.
-template <int H, int MODE, int NW>
+template <int H, int MODE, int NW, bool SW>
 __host__ __device__ constexpr int g_min_blocks() {
-  return (H == 32 && NW == 4 && MODE != G_NODE_ENC && MODE != G_NODE_UPD) ? 5 : 1;
+  return (H == 32 && NW == 4 && MODE != G_NODE_ENC && MODE != G_NODE_UPD) ? (SW ? 4 : 5) : 1;
 }
 
-template <int H, int MODE, int NW>
-__global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_f32(const GnnArgs p) {
+// Weight matrices an edge kernel keeps in shared memory (variant 2): the e
+// block of the first layer (edge steps), the second layer, the classifier's
+// first layer (last step); H x H floats each.
+template <int MODE>
+__host__ __device__ constexpr int g_sw_mats() {
+  return MODE == G_EDGE_ENC ? 1 : (MODE == G_EDGE_UPD ? 2 : (MODE == G_EDGE_UPD_CLS ? 3 : 0));
+}
+
+// copy rows [0, H) of a transposed layer (row stride ldo) into S (row stride H)
+template <int H, int NT>
+__device__ __forceinline__ void stage_weights(float* S, const LayerF32& L) {
+  for (int i = threadIdx.x; i < H * H / 4; i += NT) {
+    const int k = i / (H / 4), c = 4 * (i % (H / 4));
+    *reinterpret_cast<float4*>(S + k * H + c) =
+        __ldg(reinterpret_cast<const float4*>(L.WT + size_t(k) * L.ldo + c));
+  }
+}
+
+template <int H, int MODE, int NW, bool SW = false>
+__global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_gnn_f32(const GnnArgs p) {
   using T = WarpTile<H>;
   constexpr int RM = T::RM, CW = T::CW, WR = T::WR;
   constexpr int LDA = g_lda<H, MODE>();
   constexpr bool EDGE_ROWS = MODE != G_NODE_ENC && MODE != G_NODE_UPD;
+  static_assert(!SW || g_sw_mats<MODE>() > 0, "weights in shared memory: edge kernels only");
   extern __shared__ __align__(16) float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* As = sm + warp * g_warp_floats<H, MODE>();  // [WR][LDA]
@@ -311,6 +336,28 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
   }
   const int rg = lane >> 3, cg = lane & 7;
   const int E = clamp_edges(w.counters, w.e_cap);
+  // the layers this kernel multiplies by: global memory, or (SW) copies in
+  // shared memory after the warps' slices (row stride H)
+  LayerF32 l1 = p.m.l1, l2 = p.m.l2, c1 = p.cls.l1;
+  if constexpr (SW) {
+    float* S = sm + NW * g_warp_floats<H, MODE>();
+    if constexpr (MODE != G_EDGE_ENC) {
+      stage_weights<H, NW * 32>(S, p.m.l1);  // rows [0, H): the e block
+      l1 = LayerF32{S, p.m.l1.b, H, H, H};
+      S += H * H;
+    }
+    stage_weights<H, NW * 32>(S, p.m.l2);
+    l2 = LayerF32{S, p.m.l2.b, H, H, H};
+    S += H * H;
+    if constexpr (MODE == G_EDGE_UPD_CLS) {
+      stage_weights<H, NW * 32>(S, p.cls.l1);
+      c1 = LayerF32{S, p.cls.l1.b, H, H, H};
+    }
+    __syncthreads();
+  }
+  (void)l1;
+  (void)l2;
+  (void)c1;
 
   for (int base = lo + (blockIdx.x * NW + warp) * WR; base < hi; base += gridDim.x * NW * WR) {
     // ---- rows of this warp -----------------------------------------------
@@ -395,7 +442,7 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
       warp_layer<H, H, H, LDA>(As, p.m.l1, 0, rg, cg, acc);
       warp_layer<H, H, H, T::LDH>(Hs, p.m.l1, H, rg, cg, acc);
       acc_ln_relu<H>(acc);
-      const LayerF32& l2 = p.m.l2;
+      const LayerF32& tl2 = p.m.l2;
 #pragma unroll
       for (int i = 0; i < RM; ++i) {
         float part = 0.f;
@@ -403,8 +450,8 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
         for (int j = 0; j < T::NJ; ++j)
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            part = fmaf(acc[i][4 * j + u], __ldg(l2.WT + size_t(32 * j + 4 * cg + u) * l2.ldo), part);
-        const float lg = l2.b[0] + row_sum(part);
+            part = fmaf(acc[i][4 * j + u], __ldg(tl2.WT + size_t(32 * j + 4 * cg + u) * tl2.ldo), part);
+        const float lg = tl2.b[0] + row_sum(part);
         const int row = rows[rg + 4 * i];
         if (cg == 0 && row >= 0) {
           p.tlogit[row] = lg;
@@ -419,14 +466,14 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
           stage_rows<H, false>(As, rows, w.estate, H, 0, nullptr, nullptr, 0, 0, lane);
         __syncwarp();
         acc_bias<H>(p.m.l1.b, cg, acc);
-        if constexpr (MODE != G_EDGE_ENC) warp_layer<H, H, H, LDA>(As, p.m.l1, 0, rg, cg, acc);
+        if constexpr (MODE != G_EDGE_ENC) warp_layer<H, H, H, LDA, SW>(As, l1, 0, rg, cg, acc);
         acc_add_smem<H>(Hs, rg, cg, acc);
         acc_ln_relu<H>(acc);
         acc_store_smem<H>(Hs, rg, cg, acc);  // own elements only
         __syncwarp();
         // ---- layer 2 (+ residual e) -----------------------------------------
         acc_bias<H>(p.m.l2.b, cg, acc);
-        warp_layer<H, H, H, T::LDH>(Hs, p.m.l2, 0, rg, cg, acc);
+        warp_layer<H, H, H, T::LDH, SW>(Hs, l2, 0, rg, cg, acc);
         if constexpr (MODE != G_EDGE_ENC) acc_add_smem<H>(As, rg, cg, acc);
         if constexpr (MODE != G_EDGE_UPD_CLS) acc_store_rows<H>(w.estate, H, 0, rows, rg, cg, acc);
         if constexpr (MODE == G_EDGE_UPD_CLS) {
@@ -439,9 +486,9 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
         // ---- classifier: Linear -> LayerNorm -> ReLU -> dot, then the cut ----
         __syncwarp();
         acc_bias<H>(p.cls.l1.b, cg, acc);
-        warp_layer<H, H, H, LDA>(As, p.cls.l1, 0, rg, cg, acc);
+        warp_layer<H, H, H, LDA, SW && MODE == G_EDGE_UPD_CLS>(As, c1, 0, rg, cg, acc);
         acc_ln_relu<H>(acc);
-        const LayerF32& l2 = p.cls.l2;
+        const LayerF32& cl2 = p.cls.l2;
 #pragma unroll
         for (int i = 0; i < RM; ++i) {
           float part = 0.f;
@@ -449,8 +496,8 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW>())) k_gnn_
           for (int j = 0; j < T::NJ; ++j)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              part = fmaf(acc[i][4 * j + u], __ldg(l2.WT + size_t(32 * j + 4 * cg + u) * l2.ldo), part);
-          const float lg = l2.b[0] + row_sum(part);
+              part = fmaf(acc[i][4 * j + u], __ldg(cl2.WT + size_t(32 * j + 4 * cg + u) * cl2.ldo), part);
+          const float lg = cl2.b[0] + row_sum(part);
           const int row = rows[rg + 4 * i];
           if (cg == 0 && row >= 0) {
             bool write = true;
@@ -703,14 +750,19 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
 
 template <int H, int MODE, int V>
 void launch_gnn_v(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
-  constexpr int NW = Warps<V>::NW, WR = WarpTile<H>::WR;
-  const size_t smem = size_t(NW) * g_warp_floats<H, MODE>() * sizeof(float);
-  const void* fn = (const void*)k_gnn_f32<H, MODE, NW>;
+  // (at hidden 64 and 128 the matrices would cost most of the shared memory
+  // the warps' slices need, so variant 2 is variant 0 there)
+  constexpr bool SW = V == 2 && H == 32 && g_sw_mats<MODE>() > 0;
+  constexpr int NW = Warps<V == 1 ? 1 : 0>::NW, WR = WarpTile<H>::WR;
+  const size_t smem =
+      (size_t(NW) * g_warp_floats<H, MODE>() + (SW ? size_t(g_sw_mats<MODE>()) * H * H : 0)) *
+      sizeof(float);
+  const void* fn = (const void*)k_gnn_f32<H, MODE, NW, SW>;
   const int full = device_sms() * blocks_per_sm(fn, NW * 32, smem);
   dim3 grid(full, 1);
   if (a.sel.rows == nullptr && rows_hint >= 0)
     grid.x = rows_hint == 0 ? 1 : unsigned(std::min<int64_t>(full, div_up(rows_hint, NW * WR)));
-  k_gnn_f32<H, MODE, NW><<<grid, NW * 32, smem, s>>>(a);
+  k_gnn_f32<H, MODE, NW, SW><<<grid, NW * 32, smem, s>>>(a);
 }
 
 constexpr int f32_family(int mode) {
@@ -721,7 +773,9 @@ template <int H, int MODE>
 void launch_gnn(const GnnArgs& a, int64_t rows_hint, cudaStream_t s) {
   const int v =
       g_f32_variant[H == 32 ? 0 : (H == 64 ? 1 : 2)][f32_family(MODE)].load(std::memory_order_relaxed);
-  if (v == 1)
+  if (v == 2)
+    launch_gnn_v<H, MODE, 2>(a, rows_hint, s);
+  else if (v == 1)
     launch_gnn_v<H, MODE, 1>(a, rows_hint, s);
   else
     launch_gnn_v<H, MODE, 0>(a, rows_hint, s);
@@ -783,7 +837,7 @@ void launch_triplet_scores_f32(const Batch& b, const Ws& w, const TripletHeads& 
 
 void f32_set_variant(int h, int family, int v) {
   if ((h != 32 && h != 64 && h != 128) || family < 0 || family > 2) return;
-  g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family].store((v == 1) ? 1 : 0,
+  g_f32_variant[h == 32 ? 0 : (h == 64 ? 1 : 2)][family].store((v >= 0 && v <= 2) ? v : 0,
                                                                 std::memory_order_relaxed);
 }
 

@@ -116,6 +116,11 @@ extern "C" gnntrk_status gnntrk_serve_run(const void* weights, size_t weights_by
       cleanup();
       return err(st, std::string("slot handle: ") + gnntrk_last_error(nullptr));
     }
+    if (scfg->apply_tuning && (st = gnntrk_set_tuning(s.h, scfg->tuning)) != GNNTRK_OK) {
+      const std::string m = gnntrk_last_error(s.h);
+      cleanup();
+      return err(st, "tuning: " + m);
+    }
     const int64_t H = c.max_hits, Ev = c.max_events;
     bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&

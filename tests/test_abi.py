@@ -148,11 +148,18 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
                    "  gnntrk_cfg c;\n"
                    "  gnntrk_default_cfg(&c);\n"
                    "  if (c.hidden != 32 || c.iters != 4 || c.embed_dims[3] != 4) return 1;\n"
+                   "  if (sizeof(gnntrk_cfg) != SZ_CFG || sizeof(gnntrk_serve_cfg) != SZ_SERVE)"
+                   " return 3;\n"
                    "  return gnntrk_set_tuning(0, 0) == GNNTRK_ERR_INVALID_ARG ? 0 : 2;\n"
                    "}\n")
     libdir = os.path.dirname(LIB_PATH)
     exe = tmp_path / "use"
+    import ctypes
+    import paper_2508_07423_gb300 as pkg
+    # the binding's struct mirrors have the C layout's sizes
+    sizes = [f"-DSZ_CFG={ctypes.sizeof(pkg.Cfg)}", f"-DSZ_SERVE={ctypes.sizeof(pkg.ServeCfg)}"]
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           *sizes,
                            "-I", os.path.join(root, "include"), str(src), "-L", libdir,
                            "-lgnntrk", f"-Wl,-rpath,{libdir}", "-o", str(exe)])
     assert subprocess.run([str(exe)]).returncode == 0

@@ -9,8 +9,9 @@ low-precision paths are checked against it and against the oracle:
     hundredths of a logit after 4 steps; E4M3 keeps 4: about 6 %);
   * edges in the re-score band take exactly the FP32 path's logit and
     decision, all others keep the tensor-core result;
-  * with the re-score, BF16 agrees with the FP64 oracle on >= 99.9 % of edge
-    decisions.
+  * with the re-score, BF16 (and, with a wider band, the wide models in BF16
+    and FP8) agrees with the FP64 oracle on >= 99.9 % of edge decisions;
+    without it the wide models miss that bar (recorded as expected failures).
 """
 import math
 
@@ -171,12 +172,14 @@ def test_tensor_core_batch_equals_one_event_per_call(cfg1):
             assert np.array_equal(g[0][k], g_b[e][k]), k
 
 
-@pytest.mark.parametrize("name,prec,mean_tol,agree_min", [
-    ("cfg2_run3_single", "bf16", 0.02, 0.99),
-    ("cfg2_run3_single", "fp8", 0.2, 0.9),
-    ("cfg4_batched_fp8", "fp8", 0.2, 0.9),
+@pytest.mark.parametrize("name,prec,mean_tol", [
+    ("cfg2_run3_single", "bf16", 0.02),
+    ("cfg2_run3_single", "fp8", 0.2),
+    ("cfg4_batched_fp8", "fp8", 0.2),
 ])
-def test_wide_models(name, prec, mean_tol, agree_min):
+def test_wide_models_logit_error(name, prec, mean_tol):
+    """Without the re-score band: same graph as FP32, logit error within the
+    format's bound (BF16 8 significant bits, E4M3 4)."""
     wl = synth.workload(name)
     b = synth.workload_batch(wl, 1)
     _, g32, _ = run(wl, b, "fp32")
@@ -184,7 +187,59 @@ def test_wide_models(name, prec, mean_tol, agree_min):
     assert np.array_equal(g[0]["src"], g32[0]["src"])
     d = np.abs(g[0]["logit"].astype(np.float64) - g32[0]["logit"])
     assert d.mean() < mean_tol, d.mean()
-    assert np.mean(g[0]["kept"] == g32[0]["kept"]) >= agree_min
+
+
+@pytest.mark.parametrize("name,prec", [
+    pytest.param("cfg2_run3_single", "bf16", marks=pytest.mark.xfail(
+        strict=True, reason="BF16 alone at h64 K8 agrees with FP32 on about 99.5 % of the "
+                            "decisions; the re-score band brings it to the bar")),
+    pytest.param("cfg4_batched_fp8", "fp8", marks=pytest.mark.xfail(
+        strict=True, reason="E4M3 alone at h128 agrees with FP32 on about 95.8 % of the "
+                            "decisions; the re-score band brings it to the bar")),
+])
+def test_wide_models_without_band_miss_the_bar(name, prec):
+    """Recorded gap: the low-precision forms alone do not reach 99.9 % decision
+    agreement on seeded weights, whose logits crowd the cut."""
+    wl = synth.workload(name)
+    b = synth.workload_batch(wl, 1)
+    _, g32, _ = run(wl, b, "fp32")
+    _, g, _ = run(wl, b, prec)
+    assert np.mean(g[0]["kept"] == g32[0]["kept"]) >= 0.999
+
+
+@pytest.mark.parametrize("name,prec,band,n_events", [
+    ("cfg2_run3_single", "bf16", 0.02, 8),
+    ("cfg4_batched_fp8", "fp8", 0.05, 8),
+])
+def test_wide_models_with_band_at_the_bar(name, prec, band, n_events):
+    """With the FP32 re-score band, the wide models agree with the FP64 oracle
+    on >= 99.9 % of the edge decisions (union of both edge sets) and label
+    most events identically."""
+    import concurrent.futures as cf
+    import os
+    wl = synth.workload(name)
+    b = synth.workload_batch(wl, n_events)
+    labels, g, _ = run(wl, b, prec, band=band)
+    sh = synth.shape_of(wl)
+    m = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+    fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+
+    def one(e):
+        ev = b.event(e)
+        return oracle.find_tracks_event(m, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                        wl["k_max"], feat_scale=fs)
+    with cf.ThreadPoolExecutor(min(n_events, os.cpu_count() or 1)) as ex:
+        refs = list(ex.map(one, range(n_events)))
+    agree = union = same = 0
+    for e, ref in enumerate(refs):
+        O = {(int(s), int(t)): int(k) for s, t, k in zip(ref.src, ref.dst, ref.keep)}
+        G = {(int(s), int(t)): int(k) for s, t, k in zip(g[e]["src"], g[e]["dst"], g[e]["kept"])}
+        for key in set(O) | set(G):
+            agree += O.get(key, 0) == G.get(key, 0)
+            union += 1
+        same += np.array_equal(labels[b.offsets[e]:b.offsets[e + 1]], ref.labels)
+    assert agree / union >= 0.999, agree / union
+    assert same >= n_events // 2, same
 
 
 def test_bf16_at_hidden_128_is_rejected():
@@ -245,7 +300,7 @@ def test_autotune_picks_a_count_and_keeps_results():
     labels = torch.zeros(b.n_hits, dtype=torch.int32, device="cuda")
     choice = tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, labels)
     assert all(1 <= v <= 8 for k, v in choice.items() if k.startswith("tc_")), choice
-    assert all(v in (0, 1) for k, v in choice.items() if k.startswith("f32_")), choice
+    assert all(v in (0, 1, 2) for k, v in choice.items() if k.startswith("f32_")), choice
     tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, labels)
     tr.sync_status()
     # launch shapes do not change any result
@@ -267,10 +322,11 @@ def test_autotune_picks_a_count_and_keeps_results():
                                        ("cfg4_batched_fp8", "fp32"), ("cfg3_batched_bf16", "bf16"),
                                        ("cfg4_batched_fp8", "fp8")])
 def test_fp32_tile_variants_give_identical_results(name, prec):
-    """Every FP32 tile variant (warps per block) computes each
-    row with the same arithmetic: labels, graphs and logits are bit-identical
-    across variants, for the FP32 path and for the FP32 re-score of the
-    tensor-core paths, at hidden 32, 64 and 128."""
+    """Every FP32 variant (4 or 8 warps per block, or the edge kernels that
+    copy the next tile's rows in while a tile computes) computes each row with
+    the same arithmetic: labels, graphs and logits are bit-identical across
+    variants, for the FP32 path and for the FP32 re-score of the tensor-core
+    paths, at hidden 32, 64 and 128."""
     wl = synth.workload(name)
     b = synth.workload_batch(wl, 3)
     band = 0.02 if prec != "fp32" else 0.0
@@ -278,7 +334,7 @@ def test_fp32_tile_variants_give_identical_results(name, prec):
                                   max_events=b.n_events, edges_per_hit=32)
     ref = None
     try:
-        for v in (0, 1):
+        for v in (0, 1, 2):
             tr.set_tuning({"f32_encoders": v, "f32_node_update": v, "f32_edge_update": v})
             labels = pkg.run_batch(tr, b)
             graphs = [tr.get_graph(e) for e in range(b.n_events)]
@@ -299,7 +355,7 @@ def test_fp32_tile_variants_give_identical_results(name, prec):
 def test_set_tuning_rejects_out_of_range_choices():
     wl = synth.workload("cfg1_plain_fp32")
     tr = pkg.tracker_for_workload(wl, max_hits=1024, max_events=2)
-    for bad in ({"f32_edge_update": 2}, {"tc_edge_update": 9}, {"f32_encoders": -1}):
+    for bad in ({"f32_edge_update": 3}, {"tc_edge_update": 9}, {"f32_encoders": -1}):
         with pytest.raises(pkg.GnntrkError):
             tr.set_tuning(bad)
     tr.set_tuning({})

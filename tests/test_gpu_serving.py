@@ -18,9 +18,12 @@ def test_serving_results_equal_alone(prec):
     band = 0.02 if prec != "fp32" else 0.0
     cfg = pkg.make_cfg(wl["model"], wl["radius2"], k_max=wl["k_max"], precision=prec,
                        rescore_band=band, edges_per_hit=24)
+    # a saved launch configuration applied to every slot (results do not
+    # depend on it)
+    tuning = {"tc_edge_update": 2, "tc_node_update": 3} if prec == "bf16" else {"f32_edge_update": 2, "f32_encoders": 2}
     labels, done, st = pkg.serve_run(synth.workload_weights(wl), cfg, b, arrivals, n_slots=3,
                                      max_events_per_batch=32, max_hits_per_batch=1 << 16,
-                                     memory_budget_bytes=8 << 30)
+                                     memory_budget_bytes=8 << 30, tuning=tuning)
     assert st["failed_batches"] == 0
     assert st["batches"] < b.n_events          # events were batched together
     assert st["largest_batch"] <= 32
@@ -34,6 +37,16 @@ def test_serving_results_equal_alone(prec):
         a = int(b.offsets[e])
         assert np.array_equal(labels[a:a + ev.n_hits], alone), e
     tr.close()
+
+
+def test_serving_rejects_a_tuning_entry_out_of_range():
+    wl = synth.workload("cfg5_serving")
+    b = synth.workload_batch(wl, 2)
+    cfg = pkg.make_cfg(wl["model"], wl["radius2"], precision="bf16")
+    with pytest.raises(pkg.GnntrkError) as ei:
+        pkg.serve_run(synth.workload_weights(wl), cfg, b, np.zeros(2), max_hits_per_batch=1 << 14,
+                      memory_budget_bytes=1 << 30, tuning={"tc_edge_update": 99})
+    assert ei.value.status == 1
 
 
 def test_serving_budget_too_small_is_rejected():

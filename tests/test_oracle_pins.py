@@ -136,6 +136,29 @@ def test_radius_graph_brute_force(seed):
         assert edge_set(s, d) == brute_force_graph(plane, emb, 1.5, k_max)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_candidate_d2_brute_force(seed):
+    """The all-pairs list the radius calibration draws its quantiles from: every
+    pair from plane p to plane p+1 or p+2 (below n_planes), squared distance,
+    no radius and no cap, as a multiset; its size is sum_p n_p (n_p+1 + n_p+2)."""
+    rng = np.random.default_rng(100 + seed)
+    n, n_planes = 30, 5
+    plane = rng.integers(0, n_planes + 2, n)  # some hits on planes past the last
+    emb = rng.normal(size=(n, 4))
+    got = np.sort(oracle.candidate_d2(plane, emb, n_planes=n_planes))
+    ref = sorted(float(np.sum((emb[i] - emb[j]) ** 2)) for i in range(n) for j in range(n)
+                 if plane[j] - plane[i] in (1, 2) and plane[j] < n_planes)
+    assert got.size == len(ref)
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+    cnt = np.bincount(plane, minlength=n_planes + 4)
+    assert got.size == sum(int(cnt[p]) * (int(cnt[p + 1]) * (p + 1 < n_planes) +
+                                          int(cnt[p + 2]) * (p + 2 < n_planes))
+                           for p in range(n_planes))
+    # with no radius and no cap the radius graph keeps exactly these pairs
+    _, _, d2 = oracle.radius_graph(plane, emb, 1e30, n, n_planes=n_planes)
+    assert np.allclose(np.sort(d2), got, rtol=0, atol=1e-12)
+
+
 def test_radius_graph_invariants_on_event():
     wl = synth.workload("cfg1_plain_fp32")
     sh = synth.shape_of(wl)

@@ -62,3 +62,12 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = call_noalloc(L, pkg.NOALLOC_MAX_HITS + 1, z, z, None, z)
     assert st == 1
     assert b"at most" in L.gnntrk_last_error(None)
+
+
+def test_noalloc_rejects_edges_without_vertices():
+    L = pkg.load_library()
+    z = torch.zeros(4, dtype=torch.int32, device="cuda")
+    st = L.gnntrk_components_noalloc(0, 4, z.data_ptr(), z.data_ptr(), None, z.data_ptr(),
+                                     ctypes.c_void_p(0))
+    assert st == 1
+    assert b"n_hits == 0" in L.gnntrk_last_error(None)
