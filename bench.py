@@ -724,19 +724,21 @@ def occupancy_study(pkg, torch, dev, stream, bins=(20, 50, 100, 150, 200, 300, 4
 
 def cfg2_report(pkg, torch, dev, stream, reps=3):
     """Config 2: the run-3-like model (embed 3-128-128-128-8, IN h64 K8) on
-    100 events of 200 tracks, FP32 vs BF16: events/s with one event per call
-    and with the 100 events in one call, BF16 agreement with FP32, and both
-    against the FP64 oracle on all 100 events (decisions, score error, labels,
-    track efficiency)."""
+    100 events of 200 tracks, FP32 vs BF16 (alone, and with the FP32 re-score
+    band |s - 0.5| < 0.02): events/s with one event per call and with the 100
+    events in one call, BF16 agreement with FP32, and every form against the
+    FP64 oracle on all 100 events (decisions, score error, labels, track
+    efficiency)."""
     try:
         import oracle
         wl = synth.workload("cfg2_run3_single")
         b = synth.workload_batch(wl)
         res = {}
         graphs, labels = {}, {}
-        for prec in ("fp32", "bf16"):
-            tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events,
-                                          edges_per_hit=24, use_graph=False)
+        for name, prec, band in (("fp32", "fp32", 0.0), ("bf16", "bf16", 0.0),
+                                 ("bf16_band_0.02", "bf16", 0.02)):
+            tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=band, max_hits=b.n_hits,
+                                          max_events=b.n_events, edges_per_hit=24, use_graph=False)
             evs = []
             for e in range(b.n_events):
                 ev = b.event(e)
@@ -766,10 +768,10 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
             e2.synchronize()
             tr.sync_status(stream)
             n = reps * b.n_events
-            res[prec] = {"one_event_per_call_events_per_s": round(n / (s1.elapsed_time(e1) / 1e3), 1),
+            res[name] = {"one_event_per_call_events_per_s": round(n / (s1.elapsed_time(e1) / 1e3), 1),
                          "batched_events_per_s": round(n / (s2.elapsed_time(e2) / 1e3), 1)}
-            graphs[prec] = [tr.get_graph(e) for e in range(b.n_events)]
-            labels[prec] = lab.cpu().numpy()
+            graphs[name] = [tr.get_graph(e) for e in range(b.n_events)]
+            labels[name] = lab.cpu().numpy()
             tr.close()
         g16, g32 = graphs["bf16"], graphs["fp32"]
         sig = lambda v: 1 / (1 + np.exp(-np.asarray(v, np.float64)))
@@ -786,7 +788,7 @@ def cfg2_report(pkg, torch, dev, stream, reps=3):
         lab_ref = np.concatenate([r.labels for r in refs])
         co = metrics.batch_counts(lab_ref, b.pid, b.offsets).summary()
         vs = {}
-        for prec, gs in (("fp32", g32), ("bf16", g16)):
+        for prec, gs in graphs.items():
             ag = Agreement()
             for e in range(b.n_events):
                 ag.add(gs[e], refs[e], int(b.offsets[e + 1] - b.offsets[e]))

@@ -43,7 +43,7 @@ class GnntrkError(RuntimeError):
 
 # the entries of a launch configuration (gnntrk_autotune / gnntrk_set_tuning)
 TUNING_KEYS = ("tc_node_prep", "tc_edge_encoder", "tc_node_update", "tc_edge_update",
-               "f32_encoders", "f32_node_update", "f32_edge_update")
+               "f32_encoders", "f32_node_update", "f32_edge_update", "tc_edge_tma")
 
 
 class ServeCfg(ctypes.Structure):
@@ -326,10 +326,7 @@ class Tracker:
                                             _ptr(plane), _ptr(offsets), _ptr(out_labels),
                                             ctypes.c_void_p(s),
                                             ch.ctypes.data_as(ctypes.c_void_p)))
-        return {"tc_node_prep": int(ch[0]), "tc_edge_encoder": int(ch[1]),
-                "tc_node_update": int(ch[2]), "tc_edge_update": int(ch[3]),
-                "f32_encoders": int(ch[4]), "f32_node_update": int(ch[5]),
-                "f32_edge_update": int(ch[6])}
+        return dict(zip(TUNING_KEYS, (int(v) for v in ch)))
 
     def set_tuning(self, choice: dict):
         """Apply a launch configuration (the dict autotune returns) without timing."""

@@ -75,7 +75,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(log)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcuda"]
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -679,6 +679,7 @@ gnntrk_status gnntrk_create(const void* weights, size_t weights_bytes, const gnn
     st = (gnntrk_status)tc_upload_triplets(h->tc, L[n_gnn_layers], L[n_gnn_layers + 2],
                                            &h->d_wtrip, h->err);
   if (!st) st = alloc_workspace(h);
+  if (!st && c.precision == GNNTRK_BF16) tc_make_maps(h->tc, h->ws, h->h);
   if (st) {
     g_create_error = h->err;
     gnntrk_destroy(h);
@@ -1010,6 +1011,22 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
       tc_set_ctas(prec, hd, f, best_n[f]);
       if (choice) choice[f] = best_n[f];
     }
+    // BF16 edge step at hidden 32: per-thread row copies or TMA (choice[7])
+    if (!st && prec == GNNTRK_BF16 && h->tc.maps) {
+      double best = 1e30;
+      int best_form = 0;
+      for (int form = 0; form < 2 && !st; ++form) {
+        tc_set_edge_form(form);
+        st = trial(t);
+        const double v = stage_ms(t, "edge_update");
+        if (v < best) {
+          best = v;
+          best_form = form;
+        }
+      }
+      tc_set_edge_form(best_form);
+      if (choice) choice[7] = best_form;
+    }
   }
   // 2. FP32 kernels (the FP32 path, or the re-score of a tensor-core path):
   //    tile-shape variant per family (choice[4..6])
@@ -1062,9 +1079,12 @@ gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
   for (int f = 4; f < 7; ++f)
     if (choice[f] < 0 || choice[f] > 2)
       return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[4..6] must be an FP32 variant 0, 1 or 2");
+  if (choice[7] < 0 || choice[7] > 1)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[7] must be an edge-step form 0 or 1");
   const int prec = h->cfg.precision, hd = h->h;
   if (prec != GNNTRK_FP32)
     for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, choice[f]);
+  if (prec == GNNTRK_BF16) tc_set_edge_form(choice[7]);
   for (int f = 0; f < 3; ++f) f32_set_variant(hd, f, choice[4 + f]);
   // captured graphs hold the old launch configuration
   for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);

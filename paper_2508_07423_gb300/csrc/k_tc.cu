@@ -23,6 +23,7 @@
 // amax/448. Hidden rows are quantised per row as well. The K = 3 first layer of
 // the node encoder and the 1-unit last layer of the classifier stay FP32.
 #include <cuda_fp8.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <atomic>
@@ -941,6 +942,319 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 }
 
 // ---------------------------------------------------------------------------
+// BF16 edge step with TMA-staged tiles (hidden 32). Same arithmetic as
+// k_tc<32, BF16, M_EDGE_UPD / M_EDGE_UPD_CLS> (the MMAs see the same operand
+// values in the same K order), but the layer-1 input [e, h_src, h_dst] of a
+// tile is never touched by the threads:
+//   * segment 0 (e rows, contiguous edges) is one 2-D TMA box of 128 rows;
+//   * segments 1 and 2 (h_src, h_dst rows) are TMA row gathers, four rows per
+//     instruction, one instruction per lane of warp 0 and segment;
+// each segment lands as 128 rows x 64 bytes in the 64-byte swizzle layout
+// (8 KB, 1024-byte aligned), which the MMA reads through swizzled
+// descriptors. One tile buffer: once layer 1 has read it and every thread has
+// taken its residual row into registers, the next tile's rows load while
+// layer 2 and the epilogue run. The hidden row and the classifier input are
+// written by the threads into a no-swizzle tile as in k_tc.
+// ---------------------------------------------------------------------------
+template <int H, bool CLS>
+struct TmaLayout {
+  static constexpr int SEG = kRows * H * 2;  // one segment: 128 rows x 64 bytes
+  static constexpr int K1 = 3 * H;
+  static constexpr int W1 = 0;
+  static constexpr int W1_BYTES = H * K1 * 2;
+  static constexpr int W2 = align1k(W1 + W1_BYTES);
+  static constexpr int W2_BYTES = H * H * 2;
+  static constexpr int WC = align1k(W2 + W2_BYTES);
+  static constexpr int WC_BYTES = CLS ? H * H * 2 : 0;
+  static constexpr int A = align1k(WC + WC_BYTES);
+  static constexpr int ABUF = 3 * SEG;
+  static constexpr int HA = align1k(A + ABUF);
+  static constexpr int HA_BYTES = kRows * H * 2;
+  static constexpr int PAR = HA + HA_BYTES;
+  static constexpr int PAR_FLOATS = 4 * H + 4;  // b1, b2, bc1, c2 weights + bias
+  static constexpr int BAR = PAR + PAR_FLOATS * 4;  // [0] weights [1] mma [2] tile
+  static constexpr int TOTAL = BAR + 64;
+  static constexpr int ALLOC = TOTAL + 1024;  // room to align the base to 1024 bytes
+};
+
+// (registers capped so that five CTAs fit an SM, as their shared memory does)
+template <int H, bool CLS>
+__global__ void __launch_bounds__(kRows, 5)
+    k_tc_edge_tma(const TcArgs p, const __grid_constant__ CUtensorMap map_e,
+                  const __grid_constant__ CUtensorMap map_h) {
+  static_assert(H == 32, "one BF16 row segment of 32 elements is one 64-byte swizzle row");
+  using L = TmaLayout<H, CLS>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* sW1 = smem + L::W1;
+  uint8_t* sW2 = smem + L::W2;
+  uint8_t* sWC = smem + L::WC;
+  uint8_t* sHA = smem + L::HA;
+  float* par = reinterpret_cast<float*>(smem + L::PAR);
+  float* pb1 = par;
+  float* pb2 = par + H;
+  float* pbc = par + 2 * H;
+  float* pc2 = par + 3 * H;  // classifier layer 2: H weights, then the bias
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::BAR + 32);
+  constexpr int KCHH = H * 2 / 16;  // 16-byte chunks per row of the hidden tile
+  constexpr int MODE = CLS ? M_EDGE_UPD_CLS : M_EDGE_UPD;
+  (void)MODE;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Ws& w = p.w;
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, 32);
+    tmem_relinquish();
+  }
+  for (int i = tid; i < H; i += kRows) {
+    pb1[i] = p.b1[i];
+    pb2[i] = p.b2[i];
+    pbc[i] = CLS ? p.bc1[i] : 0.f;
+    pc2[i] = CLS ? p.c2.WT[i * p.c2.ldo] : 0.f;
+  }
+  if (tid == 0) pc2[H] = CLS ? p.c2.b[0] : 0.f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const uint32_t tmem_lane = tmem_base + (uint32_t(warp * 32) << 16);
+
+  if (tid == 0) {
+    mbar_expect_tx(&bar[0], uint32_t(L::W1_BYTES + L::W2_BYTES + L::WC_BYTES));
+    bulk_g2s(sW1, p.W1, L::W1_BYTES, &bar[0]);
+    bulk_g2s(sW2, p.W2, L::W2_BYTES, &bar[0]);
+    if (CLS) bulk_g2s(sWC, p.Wc, L::WC_BYTES, &bar[0]);
+  }
+  const bool wok = mbar_wait_bounded(&bar[0], 0, kWaitCycles);
+  const bool weights_late = __syncthreads_or(!wok);
+  bool aborted = weights_late;
+  uint32_t mma_phase = 0, a_phase = 0;
+  bool mma_pending = false, a_pending = false;
+
+  const int hi = clamp_edges(w.counters, w.e_cap);
+  const int n_tiles = (hi + kRows - 1) / kRows;
+  uint8_t* A = smem + L::A;
+
+  // warp 0: the node indices of the four rows 4 lane .. 4 lane + 3 of tile t
+  // (rows past the last edge gather node 0 and are never stored), loaded a
+  // phase ahead of their use
+  int sv[4] = {0, 0, 0, 0}, dv[4] = {0, 0, 0, 0};
+  auto load_idx = [&](int t) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = t * kRows + 4 * lane + i;
+      sv[i] = r < hi ? w.src[r] : 0;
+      dv[i] = r < hi ? w.col[r] : 0;
+    }
+  };
+  // warp 0: the loads of tile t (expect-tx first, then the box of e rows and
+  // each lane's two four-row gathers)
+  auto issue = [&](int t) {
+    if (lane == 0) {
+      mbar_expect_tx(&bar[2], uint32_t(3 * L::SEG));
+      tma_load_2d(A, &map_e, 0, t * kRows, &bar[2]);
+    }
+    __syncwarp();
+    tma_gather4(A + L::SEG + 4 * lane * (H * 2), &map_h, 0, sv[0], sv[1], sv[2], sv[3], &bar[2]);
+    tma_gather4(A + 2 * L::SEG + 4 * lane * (H * 2), &map_h, 0, dv[0], dv[1], dv[2], dv[3],
+                &bar[2]);
+  };
+  auto wait_mma = [&]() -> bool {
+    mma_pending = true;
+    const bool good = mbar_wait_bounded(&bar[1], mma_phase, kWaitCycles);
+    tc_fence_after();
+    if (__syncthreads_or(!good)) return false;
+    mma_phase ^= 1;
+    mma_pending = false;
+    return true;
+  };
+
+  if (!aborted && int(blockIdx.x) < n_tiles) {
+    if (warp == 0) {
+      load_idx(blockIdx.x);
+      issue(blockIdx.x);
+    }
+    a_pending = true;
+  }
+  for (int t = blockIdx.x; t < n_tiles && !aborted; t += gridDim.x) {
+    const int tn = t + int(gridDim.x);
+    if (warp == 0 && tn < n_tiles) load_idx(tn);  // used after layer 1
+    const bool got = mbar_wait_bounded(&bar[2], a_phase, kWaitCycles);
+    if (__syncthreads_or(!got)) {
+      aborted = true;
+      break;
+    }
+    a_phase ^= 1;
+    a_pending = false;
+    const int r = t * kRows + tid;
+    const bool valid = r < hi;
+
+    // ---- layer 1: [e, h_src, h_dst] x W1 (K = 3H, 16 per instruction) --------
+    if (tid == 0) {
+      tc_fence_after();
+      constexpr uint32_t IDESC = idesc_bf16(kRows, H);
+      constexpr uint32_t SBO_W = uint32_t(L::K1 * 2 / 16) * 128;
+      const uint32_t a0 = smem_u32(A), w0 = smem_u32(sW1);
+#pragma unroll
+      for (int k = 0; k < L::K1; k += 16) {
+        const int seg = k / H, j = (k % H) / 16;
+        const uint64_t ad = smem_desc_sw64(a0 + uint32_t(seg * L::SEG + j * 32));
+        const uint64_t bd = smem_desc(w0 + uint32_t(k * 2 / 16) * 128, 128, SBO_W);
+        mma_bf16(tmem_base, ad, bd, IDESC, k > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar[1]);
+    }
+    if (!wait_mma()) {
+      aborted = true;
+      break;
+    }
+    // the residual: this row's e from segment 0 (64-byte swizzle), kept in
+    // registers so that the buffer is free once the barrier below is passed
+    uint4 e_row[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      e_row[q] = *reinterpret_cast<const uint4*>(A + tid * (H * 2) + ((q ^ ((tid >> 1) & 3)) << 4));
+    // ---- bias + LayerNorm + ReLU -> hidden tile --------------------------------
+    float x[32];
+    {
+      float v[32];
+      tmem_ld32(tmem_lane, v);
+      tmem_wait_ld();
+      add_params<false>(v, pb1, pb1, x);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sum += x[j];
+    const float mean = sum / float(H);
+    float var = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float d = x[j] - mean;
+      var = fmaf(d, d, var);
+    }
+    const float inv = 1.0f / sqrtf(var / float(H) + kLnEps);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = fmaxf((x[j] - mean) * inv, 0.f);
+    put_row_f32<false>(sHA, tid, KCHH, 0, x, 32, 1.f);
+    fence_proxy_async();  // hidden tile (MMA operand) and the reads of A done
+    tc_fence_before();
+    __syncthreads();
+    // the tile buffer is free: the next tile's rows load during layer 2
+    if (tn < n_tiles) {
+      if (warp == 0) issue(tn);
+      a_pending = true;
+    }
+
+    // ---- layer 2 ----------------------------------------------------------------
+    if (tid == 0) {
+      tc_fence_after();
+      issue_layer<H, false>(tmem_base, sHA, sW2, H, 1);
+      mma_commit(&bar[1]);
+    }
+    if (!wait_mma()) {
+      aborted = true;
+      break;
+    }
+    float z[32];
+    {
+      float v[32];
+      tmem_ld32(tmem_lane, v);
+      tmem_wait_ld();
+      add_params<false>(v, pb2, pb2, z);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 u = e_row[q];
+      z[8 * q + 0] += bf16_lo(u.x);
+      z[8 * q + 1] += bf16_hi(u.x);
+      z[8 * q + 2] += bf16_lo(u.y);
+      z[8 * q + 3] += bf16_hi(u.y);
+      z[8 * q + 4] += bf16_lo(u.z);
+      z[8 * q + 5] += bf16_hi(u.z);
+      z[8 * q + 6] += bf16_lo(u.w);
+      z[8 * q + 7] += bf16_hi(u.w);
+    }
+    if constexpr (!CLS) {
+      if (valid) {
+        uint4* d4 = reinterpret_cast<uint4*>(w.estate16 + size_t(r) * H);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          d4[q] = make_uint4(pack_bf16(z[8 * q], z[8 * q + 1]), pack_bf16(z[8 * q + 2], z[8 * q + 3]),
+                             pack_bf16(z[8 * q + 4], z[8 * q + 5]), pack_bf16(z[8 * q + 6], z[8 * q + 7]));
+      }
+      tc_fence_before();
+      __syncthreads();  // every thread has read the tensor memory of this tile
+    } else {
+      // ---- classifier on the new edge state (rounded to BF16 as stored) -------
+#pragma unroll
+      for (int j = 0; j < 32; ++j) z[j] = __bfloat162float(__float2bfloat16_rn(z[j]));
+      put_row_f32<false>(sHA, tid, KCHH, 0, z, 32, 1.f);
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        issue_layer<H, false>(tmem_base, sHA, sWC, H, 1);
+        mma_commit(&bar[1]);
+      }
+      if (!wait_mma()) {
+        aborted = true;
+        break;
+      }
+      float c[32];
+      {
+        float v[32];
+        tmem_ld32(tmem_lane, v);
+        tmem_wait_ld();
+        add_params<false>(v, pbc, pbc, c);
+      }
+      float cs = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) cs += c[j];
+      const float cmean = cs / float(H);
+      float cvar = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float d = c[j] - cmean;
+        cvar = fmaf(d, d, cvar);
+      }
+      const float cinv = 1.0f / sqrtf(cvar / float(H) + kLnEps);
+      float logit = pc2[H];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) logit = fmaf(fmaxf((c[j] - cmean) * cinv, 0.f), pc2[j], logit);
+      if (valid) {
+        w.logit[r] = logit;
+        w.keep[r] = logit >= p.cut ? 1 : 0;
+      }
+      tc_fence_before();
+      __syncthreads();  // the hidden tile and the tensor memory are reused
+    }
+  }
+
+  // ---- clean-up: on a timeout, give what is still in flight one more bounded
+  //      wait, then free the tensor memory ---------------------------------------
+  if (aborted) {
+    if (tid == 0) set_status(w.counters, ST_TIMEOUT);
+    if (weights_late) mbar_wait_bounded(&bar[0], 0, kWaitCycles);
+    if (a_pending) mbar_wait_bounded(&bar[2], a_phase, kWaitCycles);
+    if (mma_pending) mbar_wait_bounded(&bar[1], mma_phase, kWaitCycles);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 32);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // messages of the node step from the BF16 edge states: P[v] = [sum of e over
 // v's out edges | sum over its in edges], FP32 sums in increasing list order
 // starting from zero, stored as FP32 (FP8 path: the node step quantises them
@@ -1079,6 +1393,40 @@ constexpr int family_of(int mode) {
 }
 static_assert(family_of(M_TRIP) == 3, "triplet classifier tunes with the edge family");
 constexpr int hidx(int h) { return h == 32 ? 0 : (h == 64 ? 1 : 2); }
+
+std::atomic<int> g_edge_form{0};  // BF16 edge step at hidden 32: 0 copies, 1 TMA
+
+// CTAs per SM of the TMA edge step: shared memory and tensor memory bound
+template <bool CLS>
+int tma_blocks_per_sm() {
+  using L = TmaLayout<32, CLS>;
+  static const int per_sm = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_edge_tma<32, CLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_edge_tma<32, CLS>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) cudaGetLastError();
+    int n = 233472 / (L::ALLOC + 1024);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_tc_edge_tma<32, CLS>) == cudaSuccess && fa.numRegs > 0) {
+      const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+      n = std::min(n, 65536 / (regs_warp * (kRows / 32)));
+    }
+    n = std::max(1, std::min(n, 512 / 32));
+    if (getenv("GNNTRK_VERBOSE"))
+      fprintf(stderr, "gnntrk: k_tc_edge_tma<32,%d> smem %d B, %d CTAs/SM\n", int(CLS), L::ALLOC, n);
+    return n;
+  }();
+  return per_sm;
+}
+
+template <bool CLS>
+void launch_edge_tma(const TcArgs& a, const TcModel& m, cudaStream_t s) {
+  using L = TmaLayout<32, CLS>;
+  const int grid = device_sms() * tma_blocks_per_sm<CLS>();
+  k_tc_edge_tma<32, CLS><<<grid, kRows, L::ALLOC, s>>>(a, m.map_e, m.map_h);
+}
 
 template <int H, bool FP8, int MODE>
 void launch_mode(const TcArgs& a, cudaStream_t s, int rows_hint) {
@@ -1427,11 +1775,56 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
     if (stage < 0 || stage == 2 + 2 * k) {
       set(m.edge[k]);
       const bool last = k + 1 == K;
-      launch_any(h, fp8, last && fuse ? M_EDGE_UPD_CLS : M_EDGE_UPD, a, s, -1);
+      const bool tma = !fp8 && h == 32 && m.maps && g_edge_form.load(std::memory_order_relaxed) == 1;
+      if (tma && last && fuse)
+        launch_edge_tma<true>(a, m, s);
+      else if (tma)
+        launch_edge_tma<false>(a, m, s);
+      else
+        launch_any(h, fp8, last && fuse ? M_EDGE_UPD_CLS : M_EDGE_UPD, a, s, -1);
       if (last && !fuse) launch_any(h, fp8, M_CLS, a, s, -1);
     }
   }
   if (K == 0 && (stage < 0 || stage == 1)) launch_any(h, fp8, M_CLS, a, s, -1);
+}
+
+void tc_set_edge_form(int form) { g_edge_form.store(form == 1 ? 1 : 0, std::memory_order_relaxed); }
+int tc_get_edge_form() { return g_edge_form.load(std::memory_order_relaxed); }
+
+void tc_make_maps(TcModel& m, const Ws& w, int h) {
+  m.maps = false;
+  if (h != 32 || w.estate16 == nullptr || w.hstate16 == nullptr) return;
+  // the driver's encoder, looked up through the runtime (the library does not
+  // link the driver library, so it loads on machines without a GPU driver)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      fn = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (encode == nullptr) return;
+  const cuuint32_t es[2] = {1, 1};
+  const cuuint64_t dim_e[2] = {cuuint64_t(h), cuuint64_t(w.e_cap)};
+  const cuuint64_t dim_h[2] = {cuuint64_t(h), cuuint64_t(w.h_cap)};
+  const cuuint64_t stride[1] = {cuuint64_t(h) * 2};  // bytes between rows
+  const cuuint32_t box_e[2] = {cuuint32_t(h), cuuint32_t(kRows)};
+  const cuuint32_t box_h[2] = {cuuint32_t(h), 1};  // one row high: row gathers
+  CUresult r1 = encode(&m.map_e, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                       static_cast<void*>(w.estate16), dim_e, stride, box_e, es,
+                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(&m.map_h, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                       static_cast<void*>(w.hstate16), dim_h, stride, box_h, es,
+                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  m.maps = r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
 }
 
 void tc_set_ctas(int precision, int h, int family, int n) {

@@ -2,6 +2,8 @@
 // in tensor memory. Interface used by the C ABI.
 #pragma once
 
+#include <cuda.h>
+
 #include "internal.cuh"
 
 namespace gnntrk {
@@ -20,7 +22,21 @@ struct TcModel {
   // first layers of the triplet classifiers (BF16 images in every precision)
   LayerTC art1{}, elb1{};
   bool has_trip = false;
+  // TMA tensor maps of the handle's BF16 states at hidden 32: the edge states
+  // (boxes of 128 rows) and the node states (one-row boxes for row gathers),
+  // both in the 64-byte swizzle layout; valid when `maps` is set
+  CUtensorMap map_e{}, map_h{};
+  bool maps = false;
 };
+
+// Encode the tensor maps of a BF16 handle's workspace (hidden 32); on failure
+// the TMA edge step stays unavailable and the per-thread copies run.
+void tc_make_maps(TcModel& m, const Ws& w, int h);
+
+// BF16 edge-step form at hidden 32, process wide: 0 per-thread row copies, 1
+// TMA tile load and row gathers (only where the handle has tensor maps).
+void tc_set_edge_form(int form);
+int tc_get_edge_form();
 
 // Pack the layers (blob order) for the tensor cores and upload them to one
 // device allocation (*dmem, freed by the caller). Returns a gnntrk_status.

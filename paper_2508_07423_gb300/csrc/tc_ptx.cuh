@@ -96,6 +96,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 64-byte swizzle
+// layout: rows of 64 bytes, 8-row atoms of 512 bytes (atom m at m * 512), the
+// 16-byte chunk c of row r stored at chunk c ^ ((r >> 1) & 3) of its row. The
+// atoms must start on a 1024-byte boundary (base offset 0); one MMA reads
+// K = 32 bytes of each row at byte `saddr` + k0 (k0 = 0 or 32). The leading
+// byte offset is unused for this layout (field 1 by convention); layout type
+// 4 in bits 61..63.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t(1) << 16) | (uint64_t(512 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(4) << 61);
+}
+
 // Instruction descriptors: FP32 accumulator, K-major A and B, M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
@@ -143,6 +155,29 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(m))
+      : "memory");
+}
+
+// ---- tensor memory access (TMA) --------------------------------------------
+// 2-D tiled load of the box at (x, y) of a tensor map into shared memory,
+// completing `bytes` (the box size) on the mbarrier. x * element size must be
+// a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y,
+                                            uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(m))
+      : "memory");
+}
+// Four rows y0..y3 (box one row high, columns from x) of a 2-D tensor map
+// into four consecutive box rows of shared memory.
+__device__ __forceinline__ void tma_gather4(void* dst, const void* map, int x, int y0, int y1,
+                                            int y2, int y3, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_u32(m))
       : "memory");
 }
 
