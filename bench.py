@@ -137,14 +137,22 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # roofline of one stage
 # ----------------------------------------------------------------------------
-def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: int, embed):
+def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: int, embed,
+               deg: float = 0.0):
     """Algorithmic work of ONE launch of `stage`: (bound, amount, unit-of-amount).
 
     FP32 SIMT stages are ALU bound (flops); tensor-core and gather stages are
     HBM bound (bytes). The per-unit figure (per edge / per hit) is written
-    beside each stage below; amount = figure x units of one launch.
+    beside each stage below; amount = figure x units of one launch. `deg` is
+    the batch's mean degree 2E/N (out + in edges per hit), for the messages of
+    a hit subset.
     """
     sb = 4 if precision == "fp32" else 2   # state bytes per element
+    if stage == "rescore_node_messages":
+        # FP32 sums over the listed hits: their incident edges' FP32 rows
+        # (deg per hit on average), the in-edge ids, the two list bounds, and
+        # the 2h-wide FP32 message row written
+        return "hbm", N * (deg * (h * 4 + 2) + 16 + 2 * h * 4), "byte"
     if stage == "rescore_node_prep":  # FP32 node encoder + projections (the embedding is reused)
         return "alu", N * 2.0 * (3 * h + h * h + 2 * h * h), "flop"
     if stage.startswith("rescore_"):  # the FP32 re-run (same kernels as the FP32 path)
@@ -156,11 +164,19 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
             return "alu", E * 2.0 * (h * h + h * h), "flop"
         # read e, h_src, h_dst rows; write e
         return "hbm", E * (4 * h * sb + 8), "byte"
+    if stage == "node_messages":
+        # every edge row read twice (its source's out sum, its target's in
+        # sum), the in-edge ids, the list bounds; the message row written
+        # (BF16 path: rounded to BF16; FP8 path and FP32: FP32)
+        mb = 2 if precision == "bf16" else 4
+        return "hbm", 2 * E * h * sb + 4 * E + N * (16 + 2 * h * mb), "byte"
     if stage == "node_update":
         if precision == "fp32":
             # node network (3h x h, h x h) and the two projections (2 x h x h)
             return "alu", N * 2.0 * (3 * h * h + h * h + 2 * h * h), "flop"
-        return "hbm", N * 2 * h * sb + E * 2 * h * sb + E * 8, "byte"
+        # read h and the message row, write h
+        mb = 2 if precision == "bf16" else 4
+        return "hbm", N * (2 * h * sb + 2 * h * mb), "byte"
     if stage == "edge_encoder":
         if precision == "fp32":
             # 2 h^2 flop per edge against 3 rows of 4h bytes: memory-bound;
@@ -222,7 +238,8 @@ def stage_amount(stage, launches, rows, precision, N, E, m):
     else:
         sets = [(N, E)] * max(launches, 1)
     for n_k, e_k in sets:
-        bound, amt, _ = stage_work(stage, precision, n_k, e_k, h, K, m["embed"][-1], m["embed"])
+        bound, amt, _ = stage_work(stage, precision, n_k, e_k, h, K, m["embed"][-1], m["embed"],
+                                   deg=2.0 * E / max(N, 1))
         total += amt
     return bound, total
 

@@ -348,9 +348,11 @@ gnntrk_status gnntrk_rescore_rows(gnntrk_handle* h, int32_t n, int64_t* edges, i
  * ran. Any output may be NULL. Returns the number of stages (which may exceed
  * max_stages; only max_stages are written), or -1 on error.
  * Stage names: sort, node_prep, radius_count, scan_out, radius_fill,
- * in_index, edge_encoder, node_update, edge_update, band_mark,
- * rescore_lists, rescore_node_prep, rescore_edge_encoder, rescore_node_update,
- * rescore_edge_update, components.
+ * in_index, edge_encoder, node_messages, node_update, edge_update, band_mark,
+ * rescore_lists, rescore_node_prep, rescore_edge_encoder,
+ * rescore_node_messages, rescore_node_update, rescore_edge_update,
+ * components (and, for gnntrk_find_tracks_triplets, triplets,
+ * triplet_scores, track_build).
  */
 gnntrk_status gnntrk_set_profiling(gnntrk_handle* h, int32_t enable);
 int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, double* total_ms,

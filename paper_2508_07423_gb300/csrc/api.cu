@@ -400,7 +400,8 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
   if (!tc) {
     stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 2,
+      stage(h, "node_messages", s, 1, [&] { launch_messages_f32(b, w, h->h, all, s); });
+      stage(h, "node_update", s, 1,
             [&] { launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, all, s); });
       const bool last = k + 1 == h->K;
       if (last && c.triplets) {
@@ -428,7 +429,9 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     stage(h, "edge_encoder", s, 1,
           [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 0); });
     for (int k = 0; k < h->K; ++k) {
-      stage(h, "node_update", s, 2,
+      stage(h, "node_messages", s, 1,
+            [&] { tc_messages(b, w, h->h, c.precision == GNNTRK_FP8_E4M3, s); });
+      stage(h, "node_update", s, 1,
             [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 1 + 2 * k); });
       stage(h, "edge_update", s, (k + 1 == h->K && !fused) ? 2 : 1,
             [&] { tc_gnn(b, w, h->tc, h->h, h->K, g, h->cls.l2, s, 2 + 2 * k, c.triplets != 0); });
@@ -461,7 +464,9 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       stage(h, "rescore_edge_encoder", s, 1,
             [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, esel(-1), s); });
       for (int k = 0; k < h->K; ++k) {
-        stage(h, "rescore_node_update", s, 2, [&] {
+        stage(h, "rescore_node_messages", s, 1,
+              [&] { launch_messages_f32(b, w, h->h, nsel(k), s); });
+        stage(h, "rescore_node_update", s, 1, [&] {
           launch_node_update_f32(b, w, h->node[k], h->step_proj[k], h->h, nsel(k), s);
         });
         stage(h, "rescore_edge_update", s, 1, [&] {

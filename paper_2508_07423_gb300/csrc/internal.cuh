@@ -211,7 +211,11 @@ void launch_csc(const Batch& b, const Ws& w, cudaStream_t s);
 // FP32 SIMT interaction network
 void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,
                          cudaStream_t s);
-// node step, also writing the projections for the edge step that follows
+// messages of a node step, m_v = [sum of e over out edges, sum over in edges]
+// (FP32, into the node's projection row), for the selected hits
+void launch_messages_f32(const Batch& b, const Ws& w, int h, Sel sel, cudaStream_t s);
+// node step (after launch_messages_f32), also writing the projections for the
+// edge step that follows
 void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const EdgeProj& proj,
                             int h, Sel sel, cudaStream_t s);
 // last step (cls != nullptr): also runs the classifier and writes logit/keep;

@@ -359,9 +359,38 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_
   (void)l2;
   (void)c1;
 
-  for (int base = lo + (blockIdx.x * NW + warp) * WR; base < hi; base += gridDim.x * NW * WR) {
+  // Edge rows: the index chain (row id from the list, then its source and
+  // target) is loaded ahead in registers, lane r holding row r of a tile: the
+  // row ids two tiles ahead and the source / target one tile ahead are loaded
+  // during a tile and first used in the next one, so a tile's row gathers
+  // start without waiting for its indices.
+  constexpr bool AHEAD = EDGE_ROWS && MODE != G_TRIP;
+  const int tstride = gridDim.x * NW * WR;
+  const int base0 = lo + (blockIdx.x * NW + warp) * WR;
+  auto row_at = [&](int b) {
+    const int pos = b + lane;
+    return (lane < WR && pos < hi) ? sel_row(p.sel, pos) : -1;
+  };
+  int r_cur = -1, s_cur = 0, d_cur = 0, r_next = -1;
+  if constexpr (AHEAD) {
+    r_cur = row_at(base0);
+    s_cur = r_cur >= 0 ? w.src[r_cur] : 0;
+    d_cur = r_cur >= 0 ? w.col[r_cur] : 0;
+    r_next = row_at(base0 + tstride);
+  }
+  for (int base = base0; base < hi; base += tstride) {
     // ---- rows of this warp -----------------------------------------------
-    if (lane < WR) {
+    if constexpr (AHEAD) {
+      if (lane < WR) {
+        rows[lane] = r_cur;
+        srcs[lane] = s_cur;
+        dsts[lane] = d_cur;
+      }
+      s_cur = r_next >= 0 ? w.src[r_next] : 0;
+      d_cur = r_next >= 0 ? w.col[r_next] : 0;
+      r_cur = r_next;
+      r_next = row_at(base + 2 * tstride);
+    } else if (lane < WR) {
       const int pos = base + lane;
       int row = -1, a = 0, c = 0;
       if (pos < hi) {
@@ -874,19 +903,21 @@ void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, S
   launch_gnn_any(h, G_EDGE_ENC, a, -1, s);
 }
 
+void launch_messages_f32(const Batch& b, const Ws& w, int h, Sel sel, cudaStream_t s) {
+  if (b.n_hits <= 0) return;
+  const int full = device_sms() * 8;
+  const int grid = sel.rows ? full : std::max(1, std::min(full, div_up(b.n_hits, 32)));
+  if (h == 32)
+    k_msg_f32<32><<<grid, 256, 0, s>>>(b, w, sel);
+  else if (h == 64)
+    k_msg_f32<64><<<grid, 256, 0, s>>>(b, w, sel);
+  else
+    k_msg_f32<128><<<grid, 256, 0, s>>>(b, w, sel);
+}
+
 void launch_node_update_f32(const Batch& b, const Ws& w, const Mlp2F32& m, const EdgeProj& proj,
                             int h, Sel sel, cudaStream_t s) {
   if (b.n_hits <= 0) return;
-  {
-    const int full = device_sms() * 8;
-    const int grid = sel.rows ? full : std::max(1, std::min(full, div_up(b.n_hits, 32)));
-    if (h == 32)
-      k_msg_f32<32><<<grid, 256, 0, s>>>(b, w, sel);
-    else if (h == 64)
-      k_msg_f32<64><<<grid, 256, 0, s>>>(b, w, sel);
-    else
-      k_msg_f32<128><<<grid, 256, 0, s>>>(b, w, sel);
-  }
   GnnArgs a = gnn_args(b, w, sel);
   a.m = m;
   a.proj = proj;

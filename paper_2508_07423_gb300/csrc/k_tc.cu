@@ -1731,6 +1731,16 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
   launch_any(h, m.precision == GNNTRK_FP8_E4M3 && !m.enc16, M_NODE_ENC, a, s, b.n_hits);
 }
 
+void tc_messages(const Batch& b, const Ws& w, int h, bool fp8, cudaStream_t s) {
+  const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 256 / (h / 8))));
+  if (h == 32)
+    fp8 ? k_msg_bf16<32, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<32, true><<<grid, 256, 0, s>>>(b, w);
+  else if (h == 64)
+    fp8 ? k_msg_bf16<64, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<64, true><<<grid, 256, 0, s>>>(b, w);
+  else
+    fp8 ? k_msg_bf16<128, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<128, true><<<grid, 256, 0, s>>>(b, w);
+}
+
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
             const LayerF32& cls2_f32, cudaStream_t s, int stage, bool store_final) {
   const bool fp8 = m.precision == GNNTRK_FP8_E4M3;
@@ -1761,15 +1771,9 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
     }
   }
   for (int k = 0; k < K; ++k) {
+    if (stage < 0) tc_messages(b, w, h, fp8, s);
     if (stage < 0 || stage == 1 + 2 * k) {
       set(m.node[k]);
-      const int grid = std::max(1, std::min(device_sms() * 8, div_up(b.n_hits, 256 / (h / 8))));
-      if (h == 32)
-        fp8 ? k_msg_bf16<32, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<32, true><<<grid, 256, 0, s>>>(b, w);
-      else if (h == 64)
-        fp8 ? k_msg_bf16<64, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<64, true><<<grid, 256, 0, s>>>(b, w);
-      else
-        fp8 ? k_msg_bf16<128, false><<<grid, 256, 0, s>>>(b, w) : k_msg_bf16<128, true><<<grid, 256, 0, s>>>(b, w);
       launch_any(h, fp8, M_NODE_UPD, a, s, b.n_hits);
     }
     if (stage < 0 || stage == 2 + 2 * k) {

@@ -63,10 +63,15 @@ void tc_node_prep(const Batch& b, const Ws& w, const TcModel& m, const LayerF32*
                   int n_embed, int D, int h, const GraphParams& g, const LayerF32& ne1_f32,
                   cudaStream_t s, bool do_embed = true);
 
+// Messages of a node step from the BF16 edge states (FP32 sums, stored
+// rounded to BF16 for BF16 handles and in FP32 for FP8 handles), for every hit.
+void tc_messages(const Batch& b, const Ws& w, int h, bool fp8, cudaStream_t s);
+
 // Edge encoder, K message-passing steps and the classifier with the cut;
-// writes w.logit and w.keep. stage < 0 runs everything; otherwise only
-// stage 0 (edge encoder), 1 + 2k (node step k) or 2 + 2k (edge step k, with
-// the classifier at the last step; stage 1 is the classifier when K = 0).
+// writes w.logit and w.keep. stage < 0 runs everything (messages included);
+// otherwise only stage 0 (edge encoder), 1 + 2k (node step k, after
+// tc_messages) or 2 + 2k (edge step k, with the classifier at the last step;
+// stage 1 is the classifier when K = 0).
 // With store_final the last edge step stores e^K (BF16) and the classifier
 // runs as its own kernel (the triplet classifiers read e^K).
 void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const GraphParams& g,
