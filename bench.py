@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--profile-case", default=None,
-                   choices=["headline_300ev_bf16", "headline_300ev_fp32", "triplets_int8_100ev"],
+                   choices=["headline_300ev_bf16", "headline_300ev_bf16_tuned", "headline_300ev_fp32",
+                            "triplets_int8_100ev"],
                    help="run one small case for a profiler capture (no timing, no JSON line)")
     p.add_argument("--study", default=None, choices=["occupancy"],
                    help="occupancy: throughput per event-size bin instead of the headline")
@@ -1153,9 +1154,35 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000, bands=(0.02, 0.05), oracle_e
                          "ms_per_1000_events": round(ms / len(chunks), 3),
                          "rescore_rows_per_edge": round(rows / max(edges, 1), 4)}
             tr.close()
+        # the plain FP32 path at this model, one event per call (100 events)
+        trp = pkg.tracker_for_workload(wl, precision="fp32", max_hits=max(
+            int(b0.offsets[e + 1] - b0.offsets[e]) for e in range(100)), max_events=1,
+            edges_per_hit=16)
+        evs = []
+        for e in range(100):
+            ev = b0.event(e)
+            evs.append((ev.n_hits, torch.from_numpy(ev.xyz_soa()).to(dev),
+                        torch.from_numpy(ev.plane).to(dev), torch.from_numpy(ev.offsets).to(dev),
+                        torch.empty(ev.n_hits, dtype=torch.int32, device=dev)))
+        for n_, x_, p_, o_, l_ in evs[:3]:
+            trp.find_tracks(1, n_, x_, p_, o_, l_, stream)
+        trp.sync_status(stream)
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s_.record(stream)
+            for n_, x_, p_, o_, l_ in evs:
+                trp.find_tracks(1, n_, x_, p_, o_, l_, stream)
+            e_.record(stream)
+        e_.synchronize()
+        trp.sync_status(stream)
+        trp.close()
+        plain = len(evs) / (s_.elapsed_time(e_) / 1e3)
+        res["plain_fp32_one_event_per_call"] = {"events_per_s": round(plain, 1),
+                                                "events": len(evs)}
         fp32_rate = res["fp32"]["events_per_s"]
         for name, _, _ in variants[1:]:
             res[name]["over_fp32"] = round(res[name]["events_per_s"] / fp32_rate, 3)
+            res[name]["over_plain_fp32"] = round(res[name]["events_per_s"] / plain, 2)
         # decisions against the FP32 path on the first chunk (same graph: the
         # embedding is FP32 in every precision)
         k32 = np.concatenate(first["fp32"]["kept"])
@@ -1205,14 +1232,16 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000, bands=(0.02, 0.05), oracle_e
 
 def profile_case(name, pkg, torch):
     """Small fixed cases for kernel captures (ncu): the first 300 events of the
-    headline batch (three calls, BF16 + FP32 re-score band 0.02, or FP32), or
+    headline batch (three calls, BF16 + FP32 re-score band 0.02, or FP32; the
+    _tuned case autotunes first, so the captured kernels are the variants the
+    autotuner keeps), or
     one triplet-stage call on 100 events of the triplet workload followed by
     the INT8 embedding (calibrated on the same 100 events) of the trained
     workload."""
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     if name.startswith("headline_300ev"):
-        prec = name.rsplit("_", 1)[1]
+        prec = name.split("_")[2]
         wl = synth.workload("cfg3_batched_bf16")
         b = synth.workload_batch(wl, 300)
         tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits, max_events=b.n_events,
@@ -1222,6 +1251,8 @@ def profile_case(name, pkg, torch):
         plane = torch.from_numpy(b.plane).to(dev)
         offs = torch.from_numpy(b.offsets).to(dev)
         lab = torch.zeros(b.n_hits, dtype=torch.int32, device=dev)
+        if name.endswith("_tuned"):  # the autotuner's launch configuration
+            print(name, "tuning", tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, lab))
         for _ in range(3):
             tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab)
         tr.sync_status()

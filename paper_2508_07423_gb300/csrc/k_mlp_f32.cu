@@ -293,7 +293,9 @@ __host__ __device__ constexpr int g_min_blocks() {
 
 // Weight matrices an edge kernel keeps in shared memory (variant 2): the e
 // block of the first layer (edge steps), the second layer, the classifier's
-// first layer (last step); H x H floats each.
+// first layer (last step); H x H floats each. (Staging only one matrix, so
+// that a fifth block fits an SM, measured slower: 2.14 against 2.06 ms per
+// step of the headline's re-score edge steps.)
 template <int MODE>
 __host__ __device__ constexpr int g_sw_mats() {
   return MODE == G_EDGE_ENC ? 1 : (MODE == G_EDGE_UPD ? 2 : (MODE == G_EDGE_UPD_CLS ? 3 : 0));
@@ -364,7 +366,9 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_
   // row ids two tiles ahead and the source / target one tile ahead are loaded
   // during a tile and first used in the next one, so a tile's row gathers
   // start without waiting for its indices.
-  constexpr bool AHEAD = EDGE_ROWS && MODE != G_TRIP;
+  // (variant 2 only: the index registers push the 5-block register budget of
+  // the other variants into spills)
+  constexpr bool AHEAD = SW && EDGE_ROWS && MODE != G_TRIP;
   const int tstride = gridDim.x * NW * WR;
   const int base0 = lo + (blockIdx.x * NW + warp) * WR;
   auto row_at = [&](int b) {

@@ -57,3 +57,27 @@ def test_event_range_rejects_bad_ranks():
     with pytest.raises(ValueError):
         replicas.event_range(4, 4, 10)
     assert replicas.combine(None, 3.0, 5, 7) == (3.0, 5, 7)
+
+
+def test_balanced_ranges_split_by_hits():
+    wl = synth.workload("cfg3_batched_bf16")
+    b = synth.workload_batch(wl, 64)
+    hits = np.diff(b.offsets)
+    for world in (1, 2, 3, 4, 8):
+        rng = replicas.balanced_ranges(hits, world)
+        # contiguous, in order, every event exactly once
+        assert sum(n for _, n in rng) == b.n_events
+        nxt = 0
+        for first, n in rng:
+            if n:
+                assert first == nxt
+                nxt = first + n
+        assert nxt == b.n_events
+        # each rank's hits within one event's hits of the ideal share
+        share = b.n_hits / world
+        for first, n in rng:
+            assert abs(int(hits[first:first + n].sum()) - share) <= hits.max()
+    # a heavy event goes whole to one rank; empty events still get an owner
+    assert replicas.balanced_ranges([1, 100, 1], 2) == [(0, 1), (1, 2)]
+    assert replicas.balanced_ranges([0, 0, 0, 0], 2) == [(0, 2), (2, 2)]
+    assert replicas.balanced_ranges([5], 3) == [(0, 0), (0, 1), (1, 0)]
