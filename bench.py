@@ -57,8 +57,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--profile-case", default=None,
-                   choices=["headline_300ev_bf16", "headline_300ev_bf16_tuned", "headline_300ev_fp32",
-                            "triplets_int8_100ev"],
+                   choices=["headline_300ev_bf16", "headline_300ev_bf16_tuned",
+                            "headline_300ev_bf16_tma", "headline_300ev_fp32", "triplets_int8_100ev"],
                    help="run one small case for a profiler capture (no timing, no JSON line)")
     p.add_argument("--study", default=None, choices=["occupancy"],
                    help="occupancy: throughput per event-size bin instead of the headline")
@@ -205,11 +205,13 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
     return "hbm", N * 16, "byte"
 
 
-# DRAM bytes (read + write) per row of the dominant kernels, from one ncu
-# capture of 300 events of the same workload (profiles/dram_traffic_edge_steps_300ev.md),
-# averaged over the launches of a step; scaled to this run's rows.
+# DRAM bytes (read + write) per row of the dominant kernels, from ncu
+# captures of 300 events of the same workload (the re-score edge step:
+# profiles/k_gnn_f32_rescore_edge_weights_in_smem_300ev.md, variant 2, steps 0
+# and 1; the others: profiles/dram_traffic_edge_steps_300ev.md), averaged over
+# the captured launches; scaled to this run's rows.
 TRAFFIC_PER_ROW = {
-    ("rescore_edge_update", "bf16"): 279.7,
+    ("rescore_edge_update", "bf16"): 280.3,
     ("edge_update", "bf16"): 116.9,
     ("edge_update", "fp32"): 257.6,
 }
@@ -1234,7 +1236,8 @@ def profile_case(name, pkg, torch):
     """Small fixed cases for kernel captures (ncu): the first 300 events of the
     headline batch (three calls, BF16 + FP32 re-score band 0.02, or FP32; the
     _tuned case autotunes first, so the captured kernels are the variants the
-    autotuner keeps), or
+    autotuner keeps; the _tma case runs the BF16 edge step with TMA-staged
+    tiles), or
     one triplet-stage call on 100 events of the triplet workload followed by
     the INT8 embedding (calibrated on the same 100 events) of the trained
     workload."""
@@ -1253,6 +1256,8 @@ def profile_case(name, pkg, torch):
         lab = torch.zeros(b.n_hits, dtype=torch.int32, device=dev)
         if name.endswith("_tuned"):  # the autotuner's launch configuration
             print(name, "tuning", tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, lab))
+        if name.endswith("_tma"):  # the BF16 edge step with TMA-staged tiles
+            tr.set_tuning({"tc_edge_tma": 1})
         for _ in range(3):
             tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab)
         tr.sync_status()
