@@ -370,9 +370,11 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
  *     next tile's rows are copied asynchronously while a tile computes; node
  *     kernels as variant 0); choice[4..6] = encoders, node step, edge step;
  *   - the BF16 edge step at hidden 32 (BF16 handles): form 0 (each thread
- *     copies its row's [e, h_src, h_dst] into the tile) or 1 (the tile is
- *     loaded by TMA: one box of 128 e rows and row gathers of h_src, h_dst,
- *     double-buffered); choice[7] (0 elsewhere).
+ *     copies its row's [e, h_src, h_dst] into the tile), 1 (the tile is
+ *     loaded by TMA: one box of 128 e rows and row gathers of h_src, h_dst)
+ *     or 2 (TMA-loaded tiles in a ring, with a producer warp, an MMA warp and
+ *     two epilogue warpgroups keeping several tiles in flight); choice[7]
+ *     (0 elsewhere).
  * The fastest setting of each family is kept and applies to every handle of
  * the process with the same precision and hidden width. choice: host int32 [8]
  * or NULL. Synchronous. Errors: as gnntrk_find_tracks and
@@ -389,7 +391,7 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
  * resident CTAs per SM of the tensor-core families (0 = the resource bound;
  * ignored by FP32 handles; capped by the resources each CTA needs),
  * choice[4..6] = FP32 variant 0, 1 or 2 of the encoders, node step and edge
- * step, choice[7] = BF16 edge-step form 0 or 1 (used by BF16 handles at
+ * step, choice[7] = BF16 edge-step form 0, 1 or 2 (used by BF16 handles at
  * hidden 32). Like the autotuner's result it applies to every
  * handle of the process with the same precision and hidden width, and drops
  * this handle's captured CUDA graphs (another handle's graphs keep the launch

@@ -1020,7 +1020,7 @@ gnntrk_status gnntrk_autotune(gnntrk_handle* h, int32_t n_events, int64_t n_hits
     if (!st && prec == GNNTRK_BF16 && h->tc.maps) {
       double best = 1e30;
       int best_form = 0;
-      for (int form = 0; form < 2 && !st; ++form) {
+      for (int form = 0; form < 3 && !st; ++form) {
         tc_set_edge_form(form);
         st = trial(t);
         const double v = stage_ms(t, "edge_update");
@@ -1084,8 +1084,8 @@ gnntrk_status gnntrk_set_tuning(gnntrk_handle* h, const int32_t* choice) {
   for (int f = 4; f < 7; ++f)
     if (choice[f] < 0 || choice[f] > 2)
       return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[4..6] must be an FP32 variant 0, 1 or 2");
-  if (choice[7] < 0 || choice[7] > 1)
-    return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[7] must be an edge-step form 0 or 1");
+  if (choice[7] < 0 || choice[7] > 2)
+    return fail(h, GNNTRK_ERR_INVALID_ARG, "choice[7] must be an edge-step form 0, 1 or 2");
   const int prec = h->cfg.precision, hd = h->h;
   if (prec != GNNTRK_FP32)
     for (int f = 0; f < 4; ++f) tc_set_ctas(prec, hd, f, choice[f]);

@@ -1255,6 +1255,347 @@ __global__ void __launch_bounds__(kRows, 5)
 }
 
 // ---------------------------------------------------------------------------
+// BF16 edge step at hidden 32, warp-specialised (tuning form 2): same
+// operands, K order and epilogue arithmetic as k_tc<32, BF16, M_EDGE_UPD /
+// M_EDGE_UPD_CLS>, with several tiles in flight per CTA:
+//   * warp 0 (producer) fills a ring of kWsStages tile buffers by TMA (box of
+//     128 e rows, row gathers of h_src and h_dst, as in k_tc_edge_tma);
+//   * warp 1 (one lane issues) runs the MMAs: layer 1 of tile i + 1 into one
+//     of two tensor-memory accumulators while the epilogue works on tile i in
+//     the other, then layer 2 (and the classifier) of tile i once its hidden
+//     tile is written;
+//   * two epilogue warpgroups (warps 2-5 and 6-9) take alternate tiles:
+//     bias, LayerNorm, ReLU, the hidden tile, the residual e read from the
+//     tile buffer (which then goes back to the producer), the new state or
+//     the classifier and the cut.
+// Hand-offs are mbarriers (full / empty per tile buffer; accumulator, hidden
+// tile and accumulator-free per accumulator). Every wait is bounded; a wait
+// that runs out raises a shared abort flag on which every other wait gives
+// up too, and the kernel latches ST_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kWsStages = 3;
+constexpr int kWsThreads = 320;  // producer, MMA, two epilogue warpgroups
+
+template <bool CLS>
+struct WsLayout {
+  static constexpr int H = 32;
+  static constexpr int SEG = kRows * H * 2;
+  static constexpr int K1 = 3 * H;
+  static constexpr int W1 = 0;
+  static constexpr int W1_BYTES = H * K1 * 2;
+  static constexpr int W2 = align1k(W1 + W1_BYTES);
+  static constexpr int W2_BYTES = H * H * 2;
+  static constexpr int WC = align1k(W2 + W2_BYTES);
+  static constexpr int WC_BYTES = CLS ? H * H * 2 : 0;
+  static constexpr int A = align1k(WC + WC_BYTES);
+  static constexpr int ABUF = 3 * SEG;
+  static constexpr int HA = A + kWsStages * ABUF;  // two hidden tiles
+  static constexpr int HA_BYTES = kRows * H * 2;
+  static constexpr int PAR = HA + 2 * HA_BYTES;
+  static constexpr int PAR_FLOATS = 4 * H + 4;
+  // barriers: full[S], empty[S], then per accumulator acc1, hid, acc2, cin,
+  // acc3, free (2 each)
+  static constexpr int BAR = PAR + PAR_FLOATS * 4;
+  static constexpr int NBAR = 2 * kWsStages + 12;
+  static constexpr int FLAG = BAR + NBAR * 8;  // abort flag, TMEM address
+  static constexpr int TOTAL = FLAG + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
+// Bounded wait that also gives up when another role has raised the abort flag.
+__device__ __forceinline__ bool ws_wait(uint64_t* m, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(m, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(m, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+
+template <bool CLS>
+__global__ void __launch_bounds__(kWsThreads, 2)
+    k_tc_edge_ws(const TcArgs p, const __grid_constant__ CUtensorMap map_e,
+                 const __grid_constant__ CUtensorMap map_h) {
+  constexpr int H = 32;
+  using L = WsLayout<CLS>;
+  constexpr int S = kWsStages;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* sW1 = smem + L::W1;
+  uint8_t* sW2 = smem + L::W2;
+  uint8_t* sWC = smem + L::WC;
+  float* par = reinterpret_cast<float*>(smem + L::PAR);
+  float* pb1 = par;
+  float* pb2 = par + H;
+  float* pbc = par + 2 * H;
+  float* pc2 = par + 3 * H;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
+  uint64_t* full = bar;            // [S] tile loaded
+  uint64_t* empty = bar + S;       // [S] tile buffer free (128 arrivals)
+  uint64_t* acc1 = bar + 2 * S;    // [2] layer-1 accumulator ready
+  uint64_t* hid = acc1 + 2;        // [2] hidden tile written (128)
+  uint64_t* acc2 = acc1 + 4;       // [2] layer-2 accumulator ready
+  uint64_t* cin = acc1 + 6;        // [2] classifier input written (128)
+  uint64_t* acc3 = acc1 + 8;       // [2] classifier accumulator ready
+  uint64_t* tfree = acc1 + 10;     // [2] accumulator read out (128)
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + L::FLAG);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::FLAG + 4);
+  constexpr int KCHH = H * 2 / 16;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Ws& w = p.w;
+  if (*(volatile int32_t*)&w.counters[C_STATUS] & ST_INPUT) return;
+
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kRows);
+    }
+    for (int d = 0; d < 2; ++d) {
+      mbar_init(&acc1[d], 1);
+      mbar_init(&hid[d], kRows);
+      mbar_init(&acc2[d], 1);
+      mbar_init(&cin[d], kRows);
+      mbar_init(&acc3[d], 1);
+      mbar_init(&tfree[d], kRows);
+    }
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 64);  // two accumulators of 32 columns
+    tmem_relinquish();
+  }
+  for (int i = tid; i < H; i += kWsThreads) {
+    pb1[i] = p.b1[i];
+    pb2[i] = p.b2[i];
+    pbc[i] = CLS ? p.bc1[i] : 0.f;
+    pc2[i] = CLS ? p.c2.WT[i * p.c2.ldo] : 0.f;
+  }
+  if (tid == 0) pc2[H] = CLS ? p.c2.b[0] : 0.f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+
+  // the weights come with the first tile: their bytes are counted on the
+  // first full barrier, which the MMA warp waits for before its first MMA
+  const int hi = clamp_edges(w.counters, w.e_cap);
+  const int n_tiles = (hi + kRows - 1) / kRows;
+  const int n_local = int(blockIdx.x) < n_tiles ? (n_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x) : 0;
+  // a whole warp waits; it goes on only if every lane saw the phase complete
+  // (so that the warp-collective instructions after it never diverge)
+  auto wait_warp = [&](uint64_t* m, uint32_t parity) -> bool {
+    const bool ok = ws_wait(m, parity, abort);
+    return __all_sync(0xffffffffu, ok);
+  };
+
+  if (warp == 0) {
+    // ---- producer ----------------------------------------------------------
+    for (int i = 0; i < n_local; ++i) {
+      const int t = int(blockIdx.x) + i * int(gridDim.x);
+      const int s = i % S, u = i / S;
+      if (u > 0 && !wait_warp(&empty[s], uint32_t((u - 1) & 1))) break;
+      int sv[4], dv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = t * kRows + 4 * lane + q;
+        sv[q] = r < hi ? w.src[r] : 0;
+        dv[q] = r < hi ? w.col[r] : 0;
+      }
+      uint8_t* A = smem + L::A + s * L::ABUF;
+      if (lane == 0) {
+        const uint32_t wbytes = i == 0 ? uint32_t(L::W1_BYTES + L::W2_BYTES + L::WC_BYTES) : 0u;
+        mbar_expect_tx(&full[s], uint32_t(3 * L::SEG) + wbytes);
+        if (i == 0) {
+          bulk_g2s(sW1, p.W1, L::W1_BYTES, &full[s]);
+          bulk_g2s(sW2, p.W2, L::W2_BYTES, &full[s]);
+          if (CLS) bulk_g2s(sWC, p.Wc, L::WC_BYTES, &full[s]);
+        }
+        tma_load_2d(A, &map_e, 0, t * kRows, &full[s]);
+      }
+      __syncwarp();
+      tma_gather4(A + L::SEG + 4 * lane * (H * 2), &map_h, 0, sv[0], sv[1], sv[2], sv[3], &full[s]);
+      tma_gather4(A + 2 * L::SEG + 4 * lane * (H * 2), &map_h, 0, dv[0], dv[1], dv[2], dv[3],
+                  &full[s]);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer (lane 0; the other lanes wait for it at the warp barrier)
+    if (lane == 0) {
+      constexpr uint32_t IDESC = idesc_bf16(kRows, H);
+      constexpr uint32_t SBO_W = uint32_t(L::K1 * 2 / 16) * 128;
+      auto layer1 = [&](int i) -> bool {
+        const int s = i % S, d = i & 1;
+        if (!ws_wait(&full[s], uint32_t((i / S) & 1), abort)) return false;
+        if (i >= 2 && !ws_wait(&tfree[d], uint32_t(((i >> 1) - 1) & 1), abort)) return false;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + L::A + s * L::ABUF), w0 = smem_u32(sW1);
+#pragma unroll
+        for (int k = 0; k < L::K1; k += 16) {
+          const int seg = k / H, j = (k % H) / 16;
+          const uint64_t ad = smem_desc_sw64(a0 + uint32_t(seg * L::SEG + j * 32));
+          const uint64_t bd = smem_desc(w0 + uint32_t(k * 2 / 16) * 128, 128, SBO_W);
+          mma_bf16(tmem_base + uint32_t(32 * d), ad, bd, IDESC, k > 0 ? 1u : 0u);
+        }
+        mma_commit(&acc1[d]);
+        return true;
+      };
+      bool ok = n_local == 0 || layer1(0);
+      for (int i = 0; i < n_local && ok; ++i) {
+        const int d = i & 1;
+        const uint32_t ph = uint32_t((i >> 1) & 1);
+        if (i + 1 < n_local && !layer1(i + 1)) break;
+        uint8_t* HA = smem + L::HA + d * L::HA_BYTES;
+        if (!ws_wait(&hid[d], ph, abort)) break;
+        tc_fence_after();
+        issue_layer<H, false>(tmem_base + uint32_t(32 * d), HA, sW2, H, 1);
+        mma_commit(&acc2[d]);
+        if constexpr (CLS) {
+          if (!ws_wait(&cin[d], ph, abort)) break;
+          tc_fence_after();
+          issue_layer<H, false>(tmem_base + uint32_t(32 * d), HA, sWC, H, 1);
+          mma_commit(&acc3[d]);
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warpgroups: g takes tiles i = g, g + 2, ... ---------------
+    const int g = (warp - 2) >> 2;
+    const int row = 32 * (warp & 3) + lane;  // TMEM lane of this thread
+    const uint32_t tmem_row = tmem_base + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(32 * g);
+    uint8_t* HA = smem + L::HA + g * L::HA_BYTES;
+    for (int i = g; i < n_local; i += 2) {
+      const int t = int(blockIdx.x) + i * int(gridDim.x);
+      const int s = i % S;
+      const uint32_t ph = uint32_t((i >> 1) & 1);
+      const int r = t * kRows + row;
+      const bool valid = r < hi;
+      const uint8_t* A = smem + L::A + s * L::ABUF;
+      if (!wait_warp(&acc1[g], ph)) break;
+      tc_fence_after();
+      float x[32];
+      {
+        float v[32];
+        tmem_ld32(tmem_row, v);
+        tmem_wait_ld();
+        add_params<false>(v, pb1, pb1, x);
+      }
+      float sum = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sum += x[j];
+      const float mean = sum / float(H);
+      float var = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float dd = x[j] - mean;
+        var = fmaf(dd, dd, var);
+      }
+      const float inv = 1.0f / sqrtf(var / float(H) + kLnEps);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = fmaxf((x[j] - mean) * inv, 0.f);
+      put_row_f32<false>(HA, row, KCHH, 0, x, 32, 1.f);
+      uint4 e_row[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        e_row[q] = *reinterpret_cast<const uint4*>(A + row * (H * 2) + ((q ^ ((row >> 1) & 3)) << 4));
+      fence_proxy_async();  // hidden tile to the MMA; the reads of A before its refill
+      mbar_arrive(&hid[g]);
+      mbar_arrive(&empty[s]);
+      if (!wait_warp(&acc2[g], ph)) break;
+      tc_fence_after();
+      float z[32];
+      {
+        float v[32];
+        tmem_ld32(tmem_row, v);
+        tmem_wait_ld();
+        add_params<false>(v, pb2, pb2, z);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 u = e_row[q];
+        z[8 * q + 0] += bf16_lo(u.x);
+        z[8 * q + 1] += bf16_hi(u.x);
+        z[8 * q + 2] += bf16_lo(u.y);
+        z[8 * q + 3] += bf16_hi(u.y);
+        z[8 * q + 4] += bf16_lo(u.z);
+        z[8 * q + 5] += bf16_hi(u.z);
+        z[8 * q + 6] += bf16_lo(u.w);
+        z[8 * q + 7] += bf16_hi(u.w);
+      }
+      if constexpr (!CLS) {
+        if (valid) {
+          uint4* d4 = reinterpret_cast<uint4*>(w.estate16 + size_t(r) * H);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            d4[q] = make_uint4(pack_bf16(z[8 * q], z[8 * q + 1]), pack_bf16(z[8 * q + 2], z[8 * q + 3]),
+                               pack_bf16(z[8 * q + 4], z[8 * q + 5]),
+                               pack_bf16(z[8 * q + 6], z[8 * q + 7]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = __bfloat162float(__float2bfloat16_rn(z[j]));
+        put_row_f32<false>(HA, row, KCHH, 0, z, 32, 1.f);  // layer 2 has read HA
+        fence_proxy_async();
+        mbar_arrive(&cin[g]);
+        if (!wait_warp(&acc3[g], ph)) break;
+        tc_fence_after();
+        float c[32];
+        {
+          float v[32];
+          tmem_ld32(tmem_row, v);
+          tmem_wait_ld();
+          add_params<false>(v, pbc, pbc, c);
+        }
+        float cs = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cs += c[j];
+        const float cmean = cs / float(H);
+        float cvar = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float dd = c[j] - cmean;
+          cvar = fmaf(dd, dd, cvar);
+        }
+        const float cinv = 1.0f / sqrtf(cvar / float(H) + kLnEps);
+        float logit = pc2[H];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) logit = fmaf(fmaxf((c[j] - cmean) * cinv, 0.f), pc2[j], logit);
+        if (valid) {
+          w.logit[r] = logit;
+          w.keep[r] = logit >= p.cut ? 1 : 0;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tfree[g]);  // this accumulator's tensor memory is read out
+    }
+  }
+
+  // ---- end: after an abort, let copies and MMAs in flight drain (bounded
+  //      sleep), then free the tensor memory -------------------------------------
+  __syncthreads();
+  if (*abort) {
+    if (tid == 0) set_status(w.counters, ST_TIMEOUT);
+    const long long t0 = clock64();
+    while (clock64() - t0 < 20000000LL) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 64);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // messages of the node step from the BF16 edge states: P[v] = [sum of e over
 // v's out edges | sum over its in edges], FP32 sums in increasing list order
 // starting from zero, stored as FP32 (FP8 path: the node step quantises them
@@ -1394,7 +1735,9 @@ constexpr int family_of(int mode) {
 static_assert(family_of(M_TRIP) == 3, "triplet classifier tunes with the edge family");
 constexpr int hidx(int h) { return h == 32 ? 0 : (h == 64 ? 1 : 2); }
 
-std::atomic<int> g_edge_form{0};  // BF16 edge step at hidden 32: 0 copies, 1 TMA
+// BF16 edge step at hidden 32: 0 per-thread copies, 1 TMA-staged tiles, 2
+// warp-specialised with TMA-staged tiles
+std::atomic<int> g_edge_form{0};
 
 // CTAs per SM of the TMA edge step: shared memory and tensor memory bound
 template <bool CLS>
@@ -1426,6 +1769,32 @@ void launch_edge_tma(const TcArgs& a, const TcModel& m, cudaStream_t s) {
   using L = TmaLayout<32, CLS>;
   const int grid = device_sms() * tma_blocks_per_sm<CLS>();
   k_tc_edge_tma<32, CLS><<<grid, kRows, L::ALLOC, s>>>(a, m.map_e, m.map_h);
+}
+
+// CTAs per SM of the warp-specialised edge step (shared memory bound)
+template <bool CLS>
+int ws_blocks_per_sm() {
+  using L = WsLayout<CLS>;
+  static const int per_sm = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_edge_ws<CLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_edge_ws<CLS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               100);
+    if (e != cudaSuccess) cudaGetLastError();
+    int n = std::max(1, std::min(2, 233472 / (L::ALLOC + 1024)));
+    if (getenv("GNNTRK_VERBOSE"))
+      fprintf(stderr, "gnntrk: k_tc_edge_ws<%d> smem %d B, %d CTAs/SM\n", int(CLS), L::ALLOC, n);
+    return n;
+  }();
+  return per_sm;
+}
+
+template <bool CLS>
+void launch_edge_ws(const TcArgs& a, const TcModel& m, cudaStream_t s) {
+  using L = WsLayout<CLS>;
+  const int grid = device_sms() * ws_blocks_per_sm<CLS>();
+  k_tc_edge_ws<CLS><<<grid, kWsThreads, L::ALLOC, s>>>(a, m.map_e, m.map_h);
 }
 
 template <int H, bool FP8, int MODE>
@@ -1779,11 +2148,15 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
     if (stage < 0 || stage == 2 + 2 * k) {
       set(m.edge[k]);
       const bool last = k + 1 == K;
-      const bool tma = !fp8 && h == 32 && m.maps && g_edge_form.load(std::memory_order_relaxed) == 1;
-      if (tma && last && fuse)
+      const int form = (!fp8 && h == 32 && m.maps) ? g_edge_form.load(std::memory_order_relaxed) : 0;
+      if (form == 1 && last && fuse)
         launch_edge_tma<true>(a, m, s);
-      else if (tma)
+      else if (form == 1)
         launch_edge_tma<false>(a, m, s);
+      else if (form == 2 && last && fuse)
+        launch_edge_ws<true>(a, m, s);
+      else if (form == 2)
+        launch_edge_ws<false>(a, m, s);
       else
         launch_any(h, fp8, last && fuse ? M_EDGE_UPD_CLS : M_EDGE_UPD, a, s, -1);
       if (last && !fuse) launch_any(h, fp8, M_CLS, a, s, -1);
@@ -1792,7 +2165,9 @@ void tc_gnn(const Batch& b, const Ws& w, const TcModel& m, int h, int K, const G
   if (K == 0 && (stage < 0 || stage == 1)) launch_any(h, fp8, M_CLS, a, s, -1);
 }
 
-void tc_set_edge_form(int form) { g_edge_form.store(form == 1 ? 1 : 0, std::memory_order_relaxed); }
+void tc_set_edge_form(int form) {
+  g_edge_form.store(form >= 0 && form <= 2 ? form : 0, std::memory_order_relaxed);
+}
 int tc_get_edge_form() { return g_edge_form.load(std::memory_order_relaxed); }
 
 void tc_make_maps(TcModel& m, const Ws& w, int h) {

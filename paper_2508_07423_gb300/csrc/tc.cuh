@@ -34,7 +34,8 @@ struct TcModel {
 void tc_make_maps(TcModel& m, const Ws& w, int h);
 
 // BF16 edge-step form at hidden 32, process wide: 0 per-thread row copies, 1
-// TMA tile load and row gathers (only where the handle has tensor maps).
+// TMA tile load and row gathers, 2 the same loads in a ring with producer,
+// MMA and epilogue warps (1 and 2 only where the handle has tensor maps).
 void tc_set_edge_form(int form);
 int tc_get_edge_form();
 

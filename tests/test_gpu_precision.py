@@ -300,7 +300,7 @@ def test_autotune_picks_a_count_and_keeps_results():
     labels = torch.zeros(b.n_hits, dtype=torch.int32, device="cuda")
     choice = tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, labels)
     assert all(1 <= v <= 8 for k, v in choice.items() if k.startswith("tc_") and k != "tc_edge_tma"), choice
-    assert choice["tc_edge_tma"] in (0, 1), choice
+    assert choice["tc_edge_tma"] in (0, 1, 2), choice
     assert all(v in (0, 1, 2) for k, v in choice.items() if k.startswith("f32_")), choice
     tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, labels)
     tr.sync_status()
@@ -356,17 +356,18 @@ def test_fp32_tile_variants_give_identical_results(name, prec):
 @pytest.mark.parametrize("n_events,band", [(12, 0.0), (12, 0.02), (1, 0.02)])
 def test_tma_edge_step_gives_identical_results(n_events, band):
     """The BF16 edge step with TMA-staged tiles (form 1: a box of 128 e rows and
-    row gathers of h_src, h_dst, double-buffered) gives bit-identical logits,
+    row gathers of h_src, h_dst; form 2: the same loads in a ring of tile
+    buffers with producer, MMA and epilogue warps) gives bit-identical logits,
     decisions, graphs and labels to the per-thread copies (form 0), on a batch
-    whose CTAs each run several tiles (both buffers, a ragged last tile) and on
-    one event with fewer tiles than CTAs."""
+    whose CTAs each run several tiles (every ring slot and both accumulators,
+    a ragged last tile) and on one event with fewer tiles than CTAs."""
     wl = synth.workload("cfg3_batched_bf16")
     b = synth.workload_batch(wl, n_events)
     tr = pkg.tracker_for_workload(wl, precision="bf16", rescore_band=band, max_hits=b.n_hits,
                                   max_events=b.n_events, edges_per_hit=32)
     ref = None
     try:
-        for form in (0, 1):
+        for form in (0, 1, 2):
             tr.set_tuning({"tc_edge_tma": form})
             labels = pkg.run_batch(tr, b)
             graphs = [tr.get_graph(e) for e in range(b.n_events)]
@@ -387,7 +388,7 @@ def test_set_tuning_rejects_out_of_range_choices():
     wl = synth.workload("cfg1_plain_fp32")
     tr = pkg.tracker_for_workload(wl, max_hits=1024, max_events=2)
     for bad in ({"f32_edge_update": 3}, {"tc_edge_update": 9}, {"f32_encoders": -1},
-                {"tc_edge_tma": 2}):
+                {"tc_edge_tma": 3}):
         with pytest.raises(pkg.GnntrkError):
             tr.set_tuning(bad)
     tr.set_tuning({})
