@@ -249,7 +249,6 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.parent, H);
   add(&w.counters, C_COUNT);
   add(&w.scan_blocks, (H + 4095) / 4096 + 1);
-  add(&w.ev_flag, c.max_events);
   add(&w.ev_off, int64_t(c.max_events) + 1);
   if (c.precision != GNNTRK_FP32) {
     add(&w.rs_elev, E);
@@ -445,11 +444,8 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
       // exact receptive field of the band edges, then FP32 over those rows only
       int mk = 0;
-      stage(h, "band_mark", s, 0, [&] {
-        mk = launch_rescore_sets(b, w, band_lo, band_hi, h->K, s);
-        tc_count_band_events(b, w, s);
-      });
-      h->last_launches += mk + 1;
+      stage(h, "band_mark", s, 0, [&] { mk = launch_rescore_sets(b, w, band_lo, band_hi, h->K, s); });
+      h->last_launches += mk;
       const int NL = kMaxIters + 2;
       const int32_t* cge_e = w.rs_counts + 2 * NL;  // [k + 1]: edges of step k
       const int32_t* cge_n = w.rs_counts + 5 * NL;  // [k + 1]: hits of step k

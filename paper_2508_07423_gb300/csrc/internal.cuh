@@ -103,7 +103,6 @@ struct Ws {
   int32_t* parent;      // [H] union-find parent over global input indices
   int32_t* counters;    // [C_COUNT]
   int32_t* scan_blocks; // block partials of the scan
-  int32_t* ev_flag;     // [max_events] events re-run in FP32
   int8_t* rs_elev;      // [Ecap] re-score level of each edge + 2 (0 none)
   int8_t* rs_nlev;      // [H]    re-score level of each hit + 2 (0 none)
   int32_t* rs_elist;    // [K + 1][Ecap] rows of each re-score step, index order
@@ -171,8 +170,9 @@ struct Sel {
 
 // Levels of the FP32 re-score (exact receptive field of the edges whose logit
 // lies in (band_lo, band_hi)): a row of level >= k is recomputed at step k
-// (k = -1: the encoders). Flags the events holding a band edge. Returns the
-// number of kernels launched.
+// (k = -1: the encoders); one block per event. Counts the band edges
+// (counters[C_BAND]) and the events holding one (counters[C_RERUN]). Returns
+// the number of kernels launched.
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s);
 // row lists of every re-score step: list k + 1 of w.rs_elist ([K + 1][e_cap])

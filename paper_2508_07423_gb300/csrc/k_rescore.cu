@@ -31,45 +31,28 @@ __device__ __forceinline__ bool input_bad(const int32_t* counters) {
   return (*(volatile const int32_t*)&counters[C_STATUS] & ST_INPUT) != 0;
 }
 
-// E_{K-1} = band edges, V_{K-1} = their endpoints; flags the events. Four
-// edges per thread and iteration; the band count is summed per thread and
-// added once per warp.
+// E_{K-1} = band edges, V_{K-1} = their endpoints. Returns 1 for a band edge.
 __device__ __forceinline__ int rs_init_edge(const Ws& w, int e, float l, float lo, float hi,
                                             int8_t top) {
   if (!(l > lo && l < hi)) return 0;
   w.rs_elev[e] = top;
-  const int a = w.src[e], c = w.col[e];
-  w.rs_nlev[a] = top;  // every writer stores the same value
-  w.rs_nlev[c] = top;
-  w.ev_flag[w.node_event[a]] = 1;
+  w.rs_nlev[w.src[e]] = top;  // every writer stores the same value
+  w.rs_nlev[w.col[e]] = top;
   return 1;
 }
 
-__global__ void k_rs_init(Ws w, float lo, float hi, int K) {
-  if (input_bad(w.counters)) return;
-  const int E = clamp_edges(w.counters, w.e_cap);
-  const int8_t top = int8_t((K > 0 ? K - 1 : -1) + 2);
-  const int stride = gridDim.x * blockDim.x;
-  const int E4 = E / 4;
-  int n = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E4; i += stride) {
-    const float4 l = reinterpret_cast<const float4*>(w.logit)[i];
-    n += rs_init_edge(w, 4 * i, l.x, lo, hi, top);
-    n += rs_init_edge(w, 4 * i + 1, l.y, lo, hi, top);
-    n += rs_init_edge(w, 4 * i + 2, l.z, lo, hi, top);
-    n += rs_init_edge(w, 4 * i + 3, l.w, lo, hi, top);
-  }
-  for (int e = 4 * E4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
-    n += rs_init_edge(w, e, w.logit[e], lo, hi, top);
-  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&w.counters[C_BAND], n);
-}
-
-__device__ __forceinline__ void rs_step_edge(const Ws& w, int8_t& L, int a, int c, int8_t la,
-                                             int8_t lc, int8_t ge_k, int8_t km1, bool& changed) {
+// Step k of the backward walk for one edge: the edge joins E_{k-1} if an
+// endpoint is in V_k (level >= k + 2); an edge of E_{k-1} puts its endpoints
+// in V_{k-1}. Within one sweep a hit level only rises to k + 1, which no
+// other edge of the same sweep tests for, so the sweep does not depend on
+// the order of its edges.
+__device__ __forceinline__ void rs_step_edge(const Ws& w, int e, int8_t ge_k, int8_t km1) {
+  int8_t L = w.rs_elev[e];
+  const int a = w.src[e], c = w.col[e];
+  const int8_t la = w.rs_nlev[a], lc = w.rs_nlev[c];
   if (L < km1 && (la >= ge_k || lc >= ge_k)) {
     L = km1;
-    changed = true;
+    w.rs_elev[e] = L;
   }
   if (L >= km1) {
     if (la < km1) w.rs_nlev[a] = km1;
@@ -77,35 +60,48 @@ __device__ __forceinline__ void rs_step_edge(const Ws& w, int8_t& L, int a, int 
   }
 }
 
-// four consecutive edges per thread and iteration: their levels, sources and
-// targets in one 4-byte and two 16-byte loads, the eight hit-level gathers in
-// flight together
-__global__ void k_rs_step(Ws w, int k) {
+// The whole receptive field, one block per event (events share no hits and
+// no edges): clear the event's levels, mark the band edges and their
+// endpoints, then the K backward steps with a block barrier between them;
+// counts the band edges into counters[C_BAND] and the events holding one
+// into counters[C_RERUN].
+constexpr int kRsEvThreads = 512;
+
+__global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, float lo, float hi, int K) {
   if (input_bad(w.counters)) return;
+  __shared__ int wsum[kRsEvThreads / 32];
   const int E = clamp_edges(w.counters, w.e_cap);
-  const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
-  const int stride = gridDim.x * blockDim.x;
-  const int E4 = E / 4;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E4; i += stride) {
-    char4 L4 = reinterpret_cast<const char4*>(w.rs_elev)[i];
-    const int4 a4 = reinterpret_cast<const int4*>(w.src)[i];
-    const int4 c4 = reinterpret_cast<const int4*>(w.col)[i];
-    const int8_t la0 = w.rs_nlev[a4.x], la1 = w.rs_nlev[a4.y], la2 = w.rs_nlev[a4.z], la3 = w.rs_nlev[a4.w];
-    const int8_t lc0 = w.rs_nlev[c4.x], lc1 = w.rs_nlev[c4.y], lc2 = w.rs_nlev[c4.z], lc3 = w.rs_nlev[c4.w];
-    int8_t L0 = L4.x, L1 = L4.y, L2 = L4.z, L3 = L4.w;
-    bool changed = false;
-    rs_step_edge(w, L0, a4.x, c4.x, la0, lc0, ge_k, km1, changed);
-    rs_step_edge(w, L1, a4.y, c4.y, la1, lc1, ge_k, km1, changed);
-    rs_step_edge(w, L2, a4.z, c4.z, la2, lc2, ge_k, km1, changed);
-    rs_step_edge(w, L3, a4.w, c4.w, la3, lc3, ge_k, km1, changed);
-    if (changed) reinterpret_cast<char4*>(w.rs_elev)[i] = make_char4(L0, L1, L2, L3);
+  const int8_t top = int8_t((K > 0 ? K - 1 : -1) + 2);
+  const int tid = threadIdx.x;
+  int band_total = 0, band_events = 0;
+  for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
+    const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
+    const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
+    for (int i = v0 + tid; i < v1; i += kRsEvThreads) w.rs_nlev[i] = 0;
+    for (int e = e0 + tid; e < e1; e += kRsEvThreads) w.rs_elev[e] = 0;
+    __syncthreads();
+    int n = 0;
+    for (int e = e0 + tid; e < e1; e += kRsEvThreads) n += rs_init_edge(w, e, w.logit[e], lo, hi, top);
+    __syncthreads();
+    for (int k = K - 1; k >= 0; --k) {
+      const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
+      for (int e = e0 + tid; e < e1; e += kRsEvThreads) rs_step_edge(w, e, ge_k, km1);
+      __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((tid & 31) == 0) wsum[tid >> 5] = n;
+    __syncthreads();
+    if (tid == 0) {
+      int t = 0;
+      for (int q = 0; q < kRsEvThreads / 32; ++q) t += wsum[q];
+      band_total += t;
+      band_events += t > 0;
+    }
+    __syncthreads();  // wsum is reused by the next event
   }
-  for (int e = 4 * E4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
-    int8_t L = w.rs_elev[e];
-    const int a = w.src[e], c = w.col[e];
-    bool changed = false;
-    rs_step_edge(w, L, a, c, w.rs_nlev[a], w.rs_nlev[c], ge_k, km1, changed);
-    if (changed) w.rs_elev[e] = L;
+  if (tid == 0 && band_total) {
+    atomicAdd(&w.counters[C_BAND], band_total);
+    atomicAdd(&w.counters[C_RERUN], band_events);
   }
 }
 
@@ -269,14 +265,11 @@ int rescore_sort_blocks() { return std::min(device_sms() * 4, kRsMaxBlocks); }
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s) {
   const int NL = kMaxIters + 2;
-  const int grid = device_sms() * 8;
-  cudaMemsetAsync(w.ev_flag, 0, sizeof(int32_t) * b.n_events, s);
   cudaMemsetAsync(w.rs_counts, 0, sizeof(int32_t) * 6 * NL, s);
-  cudaMemsetAsync(w.rs_elev, 0, size_t(w.e_cap), s);
-  cudaMemsetAsync(w.rs_nlev, 0, size_t(b.n_hits), s);
-  k_rs_init<<<grid, kRsThreads, 0, s>>>(w, band_lo, band_hi, K);
-  for (int k = K - 1; k >= 0; --k) k_rs_step<<<grid, kRsThreads, 0, s>>>(w, k);
-  return 1 + K;
+  if (b.n_events <= 0) return 0;
+  k_rs_event<<<std::min(b.n_events, device_sms() * 4), kRsEvThreads, 0, s>>>(b, w, band_lo,
+                                                                           band_hi, K);
+  return 1;
 }
 
 int launch_rescore_lists(const Batch& b, const Ws& w, int K, cudaStream_t s) {

@@ -1660,27 +1660,6 @@ __global__ void __launch_bounds__(256) k_msg_bf16(Batch b, Ws w) {
 }
 
 // ---------------------------------------------------------------------------
-// events holding a near-cut edge (flags set by the re-score marking): count
-// them into counters[C_RERUN] and clear the flags
-// ---------------------------------------------------------------------------
-__global__ void k_band_list(Ws w, int n_events) {
-  __shared__ int wsum[32];
-  int n = 0;
-  for (int ev = threadIdx.x; ev < n_events; ev += blockDim.x) {
-    n += w.ev_flag[ev] != 0;
-    w.ev_flag[ev] = 0;
-  }
-  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int k = 0; k < int(blockDim.x >> 5); ++k) t += wsum[k];
-    w.counters[C_RERUN] = t;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 // CTAs per SM of one kernel: the occupancy query, capped so that the CTAs of an
@@ -2251,9 +2230,6 @@ bool tc_cls_fused(int h, int precision) {
   return (fp8 ? smem_total<true>(h, M_EDGE_UPD_CLS) : smem_total<false>(h, M_EDGE_UPD_CLS)) <= kMaxSmem;
 }
 
-void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s) {
-  k_band_list<<<1, 1024, 0, s>>>(w, b.n_events);
-}
 
 namespace {
 // Self-test of the bounded waits: one thread waits on an mbarrier that no

@@ -92,9 +92,6 @@ bool tc_cls_fused(int h, int precision);
 uint8_t e4m3_from_float(float f);
 float e4m3_to_float(uint8_t c);
 
-// Count the events flagged in w.ev_flag (those holding a near-cut edge) into
-// counters[C_RERUN] and clear the flags.
-void tc_count_band_events(const Batch& b, const Ws& w, cudaStream_t s);
 
 // Launch the bounded-wait self-test: a wait on an mbarrier nothing arrives on,
 // for at most max_cycles SM cycles, then ST_TIMEOUT in counters.
