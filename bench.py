@@ -441,10 +441,23 @@ def main():
         "gpu_launches": int(stats["launches"]) * a.steps,
         "batched_over_plain": (round(value / plain["events_per_s"], 2)
                                if plain and plain.get("events_per_s") else None),
+        # the same ratio in hits/s (the plain path's 40-track events are
+        # smaller than the headline's)
+        "batched_over_plain_hits": (round(hits_total / (ms / 1e3) / plain["hits_per_s"], 2)
+                                    if plain and plain.get("hits_per_s") else None),
         "wall_s_timed": round(wall, 3),
     }
     out.update(extra)
     if rank == 0 and world == 1 and not a.no_plain:
+        # what the tensor pipe sustains at the narrow N of the network's
+        # layers (N = hidden), against which the tensor-core kernels' own
+        # tensor-pipe activity (profiles) reads
+        try:
+            out["tcgen05_probe_tflops"] = {
+                "what": "back-to-back BF16 MMAs M=128, N=n, K=16, one issuing thread per SM",
+                **{f"n{n}": round(pkg.tc_throughput(n), 1) for n in (32, 64, 128, 256)}}
+        except Exception as ex:  # reported, not fatal
+            out["tcgen05_probe_tflops"] = {"error": str(ex)}
         out["occupancy_study"] = {
             "what": "config-3 model, radius and noise at a fixed tracks per event, about 1.7 M "
                     "hits per batch: batched BF16 + FP32 re-score (one call, CUDA graph) against "
@@ -455,6 +468,7 @@ def main():
         if not a.no_plain:
             out["cfg2_report"] = cfg2_report(pkg, torch, dev, stream)
             out["fp8_report"] = fp8_report(pkg, torch, dev, stream)
+            out["fp8_trained_report"] = fp8_trained_report(pkg, torch, dev, stream)
             out["trained_report"] = trained_report(pkg, torch, dev, stream, flush)
             out["triplet_report"] = triplet_report(pkg, torch, dev, stream, flush)
             out["int8_report"] = int8_report(pkg, torch, dev, stream, flush)
@@ -1227,6 +1241,71 @@ def fp8_report(pkg, torch, dev, stream, chunk=1000, bands=(0.02, 0.05), oracle_e
         return {"workload": f"cfg4_batched_fp8: {n} events, {wl['description']}",
                 "dtype": "e4m3 GNN steps and classifier (tcgen05 kind::f8f6f4); BF16 split-operand encoders",
                 **res, "vs_fp64_oracle": vs}
+    except Exception as ex:  # reported, not fatal
+        import traceback
+        return {"error": str(ex), "trace": traceback.format_exc()[-600:]}
+
+
+def fp8_trained_report(pkg, torch, dev, stream, n_events=1000, oracle_n=200, reps=3):
+    """Config-4 events (200 tracks, 2 % noise) with a hidden-128 model trained
+    on other synthetic events (workload cfg4_trained_fp8): FP32, FP8 alone
+    and FP8 with the FP32 re-score bands |s - 0.5| < 0.02 and 0.05, each timed over
+    `n_events` events in one call and checked against the FP64 oracle on the
+    first `oracle_n` events. With trained weights the logits sit far from the
+    cut, so the band and its receptive field are small."""
+    try:
+        import oracle
+        from oracle import metrics
+        wl = synth.workload("cfg4_trained_fp8")
+        b = synth.workload_batch(wl, n_events)
+        xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+        plane = torch.from_numpy(b.plane).to(dev)
+        offs = torch.from_numpy(b.offsets).to(dev)
+        lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+        res, keep = {}, {}
+        for name, prec, band in (("fp32", "fp32", 0.0), ("fp8", "fp8", 0.0),
+                                 ("fp8_band_0.02", "fp8", 0.02), ("fp8_band_0.05", "fp8", 0.05)):
+            tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=band, max_hits=b.n_hits,
+                                          max_events=b.n_events, edges_per_hit=16, use_graph=True)
+            for _ in range(2):
+                tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+            tr.sync_status(stream)
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                s_.record(stream)
+                for _ in range(reps):
+                    tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, stream)
+                e_.record(stream)
+            e_.synchronize()
+            tr.sync_status(stream)
+            st = tr.stats()
+            res[name] = {"events_per_s": round(reps * b.n_events / (s_.elapsed_time(e_) / 1e3), 1),
+                         "band_edges": st["band"], "rescore_rows_per_edge":
+                             round(st["rescore_edges"] / max(st["edges"], 1), 4)}
+            keep[name] = ([tr.get_graph(e) for e in range(oracle_n)], lab.cpu().numpy())
+            tr.close()
+        for name in ("fp8", "fp8_band_0.02", "fp8_band_0.05"):
+            res[name]["over_fp32"] = round(res[name]["events_per_s"] / res["fp32"]["events_per_s"], 3)
+        sh = synth.shape_of(wl)
+        model = oracle.Model(synth.workload_weights(wl), sh.embed, sh.hidden, sh.iters)
+        fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+        t0 = time.perf_counter()
+        refs = oracle_events(model, b, list(range(oracle_n)), wl, fs, os.cpu_count() or 1)
+        t_or = time.perf_counter() - t0
+        lab_ref = np.concatenate([r.labels for r in refs])
+        nh = int(b.offsets[oracle_n])
+        co = metrics.batch_counts(lab_ref, b.pid[:nh], b.offsets[:oracle_n + 1]).summary()
+        vs = {"events": oracle_n, "oracle_seconds": round(t_or, 1),
+              "track_efficiency_oracle": round(co["efficiency"], 6)}
+        for name, (gs, labs) in keep.items():
+            ag = Agreement()
+            for e in range(oracle_n):
+                ag.add(gs[e], refs[e], int(b.offsets[e + 1] - b.offsets[e]))
+            cg = metrics.batch_counts(labs[:nh], b.pid[:nh], b.offsets[:oracle_n + 1]).summary()
+            vs[name] = {**ag.summary(), "track_efficiency": round(cg["efficiency"], 6),
+                        "track_efficiency_delta_pp": round(100 * abs(cg["efficiency"] - co["efficiency"]), 4)}
+        return {"workload": f"cfg4_trained_fp8: {n_events} events, {wl['description']}", **res,
+                "vs_fp64_oracle": vs}
     except Exception as ex:  # reported, not fatal
         import traceback
         return {"error": str(ex), "trace": traceback.format_exc()[-600:]}

@@ -544,6 +544,20 @@ gnntrk_status gnntrk_e4m3_encode(const float* in, uint8_t* out, int64_t n, int32
 /* Host: value of each E4M3 code (NaN for 0x7F and 0xFF). Errors: INVALID_ARG. */
 gnntrk_status gnntrk_e4m3_decode(const uint8_t* in, float* out, int64_t n);
 
+/*
+ * Tensor-core throughput probe (a measurement for the roofline of the
+ * tensor-core kernels; no pipeline work, no handle). On the current device,
+ * one CTA per SM has one thread issue `iters` rounds of four tcgen05 BF16 MMAs
+ * (M = 128, N = n, K = 16 each, FP32 accumulate in tensor memory, operands in
+ * shared memory) back to back; *ms receives the device time of that launch
+ * (synchronous; a warm-up launch runs first). Work = SMs x iters x 4 x
+ * 2 x 128 x n x 16 flop.
+ *   n: 32, 64, 128 or 256 (the interaction-network layers have N = hidden).
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (the bounded wait for the last MMA
+ * ran out). gnntrk_last_error(NULL) describes them.
+ */
+gnntrk_status gnntrk_tc_throughput(int32_t n, int64_t iters, double* ms);
+
 /* Release the handle's device memory, CUDA graphs and streams. NULL is a no-op.
  * The caller must make sure no work of this handle is still running. */
 void gnntrk_destroy(gnntrk_handle* h);

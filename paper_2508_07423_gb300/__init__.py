@@ -27,7 +27,7 @@ EXPORTS = ["gnntrk_default_cfg", "gnntrk_create", "gnntrk_find_tracks", "gnntrk_
            "gnntrk_get_graph", "gnntrk_stats", "gnntrk_set_profiling", "gnntrk_stage_times",
            "gnntrk_components_noalloc", "gnntrk_workspace_bytes", "gnntrk_serve_run",
            "gnntrk_autotune", "gnntrk_set_tuning", "gnntrk_selftest_wait", "gnntrk_rescore_rows", "gnntrk_e4m3_encode",
-           "gnntrk_e4m3_decode",
+           "gnntrk_e4m3_decode", "gnntrk_tc_throughput",
            "gnntrk_find_tracks_triplets", "gnntrk_triplet_stats", "gnntrk_get_triplets",
            "gnntrk_embed_amax", "gnntrk_set_embed_scales",
            "gnntrk_last_error", "gnntrk_destroy"]
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     L.gnntrk_e4m3_encode.restype = st
     L.gnntrk_e4m3_decode.argtypes = [vp, vp, i64]
     L.gnntrk_e4m3_decode.restype = st
+    L.gnntrk_tc_throughput.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double)]
+    L.gnntrk_tc_throughput.restype = st
     L.gnntrk_set_profiling.argtypes = [vp, i32]
     L.gnntrk_set_profiling.restype = st
     L.gnntrk_stage_times.argtypes = [vp, i32, vp, vp, vp]
@@ -434,6 +436,19 @@ def components_noalloc(n_hits: int, src, dst, kept, out_labels, stream=None):
                                      _ptr(dst), _ptr(kept), _ptr(out_labels), ctypes.c_void_p(s))
     if st != 0:
         raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+
+
+def tc_throughput(n: int, iters: int = 20000) -> float:
+    """TFLOP/s the tensor cores sustain on back-to-back BF16 MMAs of M = 128,
+    N = n, K = 16 (one issuing thread per SM); see gnntrk_tc_throughput."""
+    L = load_library()
+    ms = ctypes.c_double(0.0)
+    st = L.gnntrk_tc_throughput(n, iters, ctypes.byref(ms))
+    if st != 0:
+        raise GnntrkError(st, L.gnntrk_last_error(None).decode())
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * iters * 4 * 2.0 * 128 * n * 16 / (ms.value / 1e3) / 1e12
 
 
 def workspace_bytes(cfg: Cfg) -> int:

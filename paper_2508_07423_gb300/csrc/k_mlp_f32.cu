@@ -61,9 +61,9 @@ struct Warps {
 // Variant chosen per (hidden index, kernel family: 0 encoders, 1 node step,
 // 2 edge step and classifier); set by the autotuner, process wide. Variants:
 // 0 = 4 warps per block, 1 = 8 warps per block, 2 = 4 warps per block with the
-// edge kernels' weight matrices staged once per block in shared memory at
-// hidden 32 (the row gathers evict them from L1; node kernels, and every
-// kernel at hidden 64 and 128, run variant 0 then).
+// weight matrices of the edge kernels and the node step staged once per block
+// in shared memory at hidden 32 (the row gathers evict them from L1; the node
+// encoder, and every kernel at hidden 64 and 128, run variant 0 then).
 std::atomic<int> g_f32_variant[3][3] = {};
 
 enum GMode : int { G_NODE_ENC = 0, G_EDGE_ENC = 1, G_NODE_UPD = 2, G_EDGE_UPD = 3,
@@ -291,20 +291,26 @@ __host__ __device__ constexpr int g_min_blocks() {
   return (H == 32 && NW == 4 && MODE != G_NODE_ENC && MODE != G_NODE_UPD) ? (SW ? 4 : 5) : 1;
 }
 
-// Weight matrices an edge kernel keeps in shared memory (variant 2): the e
-// block of the first layer (edge steps), the second layer, the classifier's
-// first layer (last step); H x H floats each. (Staging only one matrix, so
-// that a fifth block fits an SM, measured slower: 2.14 against 2.06 ms per
-// step of the headline's re-score edge steps.)
+// Weight matrices a kernel keeps in shared memory (variant 2), in units of
+// H x H floats: edge steps the e block of the first layer, the second layer
+// and (last step) the classifier's first layer; the edge encoder its second
+// layer; the node step its first layer (3 blocks: h, m_out, m_in) and its
+// second layer, which leaves the node kernel at the 3 blocks per SM its
+// registers allow. (Staging only one matrix in the edge steps, so that a
+// fifth block fits an SM, measured slower: 2.14 against 2.06 ms per step of
+// the headline's re-score edge steps.)
 template <int MODE>
 __host__ __device__ constexpr int g_sw_mats() {
-  return MODE == G_EDGE_ENC ? 1 : (MODE == G_EDGE_UPD ? 2 : (MODE == G_EDGE_UPD_CLS ? 3 : 0));
+  return MODE == G_EDGE_ENC ? 1
+         : MODE == G_EDGE_UPD ? 2
+         : MODE == G_EDGE_UPD_CLS ? 3
+         : MODE == G_NODE_UPD ? 4 : 0;
 }
 
-// copy rows [0, H) of a transposed layer (row stride ldo) into S (row stride H)
-template <int H, int NT>
+// copy rows [0, R) of a transposed layer (row stride ldo) into S (row stride H)
+template <int H, int NT, int R = H>
 __device__ __forceinline__ void stage_weights(float* S, const LayerF32& L) {
-  for (int i = threadIdx.x; i < H * H / 4; i += NT) {
+  for (int i = threadIdx.x; i < R * H / 4; i += NT) {
     const int k = i / (H / 4), c = 4 * (i % (H / 4));
     *reinterpret_cast<float4*>(S + k * H + c) =
         __ldg(reinterpret_cast<const float4*>(L.WT + size_t(k) * L.ldo + c));
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_
   constexpr int RM = T::RM, CW = T::CW, WR = T::WR;
   constexpr int LDA = g_lda<H, MODE>();
   constexpr bool EDGE_ROWS = MODE != G_NODE_ENC && MODE != G_NODE_UPD;
-  static_assert(!SW || g_sw_mats<MODE>() > 0, "weights in shared memory: edge kernels only");
+  static_assert(!SW || g_sw_mats<MODE>() > 0, "weights in shared memory: edge and node-step kernels");
   extern __shared__ __align__(16) float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* As = sm + warp * g_warp_floats<H, MODE>();  // [WR][LDA]
@@ -341,7 +347,15 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_
   // the layers this kernel multiplies by: global memory, or (SW) copies in
   // shared memory after the warps' slices (row stride H)
   LayerF32 l1 = p.m.l1, l2 = p.m.l2, c1 = p.cls.l1;
-  if constexpr (SW) {
+  if constexpr (SW && MODE == G_NODE_UPD) {
+    float* S = sm + NW * g_warp_floats<H, MODE>();
+    stage_weights<H, NW * 32, 3 * H>(S, p.m.l1);  // [h, m_out, m_in] -> H
+    l1 = LayerF32{S, p.m.l1.b, 3 * H, H, H};
+    S += 3 * H * H;
+    stage_weights<H, NW * 32>(S, p.m.l2);
+    l2 = LayerF32{S, p.m.l2.b, H, H, H};
+    __syncthreads();
+  } else if constexpr (SW) {
     float* S = sm + NW * g_warp_floats<H, MODE>();
     if constexpr (MODE != G_EDGE_ENC) {
       stage_weights<H, NW * 32>(S, p.m.l1);  // rows [0, H): the e block
@@ -444,15 +458,15 @@ __global__ void __launch_bounds__(NW * 32, (g_min_blocks<H, MODE, NW, SW>())) k_
         stage_rows<H, false>(Bs, rows, w.pstate, 2 * H, H, nullptr, nullptr, 0, 0, lane);
         __syncwarp();
         acc_bias<H>(p.m.l1.b, cg, acc);
-        warp_layer<H, H, H, T::LDH>(Hs, p.m.l1, 0, rg, cg, acc);
-        warp_layer<H, H, H, LDA>(As, p.m.l1, H, rg, cg, acc);
-        warp_layer<H, H, H, T::LDH>(Bs, p.m.l1, 2 * H, rg, cg, acc);
+        warp_layer<H, H, H, T::LDH, SW>(Hs, l1, 0, rg, cg, acc);
+        warp_layer<H, H, H, LDA, SW>(As, l1, H, rg, cg, acc);
+        warp_layer<H, H, H, T::LDH, SW>(Bs, l1, 2 * H, rg, cg, acc);
         acc_ln_relu<H>(acc);
         __syncwarp();  // all lanes are done reading As
         acc_store_smem<H>(As, rg, cg, acc);
         __syncwarp();
         acc_bias<H>(p.m.l2.b, cg, acc);
-        warp_layer<H, H, H, LDA>(As, p.m.l2, 0, rg, cg, acc);
+        warp_layer<H, H, H, LDA, SW>(As, l2, 0, rg, cg, acc);
         acc_add_smem<H>(Hs, rg, cg, acc);  // residual h
       }
       acc_store_rows<H>(w.hstate, H, 0, rows, rg, cg, acc);

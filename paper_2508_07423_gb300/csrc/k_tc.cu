@@ -2232,6 +2232,88 @@ bool tc_cls_fused(int h, int precision) {
 
 
 namespace {
+// Tensor-core throughput probe: one CTA per SM, one thread issuing BF16 MMAs
+// M = 128, N = NN, K = 64 (four K = 16 instructions) back to back from shared
+// memory (zeros, no-swizzle layout) into one tensor-memory accumulator, one
+// commit at the end (bounded wait). Measures what the tensor pipe sustains at
+// the narrow N of the interaction-network layers.
+template <int NN>
+__global__ void __launch_bounds__(32, 1) k_tc_probe(int64_t iters, int32_t* flag) {
+  constexpr int K = 64;
+  __shared__ __align__(1024) uint8_t sA[kRows * K * 2];
+  __shared__ __align__(1024) uint8_t sB[NN * K * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  for (int i = threadIdx.x * 16; i < kRows * K * 2; i += 32 * 16)
+    *reinterpret_cast<uint4*>(sA + i) = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x * 16; i < NN * K * 2; i += 32 * 16)
+    *reinterpret_cast<uint4*>(sB + i) = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  tmem_alloc(&tslot, NN < 32 ? 32 : NN);
+  tmem_relinquish();
+  fence_proxy_async();
+  tc_fence_before();
+  __syncwarp();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (threadIdx.x == 0) {
+    constexpr uint32_t IDESC = idesc_bf16(kRows, NN);
+    constexpr uint32_t SBO = uint32_t(K * 2 / 16) * 128;
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int k = 0; k < K; k += 16) {
+        const uint32_t off = uint32_t(k * 2 / 16) * 128;
+        mma_bf16(tmem, smem_desc(a0 + off, 128, SBO), smem_desc(b0 + off, 128, SBO), IDESC,
+                 (it > 0 || k > 0) ? 1u : 0u);
+      }
+    }
+    mma_commit(&bar);
+    if (!mbar_wait_bounded(&bar, 0, kWaitCycles)) atomicExch(flag, 1);
+  }
+  tc_fence_before();
+  __syncwarp();
+  tc_fence_after();
+  tmem_dealloc(tmem, NN < 32 ? 32 : NN);
+}
+}  // namespace
+
+int tc_probe(int n, int64_t iters, double* ms) {
+  int32_t* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int32_t)) != cudaSuccess) return GNNTRK_ERR_OOM;
+  cudaMemset(flag, 0, sizeof(int32_t));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int grid = device_sms();
+  auto go = [&](int64_t its) {
+    if (n == 32) k_tc_probe<32><<<grid, 32>>>(its, flag);
+    else if (n == 64) k_tc_probe<64><<<grid, 32>>>(its, flag);
+    else if (n == 128) k_tc_probe<128><<<grid, 32>>>(its, flag);
+    else k_tc_probe<256><<<grid, 32>>>(its, flag);
+  };
+  go(16);  // warm-up
+  cudaEventRecord(a);
+  go(iters);
+  cudaEventRecord(b);
+  cudaError_t e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  int32_t hflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(flag);
+  if (e != cudaSuccess) return GNNTRK_ERR_CUDA;
+  if (hflag) return GNNTRK_ERR_TIMEOUT;
+  *ms = double(t);
+  return GNNTRK_OK;
+}
+
+namespace {
 // Self-test of the bounded waits: one thread waits on an mbarrier that no
 // thread ever arrives on, through the same bounded wait the tensor-core
 // kernels use, and latches ST_TIMEOUT when it runs out, as they do.
@@ -2292,6 +2374,17 @@ extern "C" gnntrk_status gnntrk_e4m3_encode(const float* in, uint8_t* out, int64
     return GNNTRK_ERR_CUDA;
   }
   return GNNTRK_OK;
+}
+
+extern "C" gnntrk_status gnntrk_tc_throughput(int32_t n, int64_t iters, double* ms) {
+  using namespace gnntrk;
+  if (!ms || (n != 32 && n != 64 && n != 128 && n != 256) || iters < 1 || iters > (int64_t(1) << 30)) {
+    set_global_error("gnntrk_tc_throughput: n must be 32, 64, 128 or 256, iters 1..2^30, ms not NULL");
+    return GNNTRK_ERR_INVALID_ARG;
+  }
+  const int st = tc_probe(n, iters, ms);
+  if (st != GNNTRK_OK) set_global_error("gnntrk_tc_throughput: the probe failed or timed out");
+  return gnntrk_status(st);
 }
 
 extern "C" gnntrk_status gnntrk_e4m3_decode(const uint8_t* in, float* out, int64_t n) {

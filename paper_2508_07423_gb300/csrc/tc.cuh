@@ -93,6 +93,10 @@ uint8_t e4m3_from_float(float f);
 float e4m3_to_float(uint8_t c);
 
 
+// Tensor-core throughput probe (gnntrk_tc_throughput): device ms of SMs x
+// iters x 4 BF16 MMAs of M = 128, N = n, K = 16; returns a gnntrk_status.
+int tc_probe(int n, int64_t iters, double* ms);
+
 // Launch the bounded-wait self-test: a wait on an mbarrier nothing arrives on,
 // for at most max_cycles SM cycles, then ST_TIMEOUT in counters.
 void tc_wait_selftest(int32_t* counters, long long max_cycles, cudaStream_t s);

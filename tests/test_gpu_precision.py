@@ -210,6 +210,7 @@ def test_wide_models_without_band_miss_the_bar(name, prec):
 @pytest.mark.parametrize("name,prec,band,n_events", [
     ("cfg2_run3_single", "bf16", 0.02, 8),
     ("cfg4_batched_fp8", "fp8", 0.05, 8),
+    ("cfg4_trained_fp8", "fp8", 0.05, 8),
 ])
 def test_wide_models_with_band_at_the_bar(name, prec, band, n_events):
     """With the FP32 re-score band, the wide models agree with the FP64 oracle
@@ -410,3 +411,11 @@ def test_device_e4m3_conversion_matches_the_oracle_codec():
     got = pkg.e4m3_encode(torch.from_numpy(vals).cuda()).cpu().numpy()
     want = quant.e4m3_encode_array(vals.astype(np.float64))
     assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
+
+
+def test_tensor_core_throughput_probe():
+    """The tcgen05 throughput probe runs and reports a rate below the chip's
+    dense BF16 peak (2.25 PFLOP/s nominal) that grows with N."""
+    rates = [pkg.tc_throughput(n, iters=4000) for n in (32, 128)]
+    assert 0 < rates[0] <= rates[1] * 1.05
+    assert rates[1] < 2600.0
