@@ -354,7 +354,7 @@ def test_fp32_tile_variants_give_identical_results(name, prec):
         tr.close()
 
 
-@pytest.mark.parametrize("n_events,band", [(12, 0.0), (12, 0.02), (1, 0.02)])
+@pytest.mark.parametrize("n_events,band", [(12, 0.0), (12, 0.02), (1, 0.02), (-1, 0.02)])
 def test_tma_edge_step_gives_identical_results(n_events, band):
     """The BF16 edge step with TMA-staged tiles (form 1: a box of 128 e rows and
     row gathers of h_src, h_dst; form 2: the same loads in a ring of tile
@@ -363,7 +363,10 @@ def test_tma_edge_step_gives_identical_results(n_events, band):
     whose CTAs each run several tiles (every ring slot and both accumulators,
     a ragged last tile) and on one event with fewer tiles than CTAs."""
     wl = synth.workload("cfg3_batched_bf16")
-    b = synth.workload_batch(wl, n_events)
+    # n_events = -1: two events at the largest occupancy (400 tracks, about
+    # 4500 hits and 65 k edges each)
+    b = (synth.workload_batch(wl, n_events) if n_events > 0 else
+         synth.gen_batch(2, 4242, {"kind": "fixed", "n": 400}, wl["noise"]))
     tr = pkg.tracker_for_workload(wl, precision="bf16", rescore_band=band, max_hits=b.n_hits,
                                   max_events=b.n_events, edges_per_hit=32)
     ref = None
@@ -374,7 +377,7 @@ def test_tma_edge_step_gives_identical_results(n_events, band):
             graphs = [tr.get_graph(e) for e in range(b.n_events)]
             if ref is None:
                 ref = (labels, graphs)
-                assert tr.stats()["edges"] > (128 * 600 if n_events > 1 else 0)
+                assert tr.stats()["edges"] > (128 * 600 if b.n_events > 1 else 0)
                 continue
             assert np.array_equal(labels, ref[0])
             for e in range(b.n_events):
