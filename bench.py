@@ -196,10 +196,10 @@ def stage_work(stage: str, precision: str, N: int, E: int, h: int, K: int, D: in
         if precision == "fp32":
             macs += 3 * h + h * h + 2 * h * h
         return "alu", N * 2.0 * macs, "flop"
-    if stage == "in_index":
-        return "hbm", E * 12 + N * 8, "byte"
-    if stage in ("radius_count", "radius_fill"):
-        return "hbm", N * D * 4 + N * 4 + (E * 12 if stage == "radius_fill" else 0), "byte"
+    if stage == "graph":
+        # the embeddings read once; per edge (col, src, d2) written, col read
+        # back and the in-edge id written; row pointers and in-edge pointers
+        return "hbm", N * D * 4 + E * (12 + 4 + 4) + N * 8, "byte"
     if stage == "components":
         return "hbm", E * 9 + N * 16, "byte"
     return "hbm", N * 16, "byte"
@@ -384,7 +384,7 @@ def main():
     # every stage with a work model: achieved rate against its roofline
     per_stage = {}
     for sname, (sms, sruns) in stages.items():
-        if sname in ("band_mark", "rescore_lists", "scan_out", "sort"):
+        if sname in ("rescore_field", "sort"):
             continue
         sb_, samt = stage_amount(sname, sruns // a.steps, rows, precision, N, E, m)
         st_ms = sms / a.steps

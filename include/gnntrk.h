@@ -347,9 +347,10 @@ gnntrk_status gnntrk_rescore_rows(gnntrk_handle* h, int32_t n, int64_t* edges, i
  * names + 32 * i), the summed device time in ms and the number of times it
  * ran. Any output may be NULL. Returns the number of stages (which may exceed
  * max_stages; only max_stages are written), or -1 on error.
- * Stage names: sort, node_prep, radius_count, scan_out, radius_fill,
- * in_index, edge_encoder, node_messages, node_update, edge_update, band_mark,
- * rescore_lists, rescore_node_prep, rescore_edge_encoder,
+ * Stage names: sort, node_prep, graph (rough graph and in-edge index),
+ * edge_encoder, node_messages, node_update, edge_update, rescore_field
+ * (receptive field of the band edges and its row lists), rescore_node_prep,
+ * rescore_edge_encoder,
  * rescore_node_messages, rescore_node_update, rescore_edge_update,
  * components (and, for gnntrk_find_tracks_triplets, triplets,
  * triplet_scores, track_build).
@@ -366,9 +367,10 @@ int32_t gnntrk_stage_times(gnntrk_handle* h, int32_t max_stages, char* names, do
  *     choice[0..3] = node encoder, edge encoder, node step, edge step;
  *   - FP32 SIMT kernels (FP32 handles, and the FP32 re-score of BF16/FP8 handles
  *     with a re-score band): variant 0 (4 warps per block), 1 (8 warps per
- *     block) or 2 (edge kernels with two stages of row buffers per warp: the
- *     next tile's rows are copied asynchronously while a tile computes; node
- *     kernels as variant 0); choice[4..6] = encoders, node step, edge step;
+ *     block) or 2 (4 warps per block with the layer weights of the edge and
+ *     node-step kernels at hidden 32 copied once per block into shared memory
+ *     and the next tile's row indices loaded ahead; other kernels and widths
+ *     run variant 0 then); choice[4..6] = encoders, node step, edge step;
  *   - the BF16 edge step at hidden 32 (BF16 handles): form 0 (each thread
  *     copies its row's [e, h_src, h_dst] into the tile), 1 (the tile is
  *     loaded by TMA: one box of 128 e rows and row gathers of h_src, h_dst)

@@ -229,7 +229,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.plane_off, int64_t(c.max_events) * (c.n_planes + 1));
   add(&w.emb, H * D);
   add(&w.deg, H);
-  add(&w.rmask, H * kMaskWords);
+  add(&w.graph_desc, c.max_events);
   add(&w.row_ptr, H + 1);
   add(&w.col, E);
   add(&w.src, E);
@@ -256,7 +256,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
     add(&w.rs_elist, E * (c.iters + 1));
     add(&w.rs_nlist, H * (c.iters + 1));
     add(&w.rs_counts, 6 * (kMaxIters + 2));
-    add(&w.rs_blk, 2 * (kMaxIters + 2) * kRsMaxBlocks);
+    add(&w.rs_desc, int64_t(c.max_events) * (1 + 4 * (kMaxIters + 1)));
   }
   const int64_t T = c.triplets ? H * c.triplets_per_hit : 0;
   if (c.triplets) {
@@ -389,13 +389,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
     else
       tc_node_prep(b, w, h->tc, h->embed, h->n_embed, h->D, h->h, g, h->node_enc.l1, s, !i8);
   });
-  stage(h, "radius_count", s, 1, [&] { launch_radius(b, w, g, h->D, false, s); });
-  stage(h, "scan_out", s, 2, [&] {
-    launch_scan(w.deg, w.row_ptr, b.n_hits, c.k_max, w.counters, C_EDGES, w.e_cap,
-                w.scan_blocks, s);
-  });
-  stage(h, "radius_fill", s, 1, [&] { launch_radius(b, w, g, h->D, true, s); });
-  stage(h, "in_index", s, 1, [&] { launch_csc(b, w, s); });
+  stage(h, "graph", s, 1, [&] { launch_graph(b, w, g, h->D, s); });
   if (!tc) {
     stage(h, "edge_encoder", s, 1, [&] { launch_edge_enc_f32(b, w, h->edge_enc, h->h, all, s); });
     for (int k = 0; k < h->K; ++k) {
@@ -442,9 +436,10 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       const double hi = double(c.score_cut) + double(c.rescore_band);
       const float band_lo = lo <= 0.0 ? -INFINITY : float(std::log(lo / (1.0 - lo)));
       const float band_hi = hi >= 1.0 ? INFINITY : float(std::log(hi / (1.0 - hi)));
-      // exact receptive field of the band edges, then FP32 over those rows only
+      // exact receptive field of the band edges and its row lists, then FP32
+      // over those rows only
       int mk = 0;
-      stage(h, "band_mark", s, 0, [&] { mk = launch_rescore_sets(b, w, band_lo, band_hi, h->K, s); });
+      stage(h, "rescore_field", s, 0, [&] { mk = launch_rescore_sets(b, w, band_lo, band_hi, h->K, s); });
       h->last_launches += mk;
       const int NL = kMaxIters + 2;
       const int32_t* cge_e = w.rs_counts + 2 * NL;  // [k + 1]: edges of step k
@@ -452,7 +447,6 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
       // each step's rows in index order: list k + 1 of rs_elist / rs_nlist
       auto esel = [&](int k) { return Sel{w.rs_elist + size_t(k + 1) * w.e_cap, cge_e + k + 1}; };
       auto nsel = [&](int k) { return Sel{w.rs_nlist + size_t(k + 1) * w.h_cap, cge_n + k + 1}; };
-      stage(h, "rescore_lists", s, 3, [&] { launch_rescore_lists(b, w, h->K, s); });
       stage(h, "rescore_node_prep", s, 1, [&] {
         launch_node_prep_f32(b, w, h->embed, h->n_embed, h->node_enc, h->enc_proj, h->D, h->h, g,
                              false, true, nsel(-1), s);
@@ -477,7 +471,7 @@ void enqueue_pipeline(gnntrk_handle* h, const Batch& b, const int64_t* offsets, 
         });
     }
   }
-  stage(h, "components", s, 2, [&] { launch_cc(b, w, s); });
+  stage(h, "components", s, 1, [&] { launch_cc(b, w, s); });
   if (h->want_tracks) {
     const float tcut = float(std::log(double(c.triplet_cut) / (1.0 - double(c.triplet_cut))));
     stage(h, "triplets", s, 6, [&] { launch_triplets(b, w, h->h, s); });

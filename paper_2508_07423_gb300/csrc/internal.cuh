@@ -13,9 +13,6 @@ namespace gnntrk {
 constexpr int kMaxPlanes = 64;
 constexpr int kMaxEmbedLayers = 8;
 constexpr int kMaxIters = 16;
-constexpr int kRsMaxBlocks = 1024;           // blocks of the re-score level sort (at most)
-constexpr int kMaskWords = 16;               // radius-search masks: up to 512 candidates
-constexpr int kMaskCands = 32 * kMaskWords;
 constexpr float kLnEps = 1e-5f;
 
 // Bits of the device status word (counters[C_STATUS]).
@@ -41,6 +38,8 @@ enum Counter : int {
   C_TRACKS = 11,      // tracks built from triplets
   C_TRACK_HITS = 12,  // hits over all those tracks
   C_TRIP_KEPT = 13,   // triplets above the triplet cut
+  C_GRAPH_TICKET = 14,  // next event of the graph kernel
+  C_RS_TICKET = 15,     // next event of the re-score receptive-field kernel
   C_COUNT = 16
 };
 
@@ -84,13 +83,13 @@ struct Ws {
   float4* pos;          // [H] sorted (x, y, z, 0)
   int32_t* plane_off;   // [max_events][n_planes + 1] sorted offsets (global)
   float* emb;           // [H][D]
-  int32_t* deg;         // [H] candidates inside the radius (uncapped)
-  uint32_t* rmask;      // [H][kMaskWords] candidates inside the radius, one bit each
+  int32_t* deg;         // [H] candidates inside the radius (uncapped), large events
+  unsigned long long* graph_desc;  // [max_events] look-back words of the graph kernel
   int32_t* row_ptr;     // [H + 1]
   int32_t* col;         // [Ecap] target (sorted position)
   int32_t* src;         // [Ecap] source (sorted position)
   float* d2;            // [Ecap]
-  int32_t* in_cnt;      // [H]
+  int32_t* in_cnt;      // [H] CSR offsets, then in-degrees (large events)
   int32_t* in_ptr;      // [H + 1]
   int32_t* in_edge;     // [Ecap] edge ids grouped by target, ascending
   float* hstate;        // [H][h]   FP32 node state (FP32 path and re-score)
@@ -108,7 +107,7 @@ struct Ws {
   int32_t* rs_elist;    // [K + 1][Ecap] rows of each re-score step, index order
   int32_t* rs_nlist;    // [K + 1][H]    hits of each re-score step, index order
   int32_t* rs_counts;   // [6][kMaxIters + 2]: [2] and [5] rows with level >= k (edges, hits)
-  int32_t* rs_blk;      // [2][kMaxIters + 1][kRsMaxBlocks] per-block offsets of the lists
+  int32_t* rs_desc;     // [max_events][1 + 4 (kMaxIters + 1)] look-back flags and counts of the lists
   int64_t* ev_off;      // [max_events + 1] copy of the call's offsets
   // triplet stage (allocated when the handle builds tracks from triplets)
   int32_t* trip_cnt_a;  // [H] articulations per hit
@@ -170,16 +169,15 @@ struct Sel {
 
 // Levels of the FP32 re-score (exact receptive field of the edges whose logit
 // lies in (band_lo, band_hi)): a row of level >= k is recomputed at step k
-// (k = -1: the encoders); one block per event. Counts the band edges
-// (counters[C_BAND]) and the events holding one (counters[C_RERUN]). Returns
-// the number of kernels launched.
+// (k = -1: the encoders); one block per event. Also the row lists of every
+// step: list k + 1 of w.rs_elist ([K + 1][e_cap]) and w.rs_nlist ([K + 1][h_cap])
+// holds the rows of step k in index order, their counts at
+// rs_counts[2 (kMaxIters + 2) + k + 1] (edges) and rs_counts[5 (kMaxIters + 2) +
+// k + 1] (hits). Counts the band edges (counters[C_BAND]), the events holding
+// one (counters[C_RERUN]) and the encoder rows (C_RERUN_EDGES, C_RERUN_HITS).
+// Returns the number of kernels launched.
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s);
-// row lists of every re-score step: list k + 1 of w.rs_elist ([K + 1][e_cap])
-// and w.rs_nlist ([K + 1][h_cap]) holds the rows of step k (k = -1: the
-// encoders) in index order, their counts at rs_counts[2 (kMaxIters + 2) + k + 1]
-// (edges) and rs_counts[5 (kMaxIters + 2) + k + 1] (hits); returns the launch count
-int launch_rescore_lists(const Batch& b, const Ws& w, int K, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (host functions), one per kernel family
@@ -199,14 +197,14 @@ void launch_node_prep_f32(const Batch& b, const Ws& w, const LayerF32* embed, in
                           const Mlp2F32& node_enc, const EdgeProj& proj, int D, int h,
                           const GraphParams& g, bool do_embed, bool do_node_enc, Sel sel,
                           cudaStream_t s);
-void launch_radius(const Batch& b, const Ws& w, const GraphParams& g, int D, bool fill,
-                   cudaStream_t s);
+// rough graph (CSR: row_ptr, col, src, d2; counters[C_EDGES]) and the in-edge
+// index (in_ptr, in_edge), one kernel
+void launch_graph(const Batch& b, const Ws& w, const GraphParams& g, int D, cudaStream_t s);
 // exclusive scan of n entries of `in` (each clamped to clamp_max) into out[0..n],
 // out[n] = total; the total also goes to counters[total_slot] and is checked
 // against `cap` (ST_CAPACITY when above).
 void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t* counters,
                  int total_slot, int64_t cap, int32_t* blocks, cudaStream_t s);
-void launch_csc(const Batch& b, const Ws& w, cudaStream_t s);
 
 // FP32 SIMT interaction network
 void launch_edge_enc_f32(const Batch& b, const Ws& w, const Mlp2F32& m, int h, Sel sel,

@@ -1,21 +1,16 @@
 // Input staging and rough-graph construction.
 //
-//  k_sort      per event, a stable counting sort of the hits by plane: the
-//              sorted order is (event, plane, input index), so the candidates of
-//              a hit on plane p (planes p+1 and p+2) form one contiguous range.
-//  k_radius    rough graph of Sec. "Hit Embedding and Rough Graph Construction":
-//              hit i on plane p joins hit j on plane p+1 or p+2 when
-//              d^2(i, j) = |e_i - e_j|^2 < d^2_max, keeping at most k_max per i
-//              (the k_max smallest by (d^2, sorted position)). One block per
-//              (event, plane p) stages the candidate embeddings in shared
-//              memory; one warp per query hit tests 32 candidates at a time and
-//              compacts the passing ones with a ballot. A count pass fills the
-//              per-hit candidate count, a scan turns it into CSR row pointers
-//              and a fill pass writes the edges in ascending target order.
-//  k_scan_*    exclusive scan in two kernels (block sums, with the last block
-//              scanning them; then block scans plus the block offset).
-//  k_csc_*     in-edge index: edges grouped by target, ascending edge id, so
-//              that message sums run in a fixed order.
+//  k_sort         per event, a stable counting sort of the hits by plane: the
+//                 sorted order is (event, plane, input index), so the
+//                 candidates of a hit on plane p (planes p+1 and p+2) form one
+//                 contiguous range.
+//  k_graph_event  per event, the rough graph of Sec. "Hit Embedding and Rough
+//                 Graph Construction" in CSR form and its in-edge index (see
+//                 the kernel's comment): degrees, offsets (block scan plus a
+//                 look-back over the earlier events), fill, in-edge lists.
+//  k_scan_*       exclusive scan in two kernels (block sums, with the last
+//                 block scanning them; then block scans plus the block offset),
+//                 used by the triplet stage.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -26,9 +21,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSortThreads = 256;
-constexpr int kRadiusThreads = 256;
-constexpr int kRadiusCountThreads = 64;  // count pass: one thread per query (about 65 per plane)
-constexpr int kCandSmemBytes = 12 * 1024;  // staged candidates (about 2-6 KB needed); 8 blocks per SM
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
 constexpr int kScanChunk = kScanThreads * kScanPer;
@@ -120,7 +112,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(Batch b, Ws w, int P) {
 }
 
 // ---------------------------------------------------------------------------
-// radius search
+// radius search helpers
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ float dist2(const float (&q)[D], const float* c) {
@@ -147,9 +139,73 @@ __device__ __forceinline__ float dist2(const float (&q)[D], const float* c) {
   return s;
 }
 
-// number of candidates with key < bound (strict) among those inside the radius
 template <int D>
-__device__ int count_below(const float (&q)[D], const float* ce, int nc, float r2,
+__device__ __forceinline__ void load_row(const float* r, float (&q)[D]) {
+  if constexpr (D % 4 == 0) {
+#pragma unroll
+    for (int d = 0; d < D; d += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(r + d);
+      q[d] = v.x;
+      q[d + 1] = v.y;
+      q[d + 2] = v.z;
+      q[d + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < D; ++d) q[d] = r[d];
+  }
+}
+
+// Candidate rows of an event, by event-local index c. Both forms give d^2 =
+// sum_d (q_d - c_d)^2 accumulated by fmaf in increasing d, bit for bit:
+//  CandRows  rows of D floats (global memory, events too large to stage);
+//  CandNegT  the event staged in shared memory transposed and negated,
+//            t[d * ns + c] = -e_c[d], so that two candidates c, c + 1 of one
+//            dimension are one 8-byte load and q_d + (-c_d) (exactly q_d - c_d)
+//            runs as a packed FP32 add, two candidates per instruction.
+template <int D>
+struct CandRows {
+  const float* e;
+  __device__ __forceinline__ float d2(const float (&q)[D], int c) const {
+    return dist2<D>(q, e + size_t(c) * D);
+  }
+  __device__ __forceinline__ void row(int c, float (&q)[D]) const { load_row<D>(e + size_t(c) * D, q); }
+};
+
+template <int D>
+struct CandNegT {
+  const float* t;
+  int ns;
+  __device__ __forceinline__ float d2(const float (&q)[D], int c) const {
+    float s = 0.0f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const float u = q[d] + t[d * ns + c];
+      s = fmaf(u, u, s);
+    }
+    return s;
+  }
+  // d^2 of the candidates c and c + 1 (c even), in one lane each
+  __device__ __forceinline__ float2 d2_pair(const float (&q)[D], int c) const {
+    float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const float2 nc = *reinterpret_cast<const float2*>(t + d * ns + c);
+      const float2 u = __fadd2_rn(make_float2(q[d], q[d]), nc);
+      s = __ffma2_rn(u, u, s);
+    }
+    return s;
+  }
+  __device__ __forceinline__ void row(int c, float (&q)[D]) const {
+#pragma unroll
+    for (int d = 0; d < D; ++d) q[d] = -t[d * ns + c];
+  }
+};
+
+// number of candidates [c0, c0 + nc) inside the radius whose key (d^2 as
+// ordered bits) is < bound (<= bound when inclusive)
+template <int D, class Cand>
+__device__ int count_below(const Cand& cd, const float (&q)[D], int c0, int nc, float r2,
                            unsigned bound, bool inclusive) {
   const int lane = threadIdx.x & 31;
   int n = 0;
@@ -157,7 +213,7 @@ __device__ int count_below(const float (&q)[D], const float* ce, int nc, float r
     const int c = base + lane;
     bool ok = false;
     if (c < nc) {
-      const float s = dist2<D>(q, ce + size_t(c) * D);
+      const float s = cd.d2(q, c0 + c);
       const unsigned key = __float_as_uint(s);
       ok = s < r2 && (inclusive ? key <= bound : key < bound);
     }
@@ -166,167 +222,433 @@ __device__ int count_below(const float (&q)[D], const float* ce, int nc, float r
   return n;
 }
 
-template <int D, bool FILL>
-__global__ void __launch_bounds__(kRadiusThreads) k_radius(Batch b, Ws w, GraphParams g) {
-  extern __shared__ float cand_s[];
-  if (input_bad(w)) return;
-  const int P = g.n_planes;
-  const int ev = blockIdx.x / (P - 1), p = blockIdx.x % (P - 1);
-  const int32_t* po = w.plane_off + size_t(ev) * (P + 1);
-  const int q0 = po[p], q1 = po[p + 1];
-  if (q0 == q1) return;
-  const int c0 = po[p + 1], c1 = po[min(p + 3, P)];
-  const int nc = c1 - c0;
+// The edges of one hit with more than k_max candidates inside the radius,
+// written by its warp: the k_max smallest keys (d^2 as ordered bits), ties
+// broken by candidate position, in ascending candidate order. T is the
+// k_max-th smallest key (bisection over the key bits); keys < T are kept,
+// then the first keys == T. Candidates are [c0, c0 + nc), event-local;
+// positions are written as pos0 + local index.
+template <int D, class Cand>
+__device__ void fill_capped(const Ws& w, const Cand& cd, const float (&qe)[D], int c0, int nc,
+                            float r2, int k_max, int64_t out0, int src_pos, int pos0) {
+  const int lane = threadIdx.x & 31;
+  unsigned lo = 0, hi = __float_as_uint(r2);
+  for (int it = 0; it < 40 && lo < hi; ++it) {
+    const unsigned mid = lo + (hi - lo) / 2;
+    if (count_below<D>(cd, qe, c0, nc, r2, mid, true) >= k_max)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const unsigned T = lo;
+  const int need_eq = k_max - count_below<D>(cd, qe, c0, nc, r2, T, false);
+  int written = 0, eq_seen = 0;
+  for (int base = 0; base < nc; base += 32) {
+    const int c = base + lane;
+    bool ok = false, eq = false;
+    float s = 0.0f;
+    if (c < nc) {
+      s = cd.d2(qe, c0 + c);
+      if (s < r2) {
+        const unsigned key = __float_as_uint(s);
+        eq = key == T;
+        ok = key < T;
+      }
+    }
+    const unsigned eqm = __ballot_sync(kFull, eq);
+    const int eq_rank = eq_seen + __popc(eqm & ((1u << lane) - 1u));
+    if (eq && eq_rank < need_eq) ok = true;
+    eq_seen += __popc(eqm);
+    const unsigned m = __ballot_sync(kFull, ok);
+    if (ok) {
+      const int64_t e = out0 + written + __popc(m & ((1u << lane) - 1u));
+      if (e < w.e_cap) {
+        w.col[e] = pos0 + c0 + c;
+        w.src[e] = src_pos;
+        w.d2[e] = s;
+      }
+    }
+    written += __popc(m);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rough graph and in-edge index, one block per event
+// ---------------------------------------------------------------------------
+// Rough graph of Sec. "Hit Embedding and Rough Graph Construction": hit i on
+// plane p joins hit j on plane p+1 or p+2 when d^2(i, j) = |e_i - e_j|^2 <
+// d^2_max, keeping at most k_max per i (the k_max smallest by (d^2, sorted
+// position)); the edges of a hit are stored in ascending target order, the
+// hits in sorted order (CSR). Then the in-edge index: each hit's in-edges in
+// ascending edge id, so that message sums run in a fixed order.
+//
+// Events go to blocks in index order by a ticket (counters[C_GRAPH_TICKET]),
+// and each event takes its global edge offset (the edges of all earlier
+// events) from a look-back over the totals its predecessors publish: an event
+// publishes its own edge count as soon as its degrees are known and its
+// inclusive prefix after its look-back, so a block only waits for blocks that
+// took their tickets before it and are therefore running. Per event:
+//   1. degrees: one thread per query hit, the 32 lanes of a warp on 32 hits
+//      of one plane, so that they read the same candidate rows (broadcast);
+//      the event's embeddings are staged in shared memory when they fit;
+//   2. CSR offsets: block scan of min(deg, k_max), look-back, row pointers;
+//   3. fill: one thread per query hit walking its candidates in ascending
+//      order; a hit over k_max is filled by its warp (fill_capped);
+//   4. in-edge index: in-degrees by shared-memory atomics, a block scan,
+//      placement by cursors, then each target's list sorted by edge id.
+constexpr int kGraphThreads = 512;
+constexpr int kGraphWarps = kGraphThreads / 32;
+constexpr int kGraphBlocksPerSm = 2;            // 16 warps each: 54-62 registers per thread
+constexpr int kGraphSmemBytes = 110 * 1024;  // an event of up to about 4600 hits staged
+constexpr int kGraphSmemInts = kGraphSmemBytes / 4;
+constexpr unsigned long long kDescAgg = 1ull << 62;  // the event's own edge count
+constexpr unsigned long long kDescInc = 2ull << 62;  // edges up to and including the event
+constexpr unsigned long long kDescVal = (1ull << 62) - 1;
+constexpr int kLookbackSpins = 1 << 22;  // x >= 100 ns sleeps: a bound of about half a second
+
+// Warp 0 of the block: publishes the event's edge count `agg` and returns the
+// edges of all earlier events, walking back over windows of 32 predecessors
+// until one has published its inclusive prefix. A wait that runs out sets
+// ST_TIMEOUT and returns what was summed.
+__device__ long long graph_lookback(unsigned long long* desc, int ev, long long agg,
+                                    int32_t* counters) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+    atomicExch(desc + ev, (ev == 0 ? +kDescInc : +kDescAgg) | static_cast<unsigned long long>(agg));
+  long long excl = 0;
+  int spins = 0;
+  for (int top = ev - 1; top >= 0; top -= 32) {
+    const int i = top - lane;
+    unsigned long long d = i >= 0 ? *reinterpret_cast<volatile unsigned long long*>(desc + i)
+                                  : +kDescInc;  // before event 0: an inclusive prefix of 0
+    while (__any_sync(kFull, (d >> 62) == 0)) {
+      if (++spins > kLookbackSpins) {
+        if (lane == 0) set_status(counters, ST_TIMEOUT);
+        return excl;
+      }
+      __nanosleep(100);
+      if ((d >> 62) == 0) d = *reinterpret_cast<volatile unsigned long long*>(desc + i);
+    }
+    const unsigned inc = __ballot_sync(kFull, (d >> 62) == 2);
+    const int stop = inc ? __ffs(inc) - 1 : 31;  // the nearest inclusive prefix
+    long long v = lane <= stop ? static_cast<long long>(d & kDescVal) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    excl += v;
+    if (inc) break;
+  }
+  if (lane == 0 && ev > 0)
+    atomicExch(desc + ev, kDescInc | static_cast<unsigned long long>(excl + agg));
+  return excl;
+}
+
+// exclusive scan of min(in[i], clamp) over i < n into out (both may be
+// shared or global memory); every thread gets the total
+__device__ int block_scan(const int32_t* in, int32_t* out, int n, int clamp, int* wsum) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const bool staged = size_t(nc) * D * sizeof(float) <= size_t(kCandSmemBytes);
-  const float* ce = staged ? cand_s : w.emb + size_t(c0) * D;
-  if (staged) {
-    if constexpr (D % 4 == 0) {
-      const float4* g4 = reinterpret_cast<const float4*>(w.emb + size_t(c0) * D);
-      float4* s4 = reinterpret_cast<float4*>(cand_s);
-      for (int k = tid; k < nc * D / 4; k += blockDim.x) s4[k] = g4[k];
-    } else {
-      for (int k = tid; k < nc * D; k += blockDim.x) cand_s[k] = w.emb[size_t(c0) * D + k];
-    }
-    __syncthreads();
-  }
-  const float r2 = g.radius2;
-  if constexpr (!FILL) {
-    // count: one thread per query, all threads stepping through the same
-    // candidates (shared-memory broadcasts); the candidates inside the radius
-    // go to the query's mask words for the fill pass
-    for (int q = q0 + tid; q < q1; q += blockDim.x) {
-      float qe[D];
+  const int per = (n + kGraphThreads - 1) / kGraphThreads;
+  const int a = min(n, tid * per), z = min(n, a + per);
+  int sum = 0;
+  for (int i = a; i < z; ++i) sum += min(in[i], clamp);
+  int x = sum;
 #pragma unroll
-      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
-      int cnt = 0;
-      for (int base = 0; base < nc; base += 32) {
-        const int m_end = min(32, nc - base);
-        unsigned m = 0;
-        for (int j = 0; j < m_end; ++j)
-          if (dist2<D>(qe, ce + size_t(base + j) * D) < r2) m |= 1u << j;
-        cnt += __popc(m);
-        if (nc <= kMaskCands) w.rmask[size_t(q) * kMaskWords + base / 32] = m;
-      }
-      w.deg[q] = cnt;
-    }
-    return;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, d);
+    if (lane >= d) x += y;
   }
-  if (FILL && nc <= kMaskCands) {
-    // one thread per query: walk the set bits of its masks (ascending
-    // candidate index, the order of the warp path), recompute d^2 only there
-    const int nwords = (nc + 31) / 32;
-    for (int q = q0 + tid; q < q1; q += blockDim.x) {
-      const int cnt = w.deg[q];
-      if (cnt > g.k_max) continue;  // capped: the warp path below selects
-      float qe[D];
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int before = 0, total = 0;
 #pragma unroll
-      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
-      int64_t e = w.row_ptr[q];
-      for (int k = 0; k < nwords; ++k) {
-        unsigned m = w.rmask[size_t(q) * kMaskWords + k];
-        while (m) {
-          const int c = k * 32 + __ffs(m) - 1;
-          m &= m - 1;
-          if (e < w.e_cap) {
-            w.col[e] = c0 + c;
-            w.src[e] = q;
-            w.d2[e] = dist2<D>(qe, ce + size_t(c) * D);
-          }
-          ++e;
-        }
-      }
-    }
+  for (int k = 0; k < kGraphWarps; ++k) {
+    const int t = wsum[k];
+    if (k < warp) before += t;
+    total += t;
   }
-  for (int q = q0 + warp; q < q1; q += nwarps) {
+  int run = before + x - sum;
+  for (int i = a; i < z; ++i) {
+    const int c = min(in[i], clamp);
+    out[i] = run;
+    run += c;
+  }
+  __syncthreads();  // out complete, wsum free
+  return total;
+}
+
+__device__ __forceinline__ int clamp31(long long v) {
+  return int(v > 0x7fffffffLL ? 0x7fffffffLL : v);
+}
+
+// The query hits of an event are processed in items of up to 32 hits of one
+// plane (a lane per hit), so that the lanes of a warp read the same
+// candidate rows; item t is on plane p with chunk_s[p] <= t < chunk_s[p + 1].
+struct GraphItem {
+  int q0, q1, c0, c1;  // its hits [q0, q1) and their candidates [c0, c1), event-local
+};
+
+__device__ __forceinline__ GraphItem graph_item(const int* po_s, const int* chunk_s, int P, int t) {
+  int p = 0;
+  while (chunk_s[p + 1] <= t) ++p;
+  return GraphItem{po_s[p] + (t - chunk_s[p]) * 32, po_s[p + 1], po_s[p + 1], po_s[min(p + 3, P)]};
+}
+
+// 1. degrees (uncapped) of the event's query hits. With PAIR (the staged,
+// transposed rows) two candidates per step from an even start cA = c0 & ~1,
+// and, when mw > 0, the in-radius candidates of hit q as bit masks:
+// mask[q * mw + k] bit b is candidate cA + 32 k + b.
+template <int D, bool PAIR, class Cand>
+__device__ void graph_degrees(const Cand& cd, const int* po_s, const int* chunk_s, int P,
+                              int n_items, float r2, int32_t* deg, uint32_t* mask, int mw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t < n_items; t += kGraphWarps) {
+    const GraphItem it = graph_item(po_s, chunk_s, P, t);
+    const int q = it.q0 + lane;
+    const bool valid = q < it.q1;
     float qe[D];
-    if constexpr (D % 4 == 0) {
-#pragma unroll
-      for (int d = 0; d < D; d += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(w.emb + size_t(q) * D + d);
-        qe[d] = v.x;
-        qe[d + 1] = v.y;
-        qe[d + 2] = v.z;
-        qe[d + 3] = v.w;
+    cd.row(valid ? q : it.q0, qe);
+    int cnt = 0;
+    if constexpr (PAIR) {
+      const int cA = it.c0 & ~1;
+      for (int wb = cA; wb < it.c1; wb += 32) {
+        const int we = min(it.c1, wb + 32);
+        unsigned m = 0;
+#pragma unroll 4
+        for (int c = wb; c < we; c += 2) {
+          const float2 s = cd.d2_pair(qe, c);
+          m |= ((s.x < r2 ? 1u : 0u) | (s.y < r2 ? 2u : 0u)) << (c - wb);
+        }
+        if (wb == cA && it.c0 != cA) m &= ~1u;       // c0 - 1 is not a candidate
+        if (we - wb < 32) m &= (1u << (we - wb)) - 1u;  // nor c1 (odd end)
+        cnt += __popc(m);
+        if (mw > 0 && valid) mask[q * mw + (wb - cA) / 32] = m;
       }
     } else {
-#pragma unroll
-      for (int d = 0; d < D; ++d) qe[d] = w.emb[size_t(q) * D + d];
+      for (int c = it.c0; c < it.c1; ++c) cnt += cd.d2(qe, c) < r2;
     }
-    const int cnt = w.deg[q];
-    // queries within k_max with stored masks were written lane-per-query above
-    if (nc <= kMaskCands && cnt <= g.k_max) continue;
-    const int64_t out0 = w.row_ptr[q];
-    // selection threshold when more than k_max candidates pass: T is the
-    // k_max-th smallest key; keys < T are kept, then the first keys == T
-    unsigned T = 0xffffffffu;
-    int need_eq = 0;
-    const bool capped = cnt > g.k_max;
-    if (capped) {
-      unsigned lo = 0, hi = __float_as_uint(r2);
-      for (int it = 0; it < 40 && lo < hi; ++it) {
-        const unsigned mid = lo + (hi - lo) / 2;
-        if (count_below<D>(qe, ce, nc, r2, mid, true) >= g.k_max)
-          hi = mid;
-        else
-          lo = mid + 1;
-      }
-      T = lo;
-      need_eq = g.k_max - count_below<D>(qe, ce, nc, r2, T, false);
-    }
-    int written = 0, eq_seen = 0;
-    for (int base = 0; base < nc; base += 32) {
-      const int c = base + lane;
-      bool ok = false, eq = false;
-      float s = 0.0f;
-      if (c < nc) {
-        s = dist2<D>(qe, ce + size_t(c) * D);
-        ok = s < r2;
-        if (capped && ok) {
-          const unsigned key = __float_as_uint(s);
-          eq = key == T;
-          ok = key < T;
-        }
-      }
-      if (capped) {
-        const unsigned eqm = __ballot_sync(kFull, eq);
-        const int eq_rank = eq_seen + __popc(eqm & ((1u << lane) - 1u));
-        if (eq && eq_rank < need_eq) ok = true;
-        eq_seen += __popc(eqm);
-      }
-      const unsigned m = __ballot_sync(kFull, ok);
-      if (ok) {
-        const int64_t e = out0 + written + __popc(m & ((1u << lane) - 1u));
+    if (valid) deg[q] = cnt;
+  }
+}
+
+// 3. fill: one lane per query hit writes its edges in ascending candidate
+// order at out = base + off[q] (walking its mask bits, or testing every
+// candidate again when there are no masks); a hit over k_max is filled by its
+// warp (fill_capped).
+template <int D, class Cand>
+__device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const int* chunk_s, int P,
+                           int n_items, float r2, int k_max, const int32_t* deg,
+                           const int32_t* off, const uint32_t* mask, int mw, long long base,
+                           int v0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t < n_items; t += kGraphWarps) {
+    const GraphItem it = graph_item(po_s, chunk_s, P, t);
+    const int q = it.q0 + lane;
+    const bool valid = q < it.q1;
+    const int cnt = valid ? deg[q] : 0;
+    if (valid && cnt > 0 && cnt <= k_max) {
+      float qe[D];
+      cd.row(q, qe);
+      int64_t e = base + off[q];
+      auto put = [&](int c, float s) {
         if (e < w.e_cap) {
-          const int t = c0 + c;
-          w.col[e] = t;
-          w.src[e] = q;
+          w.col[e] = v0 + c;
+          w.src[e] = v0 + q;
           w.d2[e] = s;
         }
+        ++e;
+      };
+      if (mw > 0) {
+        const int cA = it.c0 & ~1;
+        const int nw = (it.c1 - cA + 31) / 32;
+        for (int k = 0; k < nw; ++k) {
+          unsigned m = mask[q * mw + k];
+          while (m) {
+            const int c = cA + 32 * k + __ffs(m) - 1;
+            m &= m - 1;
+            put(c, cd.d2(qe, c));
+          }
+        }
+      } else {
+        for (int c = it.c0; c < it.c1; ++c) {
+          const float s = cd.d2(qe, c);
+          if (s < r2) put(c, s);
+        }
       }
-      written += __popc(m);
+    }
+    unsigned capped = __ballot_sync(kFull, cnt > k_max);
+    while (capped) {
+      const int qq = it.q0 + __ffs(capped) - 1;
+      capped &= capped - 1;
+      float qe[D];
+      cd.row(qq, qe);
+      fill_capped<D>(w, cd, qe, it.c0, it.c1 - it.c0, r2, k_max, base + off[qq], v0 + qq, v0);
     }
   }
 }
 
 template <int D>
-void radius_d(const Batch& b, const Ws& w, const GraphParams& g, bool fill, cudaStream_t s) {
-  const int grid = b.n_events * (g.n_planes - 1);
-  if (grid <= 0) return;
+__global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_event(Batch b, Ws w, GraphParams g) {
+  extern __shared__ __align__(16) float sm_graph[];
+  __shared__ int po_s[kMaxPlanes + 1];     // event-local plane offsets
+  __shared__ int chunk_s[kMaxPlanes + 1];  // 32-hit chunks of the query planes before p
+  __shared__ int wsum[kGraphWarps];
+  __shared__ int ticket_s, mw_s;
+  __shared__ long long base_s;
+  if (input_bad(w)) return;
+  const int P = g.n_planes;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float r2 = g.radius2;
+  const int k_max = g.k_max;
+  int32_t* sm_i = reinterpret_cast<int32_t*>(sm_graph);
+  for (;;) {
+    if (tid == 0) ticket_s = atomicAdd(&w.counters[C_GRAPH_TICKET], 1);
+    __syncthreads();
+    const int ev = ticket_s;
+    if (ev >= b.n_events) return;
+    const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
+    const int n = v1 - v0;
+    const int32_t* po = w.plane_off + size_t(ev) * (P + 1);
+    for (int i = tid; i <= P; i += kGraphThreads) po_s[i] = po[i] - v0;
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0, words = 0;
+      for (int p = 0; p + 1 < P; ++p) {
+        chunk_s[p] = run;
+        run += (po_s[p + 1] - po_s[p] + 31) / 32;
+        if (po_s[p + 1] > po_s[p])
+          words = max(words, (po_s[min(p + 3, P)] - (po_s[p + 1] & ~1) + 31) / 32);
+      }
+      chunk_s[P > 1 ? P - 1 : 0] = run;
+      mw_s = words;
+    }
+    // rows of this event, event-local index: the embeddings (staged
+    // transposed and negated when they fit: t[d * ns + i] = -e_i[d]),
+    // degrees, offsets and, when they fit too, the candidate masks
+    const int ns = (n + 2) & ~1;  // even, with a pad column read by the last pair
+    const bool staged = int64_t(D) * ns + 2 * int64_t(n) <= kGraphSmemInts;
+    int32_t* deg = staged ? sm_i + D * ns : w.deg + v0;
+    int32_t* off = staged ? sm_i + D * ns + n : w.in_cnt + v0;
+    if (staged) {
+      for (int k = tid; k < n * D; k += kGraphThreads) {
+        const int i = k / D, d = k - i * D;
+        sm_graph[d * ns + i] = -w.emb[size_t(v0) * D + k];
+      }
+      for (int k = tid; k < D * (ns - n); k += kGraphThreads) {
+        const int d = k / (ns - n);
+        sm_graph[d * ns + n + (k - d * (ns - n))] = 0.0f;
+      }
+    }
+    __syncthreads();
+    const int n_items = chunk_s[P > 1 ? P - 1 : 0];
+    const int mw = staged && int64_t(D) * ns + int64_t(n) * (2 + mw_s) <= kGraphSmemInts ? mw_s : 0;
+    uint32_t* mask = reinterpret_cast<uint32_t*>(sm_i + D * ns + 2 * n);
+    const CandNegT<D> cst{sm_graph, ns};
+    const CandRows<D> cgl{w.emb + size_t(v0) * D};
+
+    // 1. degrees (uncapped)
+    if (staged)
+      graph_degrees<D, true>(cst, po_s, chunk_s, P, n_items, r2, deg, mask, mw);
+    else
+      graph_degrees<D, false>(cgl, po_s, chunk_s, P, n_items, r2, deg, nullptr, 0);
+    if (P >= 1)
+      for (int q = po_s[P - 1] + tid; q < n; q += kGraphThreads) deg[q] = 0;  // no candidates
+    __syncthreads();
+
+    // 2. offsets: event-local exclusive scan, then the event's global base
+    const int total = block_scan(deg, off, n, k_max, wsum);
+    if (warp == 0) {
+      const long long ex = graph_lookback(w.graph_desc, ev, total, w.counters);
+      if (lane == 0) base_s = ex;
+    }
+    __syncthreads();
+    const long long base = base_s;
+    for (int i = tid; i < n; i += kGraphThreads) w.row_ptr[v0 + i] = clamp31(base + off[i]);
+    if (ev == b.n_events - 1 && tid == 0) {
+      const long long all = base + total;
+      w.row_ptr[v1] = clamp31(all);
+      w.counters[C_EDGES] = clamp31(all);
+      if (all > w.e_cap || all > 0x7fffffffLL) set_status(w.counters, ST_CAPACITY);
+    }
+
+    // 3. fill
+    if (staged)
+      graph_fill<D>(w, cst, po_s, chunk_s, P, n_items, r2, k_max, deg, off, mask, mw, base, v0);
+    else
+      graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, deg, off, nullptr, 0, base, v0);
+    __syncthreads();  // edges written; the shared rows are free
+
+    // 4. in-edge index of the event's edges [e0, e1)
+    const int e0 = int(base < w.e_cap ? base : w.e_cap);
+    const int e1 = int(base + total < w.e_cap ? base + total : w.e_cap);
+    const bool c_smem = n <= kGraphSmemInts;
+    int32_t* C = c_smem ? sm_i : w.in_cnt + v0;
+    for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
+    __syncthreads();
+    for (int e = e0 + tid; e < e1; e += kGraphThreads) atomicAdd(&C[w.col[e] - v0], 1);
+    __syncthreads();
+    {
+      const int per = (n + kGraphThreads - 1) / kGraphThreads;
+      const int a = min(n, tid * per), z = min(n, a + per);
+      int sum = 0;
+      for (int i = a; i < z; ++i) sum += C[i];
+      int x = sum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      __syncthreads();
+      int before = 0;
+      for (int k = 0; k < warp; ++k) before += wsum[k];
+      int run = before + x - sum;
+      for (int i = a; i < z; ++i) {
+        const int c = C[i];
+        C[i] = run;  // cursor
+        w.in_ptr[v0 + i] = e0 + run;
+        run += c;
+      }
+      if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
+    }
+    __syncthreads();
+    // placement and per-target sort in shared memory when the event's list
+    // fits (copied out coalesced), else in its slice of in_edge
+    const bool l_smem = c_smem && int64_t(n) + (e1 - e0) <= kGraphSmemInts;
+    int32_t* L = l_smem ? sm_i + n : w.in_edge + e0;  // L[k]: list position e0 + k
+    for (int e = e0 + tid; e < e1; e += kGraphThreads) {
+      const int k = atomicAdd(&C[w.col[e] - v0], 1);
+      L[k] = e;
+    }
+    __syncthreads();
+    // C[i] is now the end of target i's list (event-local position)
+    for (int i = tid; i < n; i += kGraphThreads) {
+      const int lo = w.in_ptr[v0 + i] - e0, hi = C[i];
+      for (int j = lo + 1; j < hi; ++j) {
+        const int key = L[j];
+        int k = j - 1;
+        while (k >= lo && L[k] > key) {
+          L[k + 1] = L[k];
+          --k;
+        }
+        L[k + 1] = key;
+      }
+    }
+    __syncthreads();
+    if (l_smem)
+      for (int k = tid; k < e1 - e0; k += kGraphThreads) w.in_edge[e0 + k] = L[k];
+    __syncthreads();  // shared memory and ticket_s are reused by the next event
+  }
+}
+
+template <int D>
+void graph_d(const Batch& b, const Ws& w, const GraphParams& g, int grid, cudaStream_t s) {
   // set once per instantiation (thread-safe initialisation of a local static)
   static const bool attr = [] {
-    cudaFuncSetAttribute(k_radius<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kCandSmemBytes);
-    cudaFuncSetAttribute(k_radius<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kCandSmemBytes);
+    cudaFuncSetAttribute(k_graph_event<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kGraphSmemBytes);
     return true;
   }();
   (void)attr;
-  if (fill)
-    k_radius<D, true><<<grid, kRadiusThreads, kCandSmemBytes, s>>>(b, w, g);
-  else
-    k_radius<D, false><<<grid, kRadiusCountThreads, kCandSmemBytes, s>>>(b, w, g);
+  k_graph_event<D><<<grid, kGraphThreads, kGraphSmemBytes, s>>>(b, w, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,86 +749,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* in, 
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = counters[total_slot];
 }
 
-// ---------------------------------------------------------------------------
-// in-edge index
-// ---------------------------------------------------------------------------
-// In-edge index, one block per event: an event's edges are the contiguous
-// range [row_ptr[v0], row_ptr[v1]) and its in-edges are among them, so its
-// in_ptr / in_edge slice is built locally: in-degrees by shared-memory atomics,
-// a block-wide exclusive scan, placement by cursors, then each target's list
-// sorted by edge id (ascending, so the message sums have a fixed order). An
-// event with more than kCscSmemHits hits counts in its slice of in_cnt.
-constexpr int kCscThreads = 512;
-constexpr int kCscSmemHits = 8192;
-constexpr int kCscSmemEdges = 12288;  // an event's in-edge list staged in shared memory
-
-__global__ void __launch_bounds__(kCscThreads) k_csc_event(Batch b, Ws w) {
-  extern __shared__ int32_t sm_csc[];
-  __shared__ int wsum[kCscThreads / 32];
-  if (input_bad(w)) return;
-  const int E = clamp_edges(w.counters, w.e_cap);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
-    const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
-    const int n = v1 - v0;
-    const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
-    int32_t* C = n <= kCscSmemHits ? sm_csc : w.in_cnt + v0;
-    for (int i = tid; i < n; i += kCscThreads) C[i] = 0;
-    __syncthreads();
-    for (int e = e0 + tid; e < e1; e += kCscThreads) atomicAdd(&C[w.col[e] - v0], 1);
-    __syncthreads();
-    // exclusive scan: thread t owns the consecutive counts [t*per, (t+1)*per)
-    const int per = (n + kCscThreads - 1) / kCscThreads;
-    const int a = min(n, tid * per), z = min(n, a + per);
-    int sum = 0;
-    for (int i = a; i < z; ++i) sum += C[i];
-    int x = sum;
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(kFull, x, d);
-      if (lane >= d) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    int before = 0;
-    for (int k = 0; k < warp; ++k) before += wsum[k];
-    int run = before + x - sum;
-    for (int i = a; i < z; ++i) {
-      const int c = C[i];
-      C[i] = run;  // cursor
-      w.in_ptr[v0 + i] = e0 + run;
-      run += c;
-    }
-    if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
-    __syncthreads();
-    // placement and per-target sort in shared memory when the event's list
-    // fits (copied out coalesced), else in its slice of in_edge
-    const bool staged = n <= kCscSmemHits && e1 - e0 <= kCscSmemEdges;
-    int32_t* L = staged ? sm_csc + kCscSmemHits : w.in_edge + e0;  // L[k]: list position e0 + k
-    for (int e = e0 + tid; e < e1; e += kCscThreads) {
-      const int k = atomicAdd(&C[w.col[e] - v0], 1);
-      L[k] = e;
-    }
-    __syncthreads();
-    // C[i] is now the end of target i's list (event-local position)
-    for (int i = tid; i < n; i += kCscThreads) {
-      const int lo = w.in_ptr[v0 + i] - e0, hi = C[i];
-      for (int j = lo + 1; j < hi; ++j) {
-        const int key = L[j];
-        int k = j - 1;
-        while (k >= lo && L[k] > key) {
-          L[k + 1] = L[k];
-          --k;
-        }
-        L[k + 1] = key;
-      }
-    }
-    __syncthreads();
-    if (staged)
-      for (int k = tid; k < e1 - e0; k += kCscThreads) w.in_edge[e0 + k] = L[k];
-    __syncthreads();  // C and the staged list are reused by the next event
-  }
-}
-
 int num_sms() {
   // queried once per process (thread-safe initialisation of a local static)
   static const int n = [] {
@@ -525,22 +767,6 @@ void launch_sort(const Batch& b, const Ws& w, int n_planes, cudaStream_t s) {
   k_sort<<<b.n_events, kSortThreads, 0, s>>>(b, w, n_planes);
 }
 
-void launch_radius(const Batch& b, const Ws& w, const GraphParams& g, int D, bool fill,
-                   cudaStream_t s) {
-  switch (D) {
-    case 1: radius_d<1>(b, w, g, fill, s); break;
-    case 2: radius_d<2>(b, w, g, fill, s); break;
-    case 3: radius_d<3>(b, w, g, fill, s); break;
-    case 4: radius_d<4>(b, w, g, fill, s); break;
-    case 5: radius_d<5>(b, w, g, fill, s); break;
-    case 6: radius_d<6>(b, w, g, fill, s); break;
-    case 7: radius_d<7>(b, w, g, fill, s); break;
-    case 8: radius_d<8>(b, w, g, fill, s); break;
-    case 16: radius_d<16>(b, w, g, fill, s); break;
-    default: break;
-  }
-}
-
 void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t* counters,
                  int total_slot, int64_t cap, int32_t* blocks, cudaStream_t s) {
   const int nb = div_up(n > 0 ? n : 1, kScanChunk);
@@ -548,16 +774,22 @@ void launch_scan(const int32_t* in, int32_t* out, int n, int clamp_max, int32_t*
   k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, clamp_max, blocks, counters, total_slot);
 }
 
-void launch_csc(const Batch& b, const Ws& w, cudaStream_t s) {
+void launch_graph(const Batch& b, const Ws& w, const GraphParams& g, int D, cudaStream_t s) {
   if (b.n_events <= 0) return;
-  static const bool attr_set = [] {
-    cudaFuncSetAttribute(k_csc_event, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (kCscSmemHits + kCscSmemEdges) * int(sizeof(int32_t)));
-    return true;
-  }();
-  (void)attr_set;
-  k_csc_event<<<std::min(b.n_events, num_sms() * 16), kCscThreads,
-                (kCscSmemHits + kCscSmemEdges) * sizeof(int32_t), s>>>(b, w);
+  cudaMemsetAsync(w.graph_desc, 0, sizeof(unsigned long long) * b.n_events, s);
+  const int grid = std::min(b.n_events, num_sms() * kGraphBlocksPerSm);
+  switch (D) {
+    case 1: graph_d<1>(b, w, g, grid, s); break;
+    case 2: graph_d<2>(b, w, g, grid, s); break;
+    case 3: graph_d<3>(b, w, g, grid, s); break;
+    case 4: graph_d<4>(b, w, g, grid, s); break;
+    case 5: graph_d<5>(b, w, g, grid, s); break;
+    case 6: graph_d<6>(b, w, g, grid, s); break;
+    case 7: graph_d<7>(b, w, g, grid, s); break;
+    case 8: graph_d<8>(b, w, g, grid, s); break;
+    case 16: graph_d<16>(b, w, g, grid, s); break;
+    default: break;
+  }
 }
 
 int device_sms() { return num_sms(); }

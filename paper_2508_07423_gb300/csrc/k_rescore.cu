@@ -9,8 +9,8 @@
 //   edge step k-1 : E_{k-1} = edges incident to V_k       (their e^k feeds the sums)
 //   node encoder  : V_{-1} = V_0 + endpoints(E_{-1}); edge encoder: E_{-1}
 // Recomputing exactly these rows in FP32 gives the band edges the same logits
-// as an FP32 run of the whole event. Before each step a stable compaction
-// lists that step's rows (level >= k) in index order.
+// as an FP32 run of the whole event. The same kernel lists each step's rows
+// (level >= k) in index order for the FP32 kernels.
 //
 // Levels are stored as int8 shifted by +2 (0 = not needed, 1 = encoders only,
 // k + 2 = up to step k), so a memset clears them.
@@ -24,20 +24,26 @@ int device_sms();
 
 namespace {
 
-constexpr int kRsThreads = 256;
-constexpr int kRsWarps = kRsThreads / 32;
-
 __device__ __forceinline__ bool input_bad(const int32_t* counters) {
   return (*(volatile const int32_t*)&counters[C_STATUS] & ST_INPUT) != 0;
 }
 
+// Levels of one event, indexed event-locally: el[e - e0] for its edges,
+// nl[v - v0] for its hits (shared memory when the event fits, else the
+// event's slices of the workspace arrays).
+struct EvLevels {
+  int8_t* el;
+  int8_t* nl;
+  int e0, v0;
+};
+
 // E_{K-1} = band edges, V_{K-1} = their endpoints. Returns 1 for a band edge.
-__device__ __forceinline__ int rs_init_edge(const Ws& w, int e, float l, float lo, float hi,
-                                            int8_t top) {
+__device__ __forceinline__ int rs_init_edge(const Ws& w, const EvLevels& L, int e, float l,
+                                            float lo, float hi, int8_t top) {
   if (!(l > lo && l < hi)) return 0;
-  w.rs_elev[e] = top;
-  w.rs_nlev[w.src[e]] = top;  // every writer stores the same value
-  w.rs_nlev[w.col[e]] = top;
+  L.el[e - L.e0] = top;
+  L.nl[w.src[e] - L.v0] = top;  // every writer stores the same value
+  L.nl[w.col[e] - L.v0] = top;
   return 1;
 }
 
@@ -46,58 +52,224 @@ __device__ __forceinline__ int rs_init_edge(const Ws& w, int e, float l, float l
 // in V_{k-1}. Within one sweep a hit level only rises to k + 1, which no
 // other edge of the same sweep tests for, so the sweep does not depend on
 // the order of its edges.
-__device__ __forceinline__ void rs_step_edge(const Ws& w, int e, int8_t ge_k, int8_t km1) {
-  int8_t L = w.rs_elev[e];
-  const int a = w.src[e], c = w.col[e];
-  const int8_t la = w.rs_nlev[a], lc = w.rs_nlev[c];
-  if (L < km1 && (la >= ge_k || lc >= ge_k)) {
-    L = km1;
-    w.rs_elev[e] = L;
+__device__ __forceinline__ void rs_step_edge(const Ws& w, const EvLevels& L, int e, int8_t ge_k,
+                                             int8_t km1) {
+  int8_t le = L.el[e - L.e0];
+  const int a = w.src[e] - L.v0, c = w.col[e] - L.v0;
+  const int8_t la = L.nl[a], lc = L.nl[c];
+  if (le < km1 && (la >= ge_k || lc >= ge_k)) {
+    le = km1;
+    L.el[e - L.e0] = le;
   }
-  if (L >= km1) {
-    if (la < km1) w.rs_nlev[a] = km1;
-    if (lc < km1) w.rs_nlev[c] = km1;
+  if (le >= km1) {
+    if (la < km1) L.nl[a] = km1;
+    if (lc < km1) L.nl[c] = km1;
   }
 }
 
-// The whole receptive field, one block per event (events share no hits and
-// no edges): clear the event's levels, mark the band edges and their
-// endpoints, then the K backward steps with a block barrier between them;
-// counts the band edges into counters[C_BAND] and the events holding one
-// into counters[C_RERUN].
+// The whole receptive field and the row lists of every step, one block per
+// event (events share no hits and no edges): clear the event's levels, mark
+// the band edges and their endpoints, the K backward steps with a block
+// barrier between them, then the event's rows of each list. List t (t = 0 ..
+// K, step k = t - 1) holds the rows of level >= k in index order, so that a
+// step's kernels visit rows in the batch's event order, as the full FP32 path
+// does. Events go to blocks in index order by a ticket (counters[C_RS_TICKET])
+// and each takes its offsets in the 2 (K + 1) lists from a look-back over the
+// counts its predecessors publish (flag 1: the event's own counts, flag 2: the
+// counts up to and including it), so a block only waits for blocks that took
+// their tickets before it. Counts the band edges into counters[C_BAND] and the
+// events holding one into counters[C_RERUN].
 constexpr int kRsEvThreads = 512;
+constexpr int kRsEvWarps = kRsEvThreads / 32;
+constexpr int kRsLists = 2 * (kMaxIters + 1);
+constexpr int kRsLookbackSpins = 1 << 22;  // x >= 100 ns sleeps: about half a second
+constexpr int kRsSmemBytes = 40 * 1024;     // levels of an event of up to 40 k hits + edges
 
-__global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, float lo, float hi, int K) {
+struct RsDesc {
+  int32_t* flag;  // [n_events]
+  int32_t* agg;   // [n_events][2 (K + 1)] the event's own counts
+  int32_t* inc;   // [n_events][2 (K + 1)] counts up to and including the event
+};
+
+__device__ __forceinline__ int ld_vol(const int32_t* p) { return *(volatile const int32_t*)p; }
+
+// The event's rows of one side (edges or hits, [r0, r1)) are cut into one
+// contiguous segment per warp, so that counting and placement need no block
+// barrier inside their loops: warp q counts its segment's rows per list,
+// a block scan over the warps gives each warp its offset in every list, and
+// the warp then places its rows in order (ballot ranks).
+__device__ __forceinline__ void rs_segment(int r0, int r1, int warp, int& a, int& z) {
+  const int len = (((r1 - r0) + kRsEvWarps - 1) / kRsEvWarps + 31) / 32 * 32;
+  a = min(r1, r0 + warp * len);
+  z = min(r1, a + len);
+}
+
+// counts of this warp's rows per list t (t = 0 .. K) into wcnt[t][warp]
+__device__ void rs_count_warp(const int8_t* lev, int r0, int r1, int K, int (*wcnt)[kRsEvWarps]) {
+  // lev[r - r0]: the level of row r
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int a, z;
+  rs_segment(r0, r1, warp, a, z);
+  int mine = 0;  // lane t holds the count of list t
+  for (int c0 = a; c0 < z; c0 += 32) {
+    const int r = c0 + lane;
+    const int l = r < z ? lev[r - r0] : 0;
+    for (int t = 0; t <= K; ++t) {
+      const int n = __popc(__ballot_sync(0xffffffffu, l >= t + 1));
+      if (lane == t) mine += n;
+    }
+  }
+  if (lane <= K) wcnt[lane][warp] = mine;
+}
+
+// this warp's rows into list t at run[t][warp] (t = 0 .. K), in index order
+__device__ void rs_place_warp(const int8_t* lev, int r0, int r1, int K, int32_t* list,
+                              int64_t stride, int (*run)[kRsEvWarps]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int a, z;
+  rs_segment(r0, r1, warp, a, z);
+  int mine = lane <= K ? run[lane][warp] : 0;  // lane t: next position in list t
+  for (int c0 = a; c0 < z; c0 += 32) {
+    const int r = c0 + lane;
+    const int l = r < z ? lev[r - r0] : 0;
+    for (int t = 0; t <= K; ++t) {
+      const unsigned m = __ballot_sync(0xffffffffu, l >= t + 1);
+      const int at = __shfl_sync(0xffffffffu, mine, t);
+      if (l >= t + 1) list[t * stride + at + __popc(m & lt)] = r;
+      if (lane == t) mine += __popc(m);
+    }
+  }
+}
+
+// Warp 0: publishes the event's counts cnt[0 .. nv) and sets base[v] to the
+// counts of all earlier events. A wait that runs out sets ST_TIMEOUT.
+__device__ void rs_lookback(const RsDesc& d, int ev, int nv, const int* cnt, int* base,
+                            int32_t* counters) {
+  const int lane = threadIdx.x & 31;
+  for (int v = lane; v < nv; v += 32) {
+    base[v] = 0;
+    (ev == 0 ? d.inc : d.agg)[size_t(ev) * nv + v] = cnt[v];
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicExch(d.flag + ev, ev == 0 ? 2 : 1);
+  int spins = 0;
+  bool timed_out = false;
+  for (int top = ev - 1; top >= 0 && !timed_out; top -= 32) {
+    const int i = top - lane;
+    int f = i >= 0 ? ld_vol(d.flag + i) : 2;  // before event 0: counts of 0
+    while (__any_sync(0xffffffffu, f == 0)) {
+      if (++spins > kRsLookbackSpins) {
+        timed_out = true;
+        break;
+      }
+      __nanosleep(100);
+      if (f == 0) f = ld_vol(d.flag + i);
+    }
+    if (timed_out) break;
+    __threadfence();  // the counts were written before the flags read above
+    const unsigned incm = __ballot_sync(0xffffffffu, f == 2);
+    const int stop = incm ? __ffs(incm) - 1 : 31;  // the nearest inclusive counts
+    const int32_t* src = f == 2 ? d.inc : d.agg;
+    for (int v = 0; v < nv; ++v) {
+      int x = (lane <= stop && i >= 0) ? ld_vol(src + size_t(i) * nv + v) : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) base[v] += x;
+    }
+    __syncwarp();
+    if (incm) break;
+  }
+  if (timed_out) {
+    if (lane == 0) set_status(counters, ST_TIMEOUT);
+    return;
+  }
+  if (ev > 0) {
+    for (int v = lane; v < nv; v += 32) d.inc[size_t(ev) * nv + v] = base[v] + cnt[v];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(d.flag + ev, 2);
+  }
+}
+
+__global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, RsDesc d, float lo,
+                                                          float hi, int K) {
+  extern __shared__ int8_t sm_lev[];  // [n hits][edges] levels of the event
   if (input_bad(w.counters)) return;
-  __shared__ int wsum[kRsEvThreads / 32];
+  __shared__ int wsum[kRsEvWarps];
+  __shared__ int wcnt[kRsLists][kRsEvWarps];  // per list and warp: rows, then offsets
+  __shared__ int cnt_s[kRsLists];
+  __shared__ int base_s[kRsLists];
+  __shared__ int ticket_s;
+  const int NL = kMaxIters + 2;
+  const int nv = 2 * (K + 1);
   const int E = clamp_edges(w.counters, w.e_cap);
   const int8_t top = int8_t((K > 0 ? K - 1 : -1) + 2);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   int band_total = 0, band_events = 0;
-  for (int ev = blockIdx.x; ev < b.n_events; ev += gridDim.x) {
+  for (;;) {
+    if (tid == 0) ticket_s = atomicAdd(&w.counters[C_RS_TICKET], 1);
+    __syncthreads();
+    const int ev = ticket_s;
+    if (ev >= b.n_events) break;
     const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
     const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
-    for (int i = v0 + tid; i < v1; i += kRsEvThreads) w.rs_nlev[i] = 0;
-    for (int e = e0 + tid; e < e1; e += kRsEvThreads) w.rs_elev[e] = 0;
+    const bool staged = (v1 - v0) + (e1 - e0) <= kRsSmemBytes;
+    const EvLevels L{staged ? sm_lev + (v1 - v0) : w.rs_elev + e0, staged ? sm_lev : w.rs_nlev + v0,
+                     e0, v0};
+    for (int i = tid; i < v1 - v0; i += kRsEvThreads) L.nl[i] = 0;
+    for (int e = tid; e < e1 - e0; e += kRsEvThreads) L.el[e] = 0;
     __syncthreads();
     int n = 0;
-    for (int e = e0 + tid; e < e1; e += kRsEvThreads) n += rs_init_edge(w, e, w.logit[e], lo, hi, top);
+    for (int e = e0 + tid; e < e1; e += kRsEvThreads)
+      n += rs_init_edge(w, L, e, w.logit[e], lo, hi, top);
     __syncthreads();
     for (int k = K - 1; k >= 0; --k) {
       const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
-      for (int e = e0 + tid; e < e1; e += kRsEvThreads) rs_step_edge(w, e, ge_k, km1);
+      for (int e = e0 + tid; e < e1; e += kRsEvThreads) rs_step_edge(w, L, e, ge_k, km1);
       __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((tid & 31) == 0) wsum[tid >> 5] = n;
+    if ((tid & 31) == 0) wsum[warp] = n;
     __syncthreads();
     if (tid == 0) {
       int t = 0;
-      for (int q = 0; q < kRsEvThreads / 32; ++q) t += wsum[q];
+      for (int q = 0; q < kRsEvWarps; ++q) t += wsum[q];
       band_total += t;
       band_events += t > 0;
     }
-    __syncthreads();  // wsum is reused by the next event
+    // the event's rows per list, their offsets, then placement
+    rs_count_warp(L.el, e0, e1, K, wcnt);
+    rs_count_warp(L.nl, v0, v1, K, wcnt + K + 1);
+    __syncthreads();
+    if (tid < nv) {  // exclusive scan over the warps, the event's count per list
+      int run = 0;
+      for (int q = 0; q < kRsEvWarps; ++q) {
+        const int c = wcnt[tid][q];
+        wcnt[tid][q] = run;
+        run += c;
+      }
+      cnt_s[tid] = run;
+    }
+    __syncthreads();
+    if (warp == 0) rs_lookback(d, ev, nv, cnt_s, base_s, w.counters);
+    __syncthreads();
+    if (tid < nv)
+      for (int q = 0; q < kRsEvWarps; ++q) wcnt[tid][q] += base_s[tid];
+    __syncthreads();
+    rs_place_warp(L.el, e0, e1, K, w.rs_elist, w.e_cap, wcnt);
+    rs_place_warp(L.nl, v0, v1, K, w.rs_nlist, w.h_cap, wcnt + K + 1);
+    if (ev == b.n_events - 1 && tid <= K) {
+      // the totals of every list
+      w.rs_counts[2 * NL + tid] = base_s[tid] + cnt_s[tid];
+      w.rs_counts[5 * NL + tid] = base_s[K + 1 + tid] + cnt_s[K + 1 + tid];
+      if (tid == 0) {
+        w.counters[C_RERUN_EDGES] = base_s[0] + cnt_s[0];
+        w.counters[C_RERUN_HITS] = base_s[K + 1] + cnt_s[K + 1];
+      }
+    }
+    __syncthreads();  // shared counts and ticket_s are reused by the next event
   }
   if (tid == 0 && band_total) {
     atomicAdd(&w.counters[C_BAND], band_total);
@@ -105,184 +277,19 @@ __global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, float 
   }
 }
 
-// Row lists of all steps in one sweep: list t (t = 0 .. K, step k = t - 1)
-// holds the rows with level >= k in index order (so a step's kernels visit
-// rows in the batch's event order, as the full FP32 path does). Each block
-// takes one contiguous chunk of rows; counts per list by ballots, offsets by
-// one warp per list, placement in the same order (stable).
-struct SortSide {
-  const int8_t* lev;
-  int32_t* list;         // [K + 1][stride]
-  int64_t stride;
-  int32_t* blk_cnt;      // [K + 1][gridDim.x] rows per block, then block offsets
-  const int32_t* n_ptr;  // row count on the device (edges) or null
-  int n_fixed;
-  int32_t* cge;          // [K + 1]: rows of step k at [k + 1]
-  int counter;           // counters index receiving the encoder step's total
-};
-
-constexpr int kRsTile = 4 * kRsThreads;  // rows per block and iteration (4 per thread)
-
-// the block's chunk of rows, a multiple of kRsTile (so every 4-row group is
-// 4-byte aligned)
-__device__ __forceinline__ void chunk_of(int n, int& lo, int& hi) {
-  const int per = (((n + gridDim.x - 1) / gridDim.x) + kRsTile - 1) / kRsTile * kRsTile;
-  lo = min(n, int(blockIdx.x) * per);
-  hi = min(n, lo + per);
-}
-
-__device__ __forceinline__ int side_rows(const SortSide& sd) {
-  return sd.n_ptr ? min(*sd.n_ptr, sd.n_fixed) : sd.n_fixed;
-}
-
-// shifted levels of the 4 rows i0 .. i0+3 (0 past hi)
-__device__ __forceinline__ void levels4(const int8_t* lev, int i0, int hi, int (&l)[4]) {
-  if (i0 + 3 < hi) {
-    const char4 v = *reinterpret_cast<const char4*>(lev + i0);
-    l[0] = v.x;
-    l[1] = v.y;
-    l[2] = v.z;
-    l[3] = v.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) l[j] = i0 + j < hi ? lev[i0 + j] : 0;
-  }
-}
-
-// rows of this block's chunk in each list (level >= t - 1, i.e. shifted >= t + 1)
-__global__ void __launch_bounds__(kRsThreads) k_rs_count(SortSide se, SortSide sn, int K,
-                                                         const int32_t* counters) {
-  if (input_bad(counters)) return;
-  const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  __shared__ int cnt[kRsWarps][kMaxIters + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int lo, hi;
-  chunk_of(side_rows(sd), lo, hi);
-  int c[kMaxIters + 1];
-#pragma unroll
-  for (int t = 0; t <= kMaxIters; ++t) c[t] = 0;
-  for (int base = lo; base < hi; base += kRsTile) {
-    int l[4];
-    levels4(sd.lev, base + 4 * threadIdx.x, hi, l);
-#pragma unroll
-    for (int t = 0; t <= kMaxIters; ++t)
-      if (t <= K) c[t] += (l[0] >= t + 1) + (l[1] >= t + 1) + (l[2] >= t + 1) + (l[3] >= t + 1);
-  }
-#pragma unroll
-  for (int t = 0; t <= kMaxIters; ++t) {
-    if (t > K) break;
-    int v = c[t];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) cnt[warp][t] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x <= K) {
-    int tot = 0;
-    for (int q = 0; q < kRsWarps; ++q) tot += cnt[q][threadIdx.x];
-    sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x] = tot;
-  }
-}
-
-// exclusive offsets per (list, block); warp t of block `side` scans list t;
-// the totals are the steps' row counts, list 0's also the re-score total
-__global__ void k_rs_offsets(SortSide se, SortSide sn, int nblk, int K, int32_t* counters) {
-  if (input_bad(counters)) return;
-  const SortSide& sd = blockIdx.x == 0 ? se : sn;
-  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
-  if (t > K) return;
-  int32_t* row = sd.blk_cnt + t * nblk;
-  int run = 0;
-  for (int b0 = 0; b0 < nblk; b0 += 32) {
-    const int v = b0 + lane < nblk ? row[b0 + lane] : 0;
-    int x = v;
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += y;
-    }
-    if (b0 + lane < nblk) row[b0 + lane] = run + x - v;
-    run += __shfl_sync(0xffffffffu, x, 31);
-  }
-  if (lane == 0) {
-    sd.cge[t] = run;
-    if (t == 0) counters[sd.counter] = run;
-  }
-}
-
-// placement in the same chunk order as the count (stable): per tile and list,
-// each thread's rows ranked by a warp scan and the block's warp totals
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(SortSide se, SortSide sn, int K,
-                                                           const int32_t* counters) {
-  if (input_bad(counters)) return;
-  const SortSide& sd = blockIdx.y == 0 ? se : sn;
-  __shared__ int wtot[2][kMaxIters + 1][kRsWarps];
-  __shared__ int run[kMaxIters + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x <= K) run[threadIdx.x] = sd.blk_cnt[threadIdx.x * gridDim.x + blockIdx.x];
-  int lo, hi;
-  chunk_of(side_rows(sd), lo, hi);
-  int par = 0;
-  for (int base = lo; base < hi; base += kRsTile, par ^= 1) {
-    const int i0 = base + 4 * threadIdx.x;
-    int l[4];
-    levels4(sd.lev, i0, hi, l);
-    int xs[kMaxIters + 1];
-#pragma unroll
-    for (int t = 0; t <= kMaxIters; ++t) {
-      if (t > K) break;
-      const int c = (l[0] >= t + 1) + (l[1] >= t + 1) + (l[2] >= t + 1) + (l[3] >= t + 1);
-      int x = c;  // inclusive scan over the warp
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-      }
-      if (lane == 31) wtot[par][t][warp] = x;
-      xs[t] = x - c;
-    }
-    __syncthreads();  // wtot[par] complete; run[] from the previous tile visible
-#pragma unroll
-    for (int t = 0; t <= kMaxIters; ++t) {
-      if (t > K) break;
-      int off = run[t] + xs[t];
-      for (int q = 0; q < warp; ++q) off += wtot[par][t][q];
-      int32_t* list = sd.list + t * sd.stride;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (l[j] >= t + 1) list[off++] = i0 + j;
-    }
-    __syncthreads();  // every thread has read run[] of this tile
-    if (threadIdx.x <= K) {
-      int tot = 0;
-      for (int q = 0; q < kRsWarps; ++q) tot += wtot[par][threadIdx.x][q];
-      run[threadIdx.x] += tot;
-    }
-  }
-}
-
 }  // namespace
-
-int rescore_sort_blocks() { return std::min(device_sms() * 4, kRsMaxBlocks); }
 
 int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_hi, int K,
                         cudaStream_t s) {
   const int NL = kMaxIters + 2;
   cudaMemsetAsync(w.rs_counts, 0, sizeof(int32_t) * 6 * NL, s);
   if (b.n_events <= 0) return 0;
-  k_rs_event<<<std::min(b.n_events, device_sms() * 4), kRsEvThreads, 0, s>>>(b, w, band_lo,
-                                                                           band_hi, K);
+  cudaMemsetAsync(w.rs_desc, 0, sizeof(int32_t) * b.n_events, s);
+  const int nv = 2 * (K + 1);
+  const RsDesc d{w.rs_desc, w.rs_desc + b.n_events, w.rs_desc + b.n_events + size_t(b.n_events) * nv};
+  k_rs_event<<<std::min(b.n_events, device_sms() * 4), kRsEvThreads, kRsSmemBytes, s>>>(
+      b, w, d, band_lo, band_hi, K);
   return 1;
-}
-
-int launch_rescore_lists(const Batch& b, const Ws& w, int K, cudaStream_t s) {
-  const int NL = kMaxIters + 2;
-  const int nblk = rescore_sort_blocks();
-  SortSide se{w.rs_elev, w.rs_elist, w.e_cap, w.rs_blk, w.counters + C_EDGES, int(w.e_cap),
-              w.rs_counts + 2 * NL, C_RERUN_EDGES};
-  SortSide sn{w.rs_nlev, w.rs_nlist, w.h_cap, w.rs_blk + (kMaxIters + 1) * kRsMaxBlocks, nullptr,
-              b.n_hits, w.rs_counts + 5 * NL, C_RERUN_HITS};
-  k_rs_count<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
-  k_rs_offsets<<<2, 32 * (K + 1), 0, s>>>(se, sn, nblk, K, w.counters);
-  k_rs_scatter<<<dim3(nblk, 2), kRsThreads, 0, s>>>(se, sn, K, w.counters);
-  return 3;
 }
 
 }  // namespace gnntrk

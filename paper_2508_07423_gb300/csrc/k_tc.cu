@@ -2152,8 +2152,8 @@ int tc_get_edge_form() { return g_edge_form.load(std::memory_order_relaxed); }
 void tc_make_maps(TcModel& m, const Ws& w, int h) {
   m.maps = false;
   if (h != 32 || w.estate16 == nullptr || w.hstate16 == nullptr) return;
-  // the driver's encoder, looked up through the runtime (the library does not
-  // link the driver library, so it loads on machines without a GPU driver)
+  // the CUDA driver API encoder, looked up through the runtime (the library does not
+  // link libcuda, so it loads on machines without a GPU driver)
   static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
