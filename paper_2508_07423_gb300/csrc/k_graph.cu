@@ -272,6 +272,44 @@ __device__ void fill_capped(const Ws& w, const Cand& cd, const float (&qe)[D], i
   }
 }
 
+// The k_max edges of a hit over k_max as its mask (the same selection as
+// fill_capped), rewritten by its warp: mrow[k] bit b is candidate
+// cA + 32 k + b, candidates [c0, c1).
+template <int D, class Cand>
+__device__ void select_capped(const Cand& cd, const float (&qe)[D], int c0, int c1, int cA,
+                              float r2, int k_max, uint32_t* mrow) {
+  const int lane = threadIdx.x & 31;
+  const int nc = c1 - c0;
+  unsigned lo = 0, hi = __float_as_uint(r2);
+  for (int it = 0; it < 40 && lo < hi; ++it) {
+    const unsigned mid = lo + (hi - lo) / 2;
+    if (count_below<D>(cd, qe, c0, nc, r2, mid, true) >= k_max)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const unsigned T = lo;
+  const int need_eq = k_max - count_below<D>(cd, qe, c0, nc, r2, T, false);
+  int eq_seen = 0;
+  for (int k = 0; cA + 32 * k < c1; ++k) {
+    const int c = cA + 32 * k + lane;
+    bool keep = false, eq = false;
+    if (c >= c0 && c < c1) {
+      const float s = cd.d2(qe, c);
+      if (s < r2) {
+        const unsigned key = __float_as_uint(s);
+        eq = key == T;
+        keep = key < T;
+      }
+    }
+    const unsigned eqm = __ballot_sync(kFull, eq);
+    if (eq && eq_seen + __popc(eqm & ((1u << lane) - 1u)) < need_eq) keep = true;
+    eq_seen += __popc(eqm);
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (lane == 0) mrow[k] = m;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // rough graph and in-edge index, one block per event
 // ---------------------------------------------------------------------------
@@ -306,15 +344,20 @@ constexpr unsigned long long kDescInc = 2ull << 62;  // edges up to and includin
 constexpr unsigned long long kDescVal = (1ull << 62) - 1;
 constexpr int kLookbackSpins = 1 << 22;  // x >= 100 ns sleeps: a bound of about half a second
 
-// Warp 0 of the block: publishes the event's edge count `agg` and returns the
-// edges of all earlier events, walking back over windows of 32 predecessors
-// until one has published its inclusive prefix. A wait that runs out sets
-// ST_TIMEOUT and returns what was summed.
-__device__ long long graph_lookback(unsigned long long* desc, int ev, long long agg,
-                                    int32_t* counters) {
+// The look-back walks back over windows of 32 predecessors until one has
+// published its inclusive prefix, summing the counts of the others. A wait
+// that runs out sets ST_TIMEOUT and returns what was summed (the event then
+// publishes no inclusive prefix; later events sum its count instead).
+// (lane 0) publishes the event's edge count: event 0's is its inclusive prefix
+__device__ __forceinline__ void graph_publish(unsigned long long* desc, int ev, long long agg) {
+  atomicExch(desc + ev, (ev == 0 ? +kDescInc : +kDescAgg) | static_cast<unsigned long long>(agg));
+}
+
+// Warp 0, after graph_publish: the edges of all earlier events, then the
+// event's inclusive prefix published.
+__device__ long long graph_wait(unsigned long long* desc, int ev, long long agg,
+                                int32_t* counters) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0)
-    atomicExch(desc + ev, (ev == 0 ? +kDescInc : +kDescAgg) | static_cast<unsigned long long>(agg));
   long long excl = 0;
   int spins = 0;
   for (int top = ev - 1; top >= 0; top -= 32) {
@@ -340,6 +383,14 @@ __device__ long long graph_lookback(unsigned long long* desc, int ev, long long 
   if (lane == 0 && ev > 0)
     atomicExch(desc + ev, kDescInc | static_cast<unsigned long long>(excl + agg));
   return excl;
+}
+
+// warp 0: publish, then wait
+__device__ __forceinline__ long long graph_lookback(unsigned long long* desc, int ev, long long agg,
+                                                    int32_t* counters) {
+  if ((threadIdx.x & 31) == 0) graph_publish(desc, ev, agg);
+  __syncwarp();
+  return graph_wait(desc, ev, agg, counters);
 }
 
 // exclusive scan of min(in[i], clamp) over i < n into out (both may be
@@ -432,7 +483,7 @@ __device__ void graph_degrees(const Cand& cd, const int* po_s, const int* chunk_
 // 3. fill: one lane per query hit writes its edges in ascending candidate
 // order at out = base + off[q] (walking its mask bits, or testing every
 // candidate again when there are no masks); a hit over k_max is filled by its
-// warp (fill_capped).
+// warp (fill_capped), unless deg is null (masks already selected).
 template <int D, class Cand>
 __device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const int* chunk_s, int P,
                            int n_items, float r2, int k_max, const int32_t* deg,
@@ -443,7 +494,8 @@ __device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const i
     const GraphItem it = graph_item(po_s, chunk_s, P, t);
     const int q = it.q0 + lane;
     const bool valid = q < it.q1;
-    const int cnt = valid ? deg[q] : 0;
+    // (deg null: the masks hold exactly the hit's edges, capped ones included)
+    const int cnt = !valid ? 0 : (deg != nullptr ? deg[q] : 1);
     if (valid && cnt > 0 && cnt <= k_max) {
       float qe[D];
       cd.row(q, qe);
@@ -485,6 +537,144 @@ __device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const i
   }
 }
 
+// In-edge index of an event from its candidate masks, before the event's
+// base is known: in-degrees C, starts St (exclusive scan), then each edge's
+// event-local id (off[q] + j for the j-th edge of hit q, i.e. its position in
+// the event's CSR) placed at L[C[c]++] of its target c.
+__device__ void csc_from_masks(const int* po_s, const int* chunk_s, int P, int n_items, int n,
+                               const int32_t* off, const uint32_t* mask, int mw, int32_t* C,
+                               int32_t* St, int32_t* L, int* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
+  __syncthreads();
+  for (int t = warp; t < n_items; t += kGraphWarps) {
+    const GraphItem it = graph_item(po_s, chunk_s, P, t);
+    const int q = it.q0 + lane;
+    if (q >= it.q1) continue;
+    const int cA = it.c0 & ~1;
+    const int nw = (it.c1 - cA + 31) / 32;
+    for (int k = 0; k < nw; ++k) {
+      unsigned m = mask[q * mw + k];
+      while (m) {
+        atomicAdd(&C[cA + 32 * k + __ffs(m) - 1], 1);
+        m &= m - 1;
+      }
+    }
+  }
+  __syncthreads();
+  block_scan(C, St, n, 0x7fffffff, wsum);
+  for (int i = tid; i < n; i += kGraphThreads) C[i] = St[i];  // cursors
+  __syncthreads();
+  for (int t = warp; t < n_items; t += kGraphWarps) {
+    const GraphItem it = graph_item(po_s, chunk_s, P, t);
+    const int q = it.q0 + lane;
+    if (q >= it.q1) continue;
+    const int cA = it.c0 & ~1;
+    const int nw = (it.c1 - cA + 31) / 32;
+    int le = off[q];
+    for (int k = 0; k < nw; ++k) {
+      unsigned m = mask[q * mw + k];
+      while (m) {
+        L[atomicAdd(&C[cA + 32 * k + __ffs(m) - 1], 1)] = le++;
+        m &= m - 1;
+      }
+    }
+  }
+  __syncthreads();  // C[c] is now the end of target c's list
+}
+
+// in_ptr and in_edge of the event from csc_from_masks once its base is known
+// (base + total within the edge capacity; the fill has written col): each
+// list ranked into ascending edge id (an entry's place is the number of
+// smaller entries in its list).
+__device__ void csc_write(const Ws& w, int n, int v0, int v1, long long base, int total,
+                          const int32_t* C, const int32_t* St, const int32_t* L) {
+  const int tid = threadIdx.x;
+  const int b = int(base);
+  for (int i = tid; i < n; i += kGraphThreads) w.in_ptr[v0 + i] = b + St[i];
+  if (tid == 0) w.in_ptr[v1] = b + total;  // the next event writes the same value
+  for (int k = tid; k < total; k += kGraphThreads) {
+    const int le = L[k];
+    const int t = w.col[b + le] - v0;
+    const int lo = St[t], hi = C[t];
+    int rank = 0;
+    for (int m = lo; m < hi; ++m) rank += L[m] < le;
+    w.in_edge[b + lo + rank] = b + le;
+  }
+}
+
+// In-edge index of the event's stored edges [e0, e1) (read back from col):
+// in-degrees by shared-memory atomics, a block scan, placement by cursors,
+// then each target's list in ascending edge id. Lists in shared memory when
+// they fit (ranked into in_edge), else in the event's slice of in_edge
+// (sorted in place); counts in in_cnt for events of more hits than fit.
+__device__ void csc_general(const Ws& w, int n, int v0, int v1, int e0, int e1, int32_t* sm_i,
+                            int* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool c_smem = n <= kGraphSmemInts;
+  int32_t* C = c_smem ? sm_i : w.in_cnt + v0;
+  for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
+  __syncthreads();
+  for (int e = e0 + tid; e < e1; e += kGraphThreads) atomicAdd(&C[w.col[e] - v0], 1);
+  __syncthreads();
+  {
+    const int per = (n + kGraphThreads - 1) / kGraphThreads;
+    const int a = min(n, tid * per), z = min(n, a + per);
+    int sum = 0;
+    for (int i = a; i < z; ++i) sum += C[i];
+    int x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < warp; ++k) before += wsum[k];
+    int run = before + x - sum;
+    for (int i = a; i < z; ++i) {
+      const int c = C[i];
+      C[i] = run;  // cursor
+      w.in_ptr[v0 + i] = e0 + run;
+      run += c;
+    }
+    if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
+  }
+  __syncthreads();
+  const bool l_smem = c_smem && int64_t(n) + (e1 - e0) <= kGraphSmemInts;
+  int32_t* L = l_smem ? sm_i + n : w.in_edge + e0;  // L[k]: list position e0 + k
+  for (int e = e0 + tid; e < e1; e += kGraphThreads) {
+    const int k = atomicAdd(&C[w.col[e] - v0], 1);
+    L[k] = e;
+  }
+  __syncthreads();
+  // C[i] is now the end of target i's list (event-local position)
+  if (l_smem) {
+    for (int k = tid; k < e1 - e0; k += kGraphThreads) {
+      const int e = L[k];
+      const int t = w.col[e] - v0;
+      const int lo = w.in_ptr[v0 + t] - e0, hi = C[t];
+      int rank = 0;
+      for (int m = lo; m < hi; ++m) rank += L[m] < e;
+      w.in_edge[e0 + lo + rank] = e;
+    }
+  } else {
+    for (int i = tid; i < n; i += kGraphThreads) {
+      const int lo = w.in_ptr[v0 + i] - e0, hi = C[i];
+      for (int j = lo + 1; j < hi; ++j) {
+        const int key = L[j];
+        int k = j - 1;
+        while (k >= lo && L[k] > key) {
+          L[k + 1] = L[k];
+          --k;
+        }
+        L[k + 1] = key;
+      }
+    }
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_event(Batch b, Ws w, GraphParams g) {
   extern __shared__ __align__(16) float sm_graph[];
@@ -520,31 +710,37 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
       chunk_s[P > 1 ? P - 1 : 0] = run;
       mw_s = words;
     }
-    // rows of this event, event-local index: the embeddings (staged
-    // transposed and negated when they fit: t[d * ns + i] = -e_i[d]),
-    // degrees, offsets and, when they fit too, the candidate masks
+    __syncthreads();  // chunk_s and mw_s (which sets the layout below) visible
+    // rows of this event, event-local index, in shared memory when they fit:
+    //   [off n][mask n*mw][deg n][t D*ns]
+    // off: CSR offsets; mask: in-radius candidates per hit (when they fit too);
+    // t: the embeddings transposed and negated, t[d * ns + i] = -e_i[d]
+    // (8-byte aligned, for the candidate pairs). Else global scratch.
     const int ns = (n + 2) & ~1;  // even, with a pad column read by the last pair
-    const bool staged = int64_t(D) * ns + 2 * int64_t(n) <= kGraphSmemInts;
-    int32_t* deg = staged ? sm_i + D * ns : w.deg + v0;
-    int32_t* off = staged ? sm_i + D * ns + n : w.in_cnt + v0;
+    const int64_t rows_ints = int64_t(D) * ns + 3;
+    const bool staged = rows_ints + 2 * int64_t(n) <= kGraphSmemInts;
+    const int mw = staged && rows_ints + int64_t(n) * (2 + mw_s) <= kGraphSmemInts ? mw_s : 0;
+    int32_t* off = staged ? sm_i : w.in_cnt + v0;
+    uint32_t* mask = reinterpret_cast<uint32_t*>(sm_i + n);
+    int32_t* deg = staged ? sm_i + n * (1 + mw) : w.deg + v0;
+    float* tT = sm_graph + ((n * (2 + mw) + 3) & ~3);
     if (staged) {
       for (int k = tid; k < n * D; k += kGraphThreads) {
         const int i = k / D, d = k - i * D;
-        sm_graph[d * ns + i] = -w.emb[size_t(v0) * D + k];
+        tT[d * ns + i] = -w.emb[size_t(v0) * D + k];
       }
       for (int k = tid; k < D * (ns - n); k += kGraphThreads) {
         const int d = k / (ns - n);
-        sm_graph[d * ns + n + (k - d * (ns - n))] = 0.0f;
+        tT[d * ns + n + (k - d * (ns - n))] = 0.0f;
       }
     }
     __syncthreads();
     const int n_items = chunk_s[P > 1 ? P - 1 : 0];
-    const int mw = staged && int64_t(D) * ns + int64_t(n) * (2 + mw_s) <= kGraphSmemInts ? mw_s : 0;
-    uint32_t* mask = reinterpret_cast<uint32_t*>(sm_i + D * ns + 2 * n);
-    const CandNegT<D> cst{sm_graph, ns};
+    const CandNegT<D> cst{tT, ns};
     const CandRows<D> cgl{w.emb + size_t(v0) * D};
 
-    // 1. degrees (uncapped)
+    // 1. degrees (uncapped); with masks, a hit over k_max keeps only its
+    //    k_max selected candidates in its mask
     if (staged)
       graph_degrees<D, true>(cst, po_s, chunk_s, P, n_items, r2, deg, mask, mw);
     else
@@ -552,10 +748,39 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
     if (P >= 1)
       for (int q = po_s[P - 1] + tid; q < n; q += kGraphThreads) deg[q] = 0;  // no candidates
     __syncthreads();
+    if (mw > 0) {
+      for (int t = warp; t < n_items; t += kGraphWarps) {
+        const GraphItem it = graph_item(po_s, chunk_s, P, t);
+        unsigned capped = __ballot_sync(kFull, it.q0 + lane < it.q1 && deg[it.q0 + lane] > k_max);
+        while (capped) {
+          const int qq = it.q0 + __ffs(capped) - 1;
+          capped &= capped - 1;
+          float qe[D];
+          cst.row(qq, qe);
+          select_capped<D>(cst, qe, it.c0, it.c1, it.c0 & ~1, r2, k_max, mask + qq * mw);
+        }
+      }
+      __syncthreads();
+    }
 
-    // 2. offsets: event-local exclusive scan, then the event's global base
+    // 2. offsets: event-local exclusive scan of min(deg, k_max)
     const int total = block_scan(deg, off, n, k_max, wsum);
-    if (warp == 0) {
+    // With masks, and room for the in-edge lists where deg and t were, the
+    // lists are built (event-local edge ids) between publishing the event's
+    // count and waiting for the earlier events' counts.
+    const int cs = n * (1 + mw);
+    const bool early = mw > 0 && int64_t(cs) + 2 * int64_t(n) + total <= kGraphSmemInts;
+    int32_t* cC = sm_i + cs;
+    int32_t* cSt = cC + n;
+    int32_t* cL = cSt + n;
+    if (early) {
+      if (tid == 0) graph_publish(w.graph_desc, ev, total);
+      csc_from_masks(po_s, chunk_s, P, n_items, n, off, mask, mw, cC, cSt, cL, wsum);
+      if (warp == 0) {
+        const long long ex = graph_wait(w.graph_desc, ev, total, w.counters);
+        if (lane == 0) base_s = ex;
+      }
+    } else if (warp == 0) {
       const long long ex = graph_lookback(w.graph_desc, ev, total, w.counters);
       if (lane == 0) base_s = ex;
     }
@@ -569,72 +794,23 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
       if (all > w.e_cap || all > 0x7fffffffLL) set_status(w.counters, ST_CAPACITY);
     }
 
-    // 3. fill
-    if (staged)
+    // 3. fill (with the early lists, t is gone: d^2 from the global rows)
+    if (early)
+      graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, nullptr, off, mask, mw, base, v0);
+    else if (staged)
       graph_fill<D>(w, cst, po_s, chunk_s, P, n_items, r2, k_max, deg, off, mask, mw, base, v0);
     else
       graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, deg, off, nullptr, 0, base, v0);
-    __syncthreads();  // edges written; the shared rows are free
+    __syncthreads();  // edges written
 
     // 4. in-edge index of the event's edges [e0, e1)
-    const int e0 = int(base < w.e_cap ? base : w.e_cap);
-    const int e1 = int(base + total < w.e_cap ? base + total : w.e_cap);
-    const bool c_smem = n <= kGraphSmemInts;
-    int32_t* C = c_smem ? sm_i : w.in_cnt + v0;
-    for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
-    __syncthreads();
-    for (int e = e0 + tid; e < e1; e += kGraphThreads) atomicAdd(&C[w.col[e] - v0], 1);
-    __syncthreads();
-    {
-      const int per = (n + kGraphThreads - 1) / kGraphThreads;
-      const int a = min(n, tid * per), z = min(n, a + per);
-      int sum = 0;
-      for (int i = a; i < z; ++i) sum += C[i];
-      int x = sum;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-      }
-      if (lane == 31) wsum[warp] = x;
-      __syncthreads();
-      int before = 0;
-      for (int k = 0; k < warp; ++k) before += wsum[k];
-      int run = before + x - sum;
-      for (int i = a; i < z; ++i) {
-        const int c = C[i];
-        C[i] = run;  // cursor
-        w.in_ptr[v0 + i] = e0 + run;
-        run += c;
-      }
-      if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
+    if (early && base + total <= w.e_cap) {
+      csc_write(w, n, v0, v1, base, total, cC, cSt, cL);
+    } else {
+      const int e0 = int(base < w.e_cap ? base : w.e_cap);
+      const int e1 = int(base + total < w.e_cap ? base + total : w.e_cap);
+      csc_general(w, n, v0, v1, e0, e1, sm_i, wsum);
     }
-    __syncthreads();
-    // placement and per-target sort in shared memory when the event's list
-    // fits (copied out coalesced), else in its slice of in_edge
-    const bool l_smem = c_smem && int64_t(n) + (e1 - e0) <= kGraphSmemInts;
-    int32_t* L = l_smem ? sm_i + n : w.in_edge + e0;  // L[k]: list position e0 + k
-    for (int e = e0 + tid; e < e1; e += kGraphThreads) {
-      const int k = atomicAdd(&C[w.col[e] - v0], 1);
-      L[k] = e;
-    }
-    __syncthreads();
-    // C[i] is now the end of target i's list (event-local position)
-    for (int i = tid; i < n; i += kGraphThreads) {
-      const int lo = w.in_ptr[v0 + i] - e0, hi = C[i];
-      for (int j = lo + 1; j < hi; ++j) {
-        const int key = L[j];
-        int k = j - 1;
-        while (k >= lo && L[k] > key) {
-          L[k + 1] = L[k];
-          --k;
-        }
-        L[k + 1] = key;
-      }
-    }
-    __syncthreads();
-    if (l_smem)
-      for (int k = tid; k < e1 - e0; k += kGraphThreads) w.in_edge[e0 + k] = L[k];
     __syncthreads();  // shared memory and ticket_s are reused by the next event
   }
 }
