@@ -480,49 +480,66 @@ __device__ void graph_degrees(const Cand& cd, const int* po_s, const int* chunk_
   }
 }
 
-// 3. fill: one lane per query hit writes its edges in ascending candidate
-// order at out = base + off[q] (walking its mask bits, or testing every
-// candidate again when there are no masks); a hit over k_max is filled by its
-// warp (fill_capped), unless deg is null (masks already selected).
+// 3. fill from the candidate masks (which hold exactly each hit's edges,
+// capped hits reduced to their selection): one lane per query hit walks the
+// set bits of its mask in ascending order, recomputes d^2 there from the
+// staged rows and writes its edges at base + off[q].
+template <int D>
+__device__ void graph_fill_masks(const Ws& w, const CandNegT<D>& cd, const int* po_s,
+                                 const int* chunk_s, int P, int n_items, const int32_t* off,
+                                 const uint32_t* mask, int mw, long long base, int v0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t < n_items; t += kGraphWarps) {
+    const GraphItem it = graph_item(po_s, chunk_s, P, t);
+    const int q = it.q0 + lane;
+    if (q >= it.q1) continue;
+    float qe[D];
+    cd.row(q, qe);
+    int64_t e = base + off[q];
+    const int cA = it.c0 & ~1;
+    const int nw = (it.c1 - cA + 31) / 32;
+    for (int k = 0; k < nw; ++k) {
+      unsigned m = mask[q * mw + k];
+      while (m) {
+        const int c = cA + 32 * k + __ffs(m) - 1;
+        m &= m - 1;
+        if (e < w.e_cap) {
+          w.col[e] = v0 + c;
+          w.src[e] = v0 + q;
+          w.d2[e] = cd.d2(qe, c);
+        }
+        ++e;
+      }
+    }
+  }
+}
+
+// 3. fill without masks: one lane per query hit tests its candidates again in
+// ascending order and writes its edges at base + off[q]; a hit over k_max is
+// filled by its warp (fill_capped).
 template <int D, class Cand>
 __device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const int* chunk_s, int P,
                            int n_items, float r2, int k_max, const int32_t* deg,
-                           const int32_t* off, const uint32_t* mask, int mw, long long base,
-                           int v0) {
+                           const int32_t* off, long long base, int v0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = warp; t < n_items; t += kGraphWarps) {
     const GraphItem it = graph_item(po_s, chunk_s, P, t);
     const int q = it.q0 + lane;
     const bool valid = q < it.q1;
-    // (deg null: the masks hold exactly the hit's edges, capped ones included)
-    const int cnt = !valid ? 0 : (deg != nullptr ? deg[q] : 1);
+    const int cnt = valid ? deg[q] : 0;
     if (valid && cnt > 0 && cnt <= k_max) {
       float qe[D];
       cd.row(q, qe);
       int64_t e = base + off[q];
-      auto put = [&](int c, float s) {
-        if (e < w.e_cap) {
-          w.col[e] = v0 + c;
-          w.src[e] = v0 + q;
-          w.d2[e] = s;
-        }
-        ++e;
-      };
-      if (mw > 0) {
-        const int cA = it.c0 & ~1;
-        const int nw = (it.c1 - cA + 31) / 32;
-        for (int k = 0; k < nw; ++k) {
-          unsigned m = mask[q * mw + k];
-          while (m) {
-            const int c = cA + 32 * k + __ffs(m) - 1;
-            m &= m - 1;
-            put(c, cd.d2(qe, c));
+      for (int c = it.c0; c < it.c1; ++c) {
+        const float s = cd.d2(qe, c);
+        if (s < r2) {
+          if (e < w.e_cap) {
+            w.col[e] = v0 + c;
+            w.src[e] = v0 + q;
+            w.d2[e] = s;
           }
-        }
-      } else {
-        for (int c = it.c0; c < it.c1; ++c) {
-          const float s = cd.d2(qe, c);
-          if (s < r2) put(c, s);
+          ++e;
         }
       }
     }
@@ -537,87 +554,36 @@ __device__ void graph_fill(const Ws& w, const Cand& cd, const int* po_s, const i
   }
 }
 
-// In-edge index of an event from its candidate masks, before the event's
-// base is known: in-degrees C, starts St (exclusive scan), then each edge's
-// event-local id (off[q] + j for the j-th edge of hit q, i.e. its position in
-// the event's CSR) placed at L[C[c]++] of its target c.
-__device__ void csc_from_masks(const int* po_s, const int* chunk_s, int P, int n_items, int n,
-                               const int32_t* off, const uint32_t* mask, int mw, int32_t* C,
-                               int32_t* St, int32_t* L, int* wsum) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
-  __syncthreads();
-  for (int t = warp; t < n_items; t += kGraphWarps) {
-    const GraphItem it = graph_item(po_s, chunk_s, P, t);
-    const int q = it.q0 + lane;
-    if (q >= it.q1) continue;
-    const int cA = it.c0 & ~1;
-    const int nw = (it.c1 - cA + 31) / 32;
-    for (int k = 0; k < nw; ++k) {
-      unsigned m = mask[q * mw + k];
-      while (m) {
-        atomicAdd(&C[cA + 32 * k + __ffs(m) - 1], 1);
-        m &= m - 1;
-      }
-    }
-  }
-  __syncthreads();
-  block_scan(C, St, n, 0x7fffffff, wsum);
-  for (int i = tid; i < n; i += kGraphThreads) C[i] = St[i];  // cursors
-  __syncthreads();
-  for (int t = warp; t < n_items; t += kGraphWarps) {
-    const GraphItem it = graph_item(po_s, chunk_s, P, t);
-    const int q = it.q0 + lane;
-    if (q >= it.q1) continue;
-    const int cA = it.c0 & ~1;
-    const int nw = (it.c1 - cA + 31) / 32;
-    int le = off[q];
-    for (int k = 0; k < nw; ++k) {
-      unsigned m = mask[q * mw + k];
-      while (m) {
-        L[atomicAdd(&C[cA + 32 * k + __ffs(m) - 1], 1)] = le++;
-        m &= m - 1;
-      }
-    }
-  }
-  __syncthreads();  // C[c] is now the end of target c's list
-}
-
-// in_ptr and in_edge of the event from csc_from_masks once its base is known
-// (base + total within the edge capacity; the fill has written col): each
-// list ranked into ascending edge id (an entry's place is the number of
-// smaller entries in its list).
-__device__ void csc_write(const Ws& w, int n, int v0, int v1, long long base, int total,
-                          const int32_t* C, const int32_t* St, const int32_t* L) {
-  const int tid = threadIdx.x;
-  const int b = int(base);
-  for (int i = tid; i < n; i += kGraphThreads) w.in_ptr[v0 + i] = b + St[i];
-  if (tid == 0) w.in_ptr[v1] = b + total;  // the next event writes the same value
-  for (int k = tid; k < total; k += kGraphThreads) {
-    const int le = L[k];
-    const int t = w.col[b + le] - v0;
-    const int lo = St[t], hi = C[t];
-    int rank = 0;
-    for (int m = lo; m < hi; ++m) rank += L[m] < le;
-    w.in_edge[b + lo + rank] = b + le;
-  }
-}
-
 // In-edge index of the event's stored edges [e0, e1) (read back from col):
 // in-degrees by shared-memory atomics, a block scan, placement by cursors,
-// then each target's list in ascending edge id. Lists in shared memory when
-// they fit (ranked into in_edge), else in the event's slice of in_edge
-// (sorted in place); counts in in_cnt for events of more hits than fit.
+// then each target's list in ascending edge id. When the counts, list starts,
+// lists and list targets all fit in shared memory, each list is ranked into
+// in_edge (an entry's place is the number of smaller entries in its list);
+// else the lists are placed in the event's slice of in_edge and sorted there
+// (counts in in_cnt for events of more hits than fit).
 __device__ void csc_general(const Ws& w, int n, int v0, int v1, int e0, int e1, int32_t* sm_i,
                             int* wsum) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  const int ne = e1 - e0;
+  const bool full = 2 * int64_t(n) + 2 * int64_t(ne) <= kGraphSmemInts;
   const bool c_smem = n <= kGraphSmemInts;
   int32_t* C = c_smem ? sm_i : w.in_cnt + v0;
+  int32_t* St = sm_i + n;               // (full only) list starts, event-local
+  int32_t* L = full ? sm_i + 2 * n : w.in_edge + e0;
+  int32_t* Tg = sm_i + 2 * n + ne;      // (full only) target of each list entry
   for (int i = tid; i < n; i += kGraphThreads) C[i] = 0;
   __syncthreads();
   for (int e = e0 + tid; e < e1; e += kGraphThreads) atomicAdd(&C[w.col[e] - v0], 1);
   __syncthreads();
-  {
+  if (full) {
+    block_scan(C, St, n, 0x7fffffff, wsum);
+    for (int i = tid; i < n; i += kGraphThreads) {
+      C[i] = St[i];  // cursor
+      w.in_ptr[v0 + i] = e0 + St[i];
+    }
+  } else {
+    // in place: C becomes the cursors, in_ptr the starts
+    const int lane = tid & 31, warp = tid >> 5;
     const int per = (n + kGraphThreads - 1) / kGraphThreads;
     const int a = min(n, tid * per), z = min(n, a + per);
     int sum = 0;
@@ -635,26 +601,25 @@ __device__ void csc_general(const Ws& w, int n, int v0, int v1, int e0, int e1, 
     int run = before + x - sum;
     for (int i = a; i < z; ++i) {
       const int c = C[i];
-      C[i] = run;  // cursor
+      C[i] = run;
       w.in_ptr[v0 + i] = e0 + run;
       run += c;
     }
-    if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
   }
+  if (tid == 0) w.in_ptr[v1] = e1;  // the next event writes the same value
   __syncthreads();
-  const bool l_smem = c_smem && int64_t(n) + (e1 - e0) <= kGraphSmemInts;
-  int32_t* L = l_smem ? sm_i + n : w.in_edge + e0;  // L[k]: list position e0 + k
   for (int e = e0 + tid; e < e1; e += kGraphThreads) {
-    const int k = atomicAdd(&C[w.col[e] - v0], 1);
+    const int t = w.col[e] - v0;
+    const int k = atomicAdd(&C[t], 1);
     L[k] = e;
+    if (full) Tg[k] = t;
   }
   __syncthreads();
   // C[i] is now the end of target i's list (event-local position)
-  if (l_smem) {
-    for (int k = tid; k < e1 - e0; k += kGraphThreads) {
-      const int e = L[k];
-      const int t = w.col[e] - v0;
-      const int lo = w.in_ptr[v0 + t] - e0, hi = C[t];
+  if (full) {
+    for (int k = tid; k < ne; k += kGraphThreads) {
+      const int e = L[k], t = Tg[k];
+      const int lo = St[t], hi = C[t];
       int rank = 0;
       for (int m = lo; m < hi; ++m) rank += L[m] < e;
       w.in_edge[e0 + lo + rank] = e;
@@ -740,7 +705,8 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
     const CandRows<D> cgl{w.emb + size_t(v0) * D};
 
     // 1. degrees (uncapped); with masks, a hit over k_max keeps only its
-    //    k_max selected candidates in its mask
+    //    k_max selected candidates in its mask (the masks then hold exactly
+    //    the edges)
     if (staged)
       graph_degrees<D, true>(cst, po_s, chunk_s, P, n_items, r2, deg, mask, mw);
     else
@@ -763,24 +729,10 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
       __syncthreads();
     }
 
-    // 2. offsets: event-local exclusive scan of min(deg, k_max)
+    // 2. offsets: event-local exclusive scan of min(deg, k_max), then the
+    //    event's base by the look-back
     const int total = block_scan(deg, off, n, k_max, wsum);
-    // With masks, and room for the in-edge lists where deg and t were, the
-    // lists are built (event-local edge ids) between publishing the event's
-    // count and waiting for the earlier events' counts.
-    const int cs = n * (1 + mw);
-    const bool early = mw > 0 && int64_t(cs) + 2 * int64_t(n) + total <= kGraphSmemInts;
-    int32_t* cC = sm_i + cs;
-    int32_t* cSt = cC + n;
-    int32_t* cL = cSt + n;
-    if (early) {
-      if (tid == 0) graph_publish(w.graph_desc, ev, total);
-      csc_from_masks(po_s, chunk_s, P, n_items, n, off, mask, mw, cC, cSt, cL, wsum);
-      if (warp == 0) {
-        const long long ex = graph_wait(w.graph_desc, ev, total, w.counters);
-        if (lane == 0) base_s = ex;
-      }
-    } else if (warp == 0) {
+    if (warp == 0) {
       const long long ex = graph_lookback(w.graph_desc, ev, total, w.counters);
       if (lane == 0) base_s = ex;
     }
@@ -794,23 +746,19 @@ __global__ void __launch_bounds__(kGraphThreads, kGraphBlocksPerSm) k_graph_even
       if (all > w.e_cap || all > 0x7fffffffLL) set_status(w.counters, ST_CAPACITY);
     }
 
-    // 3. fill (with the early lists, t is gone: d^2 from the global rows)
-    if (early)
-      graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, nullptr, off, mask, mw, base, v0);
+    // 3. fill
+    if (mw > 0)
+      graph_fill_masks<D>(w, cst, po_s, chunk_s, P, n_items, off, mask, mw, base, v0);
     else if (staged)
-      graph_fill<D>(w, cst, po_s, chunk_s, P, n_items, r2, k_max, deg, off, mask, mw, base, v0);
+      graph_fill<D>(w, cst, po_s, chunk_s, P, n_items, r2, k_max, deg, off, base, v0);
     else
-      graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, deg, off, nullptr, 0, base, v0);
-    __syncthreads();  // edges written
+      graph_fill<D>(w, cgl, po_s, chunk_s, P, n_items, r2, k_max, deg, off, base, v0);
+    __syncthreads();  // edges written; shared memory free
 
     // 4. in-edge index of the event's edges [e0, e1)
-    if (early && base + total <= w.e_cap) {
-      csc_write(w, n, v0, v1, base, total, cC, cSt, cL);
-    } else {
-      const int e0 = int(base < w.e_cap ? base : w.e_cap);
-      const int e1 = int(base + total < w.e_cap ? base + total : w.e_cap);
-      csc_general(w, n, v0, v1, e0, e1, sm_i, wsum);
-    }
+    const int e0 = int(base < w.e_cap ? base : w.e_cap);
+    const int e1 = int(base + total < w.e_cap ? base + total : w.e_cap);
+    csc_general(w, n, v0, v1, e0, e1, sm_i, wsum);
     __syncthreads();  // shared memory and ticket_s are reused by the next event
   }
 }
