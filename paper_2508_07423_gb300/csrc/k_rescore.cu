@@ -37,29 +37,29 @@ struct EvLevels {
   int e0, v0;
 };
 
-// E_{K-1} = band edges, V_{K-1} = their endpoints. Returns 1 for a band edge.
-__device__ __forceinline__ int rs_init_edge(const Ws& w, const EvLevels& L, int e, float l,
+// E_{K-1} = band edges, V_{K-1} = their endpoints (event-local a, c). Returns
+// 1 for a band edge.
+__device__ __forceinline__ int rs_init_edge(const EvLevels& L, int k, int a, int c, float l,
                                             float lo, float hi, int8_t top) {
   if (!(l > lo && l < hi)) return 0;
-  L.el[e - L.e0] = top;
-  L.nl[w.src[e] - L.v0] = top;  // every writer stores the same value
-  L.nl[w.col[e] - L.v0] = top;
+  L.el[k] = top;
+  L.nl[a] = top;  // every writer stores the same value
+  L.nl[c] = top;
   return 1;
 }
 
-// Step k of the backward walk for one edge: the edge joins E_{k-1} if an
-// endpoint is in V_k (level >= k + 2); an edge of E_{k-1} puts its endpoints
-// in V_{k-1}. Within one sweep a hit level only rises to k + 1, which no
-// other edge of the same sweep tests for, so the sweep does not depend on
-// the order of its edges.
-__device__ __forceinline__ void rs_step_edge(const Ws& w, const EvLevels& L, int e, int8_t ge_k,
+// Step k of the backward walk for one edge (event-local index ke, endpoints
+// a, c): the edge joins E_{k-1} if an endpoint is in V_k (level >= k + 2); an
+// edge of E_{k-1} puts its endpoints in V_{k-1}. Within one sweep a hit level
+// only rises to k + 1, which no other edge of the same sweep tests for, so
+// the sweep does not depend on the order of its edges.
+__device__ __forceinline__ void rs_step_edge(const EvLevels& L, int ke, int a, int c, int8_t ge_k,
                                              int8_t km1) {
-  int8_t le = L.el[e - L.e0];
-  const int a = w.src[e] - L.v0, c = w.col[e] - L.v0;
+  int8_t le = L.el[ke];
   const int8_t la = L.nl[a], lc = L.nl[c];
   if (le < km1 && (la >= ge_k || lc >= ge_k)) {
     le = km1;
-    L.el[e - L.e0] = le;
+    L.el[ke] = le;
   }
   if (le >= km1) {
     if (la < km1) L.nl[a] = km1;
@@ -83,7 +83,7 @@ constexpr int kRsEvThreads = 512;
 constexpr int kRsEvWarps = kRsEvThreads / 32;
 constexpr int kRsLists = 2 * (kMaxIters + 1);
 constexpr int kRsLookbackSpins = 1 << 22;  // x >= 100 ns sleeps: about half a second
-constexpr int kRsSmemBytes = 40 * 1024;     // levels of an event of up to 40 k hits + edges
+constexpr int kRsSmemBytes = 96 * 1024;  // endpoints and levels: about 19 k edges per event
 
 struct RsDesc {
   int32_t* flag;  // [n_events]
@@ -195,7 +195,7 @@ __device__ void rs_lookback(const RsDesc& d, int ev, int nv, const int* cnt, int
 
 __global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, RsDesc d, float lo,
                                                           float hi, int K) {
-  extern __shared__ int8_t sm_lev[];  // [n hits][edges] levels of the event
+  extern __shared__ __align__(16) int8_t sm_lev[];  // endpoints and levels of the event
   if (input_bad(w.counters)) return;
   __shared__ int wsum[kRsEvWarps];
   __shared__ int wcnt[kRsLists][kRsEvWarps];  // per list and warp: rows, then offsets
@@ -215,19 +215,39 @@ __global__ void __launch_bounds__(kRsEvThreads) k_rs_event(Batch b, Ws w, RsDesc
     if (ev >= b.n_events) break;
     const int v0 = int(w.ev_off[ev]), v1 = int(w.ev_off[ev + 1]);
     const int e0 = min(w.row_ptr[v0], E), e1 = min(w.row_ptr[v1], E);
-    const bool staged = (v1 - v0) + (e1 - e0) <= kRsSmemBytes;
-    const EvLevels L{staged ? sm_lev + (v1 - v0) : w.rs_elev + e0, staged ? sm_lev : w.rs_nlev + v0,
-                     e0, v0};
-    for (int i = tid; i < v1 - v0; i += kRsEvThreads) L.nl[i] = 0;
-    for (int e = tid; e < e1 - e0; e += kRsEvThreads) L.el[e] = 0;
+    // shared memory, when the event fits: [endpoints 4 B per edge][hit
+    // levels][edge levels]; the endpoints (event-local, 16 bits each) only
+    // for events of at most 65536 hits, read once and reused by every sweep
+    const int nh = v1 - v0, ne = e1 - e0;
+    const bool staged = nh + ne <= kRsSmemBytes;
+    const bool eps = staged && nh <= 65536 && 5 * int64_t(ne) + nh <= kRsSmemBytes;
+    uint32_t* ep = reinterpret_cast<uint32_t*>(sm_lev);
+    int8_t* lev0 = eps ? sm_lev + 4 * ne : sm_lev;
+    const EvLevels L{staged ? lev0 + nh : w.rs_elev + e0, staged ? lev0 : w.rs_nlev + v0, e0, v0};
+    for (int i = tid; i < nh; i += kRsEvThreads) L.nl[i] = 0;
+    for (int e = tid; e < ne; e += kRsEvThreads) L.el[e] = 0;
     __syncthreads();
     int n = 0;
-    for (int e = e0 + tid; e < e1; e += kRsEvThreads)
-      n += rs_init_edge(w, L, e, w.logit[e], lo, hi, top);
+    for (int k = tid; k < ne; k += kRsEvThreads) {
+      const int a = w.src[e0 + k] - v0, c = w.col[e0 + k] - v0;
+      if (eps) ep[k] = uint32_t(a) | (uint32_t(c) << 16);
+      n += rs_init_edge(L, k, a, c, w.logit[e0 + k], lo, hi, top);
+    }
     __syncthreads();
-    for (int k = K - 1; k >= 0; --k) {
-      const int8_t ge_k = int8_t(k + 2), km1 = int8_t(k + 1);
-      for (int e = e0 + tid; e < e1; e += kRsEvThreads) rs_step_edge(w, L, e, ge_k, km1);
+    for (int kk = K - 1; kk >= 0; --kk) {
+      const int8_t ge_k = int8_t(kk + 2), km1 = int8_t(kk + 1);
+      for (int k = tid; k < ne; k += kRsEvThreads) {
+        int a, c;
+        if (eps) {
+          const uint32_t u = ep[k];
+          a = int(u & 0xffffu);
+          c = int(u >> 16);
+        } else {
+          a = w.src[e0 + k] - v0;
+          c = w.col[e0 + k] - v0;
+        }
+        rs_step_edge(L, k, a, c, ge_k, km1);
+      }
       __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
@@ -287,7 +307,13 @@ int launch_rescore_sets(const Batch& b, const Ws& w, float band_lo, float band_h
   cudaMemsetAsync(w.rs_desc, 0, sizeof(int32_t) * b.n_events, s);
   const int nv = 2 * (K + 1);
   const RsDesc d{w.rs_desc, w.rs_desc + b.n_events, w.rs_desc + b.n_events + size_t(b.n_events) * nv};
-  k_rs_event<<<std::min(b.n_events, device_sms() * 4), kRsEvThreads, kRsSmemBytes, s>>>(
+  // set once per process (thread-safe initialisation of a local static)
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_rs_event, cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmemBytes);
+    return true;
+  }();
+  (void)attr;
+  k_rs_event<<<std::min(b.n_events, device_sms() * 2), kRsEvThreads, kRsSmemBytes, s>>>(
       b, w, d, band_lo, band_hi, K);
   return 1;
 }
