@@ -328,12 +328,16 @@ __device__ void select_capped(const Cand& cd, const float (&qe)[D], int c0, int 
 // took their tickets before it and are therefore running. Per event:
 //   1. degrees: one thread per query hit, the 32 lanes of a warp on 32 hits
 //      of one plane, so that they read the same candidate rows (broadcast);
-//      the event's embeddings are staged in shared memory when they fit;
+//      the event's embeddings are staged in shared memory when they fit, and
+//      then each hit's in-radius candidates are kept as a bit mask (a hit
+//      over k_max keeps its k_max selected ones);
 //   2. CSR offsets: block scan of min(deg, k_max), look-back, row pointers;
-//   3. fill: one thread per query hit walking its candidates in ascending
-//      order; a hit over k_max is filled by its warp (fill_capped);
+//   3. fill: one thread per query hit walking its mask bits in ascending
+//      order (or, without masks, its candidates; a hit over k_max is then
+//      filled by its warp, fill_capped);
 //   4. in-edge index: in-degrees by shared-memory atomics, a block scan,
-//      placement by cursors, then each target's list sorted by edge id.
+//      placement by cursors, then each target's list put in ascending edge
+//      id.
 constexpr int kGraphThreads = 512;
 constexpr int kGraphWarps = kGraphThreads / 32;
 constexpr int kGraphBlocksPerSm = 2;            // 16 warps each: 54-62 registers per thread
@@ -348,6 +352,7 @@ constexpr int kLookbackSpins = 1 << 22;  // x >= 100 ns sleeps: a bound of about
 // published its inclusive prefix, summing the counts of the others. A wait
 // that runs out sets ST_TIMEOUT and returns what was summed (the event then
 // publishes no inclusive prefix; later events sum its count instead).
+
 // (lane 0) publishes the event's edge count: event 0's is its inclusive prefix
 __device__ __forceinline__ void graph_publish(unsigned long long* desc, int ev, long long agg) {
   atomicExch(desc + ev, (ev == 0 ? +kDescInc : +kDescAgg) | static_cast<unsigned long long>(agg));
