@@ -13,7 +13,8 @@
 // (level >= k) in index order for the FP32 kernels.
 //
 // Levels are stored as int8 shifted by +2 (0 = not needed, 1 = encoders only,
-// k + 2 = up to step k), so a memset clears them.
+// k + 2 = up to step k), in shared memory for the event a block works on
+// (the workspace arrays rs_elev / rs_nlev for events too large for it).
 #include <algorithm>
 
 #include "internal.cuh"
