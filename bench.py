@@ -217,6 +217,19 @@ TRAFFIC_PER_ROW = {
 }
 
 
+# What the counters of the dominant kernels show (ncu --set full, same
+# 300-event captures as the traffic above): the roof their work is counted
+# against is not what limits them.
+COUNTERS = {
+    ("rescore_edge_update", "bf16"): {
+        "limiter": "latency: FMA pipe 50 % active, DRAM 28 % of peak, warps active 22.6 % of 64 "
+                   "(16 resident: registers and shared memory), stalls spread over shared-memory "
+                   "operand loads, fixed-latency dependencies and the FMA pipe",
+        "fma_pipe_active_pct": 50.1, "dram_pct_of_peak": 28.0, "warps_active_pct": 22.6,
+        "source": "profiles/k_gnn_f32_rescore_edge_weights_in_smem_300ev.md"},
+}
+
+
 def stage_rows_per_launch(stage, launches, rows, N, E, K):
     """Mean rows (edges or hits) one launch of `stage` processes."""
     if stage == "rescore_edge_update":
@@ -397,6 +410,8 @@ def main():
     roof = {"kernel": dname, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
             "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_unit": "DRAM bytes per launch (ncu capture of 300 events scaled by rows)",
+            "counters": (COUNTERS.get((dname, precision))
+                         if a.workload == "cfg3_batched_bf16" else None),
             "peak_src": f32_src if bound == "alu" else pk["src"],
             "launch_ms": round(launch_ms, 4),
             "work": "algorithmic work of the stage over one step / its time per step",
