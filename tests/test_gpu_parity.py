@@ -1,5 +1,7 @@
 """GPU parity: the library's FP32 path against the FP64 oracle, element by
 element, through the C ABI."""
+import math
+
 import numpy as np
 import pytest
 
@@ -366,3 +368,63 @@ def test_bounded_wait_runs_out_and_the_handle_recovers(cfg1):
     with pytest.raises(pkg.GnntrkError):
         tr.selftest_wait(0, s)
     tr.close()
+
+
+def test_cfg3_headline_form_full_batch_sampled():
+    """The headline call as bench.py times it: the 1000-event batch, BF16 with
+    the FP32 re-score band 0.02, autotuned, replayed from its CUDA graph. On
+    sampled events (first, middle, last, the largest): band edges carry the
+    FP32 path's logits bit for bit (the FP32 path run on the same full batch),
+    other edges the BF16 result; labels are the components of the kept
+    edges; decisions agree with the FP64 oracle on >= 99.9 % of the union of
+    both edge sets."""
+    from parity import cc_labels, sigmoid
+    wl = synth.workload("cfg3_batched_bf16")
+    model = model_of(wl)
+    b = synth.workload_batch(wl)
+    band = float(wl["rescore_band_score"])
+    dev = torch.device("cuda", 0)
+    xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+    plane = torch.from_numpy(b.plane).to(dev)
+    offs = torch.from_numpy(b.offsets).to(dev)
+    s = torch.cuda.Stream(device=dev)
+    sizes = np.diff(b.offsets)
+    sample = sorted({0, 1, 499, b.n_events - 1, int(np.argmax(sizes))})
+    out = {}
+    for name, prec, graph in (("fp32", "fp32", False), ("bf16", "bf16", True)):
+        tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits,
+                                      max_events=b.n_events, edges_per_hit=16, use_graph=graph)
+        lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+        if graph:
+            tr.autotune(b.n_events, b.n_hits, xyz, plane, offs, lab, s)
+        for _ in range(3 if graph else 1):  # capture, then replays
+            tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, s)
+        tr.sync_status(s)
+        torch.cuda.synchronize()
+        out[name] = (lab.cpu().numpy(), {e: tr.get_graph(e) for e in sample}, tr.stats())
+        tr.close()
+    labels, graphs, st = out["bf16"]
+    assert st["band"] > 0 and st["events"] == b.n_events
+    fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+    lo = math.log((0.5 - band) / (0.5 + band))
+    agree = union = 0
+    for e in sample:
+        g, g32 = graphs[e], out["fp32"][1][e]
+        assert np.array_equal(g["src"], g32["src"]) and np.array_equal(g["dst"], g32["dst"])
+        a, z = int(b.offsets[e]), int(b.offsets[e + 1])
+        assert np.array_equal(labels[a:z], cc_labels(z - a, g["src"], g["dst"], g["kept"]))
+        # band edges (by their FP32 logit here; the band is defined on the BF16
+        # one, so only edges clearly inside it are checked) carry the FP32 logit
+        inner = np.abs(g32["logit"]) < 0.25 * abs(lo)
+        moved = g["logit"] != g32["logit"]
+        assert np.array_equal(g["logit"][inner], g32["logit"][inner]), e
+        assert not np.any(moved & (np.abs(sigmoid(g["logit"]) - 0.5) < band)), e
+        ev = b.event(e)
+        ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                       wl["k_max"], feat_scale=fs)
+        O = {(int(i), int(j)): int(k) for i, j, k in zip(ref.src, ref.dst, ref.keep)}
+        G = {(int(i), int(j)): int(k) for i, j, k in zip(g["src"], g["dst"], g["kept"])}
+        for key in set(O) | set(G):
+            agree += O.get(key, 0) == G.get(key, 0)
+            union += 1
+    assert agree / union >= 0.999, agree / union
