@@ -58,7 +58,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--profile-case", default=None,
                    choices=["headline_300ev_bf16", "headline_300ev_bf16_tuned",
-                            "headline_300ev_bf16_tma", "headline_300ev_fp32", "triplets_int8_100ev"],
+                            "headline_300ev_bf16_tma", "headline_300ev_fp32", "triplets_int8_100ev",
+                            "cfg4_100ev_fp8"],
                    help="run one small case for a profiler capture (no timing, no JSON line)")
     p.add_argument("--study", default=None, choices=["occupancy"],
                    help="occupancy: throughput per event-size bin instead of the headline")
@@ -1327,7 +1328,8 @@ def fp8_trained_report(pkg, torch, dev, stream, n_events=1000, oracle_n=200, rep
 
 
 def profile_case(name, pkg, torch):
-    """Small fixed cases for kernel captures (ncu): the first 300 events of the
+    """Small fixed cases for kernel captures (ncu): the first 100 events of
+    config 4 in FP8 (three calls); the first 300 events of the
     headline batch (three calls, BF16 + FP32 re-score band 0.02, or FP32; the
     _tuned case autotunes first, so the captured kernels are the variants the
     autotuner keeps; the _tma case runs the BF16 edge step with TMA-staged
@@ -1337,6 +1339,17 @@ def profile_case(name, pkg, torch):
     workload."""
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if name == "cfg4_100ev_fp8":
+        # the first 100 events of config 4 (hidden 128), FP8 without a band,
+        # three calls
+        wl = synth.workload("cfg4_batched_fp8")
+        b = synth.workload_batch(wl, 100)
+        tr = pkg.tracker_for_workload(wl, precision="fp8", rescore_band=0.0, max_hits=b.n_hits,
+                                      max_events=b.n_events, edges_per_hit=16)
+        for _ in range(3):
+            pkg.run_batch(tr, b)
+        print(name, tr.stats())
+        return
     if name.startswith("headline_300ev"):
         prec = name.split("_")[2]
         wl = synth.workload("cfg3_batched_bf16")
