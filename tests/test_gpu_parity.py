@@ -1,7 +1,5 @@
 """GPU parity: the library's FP32 path against the FP64 oracle, element by
 element, through the C ABI."""
-import math
-
 import numpy as np
 import pytest
 
@@ -375,7 +373,7 @@ def test_cfg3_headline_form_full_batch_sampled():
     the FP32 re-score band 0.02, autotuned, replayed from its CUDA graph. On
     sampled events (first, middle, last, the largest): band edges carry the
     FP32 path's logits bit for bit (the FP32 path run on the same full batch),
-    other edges the BF16 result; labels are the components of the kept
+    other edges the BF16 result of the same call without the band; labels are the components of the kept
     edges; decisions agree with the FP64 oracle on >= 99.9 % of the union of
     both edge sets."""
     from parity import cc_labels, sigmoid
@@ -391,8 +389,9 @@ def test_cfg3_headline_form_full_batch_sampled():
     sizes = np.diff(b.offsets)
     sample = sorted({0, 1, 499, b.n_events - 1, int(np.argmax(sizes))})
     out = {}
-    for name, prec, graph in (("fp32", "fp32", False), ("bf16", "bf16", True)):
-        tr = pkg.tracker_for_workload(wl, precision=prec, max_hits=b.n_hits,
+    for name, prec, graph, bd in (("fp32", "fp32", False, 0.0), ("raw", "bf16", True, 0.0),
+                                  ("bf16", "bf16", True, band)):
+        tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=bd, max_hits=b.n_hits,
                                       max_events=b.n_events, edges_per_hit=16, use_graph=graph)
         lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
         if graph:
@@ -406,22 +405,85 @@ def test_cfg3_headline_form_full_batch_sampled():
     labels, graphs, st = out["bf16"]
     assert st["band"] > 0 and st["events"] == b.n_events
     fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
-    lo = math.log((0.5 - band) / (0.5 + band))
     agree = union = 0
     for e in sample:
         g, g32 = graphs[e], out["fp32"][1][e]
         assert np.array_equal(g["src"], g32["src"]) and np.array_equal(g["dst"], g32["dst"])
         a, z = int(b.offsets[e]), int(b.offsets[e + 1])
         assert np.array_equal(labels[a:z], cc_labels(z - a, g["src"], g["dst"], g["kept"]))
-        # band edges (by their FP32 logit here; the band is defined on the BF16
-        # one, so only edges clearly inside it are checked) carry the FP32 logit
-        inner = np.abs(g32["logit"]) < 0.25 * abs(lo)
-        moved = g["logit"] != g32["logit"]
-        assert np.array_equal(g["logit"][inner], g32["logit"][inner]), e
-        assert not np.any(moved & (np.abs(sigmoid(g["logit"]) - 0.5) < band)), e
+        # band edges (by the BF16 logit of the same call without the band)
+        # carry the FP32 logit, the others the BF16 one
+        raw = out["raw"][1][e]["logit"]
+        inband = np.abs(sigmoid(raw) - 0.5) < band
+        assert np.array_equal(g["logit"][inband], g32["logit"][inband]), e
+        assert np.array_equal(g["logit"][~inband], raw[~inband]), e
         ev = b.event(e)
         ref = oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
                                        wl["k_max"], feat_scale=fs)
+        O = {(int(i), int(j)): int(k) for i, j, k in zip(ref.src, ref.dst, ref.keep)}
+        G = {(int(i), int(j)): int(k) for i, j, k in zip(g["src"], g["dst"], g["kept"])}
+        for key in set(O) | set(G):
+            agree += O.get(key, 0) == G.get(key, 0)
+            union += 1
+    assert agree / union >= 0.999, agree / union
+
+
+def test_cfg4_fp8_chunk_sampled():
+    """Config 4 as bench.py runs it: a 1000-event chunk of the 10000-event
+    workload (hidden 128), FP8 with the FP32 re-score band 0.05, CUDA graph.
+    On sampled events: band edges carry the FP32 path's logits bit for bit
+    (the FP32 path on the same chunk), labels are the components of the kept
+    edges, and decisions agree with the FP64 oracle on >= 99.9 % of the union
+    of both edge sets."""
+    import concurrent.futures as cf
+    import os
+    from parity import cc_labels, sigmoid
+    wl = synth.workload("cfg4_batched_fp8")
+    model = model_of(wl)
+    b = synth.workload_batch(wl, 1000)
+    band = 0.05
+    dev = torch.device("cuda", 0)
+    xyz = torch.from_numpy(b.xyz_soa()).to(dev)
+    plane = torch.from_numpy(b.plane).to(dev)
+    offs = torch.from_numpy(b.offsets).to(dev)
+    s = torch.cuda.Stream(device=dev)
+    sizes = np.diff(b.offsets)
+    sample = sorted({0, 500, b.n_events - 1, int(np.argmax(sizes))})
+    out = {}
+    for name, prec, bd in (("fp32", "fp32", 0.0), ("raw", "fp8", 0.0), ("fp8", "fp8", band)):
+        tr = pkg.tracker_for_workload(wl, precision=prec, rescore_band=bd, max_hits=b.n_hits,
+                                      max_events=b.n_events, edges_per_hit=16, use_graph=True)
+        lab = torch.empty(b.n_hits, dtype=torch.int32, device=dev)
+        for _ in range(2):  # capture, then a replay
+            tr.find_tracks(b.n_events, b.n_hits, xyz, plane, offs, lab, s)
+        tr.sync_status(s)
+        torch.cuda.synchronize()
+        out[name] = (lab.cpu().numpy(), {e: tr.get_graph(e) for e in sample}, tr.stats())
+        tr.close()
+    labels, graphs, st = out["fp8"]
+    assert st["band"] > 0 and st["events"] == b.n_events
+    fs = pkg.feat_scale_of(pkg.make_cfg(wl["model"], wl["radius2"]))
+
+    def one(e):
+        ev = b.event(e)
+        return oracle.find_tracks_event(model, ev.x, ev.y, ev.z, ev.plane, wl["radius2"],
+                                        wl["k_max"], feat_scale=fs)
+    with cf.ThreadPoolExecutor(min(len(sample), os.cpu_count() or 1)) as ex:
+        refs = dict(zip(sample, ex.map(one, sample)))
+    agree = union = 0
+    for e in sample:
+        g, g32 = graphs[e], out["fp32"][1][e]
+        assert np.array_equal(g["src"], g32["src"]) and np.array_equal(g["dst"], g32["dst"])
+        a, z = int(b.offsets[e]), int(b.offsets[e + 1])
+        assert np.array_equal(labels[a:z], cc_labels(z - a, g["src"], g["dst"], g["kept"]))
+        # band edges (by the FP8 logit of the same call without the band)
+        # carry the FP32 logit, the others the FP8 one
+        raw = out["raw"][1][e]["logit"]
+        inband = np.abs(sigmoid(raw) - 0.5) < band
+        assert inband.any()
+        assert np.array_equal(g["logit"][inband], g32["logit"][inband]), e
+        assert np.array_equal(g["logit"][~inband], raw[~inband]), e
+        ref = refs[e]
         O = {(int(i), int(j)): int(k) for i, j, k in zip(ref.src, ref.dst, ref.keep)}
         G = {(int(i), int(j)): int(k) for i, j, k in zip(g["src"], g["dst"], g["kept"])}
         for key in set(O) | set(G):
