@@ -100,6 +100,12 @@ struct Layout {
   // [h_src, h_dst] tile (hi parts, then lo parts accumulated into the same
   // tensor memory) against the plain weight image, so it fits shared memory
   static constexpr bool SPLIT2 = SPLIT && MODE == M_EDGE_ENC && H > 64;
+  // FP8 edge steps at hidden 128 run layer 1 in three passes of K = H over a
+  // one-segment tile (e, then h_src, then h_dst) against the K chunks of the
+  // weight image; h_src and h_dst share one per-row scale and accumulate into
+  // one tensor-memory block (e into the other), so that the tiles (86 KB)
+  // and the accumulators (256 columns) of two CTAs fit an SM
+  static constexpr bool P3 = FP8 && H == 128 && (MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS);
   static constexpr int K1 = (MODE == M_NODE_ENC) ? H : (SPLIT && !SPLIT2 ? 2 : 1) * NSEG * H;
   static constexpr int K2 = (SPLIT && MODE == M_NODE_ENC) ? 2 * H : H;
   static constexpr bool HAS_W1 = MODE != M_NODE_ENC;
@@ -120,7 +126,7 @@ struct Layout {
   static constexpr bool PIPE = !FP8 && MODE == M_NODE_UPD;
   static constexpr bool PREFETCH = false;
   static constexpr int A = align1k(WC + WC_BYTES);
-  static constexpr int A_BYTES = MODE == M_NODE_ENC ? 0 : kRows * K1 * ESZ;
+  static constexpr int A_BYTES = MODE == M_NODE_ENC ? 0 : kRows * (P3 ? H : K1) * ESZ;
   static constexpr int NBUF = PIPE && PREFETCH ? 2 : 1;
   // hidden / classifier input: its own tile with two input buffers, else it
   // overwrites the layer-1 input once the layer-1 MMAs are done
@@ -131,7 +137,9 @@ struct Layout {
   static constexpr int PAR_FLOATS = 7 * H + 4 * H + 8;
   static constexpr int BAR = PAR + PAR_FLOATS * 4;
   static constexpr int TOTAL = BAR + 64;
-  static constexpr int TMEM_COLS = FP8 ? pow2_cols(NSEG * H) : pow2_cols(H);
+  // FP8: one accumulator block per layer-1 segment scale
+  static constexpr int TSEG = P3 ? 2 : (FP8 ? NSEG : 1);
+  static constexpr int TMEM_COLS = pow2_cols(TSEG * H);
 };
 
 __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
@@ -220,6 +228,39 @@ __device__ __forceinline__ float put_row_bf16(uint8_t* tile, int row, int kchunk
       *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 4) + c, kchunks)) = u;
     }
     return scale;
+  }
+}
+
+// Largest |value| of one BF16 row of H values in global memory.
+template <int H>
+__device__ __forceinline__ float row_amax_bf16(const __nv_bfloat16* src) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  float amax = 0.f;
+#pragma unroll
+  for (int c = 0; c < H / 8; ++c) {
+    const uint4 u = s4[c];
+    const uint32_t q[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) amax = fmaxf(amax, fmaxf(fabsf(bf16_lo(q[j])), fabsf(bf16_hi(q[j]))));
+  }
+  return amax;
+}
+
+// One BF16 row of H values from global memory into an E4M3 tile at element
+// k0, each value multiplied by `inv` (the caller's per-row scale).
+template <int H>
+__device__ __forceinline__ void put_row_bf16_e4m3(uint8_t* tile, int row, int kchunks, int k0,
+                                                  const __nv_bfloat16* src, float inv) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int c = 0; c < H / 16; ++c) {
+    const uint4 a = s4[2 * c], b = s4[2 * c + 1];
+    uint4 u;
+    u.x = pack_e4m3x4(bf16_lo(a.x) * inv, bf16_hi(a.x) * inv, bf16_lo(a.y) * inv, bf16_hi(a.y) * inv);
+    u.y = pack_e4m3x4(bf16_lo(a.z) * inv, bf16_hi(a.z) * inv, bf16_lo(a.w) * inv, bf16_hi(a.w) * inv);
+    u.z = pack_e4m3x4(bf16_lo(b.x) * inv, bf16_hi(b.x) * inv, bf16_lo(b.y) * inv, bf16_hi(b.y) * inv);
+    u.w = pack_e4m3x4(bf16_lo(b.z) * inv, bf16_hi(b.z) * inv, bf16_lo(b.w) * inv, bf16_hi(b.w) * inv);
+    *reinterpret_cast<uint4*>(tile + tile_off(row, (k0 >> 4) + c, kchunks)) = u;
   }
 }
 
@@ -340,6 +381,25 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, const uint8_t* A, con
       mma_e4m3(d, ad, bd, IDESC, acc);
     else
       mma_bf16(d, ad, bd, IDESC, acc);
+  }
+}
+
+// One pass of a three-pass FP8 layer 1 (K = 3H): the one-segment A tile
+// (E4M3, H per row) times K chunk `pass` of the weight image (E4M3, 3H per
+// row); pass 0 starts its accumulator, pass 1 starts the other, pass 2 adds
+// to it.
+template <int H>
+__device__ __forceinline__ void issue_pass_e4m3(uint32_t tmem, const uint8_t* A, const uint8_t* W,
+                                                int pass) {
+  constexpr uint32_t IDESC = idesc_e4m3(kRows, H);
+  constexpr uint32_t SBO_A = uint32_t(H / 16) * 128;
+  constexpr uint32_t SBO_W = uint32_t(3 * H / 16) * 128;
+  const uint32_t a0 = smem_u32(A), w0 = smem_u32(W) + uint32_t(pass * (H / 16)) * 128;
+#pragma unroll
+  for (int k = 0; k < H; k += 32) {
+    const uint32_t byte_k = uint32_t(k / 16) * 128;
+    mma_e4m3(tmem, smem_desc(a0 + byte_k, 128, SBO_A), smem_desc(w0 + byte_k, 128, SBO_W), IDESC,
+             (pass == 2 || k > 0) ? 1u : 0u);
   }
 }
 
@@ -475,6 +535,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
   const int n_tiles = (hi - lo + kRows - 1) / kRows;
   constexpr int K1 = L::K1;
   constexpr int KCH1 = K1 * L::ESZ / 16;  // 16-byte chunks per A row, layer 1
+  constexpr int KCHA = L::P3 ? H * L::ESZ / 16 : KCH1;  // per row of the A tile
   constexpr int KCHH = H * L::ESZ / 16;   // 16-byte chunks per A row, K = H
   constexpr int KCH2 = L::K2 * L::ESZ / 16;  // 16-byte chunks per A row, layer 2
 
@@ -601,11 +662,17 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           sa[1] = put_row_bf16<H, FP8>(sA, tid, KCH1, H, w.estate16 + size_t(p.t2[r]) * H, nullptr);
           seg = 2;
         } else if constexpr (MODE == M_EDGE_UPD || MODE == M_EDGE_UPD_CLS || MODE == M_CLS) {
-          sa[0] = put_row_bf16<H, FP8>(sA, tid, KCH1, 0, w.estate16 + size_t(r) * H,
+          sa[0] = put_row_bf16<H, FP8>(sA, tid, KCHA, 0, w.estate16 + size_t(r) * H,
                                        (H <= 64 && MODE != M_CLS) ? keep_row : nullptr);
           seg = 1;
         }
-        if constexpr (L::SPLIT2) {
+        if constexpr (L::P3) {
+          // pass 0 holds e alone; h_src and h_dst follow in passes 1 and 2
+          // with one scale, the larger of their two row maxima
+          const float amax = fmaxf(row_amax_bf16<H>(w.hstate16 + size_t(w.src[r]) * H),
+                                   row_amax_bf16<H>(w.hstate16 + size_t(w.col[r]) * H));
+          sa[1] = amax > 0.f ? amax / 448.f : 1.f;
+        } else if constexpr (L::SPLIT2) {
           // pass 1: [hi(h_src), hi(h_dst)] (the lo parts follow after the MMA)
           put_row_f32_part<H>(sA, tid, KCH1, 0, w.hstate + size_t(w.src[r]) * H, false);
           put_row_f32_part<H>(sA, tid, KCH1, H, w.hstate + size_t(w.col[r]) * H, false);
@@ -621,7 +688,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         }
       } else {
         float z[16] = {};
-        for (int k = 0; k < K1; k += 16) put_row_f32<FP8>(sA, tid, KCH1, k, z, 16, 1.f);
+        for (int k = 0; k < (L::P3 ? H : K1); k += 16) put_row_f32<FP8>(sA, tid, KCHA, k, z, 16, 1.f);
       }
     }
     fence_proxy_async();
@@ -633,12 +700,35 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
       // ---- 2. layer 1 ------------------------------------------------------
       if (tid == 0) {
         tc_fence_after();
-        issue_layer<H, FP8>(tmem_base, sA, sW1, K1, FP8 ? L::NSEG : 1);
+        if constexpr (L::P3)
+          issue_pass_e4m3<H>(tmem_base, sA, sW1, 0);
+        else
+          issue_layer<H, FP8>(tmem_base, sA, sW1, K1, FP8 ? L::NSEG : 1);
         mma_commit(&bar[1]);
       }
       if (!wait_mma()) {
         aborted = true;
         break;
+      }
+      if constexpr (L::P3) {
+        // passes 1 and 2: h_src, then h_dst, into the same tile (the MMAs of
+        // the pass before have read it); invalid rows keep pass 0's zeros
+        const float hinv = 1.f / sa[1];
+        for (int pass = 1; pass <= 2 && !aborted; ++pass) {
+          if (valid)
+            put_row_bf16_e4m3<H>(sA, tid, KCHA, 0,
+                                 w.hstate16 + size_t(pass == 1 ? w.src[r] : w.col[r]) * H, hinv);
+          fence_proxy_async();
+          tc_fence_before();
+          __syncthreads();
+          if (tid == 0) {
+            tc_fence_after();
+            issue_pass_e4m3<H>(tmem_base + uint32_t(H), sA, sW1, pass);
+            mma_commit(&bar[1]);
+          }
+          if (!wait_mma()) aborted = true;
+        }
+        if (aborted) break;
       }
       if constexpr (L::SPLIT2) {
         // pass 2: [lo(h_src), lo(h_dst)] into the same tile, accumulated
@@ -680,7 +770,7 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] *= sa[0];
 #pragma unroll
-          for (int s = 1; s < L::NSEG; ++s) {
+          for (int s = 1; s < L::TSEG; ++s) {
             float u[32];
             tmem_ld32(tmem_lane + uint32_t(s * H + c * 32), u);
 #pragma unroll
