@@ -19,8 +19,9 @@
 //      product) and the cut run instead of the store.
 // FP8: each input segment of layer 1 (e.g. e, h_src, h_dst) is quantised with
 // its own per-row scale amax/448 and accumulated in its own TMEM block, so the
-// epilogue can apply the scales; weights carry per-output-channel scales
-// amax/448. Hidden rows are quantised per row as well. The K = 3 first layer of
+// epilogue can apply the scales (the edge steps at hidden 128: h_src and h_dst
+// under one scale in one block, layer 1 in three passes, see Layout::P3);
+// weights carry per-output-channel scales amax/448. Hidden rows are quantised per row as well. The K = 3 first layer of
 // the node encoder and the 1-unit last layer of the classifier stay FP32.
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
