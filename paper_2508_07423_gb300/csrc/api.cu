@@ -240,6 +240,7 @@ std::vector<std::pair<void**, size_t>> workspace_plan(const gnntrk_cfg& c, int D
   add(&w.hstate, H * hd);
   add(&w.estate, E * hd);
   add(&w.pstate, H * 2 * hd);
+  if (c.precision == GNNTRK_FP8_E4M3 && hd == 128) add(&w.hamax, H);
   if (c.precision != GNNTRK_FP32) {
     add(&w.hstate16, H * hd);
     add(&w.estate16, E * hd);

@@ -97,6 +97,7 @@ struct Ws {
   float* pstate;        // [H][2h]  FP32 node projections for the next edge layer
   __nv_bfloat16* hstate16;  // [H][h]   BF16 node state (tensor-core paths)
   __nv_bfloat16* estate16;  // [Ecap][h] BF16 edge state
+  float* hamax;         // [H] largest |BF16 node state| per hit (FP8 handles at h = 128)
   float* logit;         // [Ecap]
   uint8_t* keep;        // [Ecap]
   int32_t* parent;      // [H] union-find parent over global input indices

@@ -232,21 +232,6 @@ __device__ __forceinline__ float put_row_bf16(uint8_t* tile, int row, int kchunk
   }
 }
 
-// Largest |value| of one BF16 row of H values in global memory.
-template <int H>
-__device__ __forceinline__ float row_amax_bf16(const __nv_bfloat16* src) {
-  const uint4* s4 = reinterpret_cast<const uint4*>(src);
-  float amax = 0.f;
-#pragma unroll
-  for (int c = 0; c < H / 8; ++c) {
-    const uint4 u = s4[c];
-    const uint32_t q[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) amax = fmaxf(amax, fmaxf(fabsf(bf16_lo(q[j])), fabsf(bf16_hi(q[j]))));
-  }
-  return amax;
-}
-
 // One BF16 row of H values from global memory into an E4M3 tile at element
 // k0, each value multiplied by `inv` (the caller's per-row scale).
 template <int H>
@@ -670,8 +655,8 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
         if constexpr (L::P3) {
           // pass 0 holds e alone; h_src and h_dst follow in passes 1 and 2
           // with one scale, the larger of their two row maxima
-          const float amax = fmaxf(row_amax_bf16<H>(w.hstate16 + size_t(w.src[r]) * H),
-                                   row_amax_bf16<H>(w.hstate16 + size_t(w.col[r]) * H));
+          // (the node kernels store each row's maximum as they write it)
+          const float amax = fmaxf(w.hamax[w.src[r]], w.hamax[w.col[r]]);
           sa[1] = amax > 0.f ? amax / 448.f : 1.f;
         } else if constexpr (L::SPLIT2) {
           // pass 1: [hi(h_src), hi(h_dst)] (the lo parts follow after the MMA)
@@ -900,8 +885,9 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
 
     if constexpr (MODE != M_EDGE_UPD_CLS) {
       // ---- 5. store the new state (BF16) -----------------------------------
-      __nv_bfloat16* dst = (MODE == M_NODE_ENC || MODE == M_NODE_UPD ? w.hstate16 : w.estate16) +
-                           size_t(r) * H;
+      constexpr bool NODE_ROWS = MODE == M_NODE_ENC || MODE == M_NODE_UPD;
+      __nv_bfloat16* dst = (NODE_ROWS ? w.hstate16 : w.estate16) + size_t(r) * H;
+      float row_max = 0.f;  // largest |stored value| of a node row
 #pragma unroll
       for (int c = 0; c < H / 32; ++c) {
         float z[32];
@@ -916,11 +902,22 @@ __global__ void __launch_bounds__(kRows, 1) k_tc(const TcArgs p) {
           }
           uint4* d4 = reinterpret_cast<uint4*>(dst) + c * 4;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            d4[q] = make_uint4(pack_bf16(z[8 * q], z[8 * q + 1]), pack_bf16(z[8 * q + 2], z[8 * q + 3]),
-                               pack_bf16(z[8 * q + 4], z[8 * q + 5]), pack_bf16(z[8 * q + 6], z[8 * q + 7]));
+          for (int q = 0; q < 4; ++q) {
+            const uint4 u = make_uint4(pack_bf16(z[8 * q], z[8 * q + 1]), pack_bf16(z[8 * q + 2], z[8 * q + 3]),
+                                       pack_bf16(z[8 * q + 4], z[8 * q + 5]), pack_bf16(z[8 * q + 6], z[8 * q + 7]));
+            d4[q] = u;
+            if constexpr (NODE_ROWS && H == 128) {
+              const uint32_t pk[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                row_max = fmaxf(row_max, fmaxf(fabsf(bf16_lo(pk[j])), fabsf(bf16_hi(pk[j]))));
+            }
+          }
         }
       }
+      // (read by the FP8 edge steps at hidden 128 for their shared h scale)
+      if constexpr (NODE_ROWS && H == 128)
+        if (valid && w.hamax != nullptr) w.hamax[r] = row_max;
       tc_fence_before();
     } else {
       // ---- 5'. classifier on the new edge state, then the cut ---------------
